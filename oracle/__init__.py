@@ -1,0 +1,298 @@
+"""CPU oracle for the MRF region-labelling EM path -- TEST INFRASTRUCTURE.
+
+A plain serial C implementation (``pmrf_oracle.c``) of what DPP-PMRF's
+optimisation phase computes (Lessley et al., LDAV 2018: Sections 2.1, 3.1,
+3.2, Algorithms 1-2), wrapped with ctypes and numpy.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the benchmark's CPU-baseline leg may import
+this package; the CUDA library never calls it and shares no code with it.
+
+Batches are handled here by looping over slices: every oracle routine works on
+one slice (one graph), which is how the paper itself processes a stack
+(Section 4.3.1: slice by slice).
+
+Parity pins for every function live in ``tests/test_oracle_*.py``.  The
+per-slice functions and the readings they encode:
+
+* regions / edges / cliques / hoods  -- Section 2.1, 3.1, 3.2.1, 3.2.2
+  (Construction of Neighborhoods); readings G1, G2.
+* replicate                          -- Section 3.2.2 EM step 1 (worked arrays).
+* map_sweep                          -- Section 3.2.2 EM step 2-3; G4-G7.
+* params / init                      -- Section 3.2.2 EM step 4, Algorithm 2
+  step 3; G3, G8.
+* em                                 -- Algorithm 2 steps 6-11, EM step 5; G9.
+* pll                                -- the differentiable form (G10).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBDIR = os.path.join(_HERE, "lib")
+_LIB = os.path.join(_LIBDIR, "libpmrf_oracle.so")
+
+ORC_OK, ORC_ERR_ARG, ORC_ERR_OOM = 0, 1, 3
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with plain gcc -O2 (no fast-math: the C source fixes
+    the order of every floating-point operation)."""
+    src = os.path.join(_HERE, "pmrf_oracle.c")
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
+        os.makedirs(_LIBDIR, exist_ok=True)
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fno-fast-math", "-ffp-contract=off", "-fPIC",
+                               "-shared", "-o", tmp, src, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Graph(ctypes.Structure):
+    _fields_ = [
+        ("max_id", ctypes.c_int32), ("V", ctypes.c_int32), ("n_adj", ctypes.c_int64),
+        ("C", ctypes.c_int64), ("n_clq", ctypes.c_int64), ("N_el", ctypes.c_int64),
+        ("rank", ctypes.POINTER(ctypes.c_int32)), ("npix", ctypes.POINTER(ctypes.c_int64)),
+        ("y", ctypes.POINTER(ctypes.c_double)), ("adj_off", ctypes.POINTER(ctypes.c_int64)),
+        ("adj", ctypes.POINTER(ctypes.c_int32)), ("clq_off", ctypes.POINTER(ctypes.c_int64)),
+        ("clq", ctypes.POINTER(ctypes.c_int32)), ("hood_off", ctypes.POINTER(ctypes.c_int64)),
+        ("hood", ctypes.POINTER(ctypes.c_int32)),
+    ]
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("n_labels", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("conv_window", ctypes.c_int32),
+                ("pad", ctypes.c_int32), ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
+                ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double)]
+
+
+_lib = None
+_P = ctypes.c_void_p
+
+
+def _get():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        GP = ctypes.POINTER(_Graph)
+        lib.orc_build_graph.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(GP)]
+        lib.orc_graph_from_adjacency.argtypes = [ctypes.c_int32, _P, _P, _P, ctypes.POINTER(GP)]
+        lib.orc_graph_free.argtypes = [GP]
+        lib.orc_graph_free.restype = None
+        lib.orc_replicate.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P, _P, _P]
+        lib.orc_map_sweep.argtypes = [GP, ctypes.c_int32, ctypes.c_double, _P, _P, _P, _P, _P, _P, _P, _P, _P, _P]
+        lib.orc_params.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P]
+        lib.orc_init_labels.argtypes = [GP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]
+        lib.orc_init_params.argtypes = [GP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P]
+        lib.orc_em.argtypes = [GP, ctypes.POINTER(_Config), _P, _P, _P, _P, _P]
+        lib.orc_pll.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P]
+        lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
+        _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data
+
+
+def _check(rc, what):
+    if rc != ORC_OK:
+        raise RuntimeError(f"oracle {what} failed with code {rc}")
+
+
+def _arr(p, n, dtype):
+    if n == 0:
+        return np.zeros(0, dtype=dtype)
+    return np.ctypeslib.as_array(p, shape=(n,)).astype(dtype, copy=True)
+
+
+@dataclass
+class EMConfig:
+    """EM settings (defaults: window W = 3 and tolerance 1e-4 of Section 3.2.2;
+    the iteration cap is per workload; sigma floor and threshold-init range are
+    readings G8 and G3)."""
+    n_labels: int = 2
+    beta: float = 1.0
+    max_iters: int = 20
+    conv_window: int = 3
+    conv_tol: float = 1e-4
+    sigma_min: float = 1e-6
+    init_lo: float = 0.0
+    init_hi: float = 1.0
+
+    def _c(self):
+        return _Config(self.n_labels, self.max_iters, self.conv_window, 0, self.beta, self.conv_tol,
+                       self.sigma_min, self.init_lo, self.init_hi)
+
+
+class Graph:
+    """One slice's region graph with its cliques and hoods (oracle side)."""
+
+    def __init__(self, handle):
+        self._h = handle
+        g = handle.contents
+        self.V = int(g.V)
+        self.max_id = int(g.max_id)
+        self.C = int(g.C)
+        self.N_el = int(g.N_el)
+        self.rank = _arr(g.rank, self.max_id + 1, np.int32)
+        self.npix = _arr(g.npix, self.V, np.int64)
+        self.y = _arr(g.y, self.V, np.float64)
+        self.adj_off = _arr(g.adj_off, self.V + 1, np.int64)
+        self.adj = _arr(g.adj, int(g.n_adj), np.int32)
+        self.clq_off = _arr(g.clq_off, self.C + 1, np.int64)
+        self.clq = _arr(g.clq, int(g.n_clq), np.int32)
+        self.hood_off = _arr(g.hood_off, self.C + 1, np.int64)
+        self.hood = _arr(g.hood, self.N_el, np.int32)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.orc_graph_free(h)
+            self._h = None
+
+    @property
+    def E(self):
+        return len(self.adj) // 2
+
+    # -- constructors --------------------------------------------------------
+    @classmethod
+    def from_image(cls, image: np.ndarray, region_ids: np.ndarray) -> "Graph":
+        lib = _get()
+        img = np.ascontiguousarray(image, dtype=np.float64)
+        ids = np.ascontiguousarray(region_ids, dtype=np.int32)
+        if img.shape != ids.shape or img.ndim != 2:
+            raise ValueError("image and region_ids must be 2-D of the same shape")
+        h = ctypes.POINTER(_Graph)()
+        _check(lib.orc_build_graph(_ptr(img), _ptr(ids), img.shape[0], img.shape[1], ctypes.byref(h)), "build_graph")
+        return cls(h)
+
+    @classmethod
+    def from_adjacency(cls, y, neighbours) -> "Graph":
+        """neighbours: list of iterables (symmetric, no self loops)."""
+        lib = _get()
+        V = len(neighbours)
+        lists = [sorted(set(int(u) for u in nb)) for nb in neighbours]
+        off = np.zeros(V + 1, dtype=np.int64)
+        for v, nb in enumerate(lists):
+            off[v + 1] = off[v] + len(nb)
+        adj = np.array([u for nb in lists for u in nb], dtype=np.int32)
+        if adj.size == 0:
+            adj = np.zeros(1, dtype=np.int32)
+        yy = np.ascontiguousarray(y, dtype=np.float64)
+        h = ctypes.POINTER(_Graph)()
+        _check(lib.orc_graph_from_adjacency(V, _ptr(yy), _ptr(off), _ptr(adj), ctypes.byref(h)), "from_adjacency")
+        return cls(h)
+
+    # -- method steps --------------------------------------------------------
+    def neighbours(self, v):
+        return self.adj[self.adj_off[v]:self.adj_off[v + 1]]
+
+    def cliques(self):
+        return [tuple(self.clq[self.clq_off[c]:self.clq_off[c + 1]]) for c in range(self.C)]
+
+    def hoods(self):
+        return [tuple(self.hood[self.hood_off[c]:self.hood_off[c + 1]]) for c in range(self.C)]
+
+    def map_sweep(self, L, beta, x, mu, sigma, want_elements=False, want_second=False):
+        """One MAP sweep; returns dict with x_new, E_star, S (per hood) and
+        optionally E_el [N_el, L], Emin_el, lab_el, E_second."""
+        lib = _get()
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        out = dict(x_new=np.zeros(self.V, np.uint8), E_star=np.zeros(self.V), S=np.zeros(self.C))
+        E_el = np.zeros((self.N_el, L)) if want_elements else None
+        Emin_el = np.zeros(self.N_el) if want_elements else None
+        lab_el = np.zeros(self.N_el, np.uint8) if want_elements else None
+        E2 = np.zeros(self.V) if want_second else None
+        _check(lib.orc_map_sweep(self._h, L, beta, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(out["x_new"]),
+                                 _ptr(out["E_star"]), _ptr(out["S"]), _ptr(E_el), _ptr(Emin_el), _ptr(lab_el),
+                                 _ptr(E2)), "map_sweep")
+        if want_elements:
+            out.update(E_el=E_el, Emin_el=Emin_el, lab_el=lab_el)
+        if want_second:
+            out["E_second"] = E2
+        return out
+
+    def params(self, L, x, E_star, theta_prev, sigma_min=1e-6):
+        lib = _get()
+        th = np.zeros((L, 4))
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        es = None if E_star is None else np.ascontiguousarray(E_star, dtype=np.float64)
+        prev = np.ascontiguousarray(theta_prev, dtype=np.float64).reshape(L, 4)
+        _check(lib.orc_params(self._h, L, _ptr(x), _ptr(es), _ptr(prev), sigma_min, _ptr(th)), "params")
+        return th
+
+    def init_labels(self, L, lo=0.0, hi=1.0):
+        x = np.zeros(self.V, np.uint8)
+        _check(_get().orc_init_labels(self._h, L, lo, hi, _ptr(x)), "init_labels")
+        return x
+
+    def init_params(self, L, x, lo=0.0, hi=1.0, sigma_min=1e-6):
+        th = np.zeros((L, 4))
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        _check(_get().orc_init_params(self._h, L, lo, hi, sigma_min, _ptr(x), _ptr(th)), "init_params")
+        return th
+
+    def em(self, cfg: EMConfig):
+        """Full EM loop from the threshold initialisation.  Returns dict with
+        labels, theta [L,4] (n, mu, sigma, U), iters, converged, T_hist."""
+        lib = _get()
+        x = np.zeros(self.V, np.uint8)
+        th = np.zeros((cfg.n_labels, 4))
+        it = ctypes.c_int32(0)
+        cv = ctypes.c_int32(0)
+        Th = np.zeros(cfg.max_iters)
+        c = cfg._c()
+        _check(lib.orc_em(self._h, ctypes.byref(c), _ptr(x), _ptr(th), ctypes.byref(it), ctypes.byref(cv), _ptr(Th)),
+               "em")
+        return dict(labels=x, theta=th, iters=int(it.value), converged=int(cv.value), T_hist=Th[:it.value].copy())
+
+    def pll(self, L, x, mu, sigma, beta):
+        """Pseudo-log-likelihood and its gradient: (pll, g_mu[L], g_sigma[L], g_beta)."""
+        lib = _get()
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        p = ctypes.c_double(0)
+        gb = ctypes.c_double(0)
+        gm = np.zeros(L)
+        gs = np.zeros(L)
+        _check(lib.orc_pll(self._h, L, _ptr(x), _ptr(mu), _ptr(sigma), beta, ctypes.byref(p), _ptr(gm), _ptr(gs),
+                           ctypes.byref(gb)), "pll")
+        return float(p.value), gm, gs, float(gb.value)
+
+    def label_image(self, region_ids, x):
+        ids = np.ascontiguousarray(region_ids, dtype=np.int32)
+        out = np.zeros(ids.shape, np.uint8)
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        _check(_get().orc_label_image(self._h, _ptr(ids), ids.size, _ptr(x), _ptr(out)), "label_image")
+        return out
+
+
+def replicate(hood_off, hood, L):
+    """Literal replication of the hoods by label: (testLabel, oldIndex, hoodId,
+    repHoods), each of length L * N_el."""
+    lib = _get()
+    hood_off = np.ascontiguousarray(hood_off, dtype=np.int64)
+    hood = np.ascontiguousarray(hood, dtype=np.int32)
+    C = len(hood_off) - 1
+    n = L * len(hood)
+    outs = [np.zeros(max(n, 1), np.int32) for _ in range(4)]
+    _check(lib.orc_replicate(_ptr(hood_off), _ptr(hood), C, L, *[_ptr(o) for o in outs]), "replicate")
+    return tuple(o[:n] for o in outs)
+
+
+def segment_slices(images, region_ids, cfg: EMConfig):
+    """Run the whole per-slice pipeline (graph, EM, label image) on a list of
+    slices; returns a list of (graph, em_result, label_image)."""
+    res = []
+    for img, ids in zip(images, region_ids):
+        g = Graph.from_image(img, ids)
+        r = g.em(cfg)
+        res.append((g, r, g.label_image(ids, r["labels"])))
+    return res

@@ -1,0 +1,733 @@
+/*
+ * pmrf_oracle.c -- TEST INFRASTRUCTURE, not part of the product.
+ *
+ * A plain, serial, deliberately unoptimised CPU reference of the optimisation
+ * path of DPP-PMRF (Lessley, Perciano, Heinemann, Camp, Childs, Bethel, "DPP-PMRF:
+ * Rethinking Optimization for a Probabilistic Graphical Model Using
+ * Data-Parallel Primitives", LDAV 2018).  Only the test-suite, the package's
+ * smoke check and the benchmark's CPU-baseline leg load this library; the CUDA
+ * library shares no code, header or table with it.
+ *
+ * Every function follows one passage of the paper; where the paper is silent
+ * the reading used is stated at the function (labelled G1..G11; the same labels
+ * are used in the design notes).  Floating point is IEEE double throughout,
+ * evaluated in the order written (no reassociation: build with -O2 and without
+ * -ffast-math).
+ *
+ * Notation: V regions (vertices), N(v) the sorted adjacency of v, K_c the c-th
+ * maximal clique, H_c its 1-neighbourhood ("hood"), L labels, theta_l =
+ * (n_l, mu_l, sigma_l, U_l).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_OK 0
+#define ORC_ERR_ARG 1
+#define ORC_ERR_OOM 3
+
+typedef struct {
+    int32_t max_id;   /* largest raw region id present (-1 if none) */
+    int32_t V;        /* number of regions */
+    int64_t n_adj;    /* 2E: length of adj */
+    int64_t C;        /* number of maximal cliques (= number of hoods) */
+    int64_t n_clq;    /* total clique member entries */
+    int64_t N_el;     /* total hood elements */
+    int32_t* rank;    /* [max_id+1]: compact vertex id of a raw id, -1 if absent */
+    int64_t* npix;    /* [V] pixel count of each region */
+    double* y;        /* [V] mean intensity of each region */
+    int64_t* adj_off; /* [V+1] */
+    int32_t* adj;     /* [n_adj] ascending within each vertex */
+    int64_t* clq_off; /* [C+1] */
+    int32_t* clq;     /* [n_clq] members ascending; cliques in lexicographic order */
+    int64_t* hood_off;/* [C+1] */
+    int32_t* hood;    /* [N_el] members ascending */
+} orc_graph;
+
+typedef struct {
+    int32_t n_labels, max_iters, conv_window, pad;
+    double beta, conv_tol, sigma_min, init_lo, init_hi;
+} orc_config;
+
+static int cmp_i32(const void* a, const void* b) {
+    int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
+    return (x > y) - (x < y);
+}
+
+void orc_graph_free(orc_graph* g) {
+    if (!g) return;
+    free(g->rank); free(g->npix); free(g->y); free(g->adj_off); free(g->adj);
+    free(g->clq_off); free(g->clq); free(g->hood_off); free(g->hood);
+    free(g);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Growable int32 buffer                                                     */
+typedef struct { int32_t* a; int64_t n, cap; } ivec;
+static int iv_push(ivec* v, int32_t x) {
+    if (v->n == v->cap) {
+        int64_t nc = v->cap ? 2 * v->cap : 64;
+        int32_t* na = (int32_t*)realloc(v->a, sizeof(int32_t) * (size_t)nc);
+        if (!na) return -1;
+        v->a = na; v->cap = nc;
+    }
+    v->a[v->n++] = x;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Regions (Section 2.1 and Section 3.1: a vertex per region of the
+ * oversegmentation; the data term uses the mean intensity of a region).
+ * Raw ids are compacted in ascending order: vertex v is the v-th smallest id
+ * present.  y_v = (sum of the region's pixels, added in row-major order) / count.
+ */
+static int regions(const double* image, const int32_t* ids, int64_t npx, orc_graph* g) {
+    int32_t mx = -1;
+    for (int64_t p = 0; p < npx; ++p) {
+        if (ids[p] < 0) return ORC_ERR_ARG;
+        if (ids[p] > mx) mx = ids[p];
+    }
+    g->max_id = mx;
+    g->rank = (int32_t*)malloc(sizeof(int32_t) * (size_t)(mx + 2));
+    if (!g->rank) return ORC_ERR_OOM;
+    for (int64_t i = 0; i <= mx; ++i) g->rank[i] = -1;
+    for (int64_t p = 0; p < npx; ++p) g->rank[ids[p]] = 0;
+    int32_t V = 0;
+    for (int64_t i = 0; i <= mx; ++i)
+        if (g->rank[i] == 0) g->rank[i] = V++;
+    g->V = V;
+    g->npix = (int64_t*)calloc((size_t)V + 1, sizeof(int64_t));
+    double* sum = (double*)calloc((size_t)V + 1, sizeof(double));
+    g->y = (double*)calloc((size_t)V + 1, sizeof(double));
+    if (!g->npix || !sum || !g->y) { free(sum); return ORC_ERR_OOM; }
+    for (int64_t p = 0; p < npx; ++p) {
+        int32_t v = g->rank[ids[p]];
+        sum[v] += image[p];
+        g->npix[v] += 1;
+    }
+    for (int32_t v = 0; v < V; ++v) g->y[v] = sum[v] / (double)g->npix[v];
+    free(sum);
+    return ORC_OK;
+}
+
+/*
+ * Region adjacency graph G(V,E) (Section 2.1: two regions are joined when they
+ * share a boundary; Algorithm 2, step 1).  Reading: "share a boundary" means
+ * some pair of 4-connected pixels (horizontal or vertical neighbours) carries
+ * the two ids.  Stored as CSR with each adjacency list ascending (Section
+ * 3.2.1 uses CSR).  Built by bucketing every boundary pixel pair under both of
+ * its endpoints, then sorting and de-duplicating each bucket.
+ */
+static int edges(const int32_t* ids, int64_t H, int64_t W, orc_graph* g) {
+    const int32_t V = g->V;
+    int64_t* cnt = (int64_t*)calloc((size_t)V + 1, sizeof(int64_t));
+    if (!cnt) return ORC_ERR_OOM;
+    for (int64_t r = 0; r < H; ++r)
+        for (int64_t c = 0; c < W; ++c) {
+            int32_t a = g->rank[ids[r * W + c]];
+            if (c + 1 < W) {
+                int32_t b = g->rank[ids[r * W + c + 1]];
+                if (a != b) { cnt[a]++; cnt[b]++; }
+            }
+            if (r + 1 < H) {
+                int32_t b = g->rank[ids[(r + 1) * W + c]];
+                if (a != b) { cnt[a]++; cnt[b]++; }
+            }
+        }
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+    if (!off) { free(cnt); return ORC_ERR_OOM; }
+    off[0] = 0;
+    for (int32_t v = 0; v < V; ++v) off[v + 1] = off[v] + cnt[v];
+    int32_t* bucket = (int32_t*)malloc(sizeof(int32_t) * (size_t)(off[V] + 1));
+    if (!bucket) { free(cnt); free(off); return ORC_ERR_OOM; }
+    for (int32_t v = 0; v < V; ++v) cnt[v] = 0;
+    for (int64_t r = 0; r < H; ++r)
+        for (int64_t c = 0; c < W; ++c) {
+            int32_t a = g->rank[ids[r * W + c]];
+            if (c + 1 < W) {
+                int32_t b = g->rank[ids[r * W + c + 1]];
+                if (a != b) { bucket[off[a] + cnt[a]++] = b; bucket[off[b] + cnt[b]++] = a; }
+            }
+            if (r + 1 < H) {
+                int32_t b = g->rank[ids[(r + 1) * W + c]];
+                if (a != b) { bucket[off[a] + cnt[a]++] = b; bucket[off[b] + cnt[b]++] = a; }
+            }
+        }
+    g->adj_off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+    g->adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(off[V] + 1));
+    if (!g->adj_off || !g->adj) { free(cnt); free(off); free(bucket); return ORC_ERR_OOM; }
+    int64_t n = 0;
+    g->adj_off[0] = 0;
+    for (int32_t v = 0; v < V; ++v) {
+        int32_t* b = bucket + off[v];
+        int64_t k = off[v + 1] - off[v];
+        qsort(b, (size_t)k, sizeof(int32_t), cmp_i32);
+        for (int64_t i = 0; i < k; ++i)
+            if (i == 0 || b[i] != b[i - 1]) g->adj[n++] = b[i];
+        g->adj_off[v + 1] = n;
+    }
+    g->n_adj = n;
+    free(cnt); free(off); free(bucket);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Maximal cliques (Section 3.2.1; Algorithm 2, step 2).  The paper uses a DPP
+ * clique enumerator described elsewhere; any correct enumeration gives the same
+ * set (G1).  Here: Bron-Kerbosch with Tomita pivoting, started once per vertex v
+ * with candidates {u in N(v): u > v} and excluded set {u in N(v): u < v}, so
+ * each maximal clique is reported exactly once, from its smallest member; an
+ * isolated vertex is the clique {v}.  Canonical order (ours): members
+ * ascending, cliques lexicographic.
+ */
+typedef struct { ivec out_off; ivec out; const orc_graph* g; int err; } bk_ctx;
+
+static int64_t isect(const int32_t* a, int64_t na, const int32_t* b, int64_t nb, int32_t* o) {
+    int64_t i = 0, j = 0, k = 0;
+    while (i < na && j < nb) {
+        if (a[i] < b[j]) ++i;
+        else if (a[i] > b[j]) ++j;
+        else { o[k++] = a[i]; ++i; ++j; }
+    }
+    return k;
+}
+static int contains(const int32_t* a, int64_t n, int32_t x) { /* a ascending */
+    int64_t lo = 0, hi = n;
+    while (lo < hi) {
+        int64_t m = (lo + hi) / 2;
+        if (a[m] < x) lo = m + 1; else hi = m;
+    }
+    return lo < n && a[lo] == x;
+}
+
+static void bk(bk_ctx* ctx, int32_t* R, int64_t nR, int32_t* P, int64_t nP, int32_t* X, int64_t nX) {
+    const orc_graph* g = ctx->g;
+    if (ctx->err) return;
+    if (nP == 0 && nX == 0) {
+        for (int64_t i = 0; i < nR; ++i) if (iv_push(&ctx->out, R[i])) { ctx->err = 1; return; }
+        if (iv_push(&ctx->out_off, (int32_t)ctx->out.n)) ctx->err = 1;
+        return;
+    }
+    if (nP == 0) return;
+    /* pivot: vertex of P u X with the most neighbours in P */
+    int32_t piv = -1; int64_t best = -1;
+    for (int64_t s = 0; s < nP + nX; ++s) {
+        int32_t u = s < nP ? P[s] : X[s - nP];
+        const int32_t* Nu = g->adj + g->adj_off[u];
+        int64_t du = g->adj_off[u + 1] - g->adj_off[u], k = 0;
+        for (int64_t i = 0; i < nP; ++i) k += contains(Nu, du, P[i]);
+        if (k > best) { best = k; piv = u; }
+    }
+    const int32_t* Npiv = g->adj + g->adj_off[piv];
+    int64_t dpiv = g->adj_off[piv + 1] - g->adj_off[piv];
+    /* candidates: P \ N(pivot), in ascending order; P and X are kept sorted */
+    int32_t* cand = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nP + 1));
+    int32_t* Pc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nP + 1));
+    int32_t* Xc = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nP + nX + 1));
+    int32_t* P2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nP + 1));
+    int32_t* X2 = (int32_t*)malloc(sizeof(int32_t) * (size_t)(nP + nX + 1));
+    if (!cand || !Pc || !Xc || !P2 || !X2) { ctx->err = 1; free(cand); free(Pc); free(Xc); free(P2); free(X2); return; }
+    int64_t nc = 0;
+    for (int64_t i = 0; i < nP; ++i) if (!contains(Npiv, dpiv, P[i])) cand[nc++] = P[i];
+    memcpy(Pc, P, sizeof(int32_t) * (size_t)nP);
+    memcpy(Xc, X, sizeof(int32_t) * (size_t)nX);
+    int64_t nPc = nP, nXc = nX;
+    for (int64_t ci = 0; ci < nc; ++ci) {
+        int32_t w = cand[ci];
+        const int32_t* Nw = g->adj + g->adj_off[w];
+        int64_t dw = g->adj_off[w + 1] - g->adj_off[w];
+        int64_t nP2 = isect(Pc, nPc, Nw, dw, P2);
+        int64_t nX2 = isect(Xc, nXc, Nw, dw, X2);
+        R[nR] = w;
+        bk(ctx, R, nR + 1, P2, nP2, X2, nX2);
+        /* P := P \ {w};  X := X u {w}  (both kept ascending) */
+        int64_t k = 0;
+        for (int64_t i = 0; i < nPc; ++i) if (Pc[i] != w) Pc[k++] = Pc[i];
+        nPc = k;
+        int64_t pos = nXc;
+        while (pos > 0 && Xc[pos - 1] > w) { Xc[pos] = Xc[pos - 1]; --pos; }
+        Xc[pos] = w; ++nXc;
+    }
+    free(cand); free(Pc); free(Xc); free(P2); free(X2);
+}
+
+typedef struct { const int32_t* m; int64_t n; } clq_ref;
+static int cmp_clq(const void* a, const void* b) {
+    const clq_ref* x = (const clq_ref*)a; const clq_ref* y = (const clq_ref*)b;
+    for (int64_t i = 0; i < x->n && i < y->n; ++i)
+        if (x->m[i] != y->m[i]) return x->m[i] < y->m[i] ? -1 : 1;
+    return (x->n > y->n) - (x->n < y->n);
+}
+
+static int cliques(orc_graph* g) {
+    const int32_t V = g->V;
+    bk_ctx ctx; memset(&ctx, 0, sizeof(ctx)); ctx.g = g;
+    if (iv_push(&ctx.out_off, 0)) return ORC_ERR_OOM;
+    int32_t maxdeg = 0;
+    for (int32_t v = 0; v < V; ++v) {
+        int32_t d = (int32_t)(g->adj_off[v + 1] - g->adj_off[v]);
+        if (d > maxdeg) maxdeg = d;
+    }
+    int32_t* R = (int32_t*)malloc(sizeof(int32_t) * ((size_t)maxdeg + 2));
+    int32_t* P = (int32_t*)malloc(sizeof(int32_t) * ((size_t)maxdeg + 1));
+    int32_t* X = (int32_t*)malloc(sizeof(int32_t) * ((size_t)maxdeg + 1));
+    if (!R || !P || !X) { free(R); free(P); free(X); return ORC_ERR_OOM; }
+    for (int32_t v = 0; v < V && !ctx.err; ++v) {
+        int64_t nP = 0, nX = 0;
+        for (int64_t i = g->adj_off[v]; i < g->adj_off[v + 1]; ++i) {
+            int32_t u = g->adj[i];
+            if (u > v) P[nP++] = u; else X[nX++] = u;
+        }
+        R[0] = v;
+        bk(&ctx, R, 1, P, nP, X, nX);
+    }
+    free(R); free(P); free(X);
+    if (ctx.err) { free(ctx.out.a); free(ctx.out_off.a); return ORC_ERR_OOM; }
+    const int64_t C = ctx.out_off.n - 1;
+    /* canonical order: sort members of each clique, then the cliques */
+    clq_ref* refs = (clq_ref*)malloc(sizeof(clq_ref) * ((size_t)C + 1));
+    if (!refs) { free(ctx.out.a); free(ctx.out_off.a); return ORC_ERR_OOM; }
+    for (int64_t c = 0; c < C; ++c) {
+        int32_t* m = ctx.out.a + ctx.out_off.a[c];
+        int64_t n = ctx.out_off.a[c + 1] - ctx.out_off.a[c];
+        qsort(m, (size_t)n, sizeof(int32_t), cmp_i32);
+        refs[c].m = m; refs[c].n = n;
+    }
+    qsort(refs, (size_t)C, sizeof(clq_ref), cmp_clq);
+    g->C = C;
+    g->n_clq = ctx.out.n;
+    g->clq_off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)C + 1));
+    g->clq = (int32_t*)malloc(sizeof(int32_t) * ((size_t)ctx.out.n + 1));
+    if (!g->clq_off || !g->clq) { free(refs); free(ctx.out.a); free(ctx.out_off.a); return ORC_ERR_OOM; }
+    int64_t k = 0;
+    g->clq_off[0] = 0;
+    for (int64_t c = 0; c < C; ++c) {
+        memcpy(g->clq + k, refs[c].m, sizeof(int32_t) * (size_t)refs[c].n);
+        k += refs[c].n;
+        g->clq_off[c + 1] = k;
+    }
+    free(refs); free(ctx.out.a); free(ctx.out_off.a);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * 1-neighbourhoods (Section 3.1: the vertices of a maximal clique together with
+ * every vertex within k hops of a clique vertex, k = 1; Section 3.2.2,
+ * "Construction of Neighborhoods", steps Find/Count/Get Neighbors and Remove
+ * Duplicate Neighbors).  Here written as its definition: H_c = sort(unique(K_c
+ * u N(u) for u in K_c)), one hood per clique in clique order (G2: each hood
+ * ascending by vertex id, hoods contiguous in clique order).
+ */
+static int hoods(orc_graph* g) {
+    const int64_t C = g->C;
+    g->hood_off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)C + 1));
+    if (!g->hood_off) return ORC_ERR_OOM;
+    ivec out; memset(&out, 0, sizeof(out));
+    ivec tmp; memset(&tmp, 0, sizeof(tmp));
+    g->hood_off[0] = 0;
+    for (int64_t c = 0; c < C; ++c) {
+        tmp.n = 0;
+        for (int64_t i = g->clq_off[c]; i < g->clq_off[c + 1]; ++i) {
+            int32_t u = g->clq[i];
+            if (iv_push(&tmp, u)) goto oom;
+            for (int64_t j = g->adj_off[u]; j < g->adj_off[u + 1]; ++j)
+                if (iv_push(&tmp, g->adj[j])) goto oom;
+        }
+        qsort(tmp.a, (size_t)tmp.n, sizeof(int32_t), cmp_i32);
+        for (int64_t i = 0; i < tmp.n; ++i)
+            if (i == 0 || tmp.a[i] != tmp.a[i - 1])
+                if (iv_push(&out, tmp.a[i])) goto oom;
+        g->hood_off[c + 1] = out.n;
+    }
+    g->N_el = out.n;
+    g->hood = out.a ? out.a : (int32_t*)malloc(sizeof(int32_t));
+    free(tmp.a);
+    return ORC_OK;
+oom:
+    free(out.a); free(tmp.a);
+    return ORC_ERR_OOM;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Build everything for one slice: regions, adjacency, cliques, hoods. */
+int orc_build_graph(const double* image, const int32_t* ids, int64_t H, int64_t W, orc_graph** out) {
+    if (!out || H < 0 || W < 0 || ((H * W) > 0 && (!image || !ids))) return ORC_ERR_ARG;
+    orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
+    if (!g) return ORC_ERR_OOM;
+    int rc = regions(image, ids, H * W, g);
+    if (!rc) rc = edges(ids, H, W, g);
+    if (!rc) rc = cliques(g);
+    if (!rc) rc = hoods(g);
+    if (rc) { orc_graph_free(g); return rc; }
+    *out = g;
+    return ORC_OK;
+}
+
+/* Build cliques and hoods for a given graph (adjacency must be symmetric,
+ * ascending, without self loops) and per-vertex intensities.  Used for small
+ * hand-made graphs. */
+int orc_graph_from_adjacency(int32_t V, const double* y, const int64_t* adj_off, const int32_t* adj,
+                             orc_graph** out) {
+    if (!out || V < 0) return ORC_ERR_ARG;
+    orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
+    if (!g) return ORC_ERR_OOM;
+    g->V = V; g->max_id = V - 1;
+    g->rank = (int32_t*)malloc(sizeof(int32_t) * ((size_t)V + 1));
+    g->npix = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+    g->y = (double*)malloc(sizeof(double) * ((size_t)V + 1));
+    g->adj_off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+    g->n_adj = adj_off[V];
+    g->adj = (int32_t*)malloc(sizeof(int32_t) * ((size_t)g->n_adj + 1));
+    if (!g->rank || !g->npix || !g->y || !g->adj_off || !g->adj) { orc_graph_free(g); return ORC_ERR_OOM; }
+    for (int32_t v = 0; v < V; ++v) { g->rank[v] = v; g->npix[v] = 1; g->y[v] = y[v]; }
+    memcpy(g->adj_off, adj_off, sizeof(int64_t) * ((size_t)V + 1));
+    memcpy(g->adj, adj, sizeof(int32_t) * (size_t)g->n_adj);
+    for (int32_t v = 0; v < V; ++v)
+        for (int64_t i = adj_off[v]; i < adj_off[v + 1]; ++i)
+            if (adj[i] < 0 || adj[i] >= V || adj[i] == v || (i > adj_off[v] && adj[i] <= adj[i - 1])) {
+                orc_graph_free(g);
+                return ORC_ERR_ARG;
+            }
+    int rc = cliques(g);
+    if (!rc) rc = hoods(g);
+    if (rc) { orc_graph_free(g); return rc; }
+    *out = g;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Literal replication of the hoods by label (Section 3.2.2, EM step 1,
+ * "Replicate Neighborhoods By Label"): for each hood, one copy per label, in
+ * the order hood 0 / label 0, hood 0 / label 1, ..., hood 1 / label 0, ...
+ * testLabel = label of the copy, oldIndex = index into the hoods array,
+ * hoodId = hood of the element, repHoods = hoods[oldIndex].  Output length is
+ * L * N_el.  (The CUDA path never materialises these arrays: the label copy is
+ * a register loop there.)
+ */
+int orc_replicate(const int64_t* hood_off, const int32_t* hood, int64_t C, int32_t L, int32_t* testLabel,
+                  int32_t* oldIndex, int32_t* hoodId, int32_t* repHoods) {
+    int64_t k = 0;
+    for (int64_t c = 0; c < C; ++c)
+        for (int32_t l = 0; l < L; ++l)
+            for (int64_t i = hood_off[c]; i < hood_off[c + 1]; ++i) {
+                testLabel[k] = l;
+                oldIndex[k] = (int32_t)i;
+                hoodId[k] = (int32_t)c;
+                repHoods[k] = hood[i];
+                ++k;
+            }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Data term (Section 2.1: the data term is built from the mean intensity of a
+ * region; G4): the Gaussian negative log-likelihood of y under label l without
+ * its constant 0.5*ln(2*pi):  D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l.
+ */
+static double data_term(double y, double mu, double sigma) {
+    double dev = y - mu;
+    return dev * dev / (2.0 * sigma * sigma) + log(sigma);
+}
+
+/*
+ * One MAP sweep (Section 3.2.2, EM step 2: Compute Energy Function, Compute
+ * Minimum Vertex and Label Energies, Compute Neighborhood Energy Sums;
+ * step 3: Update Output Labels; Algorithm 2, steps 7-10), with labels x and
+ * parameters (mu, sigma) of the previous iteration held fixed:
+ *
+ *   E(c,v,l) = D_l(y_v) + beta * #{u in N(v) n H_c : x_u != l}     (G4: Potts
+ *              penalty over the neighbours of v that lie inside hood c)
+ *   Emin(c,v) = min_l E(c,v,l); lab(c,v) = smallest l attaining it  (G5)
+ *   S_c = sum over v in H_c, ascending v, of Emin(c,v)
+ *   (E*_v, x'_v) = lexicographic minimum over the hoods c containing v of
+ *                  (Emin(c,v), lab(c,v))                            (G6)
+ *
+ * Optional outputs (NULL to skip): E_el [N_el*L] every E(c,v,l) in element
+ * order; Emin_el, lab_el [N_el]; E_second [V]: the smallest E(c,v,l) over all
+ * hoods c containing v with l != x'_v (INFINITY when L == 1).
+ */
+int orc_map_sweep(const orc_graph* g, int32_t L, double beta, const uint8_t* x, const double* mu,
+                  const double* sigma, uint8_t* x_new, double* E_star, double* S_hood, double* E_el,
+                  double* Emin_el, uint8_t* lab_el, double* E_second) {
+    if (!g || L < 1 || L > 255) return ORC_ERR_ARG;
+    const int32_t V = g->V;
+    int32_t* best_lab = (int32_t*)malloc(sizeof(int32_t) * ((size_t)V + 1));
+    double* best_E = (double*)malloc(sizeof(double) * ((size_t)V + 1));
+    double* E = (double*)malloc(sizeof(double) * (size_t)L);
+    if (!best_lab || !best_E || !E) { free(best_lab); free(best_E); free(E); return ORC_ERR_OOM; }
+    for (int32_t v = 0; v < V; ++v) { best_lab[v] = -1; best_E[v] = INFINITY; }
+    for (int64_t c = 0; c < g->C; ++c) {
+        const int32_t* Hc = g->hood + g->hood_off[c];
+        const int64_t nH = g->hood_off[c + 1] - g->hood_off[c];
+        double S = 0.0;
+        for (int64_t i = 0; i < nH; ++i) {
+            const int32_t v = Hc[i];
+            int32_t lab = 0;
+            for (int32_t l = 0; l < L; ++l) {
+                int64_t m = 0;
+                for (int64_t j = g->adj_off[v]; j < g->adj_off[v + 1]; ++j) {
+                    int32_t u = g->adj[j];
+                    if (contains(Hc, nH, u) && x[u] != l) ++m;
+                }
+                E[l] = data_term(g->y[v], mu[l], sigma[l]) + beta * (double)m;
+                if (E_el) E_el[(g->hood_off[c] + i) * L + l] = E[l];
+                if (E[l] < E[lab]) lab = l;
+            }
+            const double Emin = E[lab];
+            S += Emin;
+            if (Emin_el) Emin_el[g->hood_off[c] + i] = Emin;
+            if (lab_el) lab_el[g->hood_off[c] + i] = (uint8_t)lab;
+            if (Emin < best_E[v] || (Emin == best_E[v] && lab < best_lab[v])) {
+                best_E[v] = Emin;
+                best_lab[v] = lab;
+            }
+        }
+        if (S_hood) S_hood[c] = S;
+    }
+    for (int32_t v = 0; v < V; ++v) {
+        if (x_new) x_new[v] = (uint8_t)best_lab[v];
+        if (E_star) E_star[v] = best_E[v];
+    }
+    if (E_second) {
+        for (int32_t v = 0; v < V; ++v) E_second[v] = INFINITY;
+        for (int64_t c = 0; c < g->C; ++c) {
+            const int32_t* Hc = g->hood + g->hood_off[c];
+            const int64_t nH = g->hood_off[c + 1] - g->hood_off[c];
+            for (int64_t i = 0; i < nH; ++i) {
+                const int32_t v = Hc[i];
+                for (int32_t l = 0; l < L; ++l) {
+                    if (l == best_lab[v]) continue;
+                    int64_t m = 0;
+                    for (int64_t j = g->adj_off[v]; j < g->adj_off[v + 1]; ++j) {
+                        int32_t u = g->adj[j];
+                        if (contains(Hc, nH, u) && x[u] != l) ++m;
+                    }
+                    double e = data_term(g->y[v], mu[l], sigma[l]) + beta * (double)m;
+                    if (e < E_second[v]) E_second[v] = e;
+                }
+            }
+        }
+    }
+    free(best_lab); free(best_E); free(E);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Parameter update (Section 3.2.2, EM step 4, "Update Parameters": mu and sigma
+ * of each label from the intensities of the vertices carrying that label, plus
+ * the per-label sums of the vertex energies).  Readings (G8): moments over
+ * vertices; population variance (divide by n), two passes (mean first);
+ * sigma floored at sigma_min; a label with no vertex keeps its previous mu and
+ * sigma.  U_l = sum of E*_v over the vertices with label l (0 when E_star is
+ * NULL).  theta layout [L][4] = (n_l, mu_l, sigma_l, U_l).  Sums run in
+ * ascending v.
+ */
+int orc_params(const orc_graph* g, int32_t L, const uint8_t* x, const double* E_star, const double* theta_prev,
+               double sigma_min, double* theta_out) {
+    if (!g || L < 1 || !theta_prev || !theta_out) return ORC_ERR_ARG;
+    for (int32_t l = 0; l < L; ++l) {
+        int64_t n = 0;
+        double s = 0.0, u = 0.0;
+        for (int32_t v = 0; v < g->V; ++v)
+            if (x[v] == l) {
+                ++n;
+                s += g->y[v];
+                if (E_star) u += E_star[v];
+            }
+        double* t = theta_out + 4 * l;
+        if (n == 0) {
+            t[0] = 0.0; t[1] = theta_prev[4 * l + 1]; t[2] = theta_prev[4 * l + 2]; t[3] = 0.0;
+            continue;
+        }
+        const double mean = s / (double)n;
+        double ss = 0.0;
+        for (int32_t v = 0; v < g->V; ++v)
+            if (x[v] == l) {
+                double d = g->y[v] - mean;
+                ss += d * d;
+            }
+        double sd = sqrt(ss / (double)n);
+        t[0] = (double)n; t[1] = mean; t[2] = sd > sigma_min ? sd : sigma_min; t[3] = u;
+    }
+    return ORC_OK;
+}
+
+/*
+ * Initial labels (Algorithm 2, step 3).  The paper draws labels and parameters
+ * at random; reading G3 (ours) thresholds the region means instead:
+ * x_v = clamp(floor((y_v - lo) / (hi - lo) * L), 0, L-1), i.e. for L = 2 on
+ * [0,1] a cut at 0.5.
+ */
+int orc_init_labels(const orc_graph* g, int32_t L, double lo, double hi, uint8_t* x) {
+    if (!g || L < 1 || !(hi > lo)) return ORC_ERR_ARG;
+    for (int32_t v = 0; v < g->V; ++v) {
+        double q = floor((g->y[v] - lo) / (hi - lo) * (double)L);
+        int32_t l = q < 0.0 ? 0 : (q > (double)(L - 1) ? L - 1 : (int32_t)q);
+        x[v] = (uint8_t)l;
+    }
+    return ORC_OK;
+}
+
+/* Initial parameters: label-conditional moments of the initial labels; an
+ * empty label starts at the centre of its threshold bin with sigma = the bin
+ * width (G3, ours). */
+int orc_init_params(const orc_graph* g, int32_t L, double lo, double hi, double sigma_min, const uint8_t* x,
+                    double* theta) {
+    if (!g || L < 1) return ORC_ERR_ARG;
+    double* prev = (double*)malloc(sizeof(double) * 4 * (size_t)L);
+    if (!prev) return ORC_ERR_OOM;
+    for (int32_t l = 0; l < L; ++l) {
+        prev[4 * l + 0] = 0.0;
+        prev[4 * l + 1] = lo + ((double)l + 0.5) * (hi - lo) / (double)L;
+        prev[4 * l + 2] = (hi - lo) / (double)L;
+        prev[4 * l + 3] = 0.0;
+    }
+    int rc = orc_params(g, L, x, NULL, prev, sigma_min, theta);
+    free(prev);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * The EM loop (Algorithm 2, steps 6-11; Section 3.2.2, EM steps 2-5).
+ *   x^0, theta^0: orc_init_labels / orc_init_params.
+ *   for t = 1, 2, ...:
+ *     (x^t, E*, S^t) = sweep(x^{t-1}, theta^{t-1});  theta^t = params(x^t, E*)
+ *     T^t = sum_c S^t_c (ascending c)
+ *     hood c converged at t  <=>  t > W and max_{k=1..W} |S^t_c - S^{t-k}_c| < tol
+ *     stop when every hood converged (MAP convergence check), or when t > W and
+ *     max_{k=1..W} |T^t - T^{t-k}| < tol (EM convergence check), or t = max_iters.
+ * Readings (G9): "change over the previous W iterations" is the largest
+ * absolute difference against each of them; either test ends the loop.
+ * Outputs: x = x^t, theta = theta^t, *iters = t, *converged = 1 when a
+ * convergence test (not the cap) ended the loop; T_hist[t-1] = T^t (optional,
+ * length max_iters).  V == 0 returns at once with iters 0, converged 1.
+ */
+int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta, int32_t* iters, int32_t* converged,
+           double* T_hist) {
+    if (!g || !cfg || cfg->n_labels < 1 || cfg->max_iters < 1 || cfg->conv_window < 1) return ORC_ERR_ARG;
+    const int32_t L = cfg->n_labels, W = cfg->conv_window, V = g->V;
+    const int64_t C = g->C;
+    int rc = orc_init_labels(g, L, cfg->init_lo, cfg->init_hi, x);
+    if (!rc) rc = orc_init_params(g, L, cfg->init_lo, cfg->init_hi, cfg->sigma_min, x, theta);
+    if (rc) return rc;
+    *iters = 0; *converged = 1;
+    if (V == 0) return ORC_OK;
+    double* Shist = (double*)malloc(sizeof(double) * (size_t)((W + 1) * C + 1)); /* ring of W+1 */
+    double* Thist = (double*)malloc(sizeof(double) * (size_t)(W + 1));
+    uint8_t* xn = (uint8_t*)malloc((size_t)V);
+    double* Es = (double*)malloc(sizeof(double) * (size_t)V);
+    double* mu = (double*)malloc(sizeof(double) * (size_t)L);
+    double* sg = (double*)malloc(sizeof(double) * (size_t)L);
+    double* th2 = (double*)malloc(sizeof(double) * 4 * (size_t)L);
+    if (!Shist || !Thist || !xn || !Es || !mu || !sg || !th2) { rc = ORC_ERR_OOM; goto done; }
+    *converged = 0;
+    for (int32_t t = 1; t <= cfg->max_iters; ++t) {
+        for (int32_t l = 0; l < L; ++l) { mu[l] = theta[4 * l + 1]; sg[l] = theta[4 * l + 2]; }
+        double* S = Shist + (size_t)(t % (W + 1)) * (size_t)C;
+        rc = orc_map_sweep(g, L, cfg->beta, x, mu, sg, xn, Es, S, NULL, NULL, NULL, NULL);
+        if (rc) goto done;
+        memcpy(x, xn, (size_t)V);
+        rc = orc_params(g, L, x, Es, theta, cfg->sigma_min, th2);
+        if (rc) goto done;
+        memcpy(theta, th2, sizeof(double) * 4 * (size_t)L);
+        double T = 0.0;
+        for (int64_t c = 0; c < C; ++c) T += S[c];
+        Thist[t % (W + 1)] = T;
+        if (T_hist) T_hist[t - 1] = T;
+        *iters = t;
+        if (t > W) {
+            int all = 1;
+            for (int64_t c = 0; c < C && all; ++c) {
+                double dmax = 0.0;
+                for (int32_t k = 1; k <= W; ++k) {
+                    double d = fabs(S[c] - Shist[(size_t)((t - k) % (W + 1)) * (size_t)C + (size_t)c]);
+                    if (d > dmax) dmax = d;
+                }
+                if (!(dmax < cfg->conv_tol)) all = 0;
+            }
+            double dT = 0.0;
+            for (int32_t k = 1; k <= W; ++k) {
+                double d = fabs(T - Thist[(t - k) % (W + 1)]);
+                if (d > dT) dT = d;
+            }
+            if (all || dT < cfg->conv_tol) { *converged = 1; break; }
+        }
+    }
+done:
+    free(Shist); free(Thist); free(xn); free(Es); free(mu); free(sg); free(th2);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
+ * Vertex pseudo-log-likelihood and its gradient (not in the paper; the
+ * differentiable form built beside the method, reading G10).  With labels x
+ * fixed, over the full graph neighbourhood:
+ *   E_v(l) = D_l(y_v) + beta * m_v(l),   m_v(l) = #{u in N(v): x_u != l}
+ *   PLL = sum_v [ -E_v(x_v) - log sum_l exp(-E_v(l)) ]
+ * (log-sum-exp with the largest term factored out).  Gradients:
+ *   dPLL/dmu_k    = sum_v (p_v(k) - [x_v = k]) * (mu_k - y_v) / sigma_k^2
+ *   dPLL/dsigma_k = sum_v (p_v(k) - [x_v = k]) * (1/sigma_k - (y_v - mu_k)^2 / sigma_k^3)
+ *   dPLL/dbeta    = sum_v ( sum_l p_v(l) m_v(l) - m_v(x_v) )
+ * with p_v = softmax(-E_v).  Sums run in ascending v.  Any output may be NULL.
+ */
+int orc_pll(const orc_graph* g, int32_t L, const uint8_t* x, const double* mu, const double* sigma, double beta,
+            double* pll, double* g_mu, double* g_sigma, double* g_beta) {
+    if (!g || L < 1) return ORC_ERR_ARG;
+    double* E = (double*)malloc(sizeof(double) * (size_t)L);
+    double* p = (double*)malloc(sizeof(double) * (size_t)L);
+    int64_t* m = (int64_t*)malloc(sizeof(int64_t) * (size_t)L);
+    if (!E || !p || !m) { free(E); free(p); free(m); return ORC_ERR_OOM; }
+    double acc = 0.0, gb = 0.0;
+    if (g_mu) for (int32_t l = 0; l < L; ++l) g_mu[l] = 0.0;
+    if (g_sigma) for (int32_t l = 0; l < L; ++l) g_sigma[l] = 0.0;
+    for (int32_t v = 0; v < g->V; ++v) {
+        const double yv = g->y[v];
+        double emin = INFINITY;
+        for (int32_t l = 0; l < L; ++l) {
+            m[l] = 0;
+            for (int64_t j = g->adj_off[v]; j < g->adj_off[v + 1]; ++j)
+                if (x[g->adj[j]] != l) ++m[l];
+            E[l] = data_term(yv, mu[l], sigma[l]) + beta * (double)m[l];
+            if (E[l] < emin) emin = E[l];
+        }
+        double z = 0.0;
+        for (int32_t l = 0; l < L; ++l) z += exp(-(E[l] - emin));
+        const double lse = -emin + log(z); /* log sum_l exp(-E_l) */
+        acc += -E[x[v]] - lse;
+        for (int32_t l = 0; l < L; ++l) p[l] = exp(-(E[l] - emin)) / z;
+        double eb = 0.0;
+        for (int32_t l = 0; l < L; ++l) eb += p[l] * (double)m[l];
+        gb += eb - (double)m[x[v]];
+        for (int32_t k = 0; k < L; ++k) {
+            const double w = p[k] - (x[v] == k ? 1.0 : 0.0);
+            const double s2 = sigma[k] * sigma[k];
+            const double dev = yv - mu[k];
+            if (g_mu) g_mu[k] += w * (mu[k] - yv) / s2;
+            if (g_sigma) g_sigma[k] += w * (1.0 / sigma[k] - dev * dev / (s2 * sigma[k]));
+        }
+    }
+    if (pll) *pll = acc;
+    if (g_beta) *g_beta = gb;
+    free(E); free(p); free(m);
+    return ORC_OK;
+}
+
+/* Labels back to pixels (Section 3.2.2, closing paragraph: vertex labels map
+ * back to the pixels of their regions). */
+int orc_label_image(const orc_graph* g, const int32_t* ids, int64_t npx, const uint8_t* x, uint8_t* out) {
+    if (!g) return ORC_ERR_ARG;
+    for (int64_t p = 0; p < npx; ++p) {
+        if (ids[p] < 0 || ids[p] > g->max_id || g->rank[ids[p]] < 0) return ORC_ERR_ARG;
+        out[p] = x[g->rank[ids[p]]];
+    }
+    return ORC_OK;
+}
