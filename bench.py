@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput of the B300 MRF region-labelling engine (DPP-PMRF's EM path).
+
+One step = the whole path on one batch of synthetic slices: region graph +
+maximal cliques + hoods + replica structures (pmrf_build_graph), the EM loop
+(pmrf_em: MAP sweeps, replica reduction, parameter update, convergence tests),
+the label image (pmrf_label_image) and one pseudo-log-likelihood value plus its
+adjoint at the final labels (pmrf_pll, pmrf_pll_grad).
+
+Default workload: stack512 -- 512 slices of 1024x1024, per-slice seed and
+Voronoi pitch U[4,10] (10k-65k regions each), 2 labels, beta 1, <= 50 EM
+iterations; the inputs (6.4 GB) are larger than L2, so no flush is needed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank processes its own
+batch (weak scaling; no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6400.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="stack512")
+    ap.add_argument("--slices", type=int, default=None, help="slices per rank (default: the workload's)")
+    ap.add_argument("--plain-sample", type=int, default=16, help="slices timed one call per slice")
+    ap.add_argument("--cpu-slices", type=int, default=2, help="slices the oracle baseline runs")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)),
+            int(os.environ.get("LOCAL_RANK", 0)))
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except Exception:
+                self.proc.kill()
+                self.out = ""
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        rows = list(csv.reader(io.StringIO(self.out)))
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, n in enumerate(names):
+                if "Active" in r[5 + k] and "Not" not in r[5 + k]:
+                    reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def host_inputs(wl, threads=None):
+    sl = synth.make_stack(wl.slices, threads=threads or os.cpu_count())
+    img = np.stack([s.image for s in sl])
+    ids = np.stack([s.region_ids for s in sl])
+    return sl, img, ids
+
+
+def sweep_bytes(g, L, W):
+    """Algorithmic bytes of one MAP sweep of every slice, split by kernel, plus
+    the per-slice vectors needed to weight iterations by the slices still
+    active (see the design notes for the model)."""
+    vo = g.array("VERT_OFF").numpy()
+    hso = g.array("HOOD_SLICE_OFF").numpy()
+    ho = g.array("HOOD_OFF").numpy()
+    ao = g.array("ADJ_OFF").numpy()
+    ro = g.array("REP_OFF").numpy()
+    Vs = np.diff(vo)
+    Cs = np.diff(hso)
+    Es = ho[hso[1:]] - ho[hso[:-1]]
+    Adj = ao[vo[1:]] - ao[vo[:-1]]
+    Rep = ro[vo[1:]] - ro[vo[:-1]]  # replica words (== replicas when every degree <= 32)
+    # vertex pass: per vertex adj_off, rep_woff, y (8 each), label in+out (2), D table write (8L);
+    # per adjacency entry 4 B, per replica mask word 4 B
+    vb = Vs * (24 + 2 + 8 * L) + 4 * Adj + 4 * Rep
+    # hood pass: per hood hood_off + row_off (16) and the W-deep history ring (8W read + 8 write);
+    # per element hood member id + row word (8); per vertex its label and D row, read once (1 + 8L)
+    hb = Cs * (16 + 8 * W + 8) + 8 * Es + Vs * (1 + 8 * L)
+    return vb.astype(np.float64), hb.astype(np.float64), dict(V=int(Vs.sum()), C=int(Cs.sum()), N_el=int(Es.sum()),
+                                                               E=int(Adj.sum() // 2), Es=Es)
+
+
+def run_ours(a):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1809_05018_b300 as pmrf
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    base = synth.workload(a.workload)
+    n = a.slices or len(base.slices)
+    wl = synth.workload(a.workload, n_slices=n, first_slice=rank * n) if a.workload in ("stack512", "grad64") \
+        else base
+    t0 = time.time()
+    sl, img_np, ids_np = host_inputs(wl)
+    gen_s = time.time() - t0
+    S = img_np.shape[0]
+    L, beta = wl.n_labels, wl.beta
+    cfg = pmrf.EMConfig(n_labels=L, beta=beta, max_iters=wl.max_iters)
+    img_h = torch.from_numpy(img_np).pin_memory()
+    ids_h = torch.from_numpy(ids_np).pin_memory()
+    img_d = img_h.cuda()
+    ids_d = ids_h.cuda()
+    ones = torch.ones(S, dtype=torch.float64, device="cuda")
+
+    def step(img, ids):
+        g = pmrf.build_graph(img, ids)
+        out = g.em(cfg)
+        seg = g.label_image(ids, out["labels"])
+        mu = out["params"][:, :, 1].contiguous()
+        sg = out["params"][:, :, 2].contiguous()
+        pll = g.pll(L, out["labels"], mu, sg, beta)
+        gm, gs, gb = g.pll_grad(L, out["labels"], mu, sg, beta, ones[:g.S])
+        return g, out, seg, pll
+
+    for _ in range(a.warmup):
+        step(img_d, ids_d)
+    torch.cuda.synchronize()
+
+    # ---- timed region: inputs resident in HBM
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    n0 = pmrf.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    with Clocks(local) as clk:
+        e0.record()
+        for _ in range(a.steps):
+            g, out, seg, pll = step(img_d, ids_d)
+        e1.record()
+        torch.cuda.synchronize()
+    barrier()
+    launches = pmrf.launch_count() - n0
+    ms = e0.elapsed_time(e1) / a.steps
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms = float(ms_t)
+    value = S * world / (ms / 1e3)
+
+    # ---- the EM loop alone, profiled per kernel (same graph, same inputs)
+    iters = out["iters"].cpu().numpy()
+    g.set_tuning(profile=1)
+    g.em(cfg)  # capture
+    torch.cuda.synchronize()
+    ee0, ee1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(1, a.steps)
+    ee0.record()
+    for _ in range(reps):
+        o2 = g.em(cfg)
+    ee1.record()
+    torch.cuda.synchronize()
+    em_ms = ee0.elapsed_time(ee1) / reps
+    msv, msh = g.em_kernel_times()
+    vb, hb, st = sweep_bytes(g, L, cfg.conv_window)
+    # bytes per iteration t: slices still iterating at t
+    tb_v, tb_h = [], []
+    for t in range(1, len(msv) + 1):
+        act = iters >= t
+        tb_v.append(float(vb[act].sum()))
+        tb_h.append(float(hb[act].sum()))
+    evals = float((iters.astype(np.float64) * st["Es"]).sum() * L)
+    hbm, peak_kind = load_peaks()
+    bw_v = sum(tb_v) / (sum(msv) / 1e3) / 1e9 if msv else 0.0
+    bw_h = sum(tb_h) / (sum(msh) / 1e3) / 1e9 if msh else 0.0
+    dom = "k_hood" if sum(msh) >= sum(msv) else "k_vertex"
+    ach = bw_h if dom == "k_hood" else bw_v
+    per_launch = (sum(tb_h) / len(tb_h)) if dom == "k_hood" else (sum(tb_v) / len(tb_v))
+
+    # ---- plain: one call per slice on a sample of slices
+    ps = min(a.plain_sample, S)
+    torch.cuda.synchronize()
+    p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ones1 = ones[:1]
+
+    def step1(k):
+        g1 = pmrf.build_graph(img_d[k], ids_d[k])
+        o1 = g1.em(cfg)
+        g1.label_image(ids_d[k], o1["labels"])
+        mu1 = o1["params"][:, :, 1].contiguous()
+        sg1 = o1["params"][:, :, 2].contiguous()
+        g1.pll(L, o1["labels"], mu1, sg1, beta)
+        g1.pll_grad(L, o1["labels"], mu1, sg1, beta, ones1)
+
+    for k in range(min(2, ps)):  # warm the per-slice path
+        step1(k)
+    torch.cuda.synchronize()
+    p0.record()
+    for k in range(ps):
+        step1(k)
+    p1.record()
+    torch.cuda.synchronize()
+    plain = ps / (p0.elapsed_time(p1) / 1e3)
+
+    # ---- end to end: host buffers in, label image out, copies inside the timed region
+    e2e = None
+    if not a.no_e2e:
+        seg_h = torch.empty(int(img_np.size), dtype=torch.uint8).pin_memory()
+        for _ in range(1):
+            img_d.copy_(img_h, non_blocking=True)
+            ids_d.copy_(ids_h, non_blocking=True)
+            _, _, sg_, _ = step(img_d, ids_d)
+            seg_h.copy_(sg_, non_blocking=True)
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        x0.record()
+        for _ in range(a.steps):
+            img_d.copy_(img_h, non_blocking=True)
+            ids_d.copy_(ids_h, non_blocking=True)
+            _, _, sg_, _ = step(img_d, ids_d)
+            seg_h.copy_(sg_, non_blocking=True)
+        x1.record()
+        torch.cuda.synchronize()
+        barrier()
+        ems = torch.tensor([x0.elapsed_time(x1) / a.steps], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
+        e2e = {"value": S * world / (float(ems) / 1e3), "unit": "slices/s",
+               "h2d_bytes_per_step": int(img_np.nbytes + ids_np.nbytes), "d2h_bytes_per_step": int(img_np.size)}
+
+    # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
+    cpu = None
+    if rank == 0 and world == 1 and not a.no_cpu:
+        cpu = cpu_baseline(sl[:a.cpu_slices], wl)
+
+    if rank == 0:
+        line = {
+            "metric": "EM slices/s (graph build + EM loop + label image + PLL adjoint per step), batched",
+            "value": round(value, 3), "unit": "slices/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": wl.name, "slices_per_gpu": S, "height": int(img_np.shape[1]),
+                       "width": int(img_np.shape[2]), "n_labels": L, "beta": beta, "max_iters": wl.max_iters,
+                       "V": st["V"], "E": st["E"], "C": st["C"], "N_el": st["N_el"],
+                       "l2_policy": "inputs larger than L2 (6.4 GB per step)", "parallelism": f"replicas{world}"},
+            "energy_evals_per_s": round(evals / (em_ms / 1e3), 1),
+            "em_ms": round(em_ms, 3), "em_slices_per_s": round(S / (em_ms / 1e3), 3),
+            "plain_slices_per_s": round(plain, 3), "plain_sample": ps,
+            "iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
+                         "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                         "peak_source": peak_kind, "bytes_per_launch": per_launch,
+                         "k_vertex_GBs": round(bw_v, 1), "k_hood_GBs": round(bw_h, 1),
+                         "k_vertex_ms": round(sum(msv), 3), "k_hood_ms": round(sum(msh), 3)},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "clocks": clk.summary(), "gen_s": round(gen_s, 1),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(slices, wl):
+    """The oracle as it stands (serial C), full per-slice pipeline."""
+    import oracle
+    cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters)
+    t0 = time.perf_counter()
+    for s in slices:
+        g = oracle.Graph.from_image(s.image, s.region_ids)
+        r = g.em(cfg)
+        g.label_image(s.region_ids, r["labels"])
+        g.pll(wl.n_labels, r["labels"], r["theta"][:, 1], r["theta"][:, 2], wl.beta)
+    dt = time.perf_counter() - t0
+    return {"value": round(len(slices) / dt, 4), "unit": "slices/s", "cores": 1, "kind": "oracle",
+            "sample": f"{len(slices)} slices of {wl.name} ({slices[0].image.shape[0]}x{slices[0].image.shape[1]}), "
+                      f"serial C oracle: graph, cliques, hoods, EM, label image, PLL"}
+
+
+def run_reference(a):
+    """The oracle, timed on the host cores on this arm's workload; each step is
+    one slice of the batch (a bounded sample)."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    base = synth.workload(a.workload)
+    n = max(1, min(a.steps + a.warmup, len(base.slices)))
+    wl = synth.workload(a.workload, n_slices=n) if a.workload in ("stack512", "grad64") else base
+    sl = synth.make_stack(wl.slices)
+    cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters)
+
+    def one(s):
+        g = oracle.Graph.from_image(s.image, s.region_ids)
+        r = g.em(cfg)
+        g.label_image(s.region_ids, r["labels"])
+        g.pll(wl.n_labels, r["labels"], r["theta"][:, 1], r["theta"][:, 2], wl.beta)
+
+    for k in range(a.warmup):
+        one(sl[k % len(sl)])
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        one(sl[(a.warmup + k) % len(sl)])
+    dt = (time.perf_counter() - t0) / a.steps
+    v = 1.0 / dt
+    print(json.dumps({
+        "impl": "reference", "metric": "EM slices/s (graph build + EM loop + label image + PLL adjoint per step), "
+                                       "batched", "value": round(v, 4), "unit": "slices/s", "n_gpus": world,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl.name, "slices_per_step": 1, "n_labels": wl.n_labels, "beta": wl.beta,
+                   "max_iters": wl.max_iters},
+        "cpu_baseline": {"value": round(v, 4), "unit": "slices/s", "cores": 1, "kind": "oracle",
+                         "sample": f"one {wl.slices[0].height}x{wl.slices[0].width} slice per step"},
+        "e2e": {"value": round(v, 4), "unit": "slices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,311 @@
+/*
+ * pmrf.h -- C ABI of the B300 (sm_103a) MRF region-labelling engine.
+ *
+ * The engine implements the optimisation path of DPP-PMRF (Lessley et al.,
+ * "DPP-PMRF: Rethinking Optimization for a Probabilistic Graphical Model Using
+ * Data-Parallel Primitives", LDAV 2018): the region graph of an
+ * oversegmented image (Section 2.1, Algorithm 2 step 1), its maximal cliques
+ * (Algorithm 2 step 2), their 1-neighbourhoods ("hoods", Section 3.1 and
+ * Section 3.2.2 "Construction of Neighborhoods"), and the EM loop of
+ * Algorithm 2 steps 6-11 (Section 3.2.2 "EM Parameter Estimation"): a MAP sweep
+ * over every (hood, vertex, label) tuple, a per-element argmin, a reduction
+ * over each vertex's replicas, re-estimation of the per-label mean, standard
+ * deviation and energy, and the hood / total convergence tests.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named d_* are DEVICE memory owned by the caller (the engine
+ *     never frees them); h_* are HOST memory owned by the caller.  All device
+ *     buffers must be on the device the graph was built on.
+ *   - Work is enqueued on the caller's stream `stream` (NULL = legacy default
+ *     stream) and is stream-ordered; an entry point returns before the device
+ *     work has finished unless its comment says it synchronises.
+ *   - The return value is a pmrf_status; PMRF_OK = 0.  On failure nothing is
+ *     written to the caller's output buffers that the caller may rely on, and
+ *     pmrf_last_error() returns a message for the calling thread.  Errors that
+ *     a kernel detects (e.g. a hood wider than a supported limit) are recorded
+ *     in a per-graph device status word and reported by pmrf_sync_status().
+ *   - No entry point throws; no entry point traps, faults or spins without a
+ *     bound on the device.
+ *   - Floating point is IEEE binary64 for intensities, energies and parameters.
+ *   - Vertex ids are global across the slices of a batch: slice s owns vertices
+ *     [vert_off[s], vert_off[s+1]) (pmrf_graph_get, PMRF_ARR_VERT_OFF).
+ *
+ * Limits: total pixels < 2^32; total regions < 2^31; total hood elements
+ * < 2^32; 1 <= n_labels <= PMRF_MAX_LABELS; a region may touch at most
+ * PMRF_MAX_DEGREE others.
+ */
+#ifndef PMRF_H
+#define PMRF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PMRF_API __attribute__((visibility("default")))
+#else
+#define PMRF_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* CUDA stream handle (identical to cudaStream_t; declared here so that this
+ * header does not need the CUDA headers). */
+typedef struct CUstream_st* pmrf_stream_t;
+
+typedef enum {
+    PMRF_OK = 0,
+    PMRF_ERR_ARG = 1,         /* invalid argument (null pointer, bad size, bad id) */
+    PMRF_ERR_CUDA = 2,        /* a CUDA runtime call failed */
+    PMRF_ERR_OOM = 3,         /* device allocation failed */
+    PMRF_ERR_NONFINITE = 4,   /* NaN or infinite intensity */
+    PMRF_ERR_TIMEOUT = 5,     /* a bounded device wait ran out */
+    PMRF_ERR_UNSUPPORTED = 6, /* input beyond a documented limit */
+    PMRF_ERR_DEVICE = 7       /* a kernel recorded an internal error */
+} pmrf_status;
+
+#define PMRF_MAX_LABELS 8
+#define PMRF_MAX_DEGREE 4096
+
+/* Opaque graph: owns its device arrays (region map, CSR adjacency, cliques,
+ * hoods, replica structures) and the EM workspace. */
+typedef struct pmrf_graph pmrf_graph;
+
+/*
+ * EM configuration.  Defaults (pmrf_config_default): n_labels 2, beta 1,
+ * max_iters 20 (Section 3.2.2: most runs converge within 20 iterations),
+ * conv_window 3 and conv_tol 1e-4 (Section 3.2.2, MAP convergence check: the
+ * change over the previous 3 iterations below 1.0e-4), sigma_min 1e-6,
+ * threshold initialisation on [init_lo, init_hi] = [0, 1].
+ *
+ * init_from_labels = 0: labels start as the threshold of the region means:
+ *   x_v = clamp(floor((y_v - init_lo) / (init_hi - init_lo) * n_labels), 0, L-1)
+ *   (the paper draws random labels and parameters, Algorithm 2 step 3; the
+ *   threshold start replaces that draw).
+ * init_from_labels = 1: d_labels holds the starting labels (resume).
+ * The starting parameters are the label-conditional moments of the starting
+ * labels; a label with no vertex starts at the centre of its threshold bin
+ * with sigma equal to the bin width.
+ */
+typedef struct {
+    int32_t n_labels;
+    int32_t max_iters;
+    int32_t conv_window;
+    int32_t init_from_labels;
+    double beta;
+    double conv_tol;
+    double sigma_min;
+    double init_lo;
+    double init_hi;
+} pmrf_config;
+
+/* Fill *cfg with the defaults listed above.  Returns PMRF_ERR_ARG on NULL. */
+PMRF_API int pmrf_config_default(pmrf_config* cfg);
+
+/* Message describing the calling thread's last failed call ("" if none).  The
+ * string stays valid until the thread's next call into the library. */
+PMRF_API const char* pmrf_last_error(void);
+
+/* Number of kernels this library has launched in this process so far (a
+ * replay of a captured EM loop counts every kernel node it runs). */
+PMRF_API int64_t pmrf_launch_count(void);
+
+/* Version string of the library build. */
+PMRF_API const char* pmrf_version(void);
+
+/*
+ * Build the region graph, maximal cliques, hoods and replica structures of a
+ * batch of slices (Algorithm 2 steps 1, 2, 4 and 5; Sections 2.1, 3.1,
+ * 3.2.1, 3.2.2 "Construction of Neighborhoods").
+ *
+ *   d_image      f64, the slices' pixels concatenated, each slice row-major
+ *                (slice s has h_heights[s] * h_widths[s] pixels).
+ *   d_region_ids i32, same layout: the oversegmentation, any non-negative id
+ *                per pixel.  Within a slice, ids are compacted in ascending
+ *                order: vertex vert_off[s] + k is the k-th smallest id present.
+ *   n_slices     >= 1;  h_heights, h_widths: host arrays of n_slices >= 0.
+ *   out          receives the new graph (destroy with pmrf_graph_destroy).
+ *
+ * Regions are vertices; two regions are adjacent when some horizontally or
+ * vertically neighbouring pixel pair carries their two ids.  The region value
+ * y_v is the mean of the region's pixels, summed in row-major order.  Cliques:
+ * every maximal clique, members ascending, cliques in lexicographic order.
+ * Hood c = clique c plus all neighbours of its members, ascending.
+ *
+ * Synchronises `stream` (array sizes are read back to size the allocations).
+ * Errors: PMRF_ERR_ARG (null pointers, negative id, n_slices < 1, sizes),
+ * PMRF_ERR_NONFINITE (NaN/inf pixel), PMRF_ERR_UNSUPPORTED (a region with more
+ * than PMRF_MAX_DEGREE neighbours, or a limit above), PMRF_ERR_OOM,
+ * PMRF_ERR_CUDA.  On error *out is left NULL and nothing is leaked.
+ */
+PMRF_API int pmrf_build_graph(const double* d_image, const int32_t* d_region_ids, int32_t n_slices,
+                     const int64_t* h_heights, const int64_t* h_widths, pmrf_stream_t stream,
+                     pmrf_graph** out);
+
+/* Free a graph and its device memory (NULL is accepted).  Synchronises the
+ * device work that used the graph. */
+PMRF_API int pmrf_graph_destroy(pmrf_graph* g);
+
+/* Totals of a graph: vertices, undirected edges, maximal cliques (= hoods),
+ * hood elements (sum of hood sizes).  Any output may be NULL. */
+PMRF_API int pmrf_graph_stats(const pmrf_graph* g, int64_t* n_slices, int64_t* V, int64_t* E, int64_t* C,
+                     int64_t* N_el);
+
+/* Arrays that pmrf_graph_get can copy out. */
+typedef enum {
+    PMRF_ARR_VERT_OFF = 0,  /* i64 [S+1]  first vertex of each slice            */
+    PMRF_ARR_HOOD_SLICE_OFF,/* i64 [S+1]  first clique/hood of each slice        */
+    PMRF_ARR_Y,             /* f64 [V]    region means                           */
+    PMRF_ARR_NPIX,          /* i32 [V]    pixels per region                      */
+    PMRF_ARR_ADJ_OFF,       /* i64 [V+1]  CSR offsets                            */
+    PMRF_ARR_ADJ,           /* i32 [2E]   neighbours, ascending per vertex       */
+    PMRF_ARR_CLQ_OFF,       /* i64 [C+1]                                          */
+    PMRF_ARR_CLQ,           /* i32 [..]   clique members                         */
+    PMRF_ARR_HOOD_OFF,      /* i64 [C+1]                                          */
+    PMRF_ARR_HOOD,          /* i32 [N_el] hood members (element order)           */
+    PMRF_ARR_REP_OFF,       /* i64 [V+1]  replicas (hoods containing v) per vertex */
+    PMRF_ARR_REP_HOOD,      /* i32 [N_el] hood of each replica, ascending per vertex */
+    PMRF_ARR_RANK_OFF,      /* i64 [S+1]  offsets of each slice's id map         */
+    PMRF_ARR_RANK,          /* i32 [..]   global vertex of each raw id, -1 absent */
+    PMRF_ARR_COUNT
+} pmrf_array;
+
+/* Number of elements of array `which`. */
+PMRF_API int pmrf_graph_len(const pmrf_graph* g, int32_t which, int64_t* n);
+
+/* Copy array `which` into dst (host memory if to_host != 0, else device
+ * memory); dst_bytes must hold the whole array.  Synchronises `stream`. */
+PMRF_API int pmrf_graph_get(const pmrf_graph* g, int32_t which, void* dst, size_t dst_bytes, int32_t to_host,
+                   pmrf_stream_t stream);
+
+/*
+ * Initial labels (Algorithm 2 step 3, threshold form, see pmrf_config):
+ * d_labels u8 [V].
+ */
+PMRF_API int pmrf_init_labels(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, pmrf_stream_t stream);
+
+/*
+ * Parameter update (Section 3.2.2, EM step 4 "Update Parameters"), per slice
+ * and label: n_l = number of vertices with label l, mu_l their mean
+ * intensity, sigma_l = max(sigma_min, population standard deviation), U_l =
+ * sum of their vertex energies (0 when d_vertex_energy is NULL).  A label with
+ * no vertex keeps mu and sigma from d_params_prev.
+ *   d_labels        u8  [V]
+ *   d_vertex_energy f64 [V] or NULL
+ *   d_params_prev   f64 [S][L][4] (n, mu, sigma, U); only mu, sigma are read
+ *   d_params_out    f64 [S][L][4]; may alias d_params_prev
+ */
+PMRF_API int pmrf_params(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* d_labels, const double* d_vertex_energy,
+                const double* d_params_prev, double* d_params_out, pmrf_stream_t stream);
+
+/*
+ * One MAP sweep (Section 3.2.2 EM step 2 "Compute Energy Function", "Compute
+ * Minimum Vertex and Label Energies", "Compute Neighborhood Energy Sums",
+ * step 3 "Update Output Labels"; Algorithm 2 steps 7-10) with labels and
+ * parameters held fixed:
+ *   E(c,v,l)  = D_l(y_v) + beta * #{u in N(v) and in hood c : x_u != l}
+ *   D_l(y)    = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l
+ *   Emin(c,v) = min_l E(c,v,l), label = smallest l attaining it
+ *   d_hood_energy[c]   = sum over v in hood c of Emin(c,v)
+ *   (d_vertex_energy[v], d_labels_out[v]) = minimum over the hoods c that
+ *       contain v of (Emin(c,v), label), energy first, then the label.
+ *   d_labels_in u8 [V]; d_params f64 [S][L][4] (mu, sigma read);
+ *   d_labels_out u8 [V] (must not alias d_labels_in); d_vertex_energy f64 [V]
+ *   or NULL; d_hood_energy f64 [C] or NULL.
+ */
+PMRF_API int pmrf_map_sweep(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* d_labels_in, const double* d_params,
+                   uint8_t* d_labels_out, double* d_vertex_energy, double* d_hood_energy, pmrf_stream_t stream);
+
+/*
+ * The EM loop (Algorithm 2 steps 3 and 6-11; Section 3.2.2 EM steps 2-5) on
+ * every slice of the batch, each slice converging on its own:
+ *   start: labels/parameters as pmrf_config describes;
+ *   iteration t = 1, 2, ...: one MAP sweep with the labels and parameters of
+ *   t-1, then the parameter update; hood sums S_c^t and their total T^t;
+ *   hood c has converged when t > W and max_{k=1..W} |S_c^t - S_c^{t-k}| <
+ *   conv_tol; a slice stops when all its hoods have converged, or t > W and
+ *   max_{k=1..W} |T^t - T^{t-k}| < conv_tol, or t = max_iters.
+ * All slices run in one persistent launch per iteration; the whole loop is
+ * replayed from a CUDA graph.
+ *   d_labels    u8  [V]        out (in as well when init_from_labels = 1)
+ *   d_params    f64 [S][L][4]  out: (n, mu, sigma, U) of the final iteration
+ *   d_iters     i32 [S]        out: iterations run per slice
+ *   d_converged i32 [S]        out: 1 when a convergence test ended the slice
+ *   d_T_hist    f64 [S][max_iters] out or NULL: T^t per slice (unset entries 0)
+ */
+PMRF_API int pmrf_em(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_params, int32_t* d_iters,
+            int32_t* d_converged, double* d_T_hist, pmrf_stream_t stream);
+
+/*
+ * Vertex pseudo-log-likelihood (not in the paper; the differentiable form of
+ * the model).  With labels x fixed and every slice's own (mu, sigma) and one
+ * shared beta, over the full graph neighbourhood of each vertex:
+ *   E_v(l) = D_l(y_v) + beta * #{u in N(v): x_u != l}
+ *   PLL_s  = sum over v in slice s of [ -E_v(x_v) - log sum_l exp(-E_v(l)) ]
+ *   d_mu, d_sigma f64 [S][L]; d_pll f64 [S] out.
+ */
+PMRF_API int pmrf_pll(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu, const double* d_sigma,
+             double beta, double* d_pll, pmrf_stream_t stream);
+
+/*
+ * Adjoint of pmrf_pll: given d_gout f64 [S] (dLoss/dPLL_s), writes
+ *   d_gmu[s][l]    = gout_s * dPLL_s/dmu_{s,l}
+ *   d_gsigma[s][l] = gout_s * dPLL_s/dsigma_{s,l}
+ *   d_gbeta[0]     = sum_s gout_s * dPLL_s/dbeta
+ * using dE_v(l)/dmu_l = (mu_l - y_v)/sigma_l^2, dE_v(l)/dsigma_l = 1/sigma_l -
+ * (y_v - mu_l)^2/sigma_l^3, dE_v(l)/dbeta = #{u in N(v): x_u != l} and the
+ * softmax p_v = softmax(-E_v).  Any gradient output may be NULL.
+ */
+PMRF_API int pmrf_pll_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu,
+                  const double* d_sigma, double beta, const double* d_gout, double* d_gmu, double* d_gsigma,
+                  double* d_gbeta, pmrf_stream_t stream);
+
+/*
+ * Labels back to pixels (closing paragraph of Section 3.2.2): d_out[p] =
+ * d_labels[vertex of the region id of pixel p].  d_region_ids is the array the
+ * graph was built from (same layout); d_out u8, one per pixel.
+ */
+PMRF_API int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const uint8_t* d_labels, uint8_t* d_out,
+                     pmrf_stream_t stream);
+
+/*
+ * Synchronise `stream` and return the graph's device status word: PMRF_OK, or
+ * the first error a kernel recorded since the last call (the word is then
+ * cleared).  *detail (may be NULL) receives a kernel-specific code.
+ */
+PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* detail);
+
+/* Tile sizes of the persistent EM launch.  0 selects the autotuned /
+ * default value.  hood_tile: hood elements per tile (multiple of 32, 256..8192);
+ * vert_tile: vertices per tile (multiple of 32, 32..4096); ctas_per_sm: 1..8. */
+typedef struct {
+    int32_t hood_tile;
+    int32_t vert_tile;
+    int32_t ctas_per_sm;
+    int32_t use_cuda_graph; /* 1 (default) replays the iteration loop from a CUDA graph */
+    int32_t profile;        /* 1: record CUDA events around the per-iteration kernels of
+                               pmrf_em (read with pmrf_em_kernel_times) */
+} pmrf_tuning;
+
+/* Read / set the graph's tuning.  Setting discards cached launch plans. */
+PMRF_API int pmrf_get_tuning(const pmrf_graph* g, pmrf_tuning* t);
+PMRF_API int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t);
+
+/* Per-iteration device times of the last pmrf_em run on this graph, when the
+ * graph's tuning has profile = 1: ms_vertex[t-1], ms_hood[t-1] (vertex pass and
+ * hood pass of iteration t) for t = 1..*n, *n = min(max_n, iterations run by
+ * the longest slice).  Synchronises `stream`.  PMRF_ERR_ARG when profiling was
+ * off for that run. */
+PMRF_API int pmrf_em_kernel_times(pmrf_graph* g, int32_t max_n, float* ms_vertex, float* ms_hood, int32_t* n,
+                                  pmrf_stream_t stream);
+
+/* Time candidate tunings on this graph with `cfg` (runs EM several times;
+ * synchronises `stream`) and keep the fastest.  *best may be NULL. */
+PMRF_API int pmrf_autotune(pmrf_graph* g, const pmrf_config* cfg, pmrf_stream_t stream, pmrf_tuning* best);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PMRF_H */

@@ -1,0 +1,867 @@
+// build.cu -- device construction of the region graph, its maximal cliques,
+// the 1-neighbourhoods ("hoods") and the replica structures the EM sweep
+// streams (Algorithm 2 steps 1, 2, 4, 5; Sections 2.1, 3.1, 3.2.1, 3.2.2
+// "Construction of Neighborhoods" and "Replicate Neighborhoods By Label").
+//
+// Everything is computed for a whole batch at once: the slices are disjoint
+// sub-graphs of one graph whose vertex ids are global (slice s owns vertices
+// [vert_off[s], vert_off[s+1])).  Integer results are deterministic and do not
+// depend on the order atomics land in: every list filled through atomics is
+// sorted afterwards.
+#include <algorithm>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace pmrf {
+
+namespace {
+
+constexpr int PIX_THREADS = 256;
+constexpr int MAX_CLIQUE = 64;  // deepest Bron-Kerbosch recursion (largest clique)
+
+struct SliceGeo {  // per-slice geometry for the pixel kernels
+    const int64_t* pix_off;
+    const int64_t* W;
+    const int64_t* rank_off;
+};
+
+__device__ __forceinline__ int32_t vertex_of(const int32_t* ids, const int32_t* rank, int64_t rank_base, int64_t p) {
+    return rank[rank_base + ids[p]];
+}
+
+// ---------------------------------------------------------------------------
+// regions
+
+__global__ void k_validate(const double* __restrict__ img, const int32_t* __restrict__ ids,
+                           const int64_t* __restrict__ pix_off, int32_t* __restrict__ maxid, DevStatus* st) {
+    const int s = blockIdx.y;
+    const int64_t b = pix_off[s], e = pix_off[s + 1];
+    int32_t m = -1;
+    for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t id = ids[p];
+        const double v = img[p];
+        if (id < 0) record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
+        if (!isfinite(v)) record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
+        m = max(m, id);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane_id() == 0 && m >= 0) atomicMax(&maxid[s], m);
+}
+
+__global__ void k_mark_present(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                               const int64_t* __restrict__ rank_off, int32_t* __restrict__ flags) {
+    const int s = blockIdx.y;
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s];
+    for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x)
+        flags[rb + ids[p]] = 1;
+}
+
+// flags -> global vertex ids (in place), -1 for absent ids
+__global__ void k_rank(int32_t* __restrict__ flags, const int64_t* __restrict__ ex, int64_t n) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = flags[i] ? (int32_t)ex[i] : -1;
+}
+
+__global__ void k_vert_off(const int64_t* __restrict__ ex, const int64_t* __restrict__ rank_off, int32_t S,
+                           int64_t* __restrict__ vert_off) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= S) vert_off[s] = ex[rank_off[s]];
+}
+
+// per-pixel vertex with warp-aggregated counting: lanes holding the same
+// vertex add once
+__global__ void k_count_pix(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                            const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
+                            int32_t* __restrict__ npix) {
+    const int s = blockIdx.y;
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        const bool ok = p < e;
+        const int32_t v = ok ? vertex_of(ids, rank, rb, p) : -1 - lane_id();
+        const unsigned grp = __match_any_sync(0xffffffffu, v);
+        if (ok && lane_id() == __ffs(grp) - 1) atomicAdd(&npix[v], __popc(grp));
+    }
+}
+
+__global__ void k_fill_pix(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                           const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
+                           const int64_t* __restrict__ vpix_off, int32_t* __restrict__ cursor,
+                           uint32_t* __restrict__ pixlist) {
+    const int s = blockIdx.y;
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        const bool ok = p < e;
+        const int32_t v = ok ? vertex_of(ids, rank, rb, p) : -1 - lane_id();
+        const unsigned grp = __match_any_sync(0xffffffffu, v);
+        const int leader = __ffs(grp) - 1;
+        int slot = 0;
+        if (ok && lane_id() == leader) slot = atomicAdd(&cursor[v], __popc(grp));
+        slot = __shfl_sync(grp, slot, leader);
+        if (ok) {
+            const int rk = __popc(grp & ((1u << lane_id()) - 1u));
+            pixlist[vpix_off[v] + slot + rk] = (uint32_t)p;
+        }
+    }
+}
+
+// y_v: the region's pixels added one by one in row-major order, then divided
+// by the count (the same sequence of IEEE operations as a serial row-major
+// accumulation).
+__global__ void k_means(const double* __restrict__ img, const uint32_t* __restrict__ pixlist,
+                        const int64_t* __restrict__ vpix_off, int64_t V, double* __restrict__ y) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    double acc = 0.0;
+    const int64_t b = vpix_off[v], e = vpix_off[v + 1];
+    for (int64_t i = b; i < e; ++i) acc += img[pixlist[i]];
+    y[v] = acc / (double)(e - b);
+}
+
+// ---------------------------------------------------------------------------
+// edges: 4-connected pixel pairs with different regions.  A pair that repeats
+// the same (left/top, right/bottom) vertex pair as its neighbour along the
+// boundary is skipped (the earlier one stands for it); the final sort+unique
+// gives the same set either way.
+
+template <bool FILL>
+__global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                             const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
+                             const int32_t* __restrict__ rank, int32_t* __restrict__ cnt,
+                             const int64_t* __restrict__ cand_off, int32_t* __restrict__ cursor,
+                             uint32_t* __restrict__ cand) {
+    const int s = blockIdx.y;
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
+    if (W <= 0) return;
+    const int64_t H = (e - b) / W;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < e - b; q += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t r = q / W, c = q - r * W;
+        const int64_t p = b + q;
+        const int32_t a = vertex_of(ids, rank, rb, p);
+        int32_t pa[2], pb[2];
+        int np = 0;
+        if (c + 1 < W) {
+            const int32_t bb = vertex_of(ids, rank, rb, p + 1);
+            if (a != bb) {
+                bool dup = (r > 0) && vertex_of(ids, rank, rb, p - W) == a && vertex_of(ids, rank, rb, p - W + 1) == bb;
+                if (!dup) { pa[np] = a; pb[np] = bb; ++np; }
+            }
+        }
+        if (r + 1 < H) {
+            const int32_t bb = vertex_of(ids, rank, rb, p + W);
+            if (a != bb) {
+                bool dup = (c > 0) && vertex_of(ids, rank, rb, p - 1) == a && vertex_of(ids, rank, rb, p + W - 1) == bb;
+                if (!dup) { pa[np] = a; pb[np] = bb; ++np; }
+            }
+        }
+        for (int k = 0; k < np; ++k) {
+            if (!FILL) {
+                atomicAdd(&cnt[pa[k]], 1);
+                atomicAdd(&cnt[pb[k]], 1);
+            } else {
+                cand[cand_off[pa[k]] + atomicAdd(&cursor[pa[k]], 1)] = (uint32_t)pb[k];
+                cand[cand_off[pb[k]] + atomicAdd(&cursor[pb[k]], 1)] = (uint32_t)pa[k];
+            }
+        }
+    }
+}
+
+__global__ void k_check_degree(const int32_t* __restrict__ deg, int64_t V, int32_t maxdeg, DevStatus* st,
+                               int32_t* __restrict__ dmax) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    if (deg[v] > maxdeg) record_error(st, PMRF_ERR_UNSUPPORTED, SITE_DEGREE, v);
+    atomicMax(dmax, deg[v]);
+}
+
+// copy the first cnt[k] values of segment k (at src_off[k]) to dst_off[k]
+__global__ void k_compact(const uint32_t* __restrict__ src, const int64_t* __restrict__ src_off,
+                          const int64_t* __restrict__ dst_off, int64_t nseg, int32_t* __restrict__ dst) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nseg) return;
+    const int64_t b = src_off[k], o = dst_off[k], n = dst_off[k + 1] - o;
+    for (int64_t i = 0; i < n; ++i) dst[o + i] = (int32_t)src[b + i];
+}
+
+// ---------------------------------------------------------------------------
+// maximal cliques: Bron-Kerbosch with pivoting, rooted at each vertex v over
+// its higher neighbours (candidates) and lower neighbours (excluded), so each
+// maximal clique is produced once, by its smallest member.  Sets are bitsets
+// over the slots of N(v) (nw 64-bit words).
+
+struct BKFrame {  // pointers into nw-word storage
+    uint64_t *P, *X, *C, *R;
+};
+
+__device__ __forceinline__ bool bs_empty(const uint64_t* a, int nw) {
+    for (int w = 0; w < nw; ++w) if (a[w]) return false;
+    return true;
+}
+
+// local adjacency among the slots of N(v): nbm[i*nw + w]
+__device__ void build_local_adj(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t v,
+                                int d, int nw, uint64_t* nbm) {
+    const int32_t* N = adj + adj_off[v];
+    for (int i = 0; i < d; ++i) {
+        for (int w = 0; w < nw; ++w) nbm[(int64_t)i * nw + w] = 0;
+        const int32_t u = N[i];
+        const int32_t* Nu = adj + adj_off[u];
+        const int64_t du = adj_off[u + 1] - adj_off[u];
+        int64_t a = 0;
+        int j = 0;
+        while (a < du && j < d) {
+            if (Nu[a] < N[j]) ++a;
+            else if (Nu[a] > N[j]) ++j;
+            else {
+                nbm[(int64_t)i * nw + (j >> 6)] |= 1ull << (j & 63);
+                ++a;
+                ++j;
+            }
+        }
+    }
+}
+
+// Runs the enumeration rooted at v.  mode 0: count (ncl, nmem); mode 1: store
+// masks (nw words each) at out_masks.  `stack` holds MAX_CLIQUE+1 frames of
+// 4*nw words; `tmp` holds 2*nw words.  Returns false when the recursion would
+// exceed MAX_CLIQUE.
+__device__ bool bk_run(int64_t v, const int32_t* N, int d, int nw, const uint64_t* nbm, uint64_t* stack,
+                       uint64_t* tmp, int mode, int64_t* ncl, int64_t* nmem, uint64_t* out_masks) {
+    // slot of the first neighbour above v
+    int hi = 0;
+    while (hi < d && N[hi] < v) ++hi;
+    auto frame = [&](int k) {
+        BKFrame f;
+        uint64_t* base = stack + (int64_t)k * 4 * nw;
+        f.P = base;
+        f.X = base + nw;
+        f.C = base + 2 * nw;
+        f.R = base + 3 * nw;
+        return f;
+    };
+    auto emit = [&](const uint64_t* R) {
+        int64_t sz = 1;
+        for (int w = 0; w < nw; ++w) sz += __popcll(R[w]);
+        if (mode == 1) {
+            for (int w = 0; w < nw; ++w) out_masks[*ncl * nw + w] = R[w];
+        }
+        *ncl += 1;
+        *nmem += sz;
+    };
+    // choose pivot in P|X maximising |P & N(u)|; C = P & ~N(pivot)
+    auto set_candidates = [&](BKFrame f) {
+        int best = -1, bu = 0;
+        for (int w = 0; w < nw; ++w) {
+            uint64_t m = f.P[w] | f.X[w];
+            while (m) {
+                int bit = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                int u = w * 64 + bit;
+                int c = 0;
+                for (int z = 0; z < nw; ++z) c += __popcll(f.P[z] & nbm[(int64_t)u * nw + z]);
+                if (c > best) { best = c; bu = u; }
+            }
+        }
+        for (int w = 0; w < nw; ++w) f.C[w] = f.P[w] & ~nbm[(int64_t)bu * nw + w];
+    };
+    BKFrame root = frame(0);
+    for (int w = 0; w < nw; ++w) { root.P[w] = 0; root.X[w] = 0; root.R[w] = 0; }
+    for (int i = 0; i < d; ++i) {
+        if (i >= hi) root.P[i >> 6] |= 1ull << (i & 63);
+        else root.X[i >> 6] |= 1ull << (i & 63);
+    }
+    if (bs_empty(root.P, nw)) {
+        if (bs_empty(root.X, nw)) emit(root.R);  // isolated vertex: clique {v}
+        return true;
+    }
+    set_candidates(root);
+    int sp = 0;
+    while (sp >= 0) {
+        BKFrame f = frame(sp);
+        int w0 = 0;
+        while (w0 < nw && f.C[w0] == 0) ++w0;
+        if (w0 == nw) { --sp; continue; }
+        const int bit = __ffsll((long long)f.C[w0]) - 1;
+        const uint64_t m = 1ull << bit;
+        const int u = w0 * 64 + bit;
+        f.C[w0] &= ~m;
+        uint64_t* Pn = tmp;
+        uint64_t* Xn = tmp + nw;
+        for (int w = 0; w < nw; ++w) {
+            Pn[w] = f.P[w] & nbm[(int64_t)u * nw + w];
+            Xn[w] = f.X[w] & nbm[(int64_t)u * nw + w];
+        }
+        const bool pe = bs_empty(Pn, nw), xe = bs_empty(Xn, nw);
+        if (pe && xe) {
+            f.R[w0] |= m;
+            emit(f.R);
+            f.R[w0] &= ~m;
+        }
+        f.P[w0] &= ~m;
+        f.X[w0] |= m;
+        if (!pe) {
+            if (sp + 1 > MAX_CLIQUE) return false;
+            BKFrame g = frame(sp + 1);
+            for (int w = 0; w < nw; ++w) { g.P[w] = Pn[w]; g.X[w] = Xn[w]; g.R[w] = f.R[w]; }
+            g.R[w0] |= m;
+            set_candidates(g);
+            ++sp;
+        }
+    }
+    return true;
+}
+
+// lexicographic order of two maximal cliques rooted at the same vertex: the
+// lower differing slot decides (see build notes: distinct maximal cliques are
+// never nested, so one list cannot be a prefix of the other)
+__device__ __forceinline__ bool clique_less(const uint64_t* a, const uint64_t* b, int nw) {
+    for (int w = 0; w < nw; ++w) {
+        uint64_t x = a[w] ^ b[w];
+        if (x) return (a[w] & (x & (~x + 1))) != 0;
+    }
+    return false;
+}
+
+// Fast path: d <= 64, one word, stack in local memory.  mode 0 counts, mode 1
+// writes sorted cliques.  General vertices (d > 64) are skipped here.
+__global__ void k_cliques_fast(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t V,
+                               int mode, int64_t* __restrict__ ncl, int64_t* __restrict__ nmem,
+                               const int64_t* __restrict__ cq_off, const int64_t* __restrict__ mem_off,
+                               uint64_t* __restrict__ maskbuf, int64_t* __restrict__ clq_off,
+                               int32_t* __restrict__ clq, DevStatus* st) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int d = (int)(adj_off[v + 1] - adj_off[v]);
+    if (d > 64) return;
+    uint64_t nbm[64];
+    uint64_t stack[(MAX_CLIQUE + 1) * 4];
+    uint64_t tmp[2];
+    const int32_t* N = adj + adj_off[v];
+    build_local_adj(adj_off, adj, v, d, 1, nbm);
+    int64_t nc = 0, nm = 0;
+    uint64_t* out = (mode == 1) ? maskbuf + cq_off[v] : nullptr;
+    if (!bk_run(v, N, d, 1, nbm, stack, tmp, mode, &nc, &nm, out)) {
+        record_error(st, PMRF_ERR_UNSUPPORTED, SITE_MCE_STACK, v);
+        nc = 0;
+        nm = 0;
+    }
+    if (mode == 0) {
+        ncl[v] = nc;
+        nmem[v] = nm;
+        return;
+    }
+    // insertion sort of the vertex's clique masks, then member lists
+    for (int64_t i = 1; i < nc; ++i) {
+        uint64_t key = out[i];
+        int64_t j = i - 1;
+        while (j >= 0 && clique_less(&key, &out[j], 1)) { out[j + 1] = out[j]; --j; }
+        out[j + 1] = key;
+    }
+    int64_t pos = mem_off[v];
+    for (int64_t i = 0; i < nc; ++i) {
+        clq_off[cq_off[v] + i] = pos;
+        clq[pos++] = (int32_t)v;
+        uint64_t m = out[i];
+        while (m) {
+            int bit = __ffsll((long long)m) - 1;
+            m &= m - 1;
+            clq[pos++] = N[bit];
+        }
+    }
+}
+
+// General path for 64 < d <= PMRF_MAX_DEGREE: one thread per listed vertex,
+// bitsets in global scratch (gscr_off gives each vertex its region).
+__global__ void k_cliques_general(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj,
+                                  const int64_t* __restrict__ glist, int64_t ng, const int64_t* __restrict__ gscr_off,
+                                  uint64_t* __restrict__ gscr, int mode, int64_t* __restrict__ ncl,
+                                  int64_t* __restrict__ nmem, const int64_t* __restrict__ cq_off,
+                                  const int64_t* __restrict__ gmask_off, uint64_t* __restrict__ gmask,
+                                  const int64_t* __restrict__ mem_off, int64_t* __restrict__ clq_off,
+                                  int32_t* __restrict__ clq, DevStatus* st) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= ng) return;
+    const int64_t v = glist[k];
+    const int d = (int)(adj_off[v + 1] - adj_off[v]);
+    const int nw = (d + 63) / 64;
+    uint64_t* nbm = gscr + gscr_off[k];
+    uint64_t* stack = nbm + (int64_t)d * nw;
+    uint64_t* tmp = stack + (int64_t)(MAX_CLIQUE + 1) * 4 * nw;
+    const int32_t* N = adj + adj_off[v];
+    build_local_adj(adj_off, adj, v, d, nw, nbm);
+    int64_t nc = 0, nm = 0;
+    uint64_t* out = (mode == 1) ? gmask + gmask_off[k] : nullptr;
+    if (!bk_run(v, N, d, nw, nbm, stack, tmp, mode, &nc, &nm, out)) {
+        record_error(st, PMRF_ERR_UNSUPPORTED, SITE_MCE_STACK, v);
+        nc = 0;
+        nm = 0;
+    }
+    if (mode == 0) {
+        ncl[v] = nc;
+        nmem[v] = nm;
+        return;
+    }
+    // insertion sort (swap nw-word records through tmp)
+    for (int64_t i = 1; i < nc; ++i) {
+        for (int w = 0; w < nw; ++w) tmp[w] = out[i * nw + w];
+        int64_t j = i - 1;
+        while (j >= 0 && clique_less(tmp, &out[j * nw], nw)) {
+            for (int w = 0; w < nw; ++w) out[(j + 1) * nw + w] = out[j * nw + w];
+            --j;
+        }
+        for (int w = 0; w < nw; ++w) out[(j + 1) * nw + w] = tmp[w];
+    }
+    int64_t pos = mem_off[v];
+    for (int64_t i = 0; i < nc; ++i) {
+        clq_off[cq_off[v] + i] = pos;
+        clq[pos++] = (int32_t)v;
+        for (int w = 0; w < nw; ++w) {
+            uint64_t m = out[i * nw + w];
+            while (m) {
+                int bit = __ffsll((long long)m) - 1;
+                m &= m - 1;
+                clq[pos++] = N[w * 64 + bit];
+            }
+        }
+    }
+}
+
+__global__ void k_list_general(const int64_t* __restrict__ adj_off, int64_t V, int64_t* __restrict__ glist,
+                               int32_t* __restrict__ ng) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    if (adj_off[v + 1] - adj_off[v] > 64) glist[atomicAdd(ng, 1)] = v;
+}
+
+// ---------------------------------------------------------------------------
+// hoods: candidates = every member plus all its neighbours; sort+unique per clique
+
+__global__ void k_hood_count(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
+                             const int64_t* __restrict__ adj_off, int64_t C, int64_t* __restrict__ cnt) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int64_t n = 0;
+    for (int64_t i = clq_off[c]; i < clq_off[c + 1]; ++i) {
+        int32_t u = clq[i];
+        n += 1 + adj_off[u + 1] - adj_off[u];
+    }
+    cnt[c] = n;
+}
+
+__global__ void k_hood_fill(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
+                            const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t C,
+                            const int64_t* __restrict__ hc_off, uint32_t* __restrict__ hc) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int64_t o = hc_off[c];
+    for (int64_t i = clq_off[c]; i < clq_off[c + 1]; ++i) {
+        int32_t u = clq[i];
+        hc[o++] = (uint32_t)u;
+        for (int64_t j = adj_off[u]; j < adj_off[u + 1]; ++j) hc[o++] = (uint32_t)adj[j];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// replica structures
+
+__global__ void k_el_hood(const int64_t* __restrict__ hood_off, int64_t C, int32_t* __restrict__ el_hood,
+                          const int32_t* __restrict__ hood, int32_t* __restrict__ rcount, int32_t* __restrict__ hmax) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    for (int64_t e = hood_off[c]; e < hood_off[c + 1]; ++e) {
+        el_hood[e] = (int32_t)c;
+        atomicAdd(&rcount[hood[e]], 1);
+    }
+    atomicMax(hmax, (int32_t)(hood_off[c + 1] - hood_off[c]));
+}
+
+__global__ void k_rep_fill(const int32_t* __restrict__ hood, int64_t N_el, const int64_t* __restrict__ rep_off,
+                           int32_t* __restrict__ cursor, uint32_t* __restrict__ rep_el) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N_el) return;
+    const int32_t v = hood[e];
+    rep_el[rep_off[v] + atomicAdd(&cursor[v], 1)] = (uint32_t)e;
+}
+
+__global__ void k_rep_pos(const uint32_t* __restrict__ rep_el, int64_t N_el, uint32_t* __restrict__ rep_pos) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < N_el) rep_pos[rep_el[q]] = (uint32_t)q;
+}
+
+__global__ void k_row_words(const int64_t* __restrict__ hood_off, int64_t C, int64_t* __restrict__ nwords) {
+    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int64_t k = hood_off[c + 1] - hood_off[c];
+    nwords[c] = k * ceil_div(k, 32);
+}
+
+__global__ void k_rep_words(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ rcount, int64_t V,
+                            int64_t* __restrict__ nwords) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    int64_t d = adj_off[v + 1] - adj_off[v];
+    int64_t nw = d > 32 ? ceil_div(d, 32) : 1;
+    nwords[v] = (int64_t)rcount[v] * nw;
+}
+
+// For element e (vertex v in hood c at position i): row bits j where hood[j]
+// is a neighbour of v, and slot bits s where N(v)[s] lies in the hood.
+__global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
+                        const int32_t* __restrict__ el_hood, const int64_t* __restrict__ adj_off,
+                        const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
+                        uint32_t* __restrict__ row, const int64_t* __restrict__ rep_off,
+                        const uint32_t* __restrict__ rep_pos, const int64_t* __restrict__ rep_woff,
+                        uint32_t* __restrict__ rep_mask, int64_t N_el) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= N_el) return;
+    const int32_t c = el_hood[e];
+    const int64_t h0 = hood_off[c];
+    const int64_t k = hood_off[c + 1] - h0;
+    const int64_t i = e - h0;
+    const int32_t v = hood[e];
+    const int32_t* N = adj + adj_off[v];
+    const int64_t d = adj_off[v + 1] - adj_off[v];
+    const int64_t nwh = ceil_div(k, 32);
+    const int64_t nwv = d > 32 ? ceil_div(d, 32) : 1;
+    uint32_t* rw = row + row_off[c] + i * nwh;
+    uint32_t* sw = rep_mask + rep_woff[v] + (int64_t)(rep_pos[e] - rep_off[v]) * nwv;
+    uint32_t rcur = 0, scur = 0;
+    int64_t rwi = 0, swi = 0;
+    int64_t a = 0, j = 0;
+    while (a < d && j < k) {
+        const int32_t x = N[a], y = hood[h0 + j];
+        if (x < y) ++a;
+        else if (x > y) ++j;
+        else {
+            if ((j >> 5) != rwi) { rw[rwi] = rcur; rcur = 0; rwi = j >> 5; }
+            rcur |= 1u << (j & 31);
+            if ((a >> 5) != swi) { sw[swi] = scur; scur = 0; swi = a >> 5; }
+            scur |= 1u << (a & 31);
+            ++a;
+            ++j;
+        }
+    }
+    rw[rwi] = rcur;
+    sw[swi] = scur;
+}
+
+// slice offsets of cliques/hoods: cliques are grouped by their smallest vertex
+__global__ void k_slice_hoods(const int64_t* __restrict__ cq_off, const int64_t* __restrict__ vert_off, int32_t S,
+                              int64_t* __restrict__ hood_slice_off) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= S) hood_slice_off[s] = cq_off[vert_off[s]];
+}
+
+struct Scratch {  // frees every temporary on scope exit
+    cudaStream_t s;
+    std::vector<void*> ptrs;
+    template <typename T>
+    int get(T** p, int64_t n) {
+        int rc = dalloc(p, n, s);
+        if (!rc) ptrs.push_back((void*)*p);
+        return rc;
+    }
+    ~Scratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, s);
+    }
+};
+
+int check_status(pmrf_graph* g, cudaStream_t s) {
+    DevStatus h;
+    PMRF_CUDA(cudaMemcpyAsync(&h, g->d_status, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    if (h.code != 0) {
+        const char* what = "kernel error";
+        switch (h.where) {
+            case SITE_BAD_ID: what = "negative region id at pixel"; break;
+            case SITE_NONFINITE: what = "non-finite intensity at pixel"; break;
+            case SITE_DEGREE: what = "region has more neighbours than PMRF_MAX_DEGREE; vertex"; break;
+            case SITE_MCE_STACK: what = "clique larger than 64 members at vertex"; break;
+            case SITE_SORT: what = "duplicate values in a distinct-value segment"; break;
+            default: break;
+        }
+        return fail(h.code, std::string(what) + " " + std::to_string(h.detail));
+    }
+    return PMRF_OK;
+}
+
+#define LAUNCH_1D(kern, n, ...)                                                                 \
+    do {                                                                                        \
+        int64_t n_ = (n);                                                                       \
+        if (n_ > 0) { kern<<<(unsigned)ceil_div(n_, 256), 256, 0, s>>>(__VA_ARGS__); ::pmrf::note_launch(1); }              \
+        PMRF_CUDA(cudaGetLastError());                                                          \
+    } while (0)
+
+}  // namespace
+
+int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, cudaStream_t s) {
+    const int32_t S = g->S;
+    Scratch tmp{s, {}};
+    PMRF_TRY(dalloc(&g->d_status, 1, s));
+    PMRF_CUDA(cudaMemsetAsync(g->d_status, 0, sizeof(DevStatus), s));
+
+    // slice geometry
+    int64_t maxpix = 0;
+    for (int i = 0; i < S; ++i) maxpix = std::max(maxpix, g->h_pix_off[i + 1] - g->h_pix_off[i]);
+    PMRF_TRY(dalloc(&g->d_pix_off, S + 1, s));
+    PMRF_TRY(dalloc(&g->d_W, S, s));
+    PMRF_CUDA(cudaMemcpyAsync(g->d_pix_off, g->h_pix_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    PMRF_CUDA(cudaMemcpyAsync(g->d_W, g->h_W.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, s));
+    const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(maxpix, PIX_THREADS * 4), 65535));
+    const dim3 pgrid(gx, (unsigned)S);
+
+    // 1. validate + per-slice largest id
+    int32_t* d_maxid = nullptr;
+    PMRF_TRY(tmp.get(&d_maxid, S));
+    PMRF_CUDA(cudaMemsetAsync(d_maxid, 0xff, sizeof(int32_t) * S, s));
+    if (g->n_pix > 0) { k_validate<<<pgrid, PIX_THREADS, 0, s>>>(d_img, d_ids, g->d_pix_off, d_maxid, g->d_status); ::pmrf::note_launch(1); }
+    PMRF_CUDA(cudaGetLastError());
+    PMRF_TRY(check_status(g, s));
+    std::vector<int32_t> hmax(S);
+    PMRF_CUDA(cudaMemcpyAsync(hmax.data(), d_maxid, sizeof(int32_t) * S, cudaMemcpyDeviceToHost, s));
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    g->h_rank_off.assign(S + 1, 0);
+    for (int i = 0; i < S; ++i) g->h_rank_off[i + 1] = g->h_rank_off[i] + (int64_t)hmax[i] + 1;
+    g->n_rank = g->h_rank_off[S];
+    PMRF_TRY(dalloc(&g->d_rank_off, S + 1, s));
+    PMRF_CUDA(cudaMemcpyAsync(g->d_rank_off, g->h_rank_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+
+    // 2. compact ids -> global vertex ids
+    PMRF_TRY(dalloc(&g->d_rank, g->n_rank, s));
+    PMRF_CUDA(cudaMemsetAsync(g->d_rank, 0, sizeof(int32_t) * std::max<int64_t>(g->n_rank, 1), s));
+    if (g->n_pix > 0) { k_mark_present<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_rank_off, g->d_rank); ::pmrf::note_launch(1); }
+    PMRF_CUDA(cudaGetLastError());
+    int64_t* d_ex = nullptr;
+    PMRF_TRY(tmp.get(&d_ex, g->n_rank + 1));
+    PMRF_TRY(exclusive_scan_i32_to_i64(g->d_rank, d_ex, g->n_rank, s));
+    LAUNCH_1D(k_rank, g->n_rank, g->d_rank, d_ex, g->n_rank);
+    PMRF_TRY(dalloc(&g->d_vert_off, S + 1, s));
+    k_vert_off<<<(unsigned)ceil_div(S + 1, 256), 256, 0, s>>>(d_ex, g->d_rank_off, S, g->d_vert_off); ::pmrf::note_launch(1);
+    PMRF_CUDA(cudaGetLastError());
+    g->h_vert_off.assign(S + 1, 0);
+    PMRF_CUDA(cudaMemcpyAsync(g->h_vert_off.data(), g->d_vert_off, sizeof(int64_t) * (S + 1), cudaMemcpyDeviceToHost, s));
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    const int64_t V = g->h_vert_off[S];
+    g->V = V;
+    if (V >= 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "more than 2^31-1 regions");
+
+    // 3. region means (row-major order per region)
+    PMRF_TRY(dalloc(&g->d_npix, V, s));
+    PMRF_TRY(dalloc(&g->d_y, V, s));
+    PMRF_CUDA(cudaMemsetAsync(g->d_npix, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    int64_t* d_vpix_off = nullptr;
+    int32_t* d_cursor = nullptr;
+    uint32_t* d_pixlist = nullptr;
+    PMRF_TRY(tmp.get(&d_vpix_off, V + 1));
+    PMRF_TRY(tmp.get(&d_cursor, V));
+    PMRF_TRY(tmp.get(&d_pixlist, g->n_pix));
+    if (g->n_pix > 0) {
+        k_count_pix<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_rank_off, g->d_rank, g->d_npix); ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaGetLastError());
+    }
+    PMRF_TRY(exclusive_scan_i32_to_i64(g->d_npix, d_vpix_off, V, s));
+    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    if (g->n_pix > 0) {
+        k_fill_pix<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_rank_off, g->d_rank, d_vpix_off, d_cursor,
+                                                 d_pixlist); ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaGetLastError());
+    }
+    PMRF_TRY(segmented_sort_u32(d_pixlist, d_vpix_off, V, g->n_pix, false, nullptr, g->d_status, s));
+    LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y);
+
+    // 4. adjacency
+    int32_t* d_cnt = nullptr;
+    int64_t* d_cand_off = nullptr;
+    PMRF_TRY(tmp.get(&d_cnt, V));
+    PMRF_TRY(tmp.get(&d_cand_off, V + 1));
+    PMRF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    if (g->n_pix > 0) {
+        k_edge_pairs<false><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank, d_cnt,
+                                                         nullptr, nullptr, nullptr); ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaGetLastError());
+    }
+    PMRF_TRY(exclusive_scan_i32_to_i64(d_cnt, d_cand_off, V, s));
+    int64_t ncand = 0;
+    PMRF_TRY(read_i64(d_cand_off + V, &ncand, s));
+    uint32_t* d_cand = nullptr;
+    PMRF_TRY(tmp.get(&d_cand, ncand));
+    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    if (g->n_pix > 0) {
+        k_edge_pairs<true><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank,
+                                                        nullptr, d_cand_off, d_cursor, d_cand); ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaGetLastError());
+    }
+    int32_t* d_deg = d_cnt;  // reused: unique counts
+    PMRF_TRY(segmented_sort_u32(d_cand, d_cand_off, V, ncand, true, d_deg, g->d_status, s));
+    int32_t* d_dmax = nullptr;
+    PMRF_TRY(tmp.get(&d_dmax, 1));
+    PMRF_CUDA(cudaMemsetAsync(d_dmax, 0, sizeof(int32_t), s));
+    LAUNCH_1D(k_check_degree, V, d_deg, V, (int32_t)PMRF_MAX_DEGREE, g->d_status, d_dmax);
+    PMRF_TRY(check_status(g, s));
+    PMRF_TRY(dalloc(&g->d_adj_off, V + 1, s));
+    PMRF_TRY(exclusive_scan_i32_to_i64(d_deg, g->d_adj_off, V, s));
+    PMRF_TRY(read_i64(g->d_adj_off + V, &g->E2, s));
+    PMRF_CUDA(cudaMemcpyAsync(&g->max_deg, d_dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PMRF_TRY(dalloc(&g->d_adj, g->E2, s));
+    LAUNCH_1D(k_compact, V, d_cand, d_cand_off, g->d_adj_off, V, g->d_adj);
+
+    // 5. maximal cliques
+    int64_t *d_ncl = nullptr, *d_nmem = nullptr, *d_cq_off = nullptr, *d_mem_off = nullptr;
+    PMRF_TRY(tmp.get(&d_ncl, V));
+    PMRF_TRY(tmp.get(&d_nmem, V));
+    PMRF_TRY(tmp.get(&d_cq_off, V + 1));
+    PMRF_TRY(tmp.get(&d_mem_off, V + 1));
+    // general-degree vertices
+    int64_t* d_glist = nullptr;
+    int32_t* d_ng = nullptr;
+    PMRF_TRY(tmp.get(&d_glist, V));
+    PMRF_TRY(tmp.get(&d_ng, 1));
+    PMRF_CUDA(cudaMemsetAsync(d_ng, 0, sizeof(int32_t), s));
+    LAUNCH_1D(k_list_general, V, g->d_adj_off, V, d_glist, d_ng);
+    int32_t ng = 0;
+    PMRF_CUDA(cudaMemcpyAsync(&ng, d_ng, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    int64_t* d_gscr_off = nullptr;
+    uint64_t* d_gscr = nullptr;
+    int64_t* d_gmask_off = nullptr;
+    uint64_t* d_gmask = nullptr;
+    std::vector<int64_t> hgl, hdeg;
+    if (ng > 0) {
+        // general vertices sorted for determinism of the scratch layout
+        hgl.resize(ng);
+        PMRF_CUDA(cudaMemcpyAsync(hgl.data(), d_glist, sizeof(int64_t) * ng, cudaMemcpyDeviceToHost, s));
+        std::vector<int64_t> hoff(V + 1);
+        PMRF_CUDA(cudaMemcpyAsync(hoff.data(), g->d_adj_off, sizeof(int64_t) * (V + 1), cudaMemcpyDeviceToHost, s));
+        PMRF_CUDA(cudaStreamSynchronize(s));
+        std::sort(hgl.begin(), hgl.end());
+        std::vector<int64_t> so(ng + 1, 0);
+        for (int k = 0; k < ng; ++k) {
+            int64_t d = hoff[hgl[k] + 1] - hoff[hgl[k]];
+            int64_t nw = ceil_div(d, 64);
+            so[k + 1] = so[k] + d * nw + (int64_t)(MAX_CLIQUE + 1) * 4 * nw + 2 * nw;
+        }
+        PMRF_CUDA(cudaMemcpyAsync(d_glist, hgl.data(), sizeof(int64_t) * ng, cudaMemcpyHostToDevice, s));
+        PMRF_TRY(tmp.get(&d_gscr_off, ng + 1));
+        PMRF_TRY(tmp.get(&d_gscr, so[ng]));
+        PMRF_CUDA(cudaMemcpyAsync(d_gscr_off, so.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
+        hdeg.swap(so);  // keep the host vector alive until the copy has run
+        PMRF_CUDA(cudaStreamSynchronize(s));
+    }
+    LAUNCH_1D(k_cliques_fast, V, g->d_adj_off, g->d_adj, V, 0, d_ncl, d_nmem, nullptr, nullptr, nullptr, nullptr,
+              nullptr, g->d_status);
+    if (ng > 0)
+        LAUNCH_1D(k_cliques_general, ng, g->d_adj_off, g->d_adj, d_glist, (int64_t)ng, d_gscr_off, d_gscr, 0, d_ncl,
+                  d_nmem, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g->d_status);
+    PMRF_TRY(check_status(g, s));
+    PMRF_TRY(exclusive_scan_i64(d_ncl, d_cq_off, V, s));
+    PMRF_TRY(exclusive_scan_i64(d_nmem, d_mem_off, V, s));
+    PMRF_TRY(read_i64(d_cq_off + V, &g->C, s));
+    PMRF_TRY(read_i64(d_mem_off + V, &g->n_clq, s));
+    const int64_t C = g->C;
+    uint64_t* d_maskbuf = nullptr;
+    PMRF_TRY(tmp.get(&d_maskbuf, C));
+    if (ng > 0) {
+        std::vector<int64_t> hncl(ng), mo(ng + 1, 0);
+        for (int k = 0; k < ng; ++k) {
+            PMRF_CUDA(cudaMemcpyAsync(&hncl[k], d_ncl + hgl[k], sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+        }
+        std::vector<int64_t> hoff2(V + 1);
+        PMRF_CUDA(cudaMemcpyAsync(hoff2.data(), g->d_adj_off, sizeof(int64_t) * (V + 1), cudaMemcpyDeviceToHost, s));
+        PMRF_CUDA(cudaStreamSynchronize(s));
+        for (int k = 0; k < ng; ++k) mo[k + 1] = mo[k] + hncl[k] * ceil_div(hoff2[hgl[k] + 1] - hoff2[hgl[k]], 64);
+        PMRF_TRY(tmp.get(&d_gmask_off, ng + 1));
+        PMRF_TRY(tmp.get(&d_gmask, mo[ng]));
+        PMRF_CUDA(cudaMemcpyAsync(d_gmask_off, mo.data(), sizeof(int64_t) * (ng + 1), cudaMemcpyHostToDevice, s));
+        PMRF_CUDA(cudaStreamSynchronize(s));
+    }
+    PMRF_TRY(dalloc(&g->d_clq_off, C + 1, s));
+    PMRF_TRY(dalloc(&g->d_clq, g->n_clq, s));
+    LAUNCH_1D(k_cliques_fast, V, g->d_adj_off, g->d_adj, V, 1, d_ncl, d_nmem, d_cq_off, d_mem_off, d_maskbuf,
+              g->d_clq_off, g->d_clq, g->d_status);
+    if (ng > 0)
+        LAUNCH_1D(k_cliques_general, ng, g->d_adj_off, g->d_adj, d_glist, (int64_t)ng, d_gscr_off, d_gscr, 1, d_ncl,
+                  d_nmem, d_cq_off, d_gmask_off, d_gmask, d_mem_off, g->d_clq_off, g->d_clq, g->d_status);
+    PMRF_CUDA(cudaMemcpyAsync(g->d_clq_off + C, &g->n_clq, sizeof(int64_t), cudaMemcpyHostToDevice, s));
+    PMRF_TRY(dalloc(&g->d_hood_slice_off, S + 1, s));
+    k_slice_hoods<<<(unsigned)ceil_div(S + 1, 256), 256, 0, s>>>(d_cq_off, g->d_vert_off, S, g->d_hood_slice_off); ::pmrf::note_launch(1);
+    PMRF_CUDA(cudaGetLastError());
+    PMRF_TRY(check_status(g, s));
+
+    // 6. hoods
+    int64_t *d_hc_cnt = nullptr, *d_hc_off = nullptr;
+    PMRF_TRY(tmp.get(&d_hc_cnt, C));
+    PMRF_TRY(tmp.get(&d_hc_off, C + 1));
+    LAUNCH_1D(k_hood_count, C, g->d_clq_off, g->d_clq, g->d_adj_off, C, d_hc_cnt);
+    PMRF_TRY(exclusive_scan_i64(d_hc_cnt, d_hc_off, C, s));
+    int64_t nhc = 0;
+    PMRF_TRY(read_i64(d_hc_off + C, &nhc, s));
+    if (nhc >= 4294967295ll) return fail(PMRF_ERR_UNSUPPORTED, "hood candidate list longer than 2^32");
+    uint32_t* d_hc = nullptr;
+    PMRF_TRY(tmp.get(&d_hc, nhc));
+    LAUNCH_1D(k_hood_fill, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, d_hc_off, d_hc);
+    int32_t* d_hsize = nullptr;
+    PMRF_TRY(tmp.get(&d_hsize, C));
+    PMRF_TRY(segmented_sort_u32(d_hc, d_hc_off, C, nhc, true, d_hsize, g->d_status, s));
+    PMRF_TRY(dalloc(&g->d_hood_off, C + 1, s));
+    PMRF_TRY(exclusive_scan_i32_to_i64(d_hsize, g->d_hood_off, C, s));
+    PMRF_TRY(read_i64(g->d_hood_off + C, &g->N_el, s));
+    const int64_t N_el = g->N_el;
+    if (N_el >= 4294967295ll) return fail(PMRF_ERR_UNSUPPORTED, "more than 2^32-1 hood elements");
+    PMRF_TRY(dalloc(&g->d_hood, N_el, s));
+    LAUNCH_1D(k_compact, C, d_hc, d_hc_off, g->d_hood_off, C, g->d_hood);
+
+    // 7. replica structures and masks
+    int32_t *d_el_hood = nullptr, *d_rcount = nullptr, *d_hmax = nullptr;
+    PMRF_TRY(tmp.get(&d_el_hood, N_el));
+    PMRF_TRY(tmp.get(&d_rcount, V));
+    PMRF_TRY(tmp.get(&d_hmax, 1));
+    PMRF_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    PMRF_CUDA(cudaMemsetAsync(d_hmax, 0, sizeof(int32_t), s));
+    LAUNCH_1D(k_el_hood, C, g->d_hood_off, C, d_el_hood, g->d_hood, d_rcount, d_hmax);
+    PMRF_TRY(dalloc(&g->d_rep_off, V + 1, s));
+    PMRF_TRY(exclusive_scan_i32_to_i64(d_rcount, g->d_rep_off, V, s));
+    PMRF_TRY(dalloc(&g->d_rep_el, N_el, s));
+    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    LAUNCH_1D(k_rep_fill, N_el, g->d_hood, N_el, g->d_rep_off, d_cursor, g->d_rep_el);
+    PMRF_TRY(segmented_sort_u32(g->d_rep_el, g->d_rep_off, V, N_el, false, nullptr, g->d_status, s));
+    uint32_t* d_rep_pos = nullptr;
+    PMRF_TRY(tmp.get(&d_rep_pos, N_el));
+    LAUNCH_1D(k_rep_pos, N_el, g->d_rep_el, N_el, d_rep_pos);
+    int64_t* d_nw = nullptr;
+    PMRF_TRY(tmp.get(&d_nw, std::max(C, V)));
+    PMRF_TRY(dalloc(&g->d_row_off, C + 1, s));
+    LAUNCH_1D(k_row_words, C, g->d_hood_off, C, d_nw);
+    PMRF_TRY(exclusive_scan_i64(d_nw, g->d_row_off, C, s));
+    PMRF_TRY(read_i64(g->d_row_off + C, &g->n_row_words, s));
+    PMRF_TRY(dalloc(&g->d_rep_woff, V + 1, s));
+    LAUNCH_1D(k_rep_words, V, g->d_adj_off, d_rcount, V, d_nw);
+    PMRF_TRY(exclusive_scan_i64(d_nw, g->d_rep_woff, V, s));
+    PMRF_TRY(read_i64(g->d_rep_woff + V, &g->n_rep_words, s));
+    PMRF_TRY(dalloc(&g->d_row, g->n_row_words, s));
+    PMRF_TRY(dalloc(&g->d_rep_mask, g->n_rep_words, s));
+    PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
+    PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
+    LAUNCH_1D(k_masks, N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off, g->d_row,
+              g->d_rep_off, d_rep_pos, g->d_rep_woff, g->d_rep_mask, N_el);
+    PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+
+    // slice offsets of hoods and elements (host copies)
+    g->h_hood_slice_off.assign(S + 1, 0);
+    PMRF_CUDA(cudaMemcpyAsync(g->h_hood_slice_off.data(), g->d_hood_slice_off, sizeof(int64_t) * (S + 1),
+                              cudaMemcpyDeviceToHost, s));
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    g->h_el_slice_off.assign(S + 1, 0);
+    for (int i = 0; i <= S; ++i) {
+        int64_t c = g->h_hood_slice_off[i];
+        PMRF_CUDA(cudaMemcpyAsync(&g->h_el_slice_off[i], g->d_hood_off + c, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    }
+    PMRF_TRY(check_status(g, s));
+    return PMRF_OK;
+}
+
+}  // namespace pmrf

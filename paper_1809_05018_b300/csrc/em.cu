@@ -1,0 +1,1141 @@
+// em.cu -- the EM loop of DPP-PMRF on the device (Algorithm 2 steps 3, 6-11;
+// Section 3.2.2 EM steps 2-5), plus the standalone MAP sweep, parameter
+// update, threshold initialisation and label image.
+//
+// One EM iteration t is three kernels over a tile table:
+//   k_vertex<L> (vertex tiles) -- for every vertex v: the neighbour-label masks
+//     from x^{t-1}; for every replica (hood c containing v) the disagreement
+//     counts m(c,v,l) = #{u in N(v) n H_c : x_u != l} by popcount of the
+//     replica's slot mask against the label masks; their minimum over the
+//     replicas M_l(v); E*_v = min_l D_l(y_v) + beta * M_l(v) and x^t_v its
+//     smallest minimising label.  Because beta >= 0 and rounding is monotone,
+//     min_c fl(D_l + beta*m(c,v,l)) = fl(D_l + beta*min_c m(c,v,l)), so this
+//     equals the lexicographic minimum of (Emin(c,v), label) over the replicas
+//     (Section 3.2.2 "Update Output Labels", reading G6) while keeping all
+//     per-replica work in integers.  Also writes D_l(y_v) for the hood pass
+//     and the per-tile moment partials of the parameter update.
+//   k_hood<L> (hood tiles) -- for every hood element (c,v): counts of each
+//     label among v's in-hood neighbours (hood-local adjacency row against the
+//     labels of the hood's members, staged in shared memory), Emin(c,v), and
+//     S_c = sum over the hood in ascending v; the hood convergence test over
+//     the last W sums (ring buffer).
+//   k_finalize<L> (one warp per slice) -- label moments -> (n, mu, sigma, U),
+//     the total T^t, the MAP and EM convergence tests, per-slice stop flags.
+// Slices that have stopped skip all work.  The loop for t = 1..max_iters is
+// captured once into a CUDA graph and replayed.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "graph.cuh"
+
+namespace pmrf {
+
+namespace {
+
+constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
+constexpr int HT_THREADS = 256;
+constexpr int HT_CAP = 4096;        // shared-memory elements per hood tile
+
+enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
+
+struct RunCfg {
+    int32_t L, W, max_iters, init_from_labels;
+    double beta, tol, sigma_min, init_lo, init_hi;
+};
+
+struct OutPtrs {  // outputs of one pmrf_em call (read by the closing kernel)
+    uint8_t* labels;
+    double* params;
+    int32_t* iters;
+    int32_t* conv;
+    double* thist;
+};
+
+struct DevGraph {
+    int32_t S;
+    int64_t V, C;
+    const int64_t* vert_off;
+    const int64_t* hood_slice_off;
+    const double* y;
+    const int64_t* adj_off;
+    const int32_t* adj;
+    const int64_t* hood_off;
+    const int32_t* hood;
+    const int64_t* row_off;
+    const uint32_t* row;
+    const int64_t* rep_woff;
+    const uint32_t* rep_mask;
+};
+
+DevGraph view(const pmrf_graph* g) {
+    DevGraph d;
+    d.S = g->S;
+    d.V = g->V;
+    d.C = g->C;
+    d.vert_off = g->d_vert_off;
+    d.hood_slice_off = g->d_hood_slice_off;
+    d.y = g->d_y;
+    d.adj_off = g->d_adj_off;
+    d.adj = g->d_adj;
+    d.hood_off = g->d_hood_off;
+    d.hood = g->d_hood;
+    d.row_off = g->d_row_off;
+    d.row = g->d_row;
+    d.rep_woff = g->d_rep_woff;
+    d.rep_mask = g->d_rep_mask;
+    return d;
+}
+
+// initial mean of an empty label: centre of its threshold bin
+__device__ __forceinline__ double bin_centre(const RunCfg& c, int l) {
+    return c.init_lo + ((double)l + 0.5) * (c.init_hi - c.init_lo) / (double)c.L;
+}
+
+__device__ __forceinline__ int threshold_label(const RunCfg& c, double y) {
+    double q = floor((y - c.init_lo) / (c.init_hi - c.init_lo) * (double)c.L);
+    return q < 0.0 ? 0 : (q > (double)(c.L - 1) ? c.L - 1 : (int)q);
+}
+
+// ---------------------------------------------------------------------------
+// vertex pass
+
+template <int L>
+__global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* __restrict__ tiles, int mode,
+                                                       const RunCfg* __restrict__ cfgp,
+                                                       const int32_t* __restrict__ active,
+                                                       const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
+                                                       const double* __restrict__ theta, double* __restrict__ Dtab,
+                                                       const double* __restrict__ E_in, double* __restrict__ E_out,
+                                                       double* __restrict__ vpart, DevStatus* st) {
+    __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
+    __shared__ double s_red[VT_THREADS / 32][4 * L];
+    const Tile tile = tiles[blockIdx.x];
+    const int s = tile.slice;
+    if (active && !active[s]) return;
+    const RunCfg c = *cfgp;
+    if (threadIdx.x < L) {
+        const int l = threadIdx.x;
+        if (mode == MODE_INIT) {
+            s_K[l] = bin_centre(c, l);
+        } else {
+            const double mu = theta[((int64_t)s * L + l) * 4 + 1];
+            const double sg = theta[((int64_t)s * L + l) * 4 + 2];
+            s_mu[l] = mu;
+            s_inv[l] = 1.0 / (2.0 * sg * sg);
+            s_lnsig[l] = log(sg);
+            s_K[l] = mu;
+        }
+    }
+    __syncthreads();
+    const int64_t v = (int64_t)tile.a0 + threadIdx.x;
+    const bool ok = v < tile.a1;
+    double acc_n[L], acc_s1[L], acc_s2[L], acc_u[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) { acc_n[l] = 0; acc_s1[l] = 0; acc_s2[l] = 0; acc_u[l] = 0; }
+    if (ok) {
+        const double y = g.y[v];
+        int lab = 0;
+        double Estar = 0.0;
+        if (mode == MODE_INIT) {
+            lab = c.init_from_labels ? (int)x_in[v] : threshold_label(c, y);
+            if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
+        } else if (mode == MODE_PARAMS) {
+            lab = (int)x_in[v];
+            if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
+            Estar = E_in ? E_in[v] : 0.0;
+        } else {
+            // data term D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l
+            double D[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const double dev = y - s_mu[l];
+                D[l] = dev * dev * s_inv[l] + s_lnsig[l];
+            }
+            if (Dtab) {
+#pragma unroll
+                for (int l = 0; l < L; ++l) Dtab[v * L + l] = D[l];
+            }
+            const int64_t a0 = g.adj_off[v];
+            const int d = (int)(g.adj_off[v + 1] - a0);
+            const int64_t r0 = g.rep_woff[v], r1 = g.rep_woff[v + 1];
+            int M[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) M[l] = 0x7fffffff;
+            if (d <= 32) {
+                // label masks over v's adjacency slots
+                uint32_t lm[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) lm[l] = 0;
+                for (int j = 0; j < d; ++j) {
+                    const int xl = x_in[g.adj[a0 + j]];
+#pragma unroll
+                    for (int l = 1; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
+                }
+                for (int64_t r = r0; r < r1; ++r) {
+                    const uint32_t m = g.rep_mask[r];
+                    const int dc = __popc(m);
+                    int rest = dc;
+#pragma unroll
+                    for (int l = 1; l < L; ++l) {
+                        const int n = __popc(m & lm[l]);
+                        rest -= n;
+                        M[l] = min(M[l], dc - n);  // neighbours in the hood whose label is not l
+                    }
+                    M[0] = min(M[0], dc - rest);
+                }
+            } else {
+                const int nw = (d + 31) >> 5;
+                for (int64_t r = r0; r < r1; r += nw) {
+                    int cnt[L];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) cnt[l] = 0;
+                    int dc = 0;
+                    for (int w = 0; w < nw; ++w) {
+                        uint32_t m = g.rep_mask[r + w];
+                        dc += __popc(m);
+                        while (m) {
+                            const int b = __ffs(m) - 1;
+                            m &= m - 1;
+                            const int xl = x_in[g.adj[a0 + w * 32 + b]];
+#pragma unroll
+                            for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+                        }
+                    }
+#pragma unroll
+                    for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - cnt[l]);
+                }
+            }
+            // every vertex lies in at least one hood, so M_l is set
+            Estar = D[0] + c.beta * (double)M[0];
+            lab = 0;
+#pragma unroll
+            for (int l = 1; l < L; ++l) {
+                const double e = D[l] + c.beta * (double)M[l];
+                if (e < Estar) { Estar = e; lab = l; }
+            }
+            x_out[v] = (uint8_t)lab;
+            if (E_out) E_out[v] = Estar;
+        }
+        if (mode == MODE_INIT) x_out[v] = (uint8_t)lab;
+        if (mode != MODE_SWEEP) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                if (lab == l) {
+                    const double dv = y - s_K[l];
+                    acc_n[l] = 1.0;
+                    acc_s1[l] = dv;
+                    acc_s2[l] = dv * dv;
+                    acc_u[l] = Estar;
+                }
+            }
+        }
+    }
+    if (mode == MODE_SWEEP) return;
+    // deterministic block reduction of the 4L partial sums
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        acc_n[l] = warp_sum(acc_n[l]);
+        acc_s1[l] = warp_sum(acc_s1[l]);
+        acc_s2[l] = warp_sum(acc_s2[l]);
+        acc_u[l] = warp_sum(acc_u[l]);
+    }
+    if (lane_id() == 0) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            s_red[warp_id()][4 * l + 0] = acc_n[l];
+            s_red[warp_id()][4 * l + 1] = acc_s1[l];
+            s_red[warp_id()][4 * l + 2] = acc_s2[l];
+            s_red[warp_id()][4 * l + 3] = acc_u[l];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 4 * L) {
+        double t = 0.0;
+        for (int w = 0; w < VT_THREADS / 32; ++w) t += s_red[w][threadIdx.x];
+        vpart[(int64_t)tile.part * 4 * L + threadIdx.x] = t;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// hood pass
+
+template <int L>
+__device__ __forceinline__ double hood_emin(const double* __restrict__ Dtab, int64_t v, const int* cnt, int dc,
+                                            double beta) {
+    double e = Dtab[v * L + 0] + beta * (double)(dc - cnt[0]);
+#pragma unroll
+    for (int l = 1; l < L; ++l) e = fmin(e, Dtab[v * L + l] + beta * (double)(dc - cnt[l]));
+    return e;
+}
+
+// convergence bookkeeping of one hood; returns 1 when the hood is unconverged
+__device__ __forceinline__ int hood_history(double S, int64_t c, int64_t C, int t, const RunCfg& cf,
+                                            double* __restrict__ hist) {
+    const int W = cf.W;
+    int unconv = 1;
+    if (t > W) {
+        double dmax = 0.0;
+        for (int k = 1; k <= W; ++k) {
+            const double prev = hist[(int64_t)((t - k) % W) * C + c];
+            if (__double_as_longlong(prev) != __double_as_longlong(S)) dmax = fmax(dmax, fabs(S - prev));
+        }
+        unconv = (dmax < cf.tol) ? 0 : 1;
+    }
+    hist[(int64_t)(t % W) * C + c] = S;
+    return unconv;
+}
+
+template <int L>
+__global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __restrict__ tiles, int mode, int t,
+                                                     const RunCfg* __restrict__ cfgp,
+                                                     const int32_t* __restrict__ active,
+                                                     const uint8_t* __restrict__ x_in,
+                                                     const double* __restrict__ Dtab, double* __restrict__ hist,
+                                                     double* __restrict__ S_out, double* __restrict__ hpart) {
+    __shared__ uint8_t s_lab[HT_CAP];
+    __shared__ uint16_t s_hs[HT_CAP];
+    __shared__ double s_emin[HT_CAP];
+    __shared__ double s_red[2][HT_THREADS / 32];
+    const Tile tile = tiles[blockIdx.x];
+    const int s = tile.slice;
+    if (active && !active[s]) return;
+    const RunCfg cf = *cfgp;
+    const double beta = cf.beta;
+    const int64_t c0 = tile.a0, c1 = tile.a1;
+    double my_S = 0.0, my_unconv = 0.0;
+    if (c1 > c0) {
+        const int64_t e0 = g.hood_off[c0];
+        const int64_t ne = g.hood_off[c1] - e0;
+        const bool fast = tile.pad != 0;  // every hood <= 32 and ne <= HT_CAP
+        if (fast) {
+            for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) s_lab[i] = x_in[g.hood[e0 + i]];
+            for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+                const int64_t b = g.hood_off[c] - e0, e = g.hood_off[c + 1] - e0;
+                for (int64_t i = b; i < e; ++i) s_hs[i] = (uint16_t)b;
+            }
+            __syncthreads();
+            const int64_t rbase = g.row_off[c0];
+            for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) {
+                const int64_t v = g.hood[e0 + i];
+                uint32_t m = g.row[rbase + i];
+                const int hs = s_hs[i];
+                const int dc = __popc(m);
+                int cnt[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) cnt[l] = 0;
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int xl = s_lab[hs + b];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+                }
+                s_emin[i] = hood_emin<L>(Dtab, v, cnt, dc, beta);
+            }
+            __syncthreads();
+            for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
+                const int64_t b = g.hood_off[c] - e0, e = g.hood_off[c + 1] - e0;
+                double S = 0.0;
+                for (int64_t i = b; i < e; ++i) S += s_emin[i];
+                if (mode == MODE_SWEEP) {
+                    if (S_out) S_out[c] = S;
+                } else {
+                    my_unconv += (double)hood_history(S, c, g.C, t, cf, hist);
+                    my_S += S;
+                }
+            }
+        } else {
+            // general tile: hood by hood, labels read from global memory
+            for (int64_t c = c0; c < c1; ++c) {
+                const int64_t hb = g.hood_off[c];
+                const int64_t k = g.hood_off[c + 1] - hb;
+                const int64_t nwh = (k + 31) >> 5;
+                const int64_t rb = g.row_off[c];
+                double S = 0.0;  // meaningful in thread 0
+                for (int64_t i0 = 0; i0 < k; i0 += blockDim.x) {
+                    const int64_t i = i0 + threadIdx.x;
+                    if (i < k) {
+                        const int64_t v = g.hood[hb + i];
+                        int cnt[L];
+#pragma unroll
+                        for (int l = 0; l < L; ++l) cnt[l] = 0;
+                        int dc = 0;
+                        for (int64_t w = 0; w < nwh; ++w) {
+                            uint32_t m = g.row[rb + i * nwh + w];
+                            dc += __popc(m);
+                            while (m) {
+                                const int b = __ffs(m) - 1;
+                                m &= m - 1;
+                                const int xl = x_in[g.hood[hb + w * 32 + b]];
+#pragma unroll
+                                for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+                            }
+                        }
+                        s_emin[threadIdx.x] = hood_emin<L>(Dtab, v, cnt, dc, beta);
+                    }
+                    __syncthreads();
+                    if (threadIdx.x == 0) {
+                        const int64_t n = min((int64_t)blockDim.x, k - i0);
+                        for (int64_t j = 0; j < n; ++j) S += s_emin[j];
+                    }
+                    __syncthreads();
+                }
+                if (threadIdx.x == 0) {
+                    if (mode == MODE_SWEEP) {
+                        if (S_out) S_out[c] = S;
+                    } else {
+                        my_unconv += (double)hood_history(S, c, g.C, t, cf, hist);
+                        my_S += S;
+                    }
+                }
+            }
+        }
+    }
+    if (mode == MODE_SWEEP) return;
+    // per-tile partials: sum of hood sums, number of unconverged hoods
+    my_S = warp_sum(my_S);
+    my_unconv = warp_sum(my_unconv);
+    if (lane_id() == 0) { s_red[0][warp_id()] = my_S; s_red[1][warp_id()] = my_unconv; }
+    __syncthreads();
+    if (threadIdx.x < 2) {
+        double acc = 0.0;
+        for (int w = 0; w < HT_THREADS / 32; ++w) acc += s_red[threadIdx.x][w];
+        hpart[(int64_t)tile.part * 2 + threadIdx.x] = acc;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// per-slice finalisation: parameters and convergence (one warp per slice)
+
+template <int L>
+__global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict__ cfgp,
+                           const int64_t* __restrict__ vt0, const int64_t* __restrict__ ht0,
+                           const double* __restrict__ vpart, const double* __restrict__ hpart,
+                           const double* __restrict__ theta_prev, double* __restrict__ theta,
+                           const int64_t* __restrict__ vert_off, int32_t* __restrict__ active,
+                           int32_t* __restrict__ iters, int32_t* __restrict__ conv, double* __restrict__ Thist,
+                           int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op) {
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    const RunCfg cf = *cfgp;
+    const bool em = (mode == MODE_EM);
+    if (em && !active[s]) return;
+    const int lane = threadIdx.x;
+    // label moments
+    double tot[4 * L];
+#pragma unroll
+    for (int k = 0; k < 4 * L; ++k) tot[k] = 0.0;
+    for (int64_t p = vt0[s] + lane; p < vt0[s + 1]; p += 32) {
+#pragma unroll
+        for (int k = 0; k < 4 * L; ++k) tot[k] += vpart[p * 4 * L + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 4 * L; ++k) tot[k] = warp_sum(tot[k]);
+    double Tsum = 0.0, unconv = 0.0;
+    if (em) {
+        for (int64_t p = ht0[s] + lane; p < ht0[s + 1]; p += 32) {
+            Tsum += hpart[p * 2 + 0];
+            unconv += hpart[p * 2 + 1];
+        }
+        Tsum = warp_sum(Tsum);
+        unconv = warp_sum(unconv);
+    }
+    if (lane != 0) return;
+    for (int l = 0; l < L; ++l) {
+        const double n = tot[4 * l + 0];
+        double* th = theta + ((int64_t)s * L + l) * 4;
+        double mu_prev, sg_prev;
+        if (mode == MODE_INIT) {
+            mu_prev = bin_centre(cf, l);
+            sg_prev = (cf.init_hi - cf.init_lo) / (double)cf.L;
+        } else {
+            mu_prev = theta_prev[((int64_t)s * L + l) * 4 + 1];
+            sg_prev = theta_prev[((int64_t)s * L + l) * 4 + 2];
+        }
+        if (n > 0.0) {
+            const double m1 = tot[4 * l + 1] / n;
+            const double var = fmax(tot[4 * l + 2] / n - m1 * m1, 0.0);
+            const double sd = sqrt(var);
+            th[0] = n;
+            th[1] = mu_prev + m1;
+            th[2] = sd > cf.sigma_min ? sd : cf.sigma_min;
+            th[3] = (mode == MODE_INIT) ? 0.0 : tot[4 * l + 3];
+        } else {
+            th[0] = 0.0;
+            th[1] = mu_prev;
+            th[2] = sg_prev;
+            th[3] = 0.0;
+        }
+    }
+    if (mode == MODE_INIT) {
+        const bool nonempty = vert_off[s + 1] > vert_off[s];
+        active[s] = nonempty ? 1 : 0;
+        iters[s] = 0;
+        conv[s] = nonempty ? 0 : 1;
+        if (!nonempty) atomicSub(nactive, 1);
+        return;
+    }
+    if (!em) return;
+    const int W = cf.W;
+    bool tot_conv = false;
+    if (t > W) {
+        double dmax = 0.0;
+        for (int k = 1; k <= W; ++k) dmax = fmax(dmax, fabs(Tsum - Thist[(int64_t)s * W + (t - k) % W]));
+        tot_conv = dmax < cf.tol;
+    }
+    Thist[(int64_t)s * W + t % W] = Tsum;
+    if (op && op->thist) op->thist[(int64_t)s * cf.max_iters + (t - 1)] = Tsum;
+    const bool all_conv = (t > W) && unconv == 0.0;
+    iters[s] = t;
+    if (all_conv || tot_conv || t >= cf.max_iters) {
+        active[s] = 0;
+        conv[s] = (all_conv || tot_conv) ? 1 : 0;
+        atomicSub(nactive, 1);
+    }
+}
+
+// copy each slice's final labels (from the buffer its last iteration wrote)
+// and the run's outputs
+__global__ void k_close(DevGraph g, int L, const uint8_t* __restrict__ x0, const uint8_t* __restrict__ x1,
+                        const int32_t* __restrict__ iters, const int32_t* __restrict__ conv,
+                        const double* __restrict__ theta, const OutPtrs* __restrict__ op) {
+    const OutPtrs o = *op;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < g.V; v += stride) {
+        const int s = (int)(upper_bound_dev<int64_t>(g.vert_off, 0, g.S + 1, v) - 1);
+        o.labels[v] = (iters[s] & 1) ? x1[v] : x0[v];
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < (int64_t)g.S * L * 4; i += stride)
+        o.params[i] = theta[i];
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < g.S; s += stride) {
+        o.iters[s] = iters[s];
+        o.conv[s] = conv[s];
+    }
+}
+
+__global__ void k_zero_T(const OutPtrs* __restrict__ op, int64_t n) {
+    double* T = op->thist;
+    if (!T) return;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        T[i] = 0.0;
+}
+
+__global__ void k_init_labels(DevGraph g, const RunCfg* __restrict__ cfgp, uint8_t* __restrict__ x) {
+    const RunCfg c = *cfgp;
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < g.V) x[v] = (uint8_t)threshold_label(c, g.y[v]);
+}
+
+__global__ void k_label_image(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                              const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
+                              const uint8_t* __restrict__ labels, uint8_t* __restrict__ out,
+                              const int64_t* __restrict__ maxid1, DevStatus* st) {
+    const int s = blockIdx.y;
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], nr = rank_off[s + 1] - rb;
+    for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t id = ids[p];
+        int32_t v = (id >= 0 && id < nr) ? rank[rb + id] : -1;
+        if (v < 0) {
+            record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
+            out[p] = 0;
+        } else {
+            out[p] = labels[v];
+        }
+    }
+    (void)maxid1;
+}
+
+// tile table: vertex tiles then hood tiles, each grouped by slice
+__global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const int64_t* __restrict__ hood_slice_off,
+                                  const int64_t* __restrict__ row_off, const int64_t* __restrict__ ht_first,
+                                  int32_t S, int64_t n_htiles, int32_t te, Tile* __restrict__ tiles,
+                                  int64_t tile_base) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_htiles) return;
+    const int s = (int)(upper_bound_dev<int64_t>(ht_first, 0, S + 1, k) - 1);
+    const int64_t j = k - ht_first[s];
+    const int64_t cs = hood_slice_off[s], ce = hood_slice_off[s + 1];
+    const int64_t es = hood_off[cs];
+    const int64_t lo = es + j * te, hi = lo + te;
+    int64_t c0 = lower_bound_dev<int64_t>(hood_off, cs, ce, lo);
+    int64_t c1 = lower_bound_dev<int64_t>(hood_off, cs, ce, hi);
+    if (j == ht_first[s + 1] - ht_first[s] - 1) c1 = ce;
+    Tile t;
+    t.kind = 0;
+    t.slice = s;
+    t.a0 = (int32_t)c0;
+    t.a1 = (int32_t)c1;
+    t.part = (int32_t)k;
+    // fast when every hood has <= 32 members and the elements fit in shared memory
+    const int64_t ne = hood_off[c1] - hood_off[c0];
+    bool fast = ne <= HT_CAP;
+    if (fast && (row_off[c1] - row_off[c0]) != ne) fast = false;  // some hood needs > 1 word per row
+    t.pad = fast ? 1 : 0;
+    tiles[tile_base + k] = t;
+}
+
+__global__ void k_make_vert_tiles(const int64_t* __restrict__ vert_off, const int64_t* __restrict__ vt_first,
+                                  int32_t S, int64_t n_vtiles, int32_t vt, Tile* __restrict__ tiles) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n_vtiles) return;
+    const int s = (int)(upper_bound_dev<int64_t>(vt_first, 0, S + 1, k) - 1);
+    const int64_t j = k - vt_first[s];
+    Tile t;
+    t.kind = 1;
+    t.slice = s;
+    t.a0 = (int32_t)(vert_off[s] + j * vt);
+    t.a1 = (int32_t)min(vert_off[s + 1], vert_off[s] + (j + 1) * vt);
+    t.part = (int32_t)k;
+    t.pad = 0;
+    tiles[k] = t;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+
+int free_plans(pmrf_graph* g) {
+    for (auto& kv : g->plans) {
+        Plan& p = kv.second;
+        if (p.d_tiles) cudaFree(p.d_tiles);
+        if (p.d_slice_ntiles) cudaFree(p.d_slice_ntiles);
+        if (p.d_slice_vt0) cudaFree(p.d_slice_vt0);
+        if (p.d_slice_ht0) cudaFree(p.d_slice_ht0);
+    }
+    g->plans.clear();
+    for (auto& e : g->execs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    g->execs.clear();
+    return PMRF_OK;
+}
+
+int free_em(pmrf_graph* g) {
+    EMWork& w = g->em;
+    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_Dtab,
+                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    g->em = EMWork();
+    for (auto& e : g->execs)
+        if (e.exec) cudaGraphExecDestroy(e.exec);
+    g->execs.clear();
+    return PMRF_OK;
+}
+
+namespace {
+
+int effective_tiles(const pmrf_graph* g, int* te, int* vt) {
+    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : 2048;
+    *vt = VT_THREADS;  // one vertex per thread
+    (void)g;
+    return PMRF_OK;
+}
+
+int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
+    int te, vt;
+    effective_tiles(g, &te, &vt);
+    auto key = std::make_pair(te, vt);
+    auto it = g->plans.find(key);
+    if (it != g->plans.end()) {
+        *out = &it->second;
+        return PMRF_OK;
+    }
+    const int32_t S = g->S;
+    Plan p;
+    p.hood_tile = te;
+    p.vert_tile = vt;
+    std::vector<int64_t> vfirst(S + 1, 0), hfirst(S + 1, 0);
+    for (int i = 0; i < S; ++i) {
+        const int64_t nv = g->h_vert_off[i + 1] - g->h_vert_off[i];
+        const int64_t ne = g->h_el_slice_off[i + 1] - g->h_el_slice_off[i];
+        const int64_t nh = g->h_hood_slice_off[i + 1] - g->h_hood_slice_off[i];
+        vfirst[i + 1] = vfirst[i] + ceil_div(nv, vt);
+        hfirst[i + 1] = hfirst[i] + (nh > 0 ? std::max<int64_t>(1, ceil_div(ne, te)) : 0);
+    }
+    p.n_vtiles = vfirst[S];
+    p.n_htiles = hfirst[S];
+    p.n_tiles = p.n_vtiles + p.n_htiles;
+    if (p.n_tiles >= 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "too many tiles");
+    cudaError_t e;
+    e = cudaMalloc(&p.d_tiles, sizeof(Tile) * std::max<int64_t>(p.n_tiles, 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_slice_vt0, sizeof(int64_t) * (S + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&p.d_slice_ht0, sizeof(int64_t) * (S + 1));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (p.d_tiles) cudaFree(p.d_tiles);
+        if (p.d_slice_vt0) cudaFree(p.d_slice_vt0);
+        if (p.d_slice_ht0) cudaFree(p.d_slice_ht0);
+        return fail(PMRF_ERR_OOM, "tile table allocation failed");
+    }
+    PMRF_CUDA(cudaMemcpyAsync(p.d_slice_vt0, vfirst.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    PMRF_CUDA(cudaMemcpyAsync(p.d_slice_ht0, hfirst.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    if (p.n_vtiles > 0) {
+        k_make_vert_tiles<<<(unsigned)ceil_div(p.n_vtiles, 256), 256, 0, s>>>(g->d_vert_off, p.d_slice_vt0, S,
+                                                                              p.n_vtiles, vt, p.d_tiles);
+        ::pmrf::note_launch(1);
+    }
+    if (p.n_htiles > 0) {
+        k_make_hood_tiles<<<(unsigned)ceil_div(p.n_htiles, 256), 256, 0, s>>>(
+            g->d_hood_off, g->d_hood_slice_off, g->d_row_off, p.d_slice_ht0, S, p.n_htiles, te, p.d_tiles,
+            p.n_vtiles);
+        ::pmrf::note_launch(1);
+    }
+    PMRF_CUDA(cudaGetLastError());
+    PMRF_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    auto res = g->plans.emplace(key, p);
+    *out = &res.first->second;
+    return PMRF_OK;
+}
+
+int check_cfg(const pmrf_graph* g, const pmrf_config* cfg) {
+    if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
+    if (!cfg) return fail(PMRF_ERR_ARG, "config is NULL");
+    if (cfg->n_labels < 1 || cfg->n_labels > PMRF_MAX_LABELS) return fail(PMRF_ERR_ARG, "n_labels must be in [1, 8]");
+    if (!(cfg->beta >= 0.0) || !std::isfinite(cfg->beta)) return fail(PMRF_ERR_ARG, "beta must be finite and >= 0");
+    if (!(cfg->sigma_min > 0.0)) return fail(PMRF_ERR_ARG, "sigma_min must be > 0");
+    if (!(cfg->init_hi > cfg->init_lo)) return fail(PMRF_ERR_ARG, "init_hi must exceed init_lo");
+    if (cfg->conv_window < 1) return fail(PMRF_ERR_ARG, "conv_window must be >= 1");
+    if (cfg->max_iters < 1) return fail(PMRF_ERR_ARG, "max_iters must be >= 1");
+    return PMRF_OK;
+}
+
+RunCfg to_run(const pmrf_config* c) {
+    RunCfg r;
+    r.L = c->n_labels;
+    r.W = c->conv_window;
+    r.max_iters = c->max_iters;
+    r.init_from_labels = c->init_from_labels;
+    r.beta = c->beta;
+    r.tol = c->conv_tol;
+    r.sigma_min = c->sigma_min;
+    r.init_lo = c->init_lo;
+    r.init_hi = c->init_hi;
+    return r;
+}
+
+template <typename T>
+int walloc(T** p, int64_t n) {
+    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)std::max<int64_t>(n, 1) + 16);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return fail(PMRF_ERR_OOM, "EM workspace allocation failed");
+    }
+    return PMRF_OK;
+}
+
+// (re)allocate the EM workspace for (L, W, max_iters, plan)
+int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p) {
+    EMWork& w = g->em;
+    if (w.d_x[0] && w.L == rc.L && w.W == rc.W && w.max_iters >= rc.max_iters && w.n_vtiles == p.n_vtiles &&
+        w.n_htiles == p.n_htiles)
+        return PMRF_OK;
+    free_em(g);
+    const int64_t S = g->S;
+    w.L = rc.L;
+    w.W = rc.W;
+    w.max_iters = rc.max_iters;
+    w.n_vtiles = p.n_vtiles;
+    w.n_htiles = p.n_htiles;
+    int rc2 = PMRF_OK;
+    if (!rc2) rc2 = walloc(&w.d_x[0], g->V);
+    if (!rc2) rc2 = walloc(&w.d_x[1], g->V);
+    if (!rc2) rc2 = walloc(&w.d_hist, (int64_t)rc.W * g->C);
+    if (!rc2) rc2 = walloc(&w.d_vpart, p.n_vtiles * 4 * rc.L);
+    if (!rc2) rc2 = walloc(&w.d_hpart, p.n_htiles * 2);
+    if (!rc2) rc2 = walloc(&w.d_theta, S * rc.L * 4);
+    if (!rc2) rc2 = walloc(&w.d_Thist, S * rc.W);
+    if (!rc2) rc2 = walloc(&w.d_active, S);
+    if (!rc2) rc2 = walloc(&w.d_iters, S);
+    if (!rc2) rc2 = walloc(&w.d_conv, S);
+    if (!rc2) rc2 = walloc(&w.d_nactive, 1);
+    if (!rc2) rc2 = walloc(&w.d_Dtab, g->V * rc.L);  // data-term table D[v][l]
+    if (!rc2) rc2 = walloc((char**)&w.d_cfg, (int64_t)(sizeof(RunCfg) + sizeof(OutPtrs)));
+    if (rc2) free_em(g);
+    return rc2;
+}
+
+struct Launch {
+    pmrf_graph* g;
+    Plan* p;
+    DevGraph dg;
+    const Tile* vt;
+    const Tile* ht;
+    RunCfg* d_cfg;
+    OutPtrs* d_out;
+};
+
+}  // namespace
+
+// Internal entry points used by api.cu ------------------------------------------------
+
+namespace {
+
+__global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
+__global__ void k_set_active_all(int32_t* a, int32_t S) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < S) a[i] = 1;
+}
+
+template <int L>
+int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_from_labels) {
+    EMWork& w = g->em;
+    Launch z{g, p, view(g), p->d_tiles + 0, p->d_tiles + p->n_vtiles, (RunCfg*)w.d_cfg,
+             (OutPtrs*)((char*)w.d_cfg + sizeof(RunCfg))};
+    double* Dtab = w.d_Dtab;
+    const int32_t S = g->S;
+    // every slice active for INIT; nactive = S
+    k_set_active_all<<<(unsigned)ceil_div(S, 256), 256, 0, s>>>(w.d_active, S); ::pmrf::note_launch(1);
+    k_set_i32<<<1, 1, 0, s>>>(w.d_nactive, S); ::pmrf::note_launch(1);
+    (void)init_from_labels;  // the INIT pass reads buffer 1, which em_run fills from the caller
+    k_zero_T<<<64, 256, 0, s>>>(z.d_out, (int64_t)S * rc.max_iters); ::pmrf::note_launch(1);
+    if (p->n_vtiles > 0) {
+        k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
+                                                                w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
+                                                                nullptr, w.d_vpart, g->d_status);
+        ::pmrf::note_launch(1);
+    }
+    k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
+                                            w.d_hpart, nullptr, w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
+                                            w.d_conv, w.d_Thist, w.d_nactive, z.d_out); ::pmrf::note_launch(1);
+    const bool prof = g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
+    for (int t = 1; t <= rc.max_iters; ++t) {
+        const uint8_t* xin = w.d_x[(t - 1) & 1];
+        uint8_t* xout = w.d_x[t & 1];
+        if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
+        if (p->n_vtiles > 0) {
+            k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
+                                                                    xout, w.d_theta, Dtab, nullptr, nullptr,
+                                                                    w.d_vpart, g->d_status);
+            ::pmrf::note_launch(1);
+        }
+        if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
+        if (p->n_htiles > 0) {
+            k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(z.dg, z.ht, MODE_EM, t, z.d_cfg, w.d_active, xin,
+                                                                  Dtab, w.d_hist, nullptr, w.d_hpart);
+            ::pmrf::note_launch(1);
+        }
+        if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
+        k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
+                                                w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off, w.d_active,
+                                                w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out); ::pmrf::note_launch(1);
+    }
+    k_close<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->V, 256), 4096)), 256, 0, s>>>(
+        z.dg, rc.L, w.d_x[0], w.d_x[1], w.d_iters, w.d_conv, w.d_theta, z.d_out); ::pmrf::note_launch(1);
+    return PMRF_OK;
+}
+
+}  // namespace
+
+// labels and T history destinations are passed through OutPtrs so a cached
+// CUDA graph can serve any caller buffers
+int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_params, int32_t* d_iters,
+           int32_t* d_conv, double* d_T_hist, cudaStream_t s) {
+    PMRF_TRY(check_cfg(g, cfg));
+    if (!d_labels || !d_params || !d_iters || !d_conv) return fail(PMRF_ERR_ARG, "null output pointer");
+    const RunCfg rc = to_run(cfg);
+    Plan* p = nullptr;
+    PMRF_TRY(get_plan(g, s, &p));
+    PMRF_TRY(ensure_work(g, rc, *p));
+    EMWork& w = g->em;
+    // constants and output pointers for this call
+    struct {
+        RunCfg r;
+        OutPtrs o;
+    } h;
+    h.r = rc;
+    h.o.labels = d_labels;
+    h.o.params = d_params;
+    h.o.iters = d_iters;
+    h.o.conv = d_conv;
+    h.o.thist = d_T_hist;
+    PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &h, sizeof(h), cudaMemcpyHostToDevice, s));
+    if (cfg->init_from_labels) {
+        // the INIT pass reads x_in = buffer 1
+        PMRF_CUDA(cudaMemcpyAsync(w.d_x[1], d_labels, (size_t)g->V, cudaMemcpyDeviceToDevice, s));
+    }
+    if (g->tuning.profile) {
+        while ((int)g->prof_ev.size() < 3 * rc.max_iters) {
+            cudaEvent_t ev;
+            PMRF_CUDA(cudaEventCreate(&ev));
+            g->prof_ev.push_back(ev);
+        }
+        g->prof_iters = rc.max_iters;
+    } else {
+        g->prof_iters = 0;
+    }
+    const bool use_graph = g->tuning.use_cuda_graph != 0;
+    if (!use_graph) {
+        int r = PMRF_OK;
+        switch (rc.L) {
+            case 1: r = em_body<1>(g, p, rc, s, cfg->init_from_labels); break;
+            case 2: r = em_body<2>(g, p, rc, s, cfg->init_from_labels); break;
+            case 3: r = em_body<3>(g, p, rc, s, cfg->init_from_labels); break;
+            case 4: r = em_body<4>(g, p, rc, s, cfg->init_from_labels); break;
+            case 5: r = em_body<5>(g, p, rc, s, cfg->init_from_labels); break;
+            case 6: r = em_body<6>(g, p, rc, s, cfg->init_from_labels); break;
+            case 7: r = em_body<7>(g, p, rc, s, cfg->init_from_labels); break;
+            default: r = em_body<8>(g, p, rc, s, cfg->init_from_labels); break;
+        }
+        PMRF_CUDA(cudaGetLastError());
+        return r;
+    }
+    // find or capture the CUDA graph of the whole loop
+    pmrf_graph::CachedExec* ce = nullptr;
+    for (auto& e : g->execs)
+        if (e.L == rc.L && e.W == rc.W && e.max_iters == rc.max_iters && e.hood_tile == p->hood_tile &&
+            e.vert_tile == p->vert_tile)
+            ce = &e;
+    if (!ce) {
+        cudaStream_t cs;
+        PMRF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int r = PMRF_OK;
+        int64_t nodes = 0;
+        set_capture_counter(&nodes);
+        if (e == cudaSuccess) {
+            switch (rc.L) {
+                case 1: r = em_body<1>(g, p, rc, cs, cfg->init_from_labels); break;
+                case 2: r = em_body<2>(g, p, rc, cs, cfg->init_from_labels); break;
+                case 3: r = em_body<3>(g, p, rc, cs, cfg->init_from_labels); break;
+                case 4: r = em_body<4>(g, p, rc, cs, cfg->init_from_labels); break;
+                case 5: r = em_body<5>(g, p, rc, cs, cfg->init_from_labels); break;
+                case 6: r = em_body<6>(g, p, rc, cs, cfg->init_from_labels); break;
+                case 7: r = em_body<7>(g, p, rc, cs, cfg->init_from_labels); break;
+                default: r = em_body<8>(g, p, rc, cs, cfg->init_from_labels); break;
+            }
+            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        set_capture_counter(nullptr);
+        cudaGraphExec_t exec = nullptr;
+        if (e == cudaSuccess && r == PMRF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (r != PMRF_OK) return r;
+        if (e != cudaSuccess) return cuda_fail(e, "EM graph capture");
+        pmrf_graph::CachedExec c;
+        c.exec = exec;
+        c.L = rc.L;
+        c.W = rc.W;
+        c.max_iters = rc.max_iters;
+        c.hood_tile = p->hood_tile;
+        c.vert_tile = p->vert_tile;
+        c.nkernels = nodes;
+        g->execs.push_back(c);
+        ce = &g->execs.back();
+    }
+    PMRF_CUDA(cudaGraphLaunch(ce->exec, s));
+    note_launch(ce->nkernels);
+    return PMRF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// standalone sweep / params / init / label image
+
+namespace {
+
+template <int L>
+int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, const uint8_t* xin, const double* theta,
+               uint8_t* xout, double* Eout, double* Sout, double* Dtab) {
+    DevGraph dg = view(g);
+    const Tile* vt = p->d_tiles;
+    const Tile* ht = p->d_tiles + p->n_vtiles;
+    if (p->n_vtiles > 0) {
+        k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
+                                                                Dtab, nullptr, Eout, nullptr, g->d_status);
+        ::pmrf::note_launch(1);
+    }
+    if (p->n_htiles > 0) {
+        k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(dg, ht, MODE_SWEEP, 1, d_cfg, nullptr, xin, Dtab,
+                                                              nullptr, Sout, nullptr);
+        ::pmrf::note_launch(1);
+    }
+    PMRF_CUDA(cudaGetLastError());
+    return PMRF_OK;
+}
+
+template <int L>
+int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, const uint8_t* x, const double* Ein,
+                const double* prev, double* out) {
+    DevGraph dg = view(g);
+    EMWork& w = g->em;
+    if (p->n_vtiles > 0) {
+        k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
+                                                                nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
+                                                                g->d_status);
+        ::pmrf::note_launch(1);
+    }
+    k_finalize<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
+                                               w.d_vpart, w.d_hpart, prev, out, g->d_vert_off, nullptr, nullptr,
+                                               nullptr, nullptr, nullptr, nullptr); ::pmrf::note_launch(1);
+    PMRF_CUDA(cudaGetLastError());
+    return PMRF_OK;
+}
+
+int prepare(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, Plan** p, RunCfg* rc) {
+    PMRF_TRY(check_cfg(g, cfg));
+    *rc = to_run(cfg);
+    PMRF_TRY(get_plan(g, s, p));
+    PMRF_TRY(ensure_work(g, *rc, **p));
+    return PMRF_OK;
+}
+
+#define DISPATCH_L(Lv, call)                     \
+    switch (Lv) {                                \
+        case 1: { constexpr int L = 1; call; } break; \
+        case 2: { constexpr int L = 2; call; } break; \
+        case 3: { constexpr int L = 3; call; } break; \
+        case 4: { constexpr int L = 4; call; } break; \
+        case 5: { constexpr int L = 5; call; } break; \
+        case 6: { constexpr int L = 6; call; } break; \
+        case 7: { constexpr int L = 7; call; } break; \
+        default: { constexpr int L = 8; call; } break; \
+    }
+
+}  // namespace
+
+int sweep_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* xin, const double* theta, uint8_t* xout,
+              double* Eout, double* Sout, cudaStream_t s) {
+    if (!xin || !theta || !xout) return fail(PMRF_ERR_ARG, "null pointer");
+    if (xin == xout) return fail(PMRF_ERR_ARG, "d_labels_out must not alias d_labels_in");
+    Plan* p;
+    RunCfg rc;
+    PMRF_TRY(prepare(g, cfg, s, &p, &rc));
+    EMWork& w = g->em;
+    PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
+    int r = PMRF_OK;
+    DISPATCH_L(rc.L, r = sweep_body<L>(g, p, s, (const RunCfg*)w.d_cfg, xin, theta, xout, Eout, Sout,
+                                       w.d_Dtab));
+    PMRF_CUDA(cudaStreamSynchronize(s));  // the host RunCfg copy is a stack value
+    return r;
+}
+
+int params_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* x, const double* Ein, const double* prev,
+               double* out, cudaStream_t s) {
+    if (!x || !prev || !out) return fail(PMRF_ERR_ARG, "null pointer");
+    Plan* p;
+    RunCfg rc;
+    PMRF_TRY(prepare(g, cfg, s, &p, &rc));
+    EMWork& w = g->em;
+    PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
+    // out may alias prev: the finaliser reads prev's mu/sigma of a label just
+    // before writing that label, in the same thread, so aliasing is safe
+    int r = PMRF_OK;
+    DISPATCH_L(rc.L, r = params_body<L>(g, p, s, (const RunCfg*)w.d_cfg, x, Ein, prev, out));
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    return r;
+}
+
+int init_labels_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* x, cudaStream_t s) {
+    if (!x) return fail(PMRF_ERR_ARG, "null pointer");
+    Plan* p;
+    RunCfg rc;
+    PMRF_TRY(prepare(g, cfg, s, &p, &rc));
+    EMWork& w = g->em;
+    PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
+    if (g->V > 0) { k_init_labels<<<(unsigned)ceil_div(g->V, 256), 256, 0, s>>>(view(g), (const RunCfg*)w.d_cfg, x); ::pmrf::note_launch(1); }
+    PMRF_CUDA(cudaGetLastError());
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    return PMRF_OK;
+}
+
+int label_image_run(pmrf_graph* g, const int32_t* ids, const uint8_t* labels, uint8_t* out, cudaStream_t s) {
+    if (!ids || !labels || !out) return fail(PMRF_ERR_ARG, "null pointer");
+    int64_t maxpix = 0;
+    for (int i = 0; i < g->S; ++i) maxpix = std::max(maxpix, g->h_pix_off[i + 1] - g->h_pix_off[i]);
+    if (maxpix == 0) return PMRF_OK;
+    const dim3 grid((unsigned)std::min<int64_t>(ceil_div(maxpix, 1024), 65535), (unsigned)g->S);
+    k_label_image<<<grid, 256, 0, s>>>(ids, g->d_pix_off, g->d_rank_off, g->d_rank, labels, out, nullptr,
+                                       g->d_status); ::pmrf::note_launch(1);
+    PMRF_CUDA(cudaGetLastError());
+    return PMRF_OK;
+}
+
+}  // namespace pmrf
+
+// ---------------------------------------------------------------------------
+// autotuner: time the EM loop on this graph for a few hood-tile sizes and keep
+// the fastest (the vertex tile is one vertex per thread of a 256-thread CTA)
+
+namespace pmrf {
+
+int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tuning* best) {
+    PMRF_TRY(check_cfg(g, cfg));
+    const int64_t S = g->S, L = cfg->n_labels;
+    uint8_t* lab = nullptr;
+    double* par = nullptr;
+    int32_t *it = nullptr, *cv = nullptr;
+    int rc = walloc(&lab, g->V);
+    if (!rc) rc = walloc(&par, S * L * 4);
+    if (!rc) rc = walloc(&it, S);
+    if (!rc) rc = walloc(&cv, S);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
+        rc = fail(PMRF_ERR_CUDA, "event creation failed");
+    pmrf_tuning keep = g->tuning, win = g->tuning;
+    float best_ms = 1e30f;
+    const int cands[] = {1024, 2048, 4096};
+    for (int c = 0; c < 3 && !rc; ++c) {
+        pmrf_tuning t = keep;
+        t.hood_tile = cands[c];
+        cudaStreamSynchronize(s);
+        free_plans(g);
+        free_em(g);
+        g->tuning = t;
+        rc = em_run(g, cfg, lab, par, it, cv, nullptr, s);  // warm-up (plan, workspace, graph capture)
+        if (rc) break;
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && !rc; ++r) rc = em_run(g, cfg, lab, par, it, cv, nullptr, s);
+        cudaEventRecord(e1, s);
+        if (cudaEventSynchronize(e1) != cudaSuccess) rc = fail(PMRF_ERR_CUDA, "autotune timing failed");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (!rc && ms < best_ms) {
+            best_ms = ms;
+            win = t;
+        }
+    }
+    cudaStreamSynchronize(s);
+    free_plans(g);
+    free_em(g);
+    g->tuning = rc ? keep : win;
+    if (best && !rc) *best = win;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (lab) cudaFree(lab);
+    if (par) cudaFree(par);
+    if (it) cudaFree(it);
+    if (cv) cudaFree(cv);
+    return rc;
+}
+
+}  // namespace pmrf
+
+namespace pmrf {
+
+int em_kernel_times(pmrf_graph* g, int32_t max_n, float* msv, float* msh, int32_t* n, cudaStream_t s) {
+    if (!g || !n) return fail(PMRF_ERR_ARG, "null argument");
+    if (g->prof_iters <= 0) return fail(PMRF_ERR_ARG, "the last pmrf_em run was not profiled");
+    PMRF_CUDA(cudaStreamSynchronize(s));
+    std::vector<int32_t> it(g->S);
+    PMRF_CUDA(cudaMemcpy(it.data(), g->em.d_iters, sizeof(int32_t) * g->S, cudaMemcpyDeviceToHost));
+    int32_t tmax = 0;
+    for (int32_t v : it) tmax = std::max(tmax, v);
+    tmax = std::min(tmax, (int32_t)g->prof_iters);
+    tmax = std::min(tmax, max_n);
+    for (int t = 0; t < tmax; ++t) {
+        float a = 0.f, b = 0.f;
+        PMRF_CUDA(cudaEventElapsedTime(&a, g->prof_ev[3 * t + 0], g->prof_ev[3 * t + 1]));
+        PMRF_CUDA(cudaEventElapsedTime(&b, g->prof_ev[3 * t + 1], g->prof_ev[3 * t + 2]));
+        if (msv) msv[t] = a;
+        if (msh) msh[t] = b;
+    }
+    *n = tmax;
+    return PMRF_OK;
+}
+
+}  // namespace pmrf

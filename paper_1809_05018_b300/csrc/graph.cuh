@@ -1,0 +1,105 @@
+// graph.cuh -- device-resident region graph of a batch of slices, its maximal
+// cliques, hoods, replica structures and the EM workspace.
+#pragma once
+
+#include <map>
+#include <vector>
+
+#include "common.cuh"
+
+namespace pmrf {
+
+// Per-tile descriptor of the persistent EM launch.  kind 0 = hood tile (hoods
+// [a0, a1)), kind 1 = vertex tile (vertices [a0, a1)).  `part` indexes the
+// tile's partial-sum record inside its kind.
+struct Tile {
+    int32_t kind;
+    int32_t slice;
+    int32_t a0, a1;
+    int32_t part;
+    int32_t pad;
+};
+
+struct Plan {  // tile table for one tuning
+    int32_t hood_tile = 0, vert_tile = 0;
+    int64_t n_tiles = 0, n_htiles = 0, n_vtiles = 0;
+    Tile* d_tiles = nullptr;
+    int32_t* d_slice_ntiles = nullptr;   // [S] tiles per slice (both kinds)
+    int64_t* d_slice_vt0 = nullptr;      // [S+1] first vertex-tile partial of each slice
+    int64_t* d_slice_ht0 = nullptr;      // [S+1] first hood-tile partial of each slice
+};
+
+struct EMWork {  // EM scratch, sized for (L, W, plan)
+    int L = 0, W = 0, max_iters = 0;
+    int64_t n_htiles = 0, n_vtiles = 0;
+    uint8_t* d_x[2] = {nullptr, nullptr};  // label double buffer
+    double* d_hist = nullptr;      // [W][C] hood-sum ring
+    double* d_vpart = nullptr;     // [n_vtiles][L][4]
+    double* d_hpart = nullptr;     // [n_htiles][2] (T partial, unconverged count)
+    double* d_theta = nullptr;     // [S][L][4] current parameters
+    double* d_Thist = nullptr;     // [S][W] ring of totals
+    double* d_Dtab = nullptr;      // [V][L] data term of the current iteration
+    int32_t* d_active = nullptr;   // [S] slice still iterating
+    int32_t* d_iters = nullptr;    // [S]
+    int32_t* d_conv = nullptr;     // [S]
+    int32_t* d_nactive = nullptr;  // [1]
+    void* d_cfg = nullptr;         // device copy of the run's constants
+};
+
+struct pmrf_graph_impl;
+
+}  // namespace pmrf
+
+struct pmrf_graph {
+    int device = 0;
+    int32_t S = 0;
+    int64_t V = 0, E2 = 0, C = 0, n_clq = 0, N_el = 0, n_rank = 0, n_pix = 0;
+    int64_t n_row_words = 0, n_rep_words = 0;
+    int32_t max_deg = 0, max_hood = 0;
+
+    std::vector<int64_t> h_H, h_W, h_pix_off, h_vert_off, h_hood_slice_off, h_el_slice_off, h_rank_off;
+
+    int64_t* d_pix_off = nullptr;        // [S+1]
+    int64_t* d_vert_off = nullptr;       // [S+1]
+    int64_t* d_hood_slice_off = nullptr; // [S+1]
+    int64_t* d_rank_off = nullptr;       // [S+1]
+    int64_t* d_W = nullptr;              // [S] widths
+    int32_t* d_rank = nullptr;           // [n_rank]
+    double* d_y = nullptr;               // [V]
+    int32_t* d_npix = nullptr;           // [V]
+    int64_t* d_adj_off = nullptr;        // [V+1]
+    int32_t* d_adj = nullptr;            // [E2]
+    int64_t* d_clq_off = nullptr;        // [C+1]
+    int32_t* d_clq = nullptr;            // [n_clq]
+    int64_t* d_hood_off = nullptr;       // [C+1]
+    int32_t* d_hood = nullptr;           // [N_el]
+    int64_t* d_row_off = nullptr;        // [C+1] word offsets of hood-local adjacency rows
+    uint32_t* d_row = nullptr;           // [n_row_words]
+    int64_t* d_rep_off = nullptr;        // [V+1]
+    uint32_t* d_rep_el = nullptr;        // [N_el] element of each replica (ascending per vertex)
+    int64_t* d_rep_woff = nullptr;       // [V+1] word offsets of replica slot masks
+    uint32_t* d_rep_mask = nullptr;      // [n_rep_words]
+    pmrf::DevStatus* d_status = nullptr;
+
+    pmrf_tuning tuning{0, 0, 0, 1, 0};
+    // profiling events of the EM loop: per iteration t (1-based), index 3*(t-1):
+    // before the vertex pass, after it, after the hood pass
+    std::vector<cudaEvent_t> prof_ev;
+    int prof_iters = 0;  // iterations covered by the last profiled run
+    std::map<std::pair<int, int>, pmrf::Plan> plans;
+    pmrf::EMWork em;
+    // cached CUDA graphs of the EM loop, keyed by (L, W, max_iters, tile sizes);
+    // outputs and run constants are read from device memory, so one capture
+    // serves every call with the same key
+    struct CachedExec {
+        cudaGraphExec_t exec = nullptr;
+        int L = 0, W = 0, max_iters = 0, hood_tile = 0, vert_tile = 0;
+        int64_t nkernels = 0;  // kernel nodes per replay
+    };
+    std::vector<CachedExec> execs;
+};
+
+namespace pmrf {
+int free_plans(pmrf_graph* g);
+int free_em(pmrf_graph* g);
+}  // namespace pmrf

@@ -1,0 +1,201 @@
+// pll.cu -- vertex pseudo-log-likelihood of the MRF model and its hand-written
+// FP64 adjoint (the differentiable form of the model; not part of the paper's
+// algorithm).  With labels x fixed, per vertex over the full neighbourhood:
+//   E_v(l) = D_l(y_v) + beta * m_v(l),  m_v(l) = #{u in N(v): x_u != l}
+//   PLL_s  = sum_{v in s} [ -E_v(x_v) - logsumexp_l(-E_v(l)) ]
+//   dPLL/dmu_l    = sum_v (p_v(l) - [x_v = l]) (mu_l - y_v) / sigma_l^2
+//   dPLL/dsigma_l = sum_v (p_v(l) - [x_v = l]) (1/sigma_l - (y_v - mu_l)^2 / sigma_l^3)
+//   dPLL/dbeta    = sum_v ( sum_l p_v(l) m_v(l) - m_v(x_v) ),   p_v = softmax(-E_v)
+// One pass over the vertices writes per-block partial sums (deterministic
+// order); a per-slice pass adds them in block order.
+#include <algorithm>
+
+#include "graph.cuh"
+
+namespace pmrf {
+
+namespace {
+
+constexpr int PLL_THREADS = 256;
+
+template <int L>
+__global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* __restrict__ vert_off,
+                                                     const double* __restrict__ y, const int64_t* __restrict__ adj_off,
+                                                     const int32_t* __restrict__ adj, const uint8_t* __restrict__ x,
+                                                     const double* __restrict__ mu, const double* __restrict__ sigma,
+                                                     double beta, int64_t nchunk, double* __restrict__ part) {
+    constexpr int NP = 2 * L + 2;  // pll, gmu[L], gsigma[L], gbeta
+    __shared__ double s_mu[L], s_sg[L], s_inv[L], s_ln[L];
+    __shared__ double s_red[PLL_THREADS / 32][NP];
+    const int s = blockIdx.y;
+    const int64_t vb = vert_off[s], ve = vert_off[s + 1];
+    const int64_t v = vb + (int64_t)blockIdx.x * PLL_THREADS + threadIdx.x;
+    if (vb + (int64_t)blockIdx.x * PLL_THREADS >= ve) return;  // whole block beyond this slice
+    if (threadIdx.x < L) {
+        const double m = mu[(int64_t)s * L + threadIdx.x], sg = sigma[(int64_t)s * L + threadIdx.x];
+        s_mu[threadIdx.x] = m;
+        s_sg[threadIdx.x] = sg;
+        s_inv[threadIdx.x] = 1.0 / (2.0 * sg * sg);
+        s_ln[threadIdx.x] = log(sg);
+    }
+    __syncthreads();
+    double acc[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = 0.0;
+    if (v < ve) {
+        const double yv = y[v];
+        const int xv = x[v];
+        int cnt[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) cnt[l] = 0;
+        const int64_t a0 = adj_off[v], a1 = adj_off[v + 1];
+        for (int64_t j = a0; j < a1; ++j) {
+            const int xl = x[adj[j]];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+        }
+        const int d = (int)(a1 - a0);
+        double E[L], emin = 0.0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const double dev = yv - s_mu[l];
+            E[l] = dev * dev * s_inv[l] + s_ln[l] + beta * (double)(d - cnt[l]);
+            emin = (l == 0 || E[l] < emin) ? E[l] : emin;
+        }
+        double z = 0.0, p[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            p[l] = exp(-(E[l] - emin));
+            z += p[l];
+        }
+        const double inv_z = 1.0 / z;
+        double Ex = 0.0, mx = 0.0, eb = 0.0;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            p[l] *= inv_z;
+            if (l == xv) { Ex = E[l]; mx = (double)(d - cnt[l]); }
+            eb += p[l] * (double)(d - cnt[l]);
+        }
+        acc[0] = -Ex - (-emin + log(z));
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const double w = p[l] - (l == xv ? 1.0 : 0.0);
+            const double sg = s_sg[l];
+            const double dev = yv - s_mu[l];
+            acc[1 + l] = w * (s_mu[l] - yv) / (sg * sg);
+            acc[1 + L + l] = w * (1.0 / sg - dev * dev / (sg * sg * sg));
+        }
+        acc[1 + 2 * L] = eb - mx;
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane_id() == 0) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) s_red[warp_id()][k] = acc[k];
+    }
+    __syncthreads();
+    if (threadIdx.x < NP) {
+        double t = 0.0;
+        for (int w = 0; w < PLL_THREADS / 32; ++w) t += s_red[w][threadIdx.x];
+        part[((int64_t)s * nchunk + blockIdx.x) * NP + threadIdx.x] = t;
+    }
+}
+
+template <int L>
+__global__ void k_pll_final(int32_t S, const int64_t* __restrict__ vert_off, int64_t nchunk,
+                            const double* __restrict__ part, double* __restrict__ pll, const double* __restrict__ gout,
+                            double* __restrict__ gmu, double* __restrict__ gsigma, double* __restrict__ gbeta_s) {
+    constexpr int NP = 2 * L + 2;
+    const int s = blockIdx.x;
+    const int64_t nb = ceil_div(vert_off[s + 1] - vert_off[s], PLL_THREADS);
+    double tot[NP];
+#pragma unroll
+    for (int k = 0; k < NP; ++k) tot[k] = 0.0;
+    for (int64_t b = threadIdx.x; b < nb; b += 32) {
+#pragma unroll
+        for (int k = 0; k < NP; ++k) tot[k] += part[((int64_t)s * nchunk + b) * NP + k];
+    }
+#pragma unroll
+    for (int k = 0; k < NP; ++k) tot[k] = warp_sum(tot[k]);
+    if (threadIdx.x != 0) return;
+    if (pll) pll[s] = tot[0];
+    if (gout) {
+        const double go = gout[s];
+        for (int l = 0; l < L; ++l) {
+            if (gmu) gmu[(int64_t)s * L + l] = go * tot[1 + l];
+            if (gsigma) gsigma[(int64_t)s * L + l] = go * tot[1 + L + l];
+        }
+        gbeta_s[s] = go * tot[1 + 2 * L];
+    }
+}
+
+__global__ void k_sum_slices(int32_t S, const double* __restrict__ in, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double t = 0.0;
+    for (int s = 0; s < S; ++s) t += in[s];
+    *out = t;
+}
+
+__global__ void k_rep_hood(const uint32_t* __restrict__ rep_el, const int64_t* __restrict__ hood_off, int64_t C,
+                           int64_t N_el, int32_t* __restrict__ dst) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= N_el) return;
+    dst[q] = (int32_t)(upper_bound_dev<int64_t>(hood_off, 0, C + 1, (int64_t)rep_el[q]) - 1);
+}
+
+template <int L>
+int pll_body(pmrf_graph* g, const uint8_t* x, const double* mu, const double* sigma, double beta, double* pll,
+             const double* gout, double* gmu, double* gsigma, double* gbeta, cudaStream_t s) {
+    constexpr int NP = 2 * L + 2;
+    int64_t maxv = 0;
+    for (int i = 0; i < g->S; ++i) maxv = std::max(maxv, g->h_vert_off[i + 1] - g->h_vert_off[i]);
+    const int64_t nchunk = std::max<int64_t>(1, ceil_div(maxv, PLL_THREADS));
+    if (nchunk > 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "slice too large");
+    double* part = nullptr;
+    double* gb = nullptr;
+    PMRF_TRY(dalloc(&part, (int64_t)g->S * nchunk * NP, s));
+    int rc = dalloc(&gb, g->S, s);
+    if (rc) { dfree(part, s); return rc; }
+    if (maxv > 0) {
+        const dim3 grid((unsigned)nchunk, (unsigned)g->S);
+        k_pll<L><<<grid, PLL_THREADS, 0, s>>>(g->S, g->d_vert_off, g->d_y, g->d_adj_off, g->d_adj, x, mu, sigma, beta,
+                                             nchunk, part); ::pmrf::note_launch(1);
+    }
+    k_pll_final<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, g->d_vert_off, nchunk, part, pll, gout, gmu, gsigma, gb); ::pmrf::note_launch(1);
+    if (gout && gbeta) { k_sum_slices<<<1, 32, 0, s>>>(g->S, gb, gbeta); ::pmrf::note_launch(1); }
+    cudaError_t e = cudaGetLastError();
+    dfree(part, s);
+    dfree(gb, s);
+    if (e != cudaSuccess) return cuda_fail(e, "pll kernels");
+    return PMRF_OK;
+}
+
+}  // namespace
+
+int pll_run(pmrf_graph* g, int32_t L, const uint8_t* x, const double* mu, const double* sigma, double beta,
+            double* pll, const double* gout, double* gmu, double* gsigma, double* gbeta, cudaStream_t s) {
+    if (L < 1 || L > PMRF_MAX_LABELS) return fail(PMRF_ERR_ARG, "n_labels must be in [1, 8]");
+    if (!x || !mu || !sigma) return fail(PMRF_ERR_ARG, "null pointer");
+    if (!std::isfinite(beta)) return fail(PMRF_ERR_ARG, "beta must be finite");
+    switch (L) {
+        case 1: return pll_body<1>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        case 2: return pll_body<2>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        case 3: return pll_body<3>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        case 4: return pll_body<4>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        case 5: return pll_body<5>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        case 6: return pll_body<6>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        case 7: return pll_body<7>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+        default: return pll_body<8>(g, x, mu, sigma, beta, pll, gout, gmu, gsigma, gbeta, s);
+    }
+}
+
+int export_rep_hood(pmrf_graph* g, int32_t* dst, cudaStream_t s) {
+    if (g->N_el > 0) {
+        k_rep_hood<<<(unsigned)ceil_div(g->N_el, 256), 256, 0, s>>>(g->d_rep_el, g->d_hood_off, g->C, g->N_el, dst);
+        ::pmrf::note_launch(1);
+    }
+    PMRF_CUDA(cudaGetLastError());
+    return PMRF_OK;
+}
+
+}  // namespace pmrf

@@ -1,0 +1,266 @@
+// segsort.cu -- segmented ascending sort (optionally with de-duplication) of
+// u32 values laid out as CSR segments.  Used by the graph build for
+//   * the pixel list of each region (row-major order => the region sum is
+//     added in row-major order),
+//   * the candidate neighbour list of each region (sort + unique => CSR
+//     adjacency),
+//   * the replica list of each vertex (hoods containing it, ascending).
+//
+// Small segments (<= SMALL_MAX values) are grouped into shared-memory tiles
+// and sorted with a bitonic network on 64-bit keys (segment, value).  Larger
+// segments are sorted through a bitmap over their value range (one CTA per
+// segment), which requires distinct values unless `unique` is requested.
+#include <vector>
+
+#include "common.cuh"
+
+namespace pmrf {
+
+namespace {
+
+constexpr int SORT_THREADS = 512;
+constexpr int SORT_CAP = 4096;       // keys per shared-memory group
+constexpr int SMALL_MAX = 2048;      // longest segment sorted in shared memory
+constexpr int WINDOW = 2048;         // segment starts per tile window
+
+__device__ __forceinline__ void bitonic_sort_smem(uint64_t* key, int npow2) {
+    for (int k = 2; k <= npow2; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+                int ixj = i ^ j;
+                if (ixj > i) {
+                    uint64_t a = key[i], b = key[ixj];
+                    bool up = ((i & k) == 0);
+                    if ((a > b) == up) {
+                        key[i] = b;
+                        key[ixj] = a;
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// One CTA per window of segment starts.  Segments of the window are processed
+// in consecutive groups whose total length fits SORT_CAP; big segments are
+// skipped (handled by the bitmap kernels).
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_small(uint32_t* __restrict__ vals,
+                                                             const int64_t* __restrict__ off, int64_t nseg,
+                                                             int64_t n, int unique, int32_t* __restrict__ ucount) {
+    __shared__ uint64_t key[SORT_CAP];
+    __shared__ int64_t s_k0, s_k1;
+    const int64_t wlo = (int64_t)blockIdx.x * WINDOW, whi = wlo + WINDOW;
+    if (threadIdx.x == 0) {
+        // segments with start in [wlo, whi); empty segments at the same start
+        // are included by the first window whose range holds that start.
+        s_k0 = lower_bound_dev<int64_t>(off, 0, nseg, wlo);
+        s_k1 = lower_bound_dev<int64_t>(off, 0, nseg, whi);
+        if (whi > n) s_k1 = nseg;  // last window takes the trailing (empty) segments
+    }
+    __syncthreads();
+    const int64_t k0 = s_k0, k1 = s_k1;
+    int64_t k = k0;
+    while (k < k1) {
+        // form a group [k, kg) of small segments with total length <= SORT_CAP
+        int64_t kg = k;
+        const int64_t gstart = off[k];
+        while (kg < k1) {
+            int64_t len = off[kg + 1] - off[kg];
+            if (len > SMALL_MAX) break;
+            if (off[kg + 1] - gstart > SORT_CAP) break;
+            ++kg;
+        }
+        if (kg == k) {  // a big segment: leave it to the bitmap path
+            k = k + 1;
+            continue;
+        }
+        const int64_t gend = off[kg];
+        const int cnt = (int)(gend - gstart);
+        int npow2 = 1;
+        while (npow2 < cnt) npow2 <<= 1;
+        // load keys: (segment index within group << 32) | value
+        for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
+            if (i < cnt) {
+                int64_t p = gstart + i;
+                // segment of position p: linear scan from k is fine for tiny groups,
+                // but groups can hold many segments: binary search in off[k..kg)
+                int64_t sidx = upper_bound_dev<int64_t>(off, k, kg, p) - 1 - k;
+                key[i] = ((uint64_t)sidx << 32) | (uint64_t)vals[p];
+            } else {
+                key[i] = ~0ull;
+            }
+        }
+        __syncthreads();
+        if (cnt > 1) bitonic_sort_smem(key, npow2);
+        if (!unique) {
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) vals[gstart + i] = (uint32_t)(key[i] & 0xffffffffu);
+        } else {
+            for (int64_t sg = k + threadIdx.x; sg < kg; sg += blockDim.x) {
+                const int b = (int)(off[sg] - gstart), e = (int)(off[sg + 1] - gstart);
+                int u = 0;
+                uint32_t prev = 0;
+                for (int i = b; i < e; ++i) {
+                    uint32_t v = (uint32_t)(key[i] & 0xffffffffu);
+                    if (i == b || v != prev) vals[off[sg] + u++] = v;
+                    prev = v;
+                }
+                ucount[sg] = u;
+            }
+        }
+        __syncthreads();
+        k = kg;
+    }
+}
+
+__global__ void k_mark_big(const int64_t* __restrict__ off, int64_t nseg, int64_t* __restrict__ list,
+                           int32_t* __restrict__ nlist) {
+    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nseg) return;
+    if (off[k + 1] - off[k] > SMALL_MAX) {
+        int slot = atomicAdd(nlist, 1);
+        list[slot] = k;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_big_minmax(const uint32_t* __restrict__ vals,
+                                                     const int64_t* __restrict__ off,
+                                                     const int64_t* __restrict__ list,
+                                                     uint32_t* __restrict__ mn, uint32_t* __restrict__ mx) {
+    __shared__ uint32_t smin[32], smax[32];
+    const int64_t k = list[blockIdx.x];
+    uint32_t a = 0xffffffffu, b = 0;
+    for (int64_t i = off[k] + threadIdx.x; i < off[k + 1]; i += blockDim.x) {
+        uint32_t v = vals[i];
+        a = min(a, v);
+        b = max(b, v);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a = min(a, __shfl_xor_sync(0xffffffffu, a, o));
+        b = max(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if (lane_id() == 0) { smin[warp_id()] = a; smax[warp_id()] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) { a = min(a, smin[w]); b = max(b, smax[w]); }
+        a = min(a, smin[0]);
+        b = max(b, smax[0]);
+        mn[blockIdx.x] = a;
+        mx[blockIdx.x] = b;
+    }
+}
+
+__global__ void __launch_bounds__(1024) k_big_bitmap(uint32_t* __restrict__ vals, const int64_t* __restrict__ off,
+                                                     const int64_t* __restrict__ list,
+                                                     const uint32_t* __restrict__ mn,
+                                                     const int64_t* __restrict__ bm_off, uint32_t* __restrict__ bm,
+                                                     int unique, int32_t* __restrict__ ucount, DevStatus* st) {
+    __shared__ int64_t wsum[32];
+    __shared__ int64_t carry;
+    const int64_t k = list[blockIdx.x];
+    const int64_t b = off[k], e = off[k + 1];
+    const uint32_t lo = mn[blockIdx.x];
+    uint32_t* bits = bm + bm_off[blockIdx.x];
+    const int64_t nwords = bm_off[blockIdx.x + 1] - bm_off[blockIdx.x];
+    for (int64_t i = b + threadIdx.x; i < e; i += blockDim.x) {
+        uint32_t d = vals[i] - lo;
+        atomicOr(&bits[d >> 5], 1u << (d & 31));
+    }
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    // ordered emission: block scan of popcounts over chunks of blockDim words
+    for (int64_t w0 = 0; w0 < nwords; w0 += blockDim.x) {
+        int64_t w = w0 + threadIdx.x;
+        uint32_t word = (w < nwords) ? bits[w] : 0u;
+        int c = __popc(word);
+        int x = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, x, o);
+            if (lane_id() >= o) x += y;
+        }
+        if (lane_id() == 31) wsum[warp_id()] = x;
+        __syncthreads();
+        if (warp_id() == 0) {
+            int64_t t = (lane_id() < (int)(blockDim.x >> 5)) ? wsum[lane_id()] : 0;
+            for (int o = 1; o < 32; o <<= 1) {
+                int64_t y = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane_id() >= o) t += y;
+            }
+            if (lane_id() < (int)(blockDim.x >> 5)) wsum[lane_id()] = t;
+        }
+        __syncthreads();
+        int64_t pos = carry + (x - c) + (warp_id() > 0 ? wsum[warp_id() - 1] : 0);
+        while (word) {
+            int bit = __ffs(word) - 1;
+            word &= word - 1;
+            vals[b + pos++] = lo + (uint32_t)(w * 32 + bit);
+        }
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = pos;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        if (unique) ucount[k] = (int32_t)carry;
+        else if (carry != e - b) record_error(st, PMRF_ERR_DEVICE, SITE_SORT, k);
+    }
+}
+
+}  // namespace
+
+int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, bool unique, int32_t* ucount,
+                       DevStatus* st, cudaStream_t s) {
+    if (nseg <= 0) return PMRF_OK;
+    const int64_t nwin = ceil_div(n > 0 ? n : 1, WINDOW);
+    k_sort_small<<<(unsigned)nwin, SORT_THREADS, 0, s>>>(vals, off, nseg, n, unique ? 1 : 0, ucount); ::pmrf::note_launch(1);
+    PMRF_CUDA(cudaGetLastError());
+
+    // big segments
+    int64_t* list = nullptr;
+    int32_t* nlist = nullptr;
+    PMRF_TRY(dalloc(&nlist, 1, s));
+    int rc = dalloc(&list, nseg, s);
+    if (rc) { dfree(nlist, s); return rc; }
+    cudaMemsetAsync(nlist, 0, sizeof(int32_t), s);
+    k_mark_big<<<(unsigned)ceil_div(nseg, 256), 256, 0, s>>>(off, nseg, list, nlist); ::pmrf::note_launch(1);
+    int32_t nbig = 0;
+    cudaMemcpyAsync(&nbig, nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) { dfree(nlist, s); dfree(list, s); return cuda_fail(e, "segmented sort"); }
+    if (nbig > 0) {
+        uint32_t *mn = nullptr, *mx = nullptr;
+        int64_t* bmo = nullptr;
+        uint32_t* bm = nullptr;
+        rc = dalloc(&mn, nbig, s);
+        if (!rc) rc = dalloc(&mx, nbig, s);
+        if (!rc) rc = dalloc(&bmo, nbig + 1, s);
+        if (!rc) {
+            k_big_minmax<<<nbig, 1024, 0, s>>>(vals, off, list, mn, mx); ::pmrf::note_launch(1);
+            std::vector<uint32_t> hmn(nbig), hmx(nbig);
+            cudaMemcpyAsync(hmn.data(), mn, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, s);
+            cudaMemcpyAsync(hmx.data(), mx, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, s);
+            e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) rc = cuda_fail(e, "segmented sort (big)");
+            if (!rc) {
+                std::vector<int64_t> hbo(nbig + 1, 0);
+                for (int i = 0; i < nbig; ++i) hbo[i + 1] = hbo[i] + ceil_div((int64_t)hmx[i] - hmn[i] + 1, 32);
+                cudaMemcpyAsync(bmo, hbo.data(), sizeof(int64_t) * (nbig + 1), cudaMemcpyHostToDevice, s);
+                rc = dalloc(&bm, hbo[nbig], s);
+                if (!rc) {
+                    cudaMemsetAsync(bm, 0, sizeof(uint32_t) * hbo[nbig], s);
+                    k_big_bitmap<<<nbig, 1024, 0, s>>>(vals, off, list, mn, bmo, bm, unique ? 1 : 0, ucount, st); ::pmrf::note_launch(1);
+                    e = cudaGetLastError();
+                    if (e != cudaSuccess) rc = cuda_fail(e, "k_big_bitmap");
+                    // the host vector hbo must outlive the async copy
+                    cudaError_t e2 = cudaStreamSynchronize(s);
+                    if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "segmented sort (big)");
+                }
+            }
+        }
+        dfree(mn, s); dfree(mx, s); dfree(bmo, s); dfree(bm, s);
+    }
+    dfree(nlist, s);
+    dfree(list, s);
+    return rc;
+}
+
+}  // namespace pmrf

@@ -1,0 +1,323 @@
+"""CUDA path vs the CPU oracle, element by element, on seeded synthetic
+inputs.  Integer results (graph, cliques, hoods, replica lists) must be
+identical; labels equal wherever the oracle's label-energy gap exceeds 1e-9
+relative; parameters within 1e-10 relative; hood energies within 1e-12."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from pmrf_testutil import (ENERGY_RTOL, PARAM_RTOL, assert_graph_equal, assert_labels_match, dev_tensors,
+                           gpu_arrays, label_gap, rel_close, rep_lists_from_oracle, slice_view, small_specs)
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+def _pmrf():
+    import paper_1809_05018_b300 as pmrf
+    return pmrf
+
+
+# --------------------------------------------------------------------------
+# graph construction
+
+@pytest.mark.parametrize("which", ["slice256", "batch"])
+def test_graph_matches_oracle(which):
+    pmrf = _pmrf()
+    if which == "slice256":
+        specs = synth.workload("slice256").slices
+    else:
+        specs = small_specs(6, seed0=40)
+    sl = synth.make_stack(specs)
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    arrs = gpu_arrays(g)
+    assert g.S == len(sl)
+    for s, one in enumerate(sl):
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        gv = slice_view(arrs, s)
+        assert_graph_equal(og, gv)
+        # replica lists: hoods containing each vertex, ascending
+        ro = arrs["REP_OFF"]
+        v0 = gv["v0"]
+        want = rep_lists_from_oracle(og)
+        for v in range(og.V):
+            got = (arrs["REP_HOOD"][ro[v0 + v]:ro[v0 + v + 1]] - gv["c0"]).tolist()
+            assert got == want[v], (s, v)
+        # raw id map: compact ids ascending, -1 where absent
+        rk = arrs["RANK"][arrs["RANK_OFF"][s]:arrs["RANK_OFF"][s + 1]]
+        assert np.array_equal(np.where(og.rank >= 0, og.rank + v0, -1), rk)
+
+
+def test_graph_edge_cases():
+    pmrf = _pmrf()
+    # one region; a region touching 40 others (general paths, degree > 32 and
+    # hoods wider than 32); non-contiguous ids; an empty slice in the batch
+    one = (np.full((8, 9), 0.25), np.full((8, 9), 5, np.int32))
+    H, W = 24, 140
+    ids = np.zeros((H, W), np.int32)
+    ids[1:, :] = 1000  # background: 3220 pixels, 70 neighbours, hoods of 71+ members
+    for k in range(70):  # a strip of small cells along the top touching the background
+        ids[0, 2 * k:2 * k + 2] = 7 + 3 * k
+    img = np.random.default_rng(0).random((H, W))
+    big = (img, ids)
+    empty = (np.zeros((0, 5)), np.zeros((0, 5), np.int32))
+    cases = [one, big, empty]
+    imgs = [torch.from_numpy(a).cuda() for a, _ in cases]
+    idt = [torch.from_numpy(b).cuda() for _, b in cases]
+    g = pmrf.build_graph(imgs, idt)
+    arrs = gpu_arrays(g)
+    for s, (a, b) in enumerate(cases):
+        og = oracle.Graph.from_image(a, b)
+        assert_graph_equal(og, slice_view(arrs, s))
+    # the EM loop through the general (wide) paths
+    for L in (2, 3):
+        cfg = pmrf.EMConfig(n_labels=L, beta=0.3, max_iters=15)
+        out = g.em(cfg)
+        g.sync_status()
+        _em_compare([type("S", (), dict(image=a, region_ids=b)) for a, b in cases],
+                    oracle.EMConfig(n_labels=L, beta=0.3, max_iters=15), cfg, g, out)
+
+
+def test_build_rejects_bad_input():
+    pmrf = _pmrf()
+    img = torch.rand(8, 8, dtype=torch.float64, device="cuda")
+    ids = torch.zeros(8, 8, dtype=torch.int32, device="cuda")
+    ids[3, 3] = -2
+    with pytest.raises(pmrf.PmrfError) as e:
+        pmrf.build_graph(img, ids)
+    assert e.value.code == 1
+    ids[3, 3] = 0
+    img[2, 2] = float("nan")
+    with pytest.raises(pmrf.PmrfError) as e:
+        pmrf.build_graph(img, ids)
+    assert e.value.code == 4
+    # the context is still usable afterwards
+    img[2, 2] = 0.5
+    g = pmrf.build_graph(img, ids)
+    assert g.V == 1
+
+
+# --------------------------------------------------------------------------
+# one MAP sweep, lock-step (same labels and parameters on both sides)
+
+@pytest.mark.parametrize("L", [2, 3])
+def test_map_sweep_lockstep(L):
+    pmrf = _pmrf()
+    specs = small_specs(4, seed0=7)
+    sl = synth.make_stack(specs)
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    rng = np.random.default_rng(L)
+    x = rng.integers(0, L, g.V).astype(np.uint8)
+    theta = np.zeros((g.S, L, 4))
+    theta[:, :, 1] = np.sort(rng.uniform(0.2, 0.8, (g.S, L)), axis=1)
+    theta[:, :, 2] = rng.uniform(0.05, 0.3, (g.S, L))
+    cfg = pmrf.EMConfig(n_labels=L, beta=0.8)
+    xo, ev, eh = g.map_sweep(cfg, torch.from_numpy(x).cuda(), torch.from_numpy(theta).cuda())
+    xo, ev, eh = xo.cpu().numpy(), ev.cpu().numpy(), eh.cpu().numpy()
+    arrs = gpu_arrays(g)
+    for s, one in enumerate(sl):
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        v0, v1 = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        c0, c1 = arrs["HOOD_SLICE_OFF"][s], arrs["HOOD_SLICE_OFF"][s + 1]
+        r = og.map_sweep(L, cfg.beta, x[v0:v1], theta[s, :, 1], theta[s, :, 2], want_second=True)
+        gap = label_gap(r["E_star"], r["E_second"])
+        assert_labels_match(xo[v0:v1], r["x_new"], gap, f"slice {s}")
+        assert rel_close(ev[v0:v1], r["E_star"], 1e-12, 1e-13)
+        assert rel_close(eh[c0:c1], r["S"], ENERGY_RTOL, 1e-12)
+
+
+def test_params_match_oracle():
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(3, seed0=70))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    L = 3
+    rng = np.random.default_rng(5)
+    x = rng.integers(0, L, g.V).astype(np.uint8)
+    arrs = gpu_arrays(g)
+    v0, v1 = arrs["VERT_OFF"][1], arrs["VERT_OFF"][2]
+    x[v0:v1][x[v0:v1] == 2] = 0  # slice 1: label 2 empty -> keeps the previous values
+    E = rng.normal(size=g.V)
+    prev = np.zeros((g.S, L, 4))
+    prev[:, :, 1] = [0.1, 0.5, 0.9]
+    prev[:, :, 2] = [0.2, 0.3, 0.4]
+    cfg = pmrf.EMConfig(n_labels=L)
+    th = g.params(cfg, torch.from_numpy(x).cuda(), torch.from_numpy(E).cuda(), torch.from_numpy(prev).cuda())
+    th = th.cpu().numpy()
+    for s, one in enumerate(sl):
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        a, b = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        want = og.params(L, x[a:b], E[a:b], prev[s])
+        assert np.array_equal(th[s, :, 0], want[:, 0])
+        assert rel_close(th[s, :, 1:3], want[:, 1:3], PARAM_RTOL)
+        assert rel_close(th[s, :, 3], want[:, 3], 1e-12, 1e-12)
+
+
+# --------------------------------------------------------------------------
+# the EM loop end to end
+
+def _em_compare(sl, cfg_o, cfg_g, g, out):
+    x = out["labels"].cpu().numpy()
+    th = out["params"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    cv = out["converged"].cpu().numpy()
+    arrs = gpu_arrays(g)
+    for s, one in enumerate(sl):
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        r = og.em(cfg_o)
+        a, b = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        assert it[s] == r["iters"], (s, it[s], r["iters"])
+        assert cv[s] == r["converged"]
+        assert np.array_equal(x[a:b], r["labels"]), (s, int((x[a:b] != r["labels"]).sum()))
+        assert np.array_equal(th[s, :, 0], r["theta"][:, 0])
+        assert rel_close(th[s, :, 1:3], r["theta"][:, 1:3], PARAM_RTOL)
+        assert rel_close(th[s, :, 3], r["theta"][:, 3], 1e-11, 1e-11)
+
+
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_em_slice256_matches_oracle(use_graph):
+    pmrf = _pmrf()
+    wl = synth.workload("slice256")
+    sl = synth.make_stack(wl.slices)
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    g.set_tuning(use_cuda_graph=use_graph)
+    cfg = pmrf.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters)
+    out = g.em(cfg, want_T=True)
+    g.sync_status()
+    _em_compare(sl, oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters), cfg, g, out)
+    # T history matches the oracle's totals up to summation order
+    og = oracle.Graph.from_image(sl[0].image, sl[0].region_ids)
+    r = og.em(oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters))
+    T = out["T_hist"].cpu().numpy()[0, :r["iters"]]
+    assert rel_close(T, r["T_hist"], ENERGY_RTOL)
+
+
+@pytest.mark.parametrize("L,beta", [(2, 1.0), (3, 1.5), (2, 0.0)])
+def test_em_batch_uneven_matches_oracle(L, beta):
+    pmrf = _pmrf()
+    specs = small_specs(6, seed0=100 + L)
+    if L == 3:
+        specs = [synth.scaled(synth.workload("large8192").slices[0], sp.height, sp.width, seed=sp.seed)
+                 for sp in specs]
+    sl = synth.make_stack(specs)
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    cfg = pmrf.EMConfig(n_labels=L, beta=beta, max_iters=30)
+    out = g.em(cfg)
+    _em_compare(sl, oracle.EMConfig(n_labels=L, beta=beta, max_iters=30), cfg, g, out)
+
+
+def test_batched_equals_per_slice():
+    """Slices in one batch give exactly what each gives alone."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(5, seed0=300))
+    imgs, ids = dev_tensors(sl)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=25)
+    gb = pmrf.build_graph(imgs, ids)
+    ob = gb.em(cfg)
+    xb = ob["labels"].cpu().numpy()
+    vo = gb.array("VERT_OFF").numpy()
+    for s in range(len(sl)):
+        g1 = pmrf.build_graph(imgs[s], ids[s])
+        o1 = g1.em(cfg)
+        assert np.array_equal(o1["labels"].cpu().numpy(), xb[vo[s]:vo[s + 1]])
+        assert int(o1["iters"][0]) == int(ob["iters"][s])
+        assert torch.equal(o1["params"][0], ob["params"][s])
+
+
+def test_em_resume_from_labels():
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(2, seed0=500))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=40)
+    full = g.em(cfg)
+    # stopping early then resuming from the labels reaches the same fixed point
+    part = g.em(pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=3))
+    res = g.em(cfg, labels=part["labels"].clone())
+    assert torch.equal(res["labels"], full["labels"])
+
+
+def test_label_image_matches_oracle():
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(3, seed0=900))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    out = g.em(pmrf.EMConfig())
+    seg = g.label_image(ids, out["labels"]).cpu().numpy()
+    arrs = gpu_arrays(g)
+    x = out["labels"].cpu().numpy()
+    o = 0
+    for s, one in enumerate(sl):
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        a, b = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        want = og.label_image(one.region_ids, x[a:b]).ravel()
+        assert np.array_equal(seg[o:o + want.size], want)
+        o += want.size
+
+
+# --------------------------------------------------------------------------
+# pseudo-log-likelihood and its adjoint
+
+def test_pll_and_adjoint_match_oracle():
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(3, seed0=1200))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    L = 2
+    out = g.em(pmrf.EMConfig(n_labels=L))
+    mu = out["params"][:, :, 1].contiguous()
+    sg = out["params"][:, :, 2].contiguous()
+    beta = 0.7
+    pll = g.pll(L, out["labels"], mu, sg, beta).cpu().numpy()
+    gout = torch.tensor([1.0, -2.0, 0.5], dtype=torch.float64, device="cuda")
+    gmu, gsg, gb = g.pll_grad(L, out["labels"], mu, sg, beta, gout)
+    x = out["labels"].cpu().numpy()
+    arrs = gpu_arrays(g)
+    gbeta = 0.0
+    for s, one in enumerate(sl):
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        a, b = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        f, om, osg, ob = og.pll(L, x[a:b], mu[s].cpu().numpy(), sg[s].cpu().numpy(), beta)
+        assert rel_close(pll[s], f, 1e-12, 1e-9)
+        go = float(gout[s])
+        assert rel_close(gmu[s].cpu().numpy(), go * om, 1e-10, 1e-8)
+        assert rel_close(gsg[s].cpu().numpy(), go * osg, 1e-10, 1e-8)
+        gbeta += go * ob
+    assert rel_close(float(gb[0]), gbeta, 1e-10, 1e-8)
+
+
+def test_pll_autograd_vs_central_differences():
+    pmrf = _pmrf()
+    from paper_1809_05018_b300.autograd import fit_beta
+    sl = synth.make_stack(small_specs(2, seed0=1300))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    out = g.em(pmrf.EMConfig())
+    mu = out["params"][:, :, 1].clone().requires_grad_(True)
+    sg = out["params"][:, :, 2].clone().requires_grad_(True)
+    beta = torch.tensor(0.6, dtype=torch.float64, device="cuda", requires_grad=True)
+    lab = out["labels"]
+    f = pmrf.PLL.apply(mu, sg, beta, g, lab).sum()
+    f.backward()
+    h = 1e-6
+
+    def F(m, s, b):
+        return float(pmrf.PLL.apply(m, s, b, g, lab).sum())
+
+    with torch.no_grad():
+        for (i, j) in [(0, 0), (1, 1)]:
+            e = torch.zeros_like(mu)
+            e[i, j] = h
+            fd = (F(mu + e, sg, beta) - F(mu - e, sg, beta)) / (2 * h)
+            assert abs(fd - float(mu.grad[i, j])) <= 1e-5 * max(1.0, abs(fd))
+            fd = (F(mu, sg + e, beta) - F(mu, sg - e, beta)) / (2 * h)
+            assert abs(fd - float(sg.grad[i, j])) <= 1e-5 * max(1.0, abs(fd))
+        fd = (F(mu, sg, beta + h) - F(mu, sg, beta - h)) / (2 * h)
+        assert abs(fd - float(beta.grad)) <= 1e-5 * max(1.0, abs(fd))
+    traj = fit_beta(g, lab, mu.detach(), sg.detach(), beta0=0.2, steps=30)
+    assert len(traj) == 31 and all(b >= 0 for b in traj)
