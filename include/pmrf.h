@@ -262,6 +262,33 @@ PMRF_API int pmrf_pll_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_lab
                   double* d_gbeta, pmrf_stream_t stream);
 
 /*
+ * Allocation-free variant of pmrf_pll_grad; the paper has no counterpart.
+ * Same inputs, outputs and results as pmrf_pll_grad, but it allocates no
+ * memory: no cudaMalloc, no stream-ordered allocation, no host allocation on
+ * the device's behalf.  It is meant for callers that cannot allocate when they
+ * need the gradient -- for example code issuing work while a stream is being
+ * captured into a CUDA graph, or an application whose device memory is held by
+ * its own allocator -- once the graph itself has been built.
+ *   Scratch: the per-block partial sums go to one fixed array inside the
+ *   library, PMRF_PLL_NOALLOC_MAX_DOUBLES doubles (8 MiB), which every GPU that
+ *   loads the library keeps until the process exits.  A call needs
+ *   S * ceil(V_max / 256) * (2 * n_labels + 2) + S doubles (S slices, V_max the
+ *   regions of the largest slice); a larger request fails with
+ *   PMRF_ERR_UNSUPPORTED and a message giving the size.
+ *   Set-up: the first call on a device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call
+ *   before any stream capture.
+ *   Sharing: all calls use the same array.  Each call writes every entry it
+ *   reads, so earlier calls leave nothing behind that matters, but calls whose
+ *   work overlaps on the GPU (different streams or threads) race on the array;
+ *   order them.  d_gout must not be NULL.
+ */
+#define PMRF_PLL_NOALLOC_MAX_DOUBLES (1 << 20)
+PMRF_API int pmrf_pll_grad_noalloc(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu,
+                                   const double* d_sigma, double beta, const double* d_gout, double* d_gmu,
+                                   double* d_gsigma, double* d_gbeta, pmrf_stream_t stream);
+
+/*
  * Labels back to pixels (closing paragraph of Section 3.2.2): d_out[p] =
  * d_labels[vertex of the region id of pixel p].  d_region_ids is the array the
  * graph was built from (same layout); d_out u8, one per pixel.

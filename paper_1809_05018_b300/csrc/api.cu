@@ -45,6 +45,8 @@ int pll_run(pmrf_graph* g, int32_t L, const uint8_t* x, const double* mu, const 
 int export_rep_hood(pmrf_graph* g, int32_t* dst, cudaStream_t s);
 int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tuning* best);
 int em_kernel_times(pmrf_graph* g, int32_t max_n, float* msv, float* msh, int32_t* n, cudaStream_t s);
+int pll_grad_noalloc_run(pmrf_graph* g, int32_t L, const uint8_t* x, const double* mu, const double* sigma,
+                         double beta, const double* gout, double* gmu, double* gsigma, double* gbeta, cudaStream_t s);
 
 namespace {
 
@@ -277,6 +279,16 @@ int pmrf_pll_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, cons
     PMRF_TRY(check_device(g));
     return pll_run(g, n_labels, d_labels, d_mu, d_sigma, beta, nullptr, d_gout, d_gmu, d_gsigma, d_gbeta,
                    (cudaStream_t)stream);
+}
+
+int pmrf_pll_grad_noalloc(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu,
+                          const double* d_sigma, double beta, const double* d_gout, double* d_gmu, double* d_gsigma,
+                          double* d_gbeta, pmrf_stream_t stream) {
+    g_last_error.clear();
+    if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
+    PMRF_TRY(check_device(g));
+    return pll_grad_noalloc_run(g, n_labels, d_labels, d_mu, d_sigma, beta, d_gout, d_gmu, d_gsigma, d_gbeta,
+                                (cudaStream_t)stream);
 }
 
 int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const uint8_t* d_labels, uint8_t* d_out,

@@ -9,6 +9,8 @@
 // One pass over the vertices writes per-block partial sums (deterministic
 // order); a per-slice pass adds them in block order.
 #include <algorithm>
+#include <mutex>
+#include <string>
 
 #include "graph.cuh"
 
@@ -196,6 +198,104 @@ int export_rep_hood(pmrf_graph* g, int32_t* dst, cudaStream_t s) {
     }
     PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;
+}
+
+}  // namespace pmrf
+
+// ---------------------------------------------------------------------------
+// Allocation-free adjoint (pmrf_pll_grad_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need the
+// gradient: code running while a stream is being captured into a CUDA graph
+// (allocation calls are not allowed there), code inside a host callback, or an
+// application whose memory is fully claimed by its own pool allocator.  For
+// them the adjoint's per-block partial sums live in the fixed array below,
+// which is part of the loaded module: every GPU that loads this library holds
+// PMRF_PLL_NOALLOC_MAX_DOUBLES doubles (8 MiB) of it until the process exits.
+//
+// The array's name is only a stand-in in host code; its device address is
+// looked up with cudaGetSymbolAddress once per device (with that device
+// current), on the first call made on that device.  Every call shares the
+// array, so calls whose work overlaps on the GPU (other streams, other host
+// threads) race on it and must be ordered by the caller.  Each call writes
+// every entry it later reads, so nothing left by an earlier call is used.
+
+static __device__ __align__(256) double pmrf_pll_noalloc_scratch[PMRF_PLL_NOALLOC_MAX_DOUBLES];
+
+namespace pmrf {
+
+namespace {
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[kMaxDevices] = {};
+
+int noalloc_scratch(double** out) {
+    int dev = -1;
+    PMRF_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PMRF_ERR_UNSUPPORTED, "device index beyond 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, pmrf_pll_noalloc_scratch);
+        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(pmrf_pll_noalloc_scratch)");
+        g_noalloc_ptr[dev] = (double*)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return PMRF_OK;
+}
+
+template <int L>
+int pll_grad_noalloc_body(pmrf_graph* g, const uint8_t* x, const double* mu, const double* sigma, double beta,
+                          const double* gout, double* gmu, double* gsigma, double* gbeta, cudaStream_t s) {
+    constexpr int NP = 2 * L + 2;
+    int64_t maxv = 0;
+    for (int i = 0; i < g->S; ++i) maxv = std::max(maxv, g->h_vert_off[i + 1] - g->h_vert_off[i]);
+    const int64_t nchunk = std::max<int64_t>(1, ceil_div(maxv, PLL_THREADS));
+    const int64_t need = (int64_t)g->S * nchunk * NP + g->S;
+    if (need > (int64_t)PMRF_PLL_NOALLOC_MAX_DOUBLES)
+        return fail(PMRF_ERR_UNSUPPORTED, "pmrf_pll_grad_noalloc needs " + std::to_string(need) +
+                                              " doubles of scratch (slices x ceil(largest slice's regions / 256) x (2 "
+                                              "n_labels + 2) + slices), above its fixed " +
+                                              std::to_string((int64_t)PMRF_PLL_NOALLOC_MAX_DOUBLES) +
+                                              "; use pmrf_pll_grad or smaller batches");
+    double* scr = nullptr;
+    PMRF_TRY(noalloc_scratch(&scr));
+    double* part = scr;
+    double* gb = scr + (int64_t)g->S * nchunk * NP;
+    if (maxv > 0) {
+        const dim3 grid((unsigned)nchunk, (unsigned)g->S);
+        k_pll<L><<<grid, PLL_THREADS, 0, s>>>(g->S, g->d_vert_off, g->d_y, g->d_adj_off, g->d_adj, x, mu, sigma, beta,
+                                             nchunk, part);
+        ::pmrf::note_launch(1);
+    }
+    k_pll_final<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, g->d_vert_off, nchunk, part, nullptr, gout, gmu, gsigma, gb);
+    ::pmrf::note_launch(1);
+    if (gbeta) {
+        k_sum_slices<<<1, 32, 0, s>>>(g->S, gb, gbeta);
+        ::pmrf::note_launch(1);
+    }
+    PMRF_CUDA(cudaGetLastError());
+    return PMRF_OK;
+}
+
+}  // namespace
+
+int pll_grad_noalloc_run(pmrf_graph* g, int32_t L, const uint8_t* x, const double* mu, const double* sigma,
+                         double beta, const double* gout, double* gmu, double* gsigma, double* gbeta, cudaStream_t s) {
+    if (L < 1 || L > PMRF_MAX_LABELS) return fail(PMRF_ERR_ARG, "n_labels must be in [1, 8]");
+    if (!x || !mu || !sigma || !gout) return fail(PMRF_ERR_ARG, "null pointer");
+    if (!std::isfinite(beta)) return fail(PMRF_ERR_ARG, "beta must be finite");
+    switch (L) {
+        case 1: return pll_grad_noalloc_body<1>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        case 2: return pll_grad_noalloc_body<2>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        case 3: return pll_grad_noalloc_body<3>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        case 4: return pll_grad_noalloc_body<4>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        case 5: return pll_grad_noalloc_body<5>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        case 6: return pll_grad_noalloc_body<6>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        case 7: return pll_grad_noalloc_body<7>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+        default: return pll_grad_noalloc_body<8>(g, x, mu, sigma, beta, gout, gmu, gsigma, gbeta, s);
+    }
 }
 
 }  // namespace pmrf
