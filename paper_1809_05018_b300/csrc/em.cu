@@ -36,6 +36,7 @@ namespace {
 constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
 constexpr int HT_THREADS = 256;
 constexpr int HT_CAP = 4096;        // shared-memory elements per hood tile
+constexpr int KAPPA_MAX_L = 3;      // labels up to which the hood pass decides in integers
 
 enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
 
@@ -107,13 +108,15 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                                                        const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
                                                        const double* __restrict__ theta, double* __restrict__ Dtab,
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
-                                                       double* __restrict__ vpart, DevStatus* st) {
-    __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
+                                                       double* __restrict__ vpart, DevStatus* st,
+                                                       uint32_t* __restrict__ kap_out) {
+    __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L], s_invb;
     __shared__ double s_red[VT_THREADS / 32][4 * L];
     const Tile tile = tiles[blockIdx.x];
     const int s = tile.slice;
     if (active && !active[s]) return;
     const RunCfg c = *cfgp;
+    if (threadIdx.x == 0) s_invb = c.beta > 0.0 ? 1.0 / c.beta : 0.0;
     if (threadIdx.x < L) {
         const int l = threadIdx.x;
         if (mode == MODE_INIT) {
@@ -155,6 +158,30 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
             if (Dtab) {
 #pragma unroll
                 for (int l = 0; l < L; ++l) Dtab[v * L + l] = D[l];
+            }
+            if (kap_out && L >= 2 && L <= KAPPA_MAX_L) {
+                // integer decision thresholds for the hood pass: label a is
+                // preferred over b > a in a hood iff n_a - n_b >= kappa_ab,
+                // kappa_ab = ceil((D_a - D_b) / beta), clamped to [-32, 32]
+                uint32_t pk = 0;
+                int idx = 0;
+#pragma unroll
+                for (int a = 0; a < L; ++a) {
+#pragma unroll
+                    for (int b = a + 1; b < L; ++b) {
+                        const double dl = D[a] - D[b];
+                        int q;
+                        if (c.beta > 0.0) {
+                            const double r = fmin(fmax(ceil(dl * s_invb), -32.0), 32.0);
+                            q = (int)r;
+                        } else {
+                            q = dl <= 0.0 ? -32 : 32;
+                        }
+                        pk |= (uint32_t)(uint8_t)(int8_t)q << (8 * idx);
+                        ++idx;
+                    }
+                }
+                kap_out[v] = pk;
             }
             const int64_t a0 = g.adj_off[v];
             const int d = (int)(g.adj_off[v + 1] - a0);
@@ -292,8 +319,10 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
                                                      const double* __restrict__ Dtab, double* __restrict__ hist,
-                                                     double* __restrict__ S_out, double* __restrict__ hpart) {
+                                                     double* __restrict__ S_out, double* __restrict__ hpart,
+                                                     const uint32_t* __restrict__ kap) {
     __shared__ uint8_t s_lab[HT_CAP];
+    __shared__ uint8_t s_m[HT_CAP];
     __shared__ uint16_t s_hs[HT_CAP];
     __shared__ double s_emin[HT_CAP];
     __shared__ double s_red[2][HT_THREADS / 32];
@@ -331,13 +360,35 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
 #pragma unroll
                     for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
                 }
-                s_emin[i] = hood_emin<L>(Dtab, v, cnt, dc, beta);
+                if (L >= 2 && L <= KAPPA_MAX_L && kap) {
+                    // Emin(c,v) = D_best(y_v) + beta * (dc - n_best): the label is
+                    // chosen with the vertex's integer thresholds, so the only
+                    // floating-point work per element is the hood sum
+                    const uint32_t pk = kap[v];
+                    int best = 0;
+#pragma unroll
+                    for (int l = 1; l < L; ++l) {
+                        const int idx = best * L - best * (best + 1) / 2 + (l - best - 1);  // pair (best, l)
+                        const int kv = (int)(int8_t)((pk >> (8 * idx)) & 0xffu);
+                        if (cnt[best] - cnt[l] < kv) best = l;
+                    }
+                    s_emin[i] = Dtab[v * L + best];
+                    s_m[i] = (uint8_t)(dc - cnt[best]);
+                } else {
+                    s_emin[i] = hood_emin<L>(Dtab, v, cnt, dc, beta);
+                    s_m[i] = 0;
+                }
             }
             __syncthreads();
             for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
                 const int64_t b = g.hood_off[c] - e0, e = g.hood_off[c + 1] - e0;
-                double S = 0.0;
-                for (int64_t i = b; i < e; ++i) S += s_emin[i];
+                double SD = 0.0;
+                int ms = 0;
+                for (int64_t i = b; i < e; ++i) {
+                    SD += s_emin[i];
+                    ms += s_m[i];
+                }
+                const double S = fma(beta, (double)ms, SD);
                 if (mode == MODE_SWEEP) {
                     if (S_out) S_out[c] = S;
                 } else {
@@ -614,7 +665,7 @@ int free_plans(pmrf_graph* g) {
 int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
     void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_Dtab,
-                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
+                  w.d_kappa, w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFree(p);
     g->em = EMWork();
@@ -752,6 +803,7 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p) {
     if (!rc2) rc2 = walloc(&w.d_conv, S);
     if (!rc2) rc2 = walloc(&w.d_nactive, 1);
     if (!rc2) rc2 = walloc(&w.d_Dtab, g->V * rc.L);  // data-term table D[v][l]
+    if (!rc2) rc2 = walloc(&w.d_kappa, g->V);        // integer label thresholds per vertex
     if (!rc2) rc2 = walloc((char**)&w.d_cfg, (int64_t)(sizeof(RunCfg) + sizeof(OutPtrs)));
     if (rc2) free_em(g);
     return rc2;
@@ -794,7 +846,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
                                                                 w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
-                                                                nullptr, w.d_vpart, g->d_status);
+                                                                nullptr, w.d_vpart, g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
@@ -808,13 +860,13 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (p->n_vtiles > 0) {
             k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
                                                                     xout, w.d_theta, Dtab, nullptr, nullptr,
-                                                                    w.d_vpart, g->d_status);
+                                                                    w.d_vpart, g->d_status, w.d_kappa);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
         if (p->n_htiles > 0) {
             k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(z.dg, z.ht, MODE_EM, t, z.d_cfg, w.d_active, xin,
-                                                                  Dtab, w.d_hist, nullptr, w.d_hpart);
+                                                                  Dtab, w.d_hist, nullptr, w.d_hpart, w.d_kappa);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
@@ -940,18 +992,18 @@ namespace {
 
 template <int L>
 int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, const uint8_t* xin, const double* theta,
-               uint8_t* xout, double* Eout, double* Sout, double* Dtab) {
+               uint8_t* xout, double* Eout, double* Sout, double* Dtab, uint32_t* kap) {
     DevGraph dg = view(g);
     const Tile* vt = p->d_tiles;
     const Tile* ht = p->d_tiles + p->n_vtiles;
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
-                                                                Dtab, nullptr, Eout, nullptr, g->d_status);
+                                                                Dtab, nullptr, Eout, nullptr, g->d_status, kap);
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
         k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(dg, ht, MODE_SWEEP, 1, d_cfg, nullptr, xin, Dtab,
-                                                              nullptr, Sout, nullptr);
+                                                              nullptr, Sout, nullptr, kap);
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
@@ -966,7 +1018,7 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
                                                                 nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
-                                                                g->d_status);
+                                                                g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
@@ -1009,7 +1061,7 @@ int sweep_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* xin, const d
     PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
     int r = PMRF_OK;
     DISPATCH_L(rc.L, r = sweep_body<L>(g, p, s, (const RunCfg*)w.d_cfg, xin, theta, xout, Eout, Sout,
-                                       w.d_Dtab));
+                                       w.d_Dtab, w.d_kappa));
     PMRF_CUDA(cudaStreamSynchronize(s));  // the host RunCfg copy is a stack value
     return r;
 }

@@ -39,6 +39,7 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     double* d_theta = nullptr;     // [S][L][4] current parameters
     double* d_Thist = nullptr;     // [S][W] ring of totals
     double* d_Dtab = nullptr;      // [V][L] data term of the current iteration
+    uint32_t* d_kappa = nullptr;   // [V] packed int8 label-pair thresholds (L <= 3)
     int32_t* d_active = nullptr;   // [S] slice still iterating
     int32_t* d_iters = nullptr;    // [S]
     int32_t* d_conv = nullptr;     // [S]

@@ -6,10 +6,11 @@
 //     adjacency),
 //   * the replica list of each vertex (hoods containing it, ascending).
 //
-// Small segments (<= SMALL_MAX values) are grouped into shared-memory tiles
-// and sorted with a bitonic network on 64-bit keys (segment, value).  Larger
+// Short segments (<= 256 values) are sorted by one warp each in registers;
+// medium ones (<= SMALL_MAX) by a CTA with a shared-memory bitonic network.  Larger
 // segments are sorted through a bitmap over their value range (one CTA per
 // segment), which requires distinct values unless `unique` is requested.
+#include <algorithm>
 #include <vector>
 
 #include "common.cuh"
@@ -22,6 +23,7 @@ constexpr int SORT_THREADS = 512;
 constexpr int SORT_CAP = 4096;       // keys per shared-memory group
 constexpr int SMALL_MAX = 2048;      // longest segment sorted in shared memory
 constexpr int WINDOW = 2048;         // segment starts per tile window
+constexpr int WARP_MAX = 256;        // longest segment sorted by one warp in registers
 
 __device__ __forceinline__ void bitonic_sort_smem(uint64_t* key, int npow2) {
     for (int k = 2; k <= npow2; k <<= 1) {
@@ -42,9 +44,9 @@ __device__ __forceinline__ void bitonic_sort_smem(uint64_t* key, int npow2) {
     }
 }
 
-// One CTA per window of segment starts.  Segments of the window are processed
-// in consecutive groups whose total length fits SORT_CAP; big segments are
-// skipped (handled by the bitmap kernels).
+// One CTA per window of segment starts.  Sorts the window's medium segments
+// (WARP_MAX < length <= SMALL_MAX) one at a time in shared memory; short ones
+// belong to k_sort_warp and long ones to the bitmap kernels.
 __global__ void __launch_bounds__(SORT_THREADS) k_sort_small(uint32_t* __restrict__ vals,
                                                              const int64_t* __restrict__ off, int64_t nseg,
                                                              int64_t n, int unique, int32_t* __restrict__ ucount) {
@@ -60,56 +62,120 @@ __global__ void __launch_bounds__(SORT_THREADS) k_sort_small(uint32_t* __restric
     }
     __syncthreads();
     const int64_t k0 = s_k0, k1 = s_k1;
-    int64_t k = k0;
-    while (k < k1) {
-        // form a group [k, kg) of small segments with total length <= SORT_CAP
-        int64_t kg = k;
+    for (int64_t k = k0; k < k1; ++k) {
         const int64_t gstart = off[k];
-        while (kg < k1) {
-            int64_t len = off[kg + 1] - off[kg];
-            if (len > SMALL_MAX) break;
-            if (off[kg + 1] - gstart > SORT_CAP) break;
-            ++kg;
-        }
-        if (kg == k) {  // a big segment: leave it to the bitmap path
-            k = k + 1;
-            continue;
-        }
-        const int64_t gend = off[kg];
-        const int cnt = (int)(gend - gstart);
+        const int cnt = (int)(off[k + 1] - gstart);
+        if (cnt <= WARP_MAX || cnt > SMALL_MAX) continue;  // warp kernel / bitmap path
         int npow2 = 1;
         while (npow2 < cnt) npow2 <<= 1;
-        // load keys: (segment index within group << 32) | value
-        for (int i = threadIdx.x; i < npow2; i += blockDim.x) {
-            if (i < cnt) {
-                int64_t p = gstart + i;
-                // segment of position p: linear scan from k is fine for tiny groups,
-                // but groups can hold many segments: binary search in off[k..kg)
-                int64_t sidx = upper_bound_dev<int64_t>(off, k, kg, p) - 1 - k;
-                key[i] = ((uint64_t)sidx << 32) | (uint64_t)vals[p];
-            } else {
-                key[i] = ~0ull;
-            }
-        }
+        for (int i = threadIdx.x; i < npow2; i += blockDim.x) key[i] = (i < cnt) ? (uint64_t)vals[gstart + i] : ~0ull;
         __syncthreads();
-        if (cnt > 1) bitonic_sort_smem(key, npow2);
+        bitonic_sort_smem(key, npow2);
         if (!unique) {
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) vals[gstart + i] = (uint32_t)(key[i] & 0xffffffffu);
-        } else {
-            for (int64_t sg = k + threadIdx.x; sg < kg; sg += blockDim.x) {
-                const int b = (int)(off[sg] - gstart), e = (int)(off[sg + 1] - gstart);
-                int u = 0;
-                uint32_t prev = 0;
-                for (int i = b; i < e; ++i) {
-                    uint32_t v = (uint32_t)(key[i] & 0xffffffffu);
-                    if (i == b || v != prev) vals[off[sg] + u++] = v;
-                    prev = v;
-                }
-                ucount[sg] = u;
-            }
+            for (int i = threadIdx.x; i < cnt; i += blockDim.x) vals[gstart + i] = (uint32_t)key[i];
+        } else if (threadIdx.x == 0) {
+            int u = 0;
+            for (int i = 0; i < cnt; ++i)
+                if (i == 0 || key[i] != key[i - 1]) vals[gstart + u++] = (uint32_t)key[i];
+            ucount[k] = u;
         }
         __syncthreads();
-        k = kg;
+    }
+}
+
+// Segments of at most 32*E values: one warp per segment, E values per lane in
+// registers (lane l holds positions l*E .. l*E+E-1), bitonic network with
+// in-register exchanges for distances below E and shuffles above.
+template <int E>
+__device__ __forceinline__ void warp_sort_seg(uint32_t* __restrict__ vals, int64_t b, int len, bool unique,
+                                              int32_t* __restrict__ ucount, int64_t k) {
+    constexpr int N = 32 * E;
+    const int lane = lane_id();
+    uint32_t a[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = lane * E + r;
+        a[r] = i < len ? vals[b + i] : 0xffffffffu;
+    }
+#pragma unroll
+    for (int kk = 2; kk <= N; kk <<= 1) {
+#pragma unroll
+        for (int jj = kk >> 1; jj > 0; jj >>= 1) {
+            if (jj >= E) {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    const int i = lane * E + r;
+                    const uint32_t o = __shfl_xor_sync(0xffffffffu, a[r], jj / E);
+                    const bool up = (i & kk) == 0;
+                    const bool lower = (i & jj) == 0;
+                    a[r] = (lower == up) ? min(a[r], o) : max(a[r], o);
+                }
+            } else {
+#pragma unroll
+                for (int r = 0; r < E; ++r) {
+                    if ((r & jj) == 0) {
+                        const int r2 = r | jj;
+                        const bool up = ((lane * E + r) & kk) == 0;
+                        const uint32_t x = a[r], y = a[r2];
+                        if ((x > y) == up) {
+                            a[r] = y;
+                            a[r2] = x;
+                        }
+                    }
+                }
+            }
+        }
+    }
+    if (!unique) {
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int i = lane * E + r;
+            if (i < len) vals[b + i] = a[r];
+        }
+        return;
+    }
+    // keep the first of each run of equal values
+    const uint32_t prev_last = __shfl_up_sync(0xffffffffu, a[E - 1], 1);
+    int c = 0;
+    bool f[E];
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int i = lane * E + r;
+        const uint32_t prev = (r == 0) ? prev_last : a[r - 1];
+        f[r] = (i < len) && (i == 0 || a[r] != prev);
+        c += f[r];
+    }
+    int x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+    }
+    int pos = x - c;
+#pragma unroll
+    for (int r = 0; r < E; ++r)
+        if (f[r]) vals[b + pos++] = a[r];
+    if (lane == 31) ucount[k] = x;
+}
+
+__global__ void __launch_bounds__(256) k_sort_warp(uint32_t* __restrict__ vals, const int64_t* __restrict__ off,
+                                                   int64_t nseg, int unique, int32_t* __restrict__ ucount) {
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t k = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5); k < nseg; k += warps) {
+        const int64_t b = off[k];
+        const int64_t n64 = off[k + 1] - b;
+        const int len = n64 > WARP_MAX ? WARP_MAX + 1 : (int)n64;
+        if (len <= 1) {
+            if (unique && lane_id() == 0) ucount[k] = len;
+        } else if (len <= 32) {
+            warp_sort_seg<1>(vals, b, len, unique, ucount, k);
+        } else if (len <= 64) {
+            warp_sort_seg<2>(vals, b, len, unique, ucount, k);
+        } else if (len <= 128) {
+            warp_sort_seg<4>(vals, b, len, unique, ucount, k);
+        } else if (len <= WARP_MAX) {
+            warp_sort_seg<8>(vals, b, len, unique, ucount, k);
+        }
     }
 }
 
@@ -211,6 +277,14 @@ int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t
                        DevStatus* st, cudaStream_t s) {
     if (nseg <= 0) return PMRF_OK;
     const int64_t nwin = ceil_div(n > 0 ? n : 1, WINDOW);
+    {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t blocks = std::max<int64_t>(1, std::min<int64_t>(ceil_div(nseg, 8), (int64_t)sms * 16));
+        k_sort_warp<<<(unsigned)blocks, 256, 0, s>>>(vals, off, nseg, unique ? 1 : 0, ucount);
+        ::pmrf::note_launch(1);
+    }
     k_sort_small<<<(unsigned)nwin, SORT_THREADS, 0, s>>>(vals, off, nseg, n, unique ? 1 : 0, ucount); ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
 

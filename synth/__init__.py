@@ -13,7 +13,7 @@ import ctypes
 import os
 import subprocess
 from concurrent.futures import ThreadPoolExecutor
-from dataclasses import dataclass, replace
+from dataclasses import dataclass, replace  # noqa: F401  (replace is re-exported)
 
 import numpy as np
 

@@ -321,3 +321,22 @@ def test_pll_autograd_vs_central_differences():
         assert abs(fd - float(beta.grad)) <= 1e-5 * max(1.0, abs(fd))
     traj = fit_beta(g, lab, mu.detach(), sg.detach(), beta0=0.2, steps=30)
     assert len(traj) == 31 and all(b >= 0 for b in traj)
+
+
+def test_large_regions_match_oracle():
+    """Regions of ~600-2000 pixels: pixel lists take the shared-memory sort,
+    candidate-neighbour lists the widest warp sort."""
+    pmrf = _pmrf()
+    base = synth.workload("slice256").slices[0]
+    specs = [synth.replace(synth.scaled(base, 160, 200, seed=77), pitch_min=26.0, pitch_max=45.0, jitter=8.0),
+             synth.replace(synth.scaled(base, 96, 300, seed=78), pitch_min=40.0, pitch_max=40.0, jitter=3.0)]
+    sl = synth.make_stack(specs)
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    arrs = gpu_arrays(g)
+    npix = arrs["NPIX"]
+    assert npix.max() > 256  # the shared-memory path ran
+    for s, one in enumerate(sl):
+        assert_graph_equal(oracle.Graph.from_image(one.image, one.region_ids), slice_view(arrs, s))
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=20)
+    _em_compare(sl, oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20), cfg, g, g.em(cfg))
