@@ -303,8 +303,10 @@ PMRF_API int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const 
  */
 PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* detail);
 
-/* Tile sizes of the persistent EM launch.  0 selects the autotuned /
- * default value.  hood_tile: hood elements per tile (multiple of 32, 256..8192);
+/* Tile sizes of the EM launches.  0 selects the autotuned / default value.
+ * hood_tile: hood elements per tile window (multiple of 32, 128..1248; a tile
+ * holds the hoods starting in its window, at most hood_tile + 31 elements when
+ * every hood has <= 32 members, default 1024);
  * vert_tile: vertices per tile (multiple of 32, 32..4096); ctas_per_sm: 1..8. */
 typedef struct {
     int32_t hood_tile;

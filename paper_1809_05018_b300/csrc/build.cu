@@ -510,13 +510,14 @@ __global__ void k_rep_words(const int64_t* __restrict__ adj_off, const int32_t* 
 }
 
 // For element e (vertex v in hood c at position i): row bits j where hood[j]
-// is a neighbour of v, and slot bits s where N(v)[s] lies in the hood.
+// is a neighbour of v, and slot bits s where N(v)[s] lies in the hood (stored
+// vertex-major with the replicas and, for degrees <= 32, element-major too).
 __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
                         const int32_t* __restrict__ el_hood, const int64_t* __restrict__ adj_off,
                         const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
                         uint32_t* __restrict__ row, const int64_t* __restrict__ rep_off,
                         const uint32_t* __restrict__ rep_pos, const int64_t* __restrict__ rep_woff,
-                        uint32_t* __restrict__ rep_mask, int64_t N_el) {
+                        uint32_t* __restrict__ rep_mask, uint32_t* __restrict__ el_slot, int64_t N_el) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N_el) return;
     const int32_t c = el_hood[e];
@@ -548,6 +549,8 @@ __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __r
     }
     rw[rwi] = rcur;
     sw[swi] = scur;
+    // the same slot mask in element (hood-major) order, for vertices of degree <= 32
+    el_slot[e] = (d <= 32) ? scur : 0u;
 }
 
 // slice offsets of cliques/hoods: cliques are grouped by their smallest vertex
@@ -844,10 +847,11 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(read_i64(g->d_rep_woff + V, &g->n_rep_words, s));
     PMRF_TRY(dalloc(&g->d_row, g->n_row_words, s));
     PMRF_TRY(dalloc(&g->d_rep_mask, g->n_rep_words, s));
+    PMRF_TRY(dalloc(&g->d_el_slot, N_el, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
     LAUNCH_1D(k_masks, N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off, g->d_row,
-              g->d_rep_off, d_rep_pos, g->d_rep_woff, g->d_rep_mask, N_el);
+              g->d_rep_off, d_rep_pos, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, N_el);
     PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
     // slice offsets of hoods and elements (host copies)

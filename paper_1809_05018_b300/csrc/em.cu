@@ -35,8 +35,11 @@ namespace {
 
 constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
 constexpr int HT_THREADS = 256;
-constexpr int HT_CAP = 4096;        // shared-memory elements per hood tile
-constexpr int KAPPA_MAX_L = 3;      // labels up to which the hood pass decides in integers
+constexpr int EPT = 5;                        // hood elements per thread in a fast hood tile
+constexpr int HT_CAP = HT_THREADS * EPT;      // elements a fast hood tile can hold (L <= 4)
+// elements a fast hood tile holds (the same for every label count)
+__host__ __device__ constexpr int hood_cap(int L) { return L > 0 ? HT_CAP : HT_CAP; }
+static_assert(hood_cap(8) % HT_THREADS == 0 && hood_cap(2) % HT_THREADS == 0, "whole elements per thread");
 
 enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
 
@@ -67,6 +70,7 @@ struct DevGraph {
     const uint32_t* row;
     const int64_t* rep_woff;
     const uint32_t* rep_mask;
+    const uint32_t* el_slot;
 };
 
 DevGraph view(const pmrf_graph* g) {
@@ -85,6 +89,7 @@ DevGraph view(const pmrf_graph* g) {
     d.row = g->d_row;
     d.rep_woff = g->d_rep_woff;
     d.rep_mask = g->d_rep_mask;
+    d.el_slot = g->d_el_slot;
     return d;
 }
 
@@ -99,6 +104,48 @@ __device__ __forceinline__ int threshold_label(const RunCfg& c, double y) {
 }
 
 // ---------------------------------------------------------------------------
+// exact hood sums
+//
+// A double is m * 2^e with a 53-bit integer m; its value in units of 2^-80 is
+// m shifted by e + 80, held exactly in a signed 128-bit integer whenever
+// 2^-27 <= |d| < 2^46 (smaller magnitudes are truncated, an error below
+// 1e-24; larger ones saturate).  Sums of such integers are exact and
+// independent of order, so a hood sum is the exact sum of its FP64 terms,
+// rounded to double once.  This keeps the per-element work of the hood pass in
+// the integer pipes (the FP64 pipe of this part is small).
+
+__device__ __forceinline__ __int128 fix80(double d) {
+    const long long bits = __double_as_longlong(d);
+    const int ex = (int)((bits >> 52) & 0x7ff);
+    unsigned long long man = (unsigned long long)bits & 0xfffffffffffffull;
+    if (ex != 0) man |= 1ull << 52;
+    const int sh = (ex == 0 ? 1 : ex) - 995;  // value = man * 2^(ex - 1075), units of 2^-80
+    __int128 r;
+    if (sh >= 0) {
+        r = sh > 73 ? ((__int128)1 << 126) : ((__int128)man << sh);
+    } else {
+        r = sh <= -53 ? (__int128)0 : (__int128)(man >> (-sh));
+    }
+    return bits < 0 ? -r : r;
+}
+
+__device__ __forceinline__ double unfix80(__int128 x) {
+    // from the magnitude, so that the low word of a small negative value does
+    // not round (|x| < 2^64 converts with a single rounding)
+    const bool neg = x < 0;
+    const __int128 a = neg ? -x : x;
+    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
+    const double r = fma((double)hi, 0x1p64, (double)lo) * 0x1p-80;
+    return neg ? -r : r;
+}
+
+__device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
+    const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(x >> 64), o);
+    const unsigned long long lo = __shfl_xor_sync(0xffffffffu, (unsigned long long)x, o);
+    return ((__int128)hi << 64) | (__int128)lo;
+}
+
+// ---------------------------------------------------------------------------
 // vertex pass
 
 template <int L>
@@ -106,17 +153,18 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                                                        const RunCfg* __restrict__ cfgp,
                                                        const int32_t* __restrict__ active,
                                                        const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
-                                                       const double* __restrict__ theta, double* __restrict__ Dtab,
+                                                       const double* __restrict__ theta, __int128* __restrict__ Dfix,
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
                                                        double* __restrict__ vpart, DevStatus* st,
-                                                       uint32_t* __restrict__ kap_out) {
-    __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L], s_invb;
-    __shared__ double s_red[VT_THREADS / 32][4 * L];
+                                                       uint32_t* __restrict__ lm_out) {
+    __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
+    __shared__ double s_vq[3][VT_THREADS];
+    __shared__ double s_vc[3 * L][8];
+    __shared__ uint8_t s_vl[VT_THREADS];
     const Tile tile = tiles[blockIdx.x];
     const int s = tile.slice;
     if (active && !active[s]) return;
     const RunCfg c = *cfgp;
-    if (threadIdx.x == 0) s_invb = c.beta > 0.0 ? 1.0 / c.beta : 0.0;
     if (threadIdx.x < L) {
         const int l = threadIdx.x;
         if (mode == MODE_INIT) {
@@ -133,9 +181,8 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     __syncthreads();
     const int64_t v = (int64_t)tile.a0 + threadIdx.x;
     const bool ok = v < tile.a1;
-    double acc_n[L], acc_s1[L], acc_s2[L], acc_u[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) { acc_n[l] = 0; acc_s1[l] = 0; acc_s2[l] = 0; acc_u[l] = 0; }
+    int vlab = 0;
+    double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
     if (ok) {
         const double y = g.y[v];
         int lab = 0;
@@ -155,33 +202,10 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                 const double dev = y - s_mu[l];
                 D[l] = dev * dev * s_inv[l] + s_lnsig[l];
             }
-            if (Dtab) {
+            if (Dfix) {
+                // the hood pass works on these energies in exact fixed point
 #pragma unroll
-                for (int l = 0; l < L; ++l) Dtab[v * L + l] = D[l];
-            }
-            if (kap_out && L >= 2 && L <= KAPPA_MAX_L) {
-                // integer decision thresholds for the hood pass: label a is
-                // preferred over b > a in a hood iff n_a - n_b >= kappa_ab,
-                // kappa_ab = ceil((D_a - D_b) / beta), clamped to [-32, 32]
-                uint32_t pk = 0;
-                int idx = 0;
-#pragma unroll
-                for (int a = 0; a < L; ++a) {
-#pragma unroll
-                    for (int b = a + 1; b < L; ++b) {
-                        const double dl = D[a] - D[b];
-                        int q;
-                        if (c.beta > 0.0) {
-                            const double r = fmin(fmax(ceil(dl * s_invb), -32.0), 32.0);
-                            q = (int)r;
-                        } else {
-                            q = dl <= 0.0 ? -32 : 32;
-                        }
-                        pk |= (uint32_t)(uint8_t)(int8_t)q << (8 * idx);
-                        ++idx;
-                    }
-                }
-                kap_out[v] = pk;
+                for (int l = 0; l < L; ++l) Dfix[v * L + l] = fix80(D[l]);
             }
             const int64_t a0 = g.adj_off[v];
             const int d = (int)(g.adj_off[v + 1] - a0);
@@ -197,21 +221,24 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                 for (int j = 0; j < d; ++j) {
                     const int xl = x_in[g.adj[a0 + j]];
 #pragma unroll
-                    for (int l = 1; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
+                    for (int l = 0; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
+                }
+                if (lm_out) {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) lm_out[v * L + l] = lm[l];
                 }
                 for (int64_t r = r0; r < r1; ++r) {
                     const uint32_t m = g.rep_mask[r];
                     const int dc = __popc(m);
-                    int rest = dc;
 #pragma unroll
-                    for (int l = 1; l < L; ++l) {
-                        const int n = __popc(m & lm[l]);
-                        rest -= n;
-                        M[l] = min(M[l], dc - n);  // neighbours in the hood whose label is not l
-                    }
-                    M[0] = min(M[0], dc - rest);
+                    for (int l = 0; l < L; ++l)
+                        M[l] = min(M[l], dc - __popc(m & lm[l]));  // neighbours in the hood whose label is not l
                 }
             } else {
+                if (lm_out) {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) lm_out[v * L + l] = 0u;  // not read: such vertices are in general tiles
+                }
                 const int nw = (d + 31) >> 5;
                 for (int64_t r = r0; r < r1; r += nw) {
                     int cnt[L];
@@ -246,68 +273,81 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
         }
         if (mode == MODE_INIT) x_out[v] = (uint8_t)lab;
         if (mode != MODE_SWEEP) {
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                if (lab == l) {
-                    const double dv = y - s_K[l];
-                    acc_n[l] = 1.0;
-                    acc_s1[l] = dv;
-                    acc_s2[l] = dv * dv;
-                    acc_u[l] = Estar;
-                }
-            }
+            const double dv = y - s_K[lab];
+            vlab = lab;
+            vq0 = dv;
+            vq1 = dv * dv;
+            vq2 = Estar;
         }
     }
     if (mode == MODE_SWEEP) return;
-    // deterministic block reduction of the 4L partial sums
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        acc_n[l] = warp_sum(acc_n[l]);
-        acc_s1[l] = warp_sum(acc_s1[l]);
-        acc_s2[l] = warp_sum(acc_s2[l]);
-        acc_u[l] = warp_sum(acc_u[l]);
-    }
-    if (lane_id() == 0) {
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            s_red[warp_id()][4 * l + 0] = acc_n[l];
-            s_red[warp_id()][4 * l + 1] = acc_s1[l];
-            s_red[warp_id()][4 * l + 2] = acc_s2[l];
-            s_red[warp_id()][4 * l + 3] = acc_u[l];
+    // deterministic per-label sums of the tile: each vertex contributes to the
+    // label it carries; 8 threads per (label, quantity) add 32 entries each in
+    // order, then one thread adds the 8 results (no shuffle trees: the FP64
+    // pipe is the scarce unit)
+    s_vl[threadIdx.x] = ok ? (uint8_t)vlab : (uint8_t)0xff;
+    s_vq[0][threadIdx.x] = vq0;
+    s_vq[1][threadIdx.x] = vq1;
+    s_vq[2][threadIdx.x] = vq2;
+    __syncthreads();
+    if (threadIdx.x < 3 * L * 8) {
+        const int lq = threadIdx.x >> 3, w = threadIdx.x & 7;
+        const int l = lq / 3, q = lq % 3;
+        double a = 0.0;
+        for (int j = 0; j < 32; ++j) {
+            const int i = w * 32 + j;
+            if (s_vl[i] == l) a += s_vq[q][i];
         }
+        s_vc[lq][w] = a;
+    } else if (threadIdx.x >= 3 * L * 8 && threadIdx.x < 3 * L * 8 + L) {
+        const int l = threadIdx.x - 3 * L * 8;
+        int n = 0;
+        for (int i = 0; i < VT_THREADS; ++i) n += (s_vl[i] == l);
+        vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
     }
     __syncthreads();
-    if (threadIdx.x < 4 * L) {
-        double t = 0.0;
-        for (int w = 0; w < VT_THREADS / 32; ++w) t += s_red[w][threadIdx.x];
-        vpart[(int64_t)tile.part * 4 * L + threadIdx.x] = t;
+    if (threadIdx.x < 3 * L) {
+        double a = 0.0;
+        for (int w = 0; w < 8; ++w) a += s_vc[threadIdx.x][w];
+        const int l = threadIdx.x / 3, q = threadIdx.x % 3;
+        vpart[(int64_t)tile.part * 4 * L + 4 * l + 1 + q] = a;
     }
 }
 
 // ---------------------------------------------------------------------------
 // hood pass
 
+// exact min_l D_l(y_v) + beta * (dc - cnt_l) in units of 2^-80, ties to the
+// lower label
 template <int L>
-__device__ __forceinline__ double hood_emin(const double* __restrict__ Dtab, int64_t v, const int* cnt, int dc,
-                                            double beta) {
-    double e = Dtab[v * L + 0] + beta * (double)(dc - cnt[0]);
+__device__ __forceinline__ __int128 hood_emin_fix(const __int128* __restrict__ Dfix, int64_t v, const int* cnt,
+                                                  int dc, __int128 beta_fix) {
+    __int128 e = Dfix[v * L + 0] + beta_fix * (__int128)(dc - cnt[0]);
 #pragma unroll
-    for (int l = 1; l < L; ++l) e = fmin(e, Dtab[v * L + l] + beta * (double)(dc - cnt[l]));
+    for (int l = 1; l < L; ++l) {
+        const __int128 x = Dfix[v * L + l] + beta_fix * (__int128)(dc - cnt[l]);
+        if (x < e) e = x;
+    }
     return e;
 }
 
 // convergence bookkeeping of one hood; returns 1 when the hood is unconverged
 __device__ __forceinline__ int hood_history(double S, int64_t c, int64_t C, int t, const RunCfg& cf,
                                             double* __restrict__ hist) {
+    // converged iff t > W and |S - S^{t-k}| < tol for every k = 1..W; equal
+    // bit patterns need no floating-point work, and the first failing k decides
     const int W = cf.W;
     int unconv = 1;
     if (t > W) {
-        double dmax = 0.0;
+        unconv = 0;
         for (int k = 1; k <= W; ++k) {
             const double prev = hist[(int64_t)((t - k) % W) * C + c];
-            if (__double_as_longlong(prev) != __double_as_longlong(S)) dmax = fmax(dmax, fabs(S - prev));
+            if (__double_as_longlong(prev) == __double_as_longlong(S)) continue;
+            if (!(fabs(S - prev) < cf.tol)) {
+                unconv = 1;
+                break;
+            }
         }
-        unconv = (dmax < cf.tol) ? 0 : 1;
     }
     hist[(int64_t)(t % W) * C + c] = S;
     return unconv;
@@ -318,82 +358,69 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                                                      const RunCfg* __restrict__ cfgp,
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
-                                                     const double* __restrict__ Dtab, double* __restrict__ hist,
+                                                     const __int128* __restrict__ Dfix, double* __restrict__ hist,
                                                      double* __restrict__ S_out, double* __restrict__ hpart,
-                                                     const uint32_t* __restrict__ kap) {
-    __shared__ uint8_t s_lab[HT_CAP];
-    __shared__ uint8_t s_m[HT_CAP];
-    __shared__ uint16_t s_hs[HT_CAP];
-    __shared__ double s_emin[HT_CAP];
-    __shared__ double s_red[2][HT_THREADS / 32];
+                                                     const uint32_t* __restrict__ lm) {
+    constexpr int CAP = hood_cap(L);
+    __shared__ __int128 s_fix[CAP];
+    __shared__ __int128 s_wsum[HT_THREADS / 32];
+    __shared__ int s_unconv;
     const Tile tile = tiles[blockIdx.x];
     const int s = tile.slice;
     if (active && !active[s]) return;
     const RunCfg cf = *cfgp;
-    const double beta = cf.beta;
+    const __int128 beta_fix = fix80(cf.beta);
     const int64_t c0 = tile.a0, c1 = tile.a1;
-    double my_S = 0.0, my_unconv = 0.0;
+    __int128 my_T = 0;
+    int my_unconv = 0;
+    if (threadIdx.x == 0) s_unconv = 0;
     if (c1 > c0) {
         const int64_t e0 = g.hood_off[c0];
-        const int64_t ne = g.hood_off[c1] - e0;
-        const bool fast = tile.pad != 0;  // every hood <= 32 and ne <= HT_CAP
+        const int ne = (int)(g.hood_off[c1] - e0);
+        // fast tile (flag set when the tile table was built): the elements fit,
+        // every hood has <= 32 members and every element's vertex degree <= 32
+        const bool fast = tile.pad != 0 && ne <= CAP;
         if (fast) {
-            for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) s_lab[i] = x_in[g.hood[e0 + i]];
-            for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-                const int64_t b = g.hood_off[c] - e0, e = g.hood_off[c + 1] - e0;
-                for (int64_t i = b; i < e; ++i) s_hs[i] = (uint16_t)b;
+            // every element's vertex has degree <= 32 and every hood <= 32
+            // members: the counts of each label among v's neighbours inside
+            // hood c are popcounts of the element's slot mask against the
+            // vertex's label masks, so every load depends only on v
+            constexpr int EPTL = CAP / HT_THREADS;
+            int32_t vv[EPTL];
+            uint32_t sm[EPTL];
+#pragma unroll
+            for (int q = 0; q < EPTL; ++q) {
+                const int i = threadIdx.x + q * HT_THREADS;
+                vv[q] = 0;
+                sm[q] = 0;
+                if (i < ne) {
+                    vv[q] = g.hood[e0 + i];
+                    sm[q] = g.el_slot[e0 + i];
+                }
             }
-            __syncthreads();
-            const int64_t rbase = g.row_off[c0];
-            for (int64_t i = threadIdx.x; i < ne; i += blockDim.x) {
-                const int64_t v = g.hood[e0 + i];
-                uint32_t m = g.row[rbase + i];
-                const int hs = s_hs[i];
+#pragma unroll
+            for (int q = 0; q < EPTL; ++q) {
+                const int i = threadIdx.x + q * HT_THREADS;
+                if (i >= ne) continue;
+                const int64_t v = vv[q];
+                const uint32_t m = sm[q];
                 const int dc = __popc(m);
                 int cnt[L];
 #pragma unroll
-                for (int l = 0; l < L; ++l) cnt[l] = 0;
-                while (m) {
-                    const int b = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int xl = s_lab[hs + b];
-#pragma unroll
-                    for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
-                }
-                if (L >= 2 && L <= KAPPA_MAX_L && kap) {
-                    // Emin(c,v) = D_best(y_v) + beta * (dc - n_best): the label is
-                    // chosen with the vertex's integer thresholds, so the only
-                    // floating-point work per element is the hood sum
-                    const uint32_t pk = kap[v];
-                    int best = 0;
-#pragma unroll
-                    for (int l = 1; l < L; ++l) {
-                        const int idx = best * L - best * (best + 1) / 2 + (l - best - 1);  // pair (best, l)
-                        const int kv = (int)(int8_t)((pk >> (8 * idx)) & 0xffu);
-                        if (cnt[best] - cnt[l] < kv) best = l;
-                    }
-                    s_emin[i] = Dtab[v * L + best];
-                    s_m[i] = (uint8_t)(dc - cnt[best]);
-                } else {
-                    s_emin[i] = hood_emin<L>(Dtab, v, cnt, dc, beta);
-                    s_m[i] = 0;
-                }
+                for (int l = 0; l < L; ++l) cnt[l] = __popc(m & lm[v * L + l]);
+                s_fix[i] = hood_emin_fix<L>(Dfix, v, cnt, dc, beta_fix);
             }
             __syncthreads();
-            for (int64_t c = c0 + threadIdx.x; c < c1; c += blockDim.x) {
-                const int64_t b = g.hood_off[c] - e0, e = g.hood_off[c + 1] - e0;
-                double SD = 0.0;
-                int ms = 0;
-                for (int64_t i = b; i < e; ++i) {
-                    SD += s_emin[i];
-                    ms += s_m[i];
-                }
-                const double S = fma(beta, (double)ms, SD);
+            for (int64_t c = c0 + threadIdx.x; c < c1; c += HT_THREADS) {
+                const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
+                __int128 sd = 0;
+                for (int i = b; i < e; ++i) sd += s_fix[i];
+                const double S = unfix80(sd);
                 if (mode == MODE_SWEEP) {
                     if (S_out) S_out[c] = S;
                 } else {
-                    my_unconv += (double)hood_history(S, c, g.C, t, cf, hist);
-                    my_S += S;
+                    my_unconv += hood_history(S, c, g.C, t, cf, hist);
+                    my_T += sd;
                 }
             }
         } else {
@@ -403,56 +430,60 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                 const int64_t k = g.hood_off[c + 1] - hb;
                 const int64_t nwh = (k + 31) >> 5;
                 const int64_t rb = g.row_off[c];
-                double S = 0.0;  // meaningful in thread 0
-                for (int64_t i0 = 0; i0 < k; i0 += blockDim.x) {
-                    const int64_t i = i0 + threadIdx.x;
-                    if (i < k) {
-                        const int64_t v = g.hood[hb + i];
-                        int cnt[L];
+                __int128 part = 0;
+                for (int64_t i = threadIdx.x; i < k; i += HT_THREADS) {
+                    const int64_t v = g.hood[hb + i];
+                    int cnt[L];
 #pragma unroll
-                        for (int l = 0; l < L; ++l) cnt[l] = 0;
-                        int dc = 0;
-                        for (int64_t w = 0; w < nwh; ++w) {
-                            uint32_t m = g.row[rb + i * nwh + w];
-                            dc += __popc(m);
-                            while (m) {
-                                const int b = __ffs(m) - 1;
-                                m &= m - 1;
-                                const int xl = x_in[g.hood[hb + w * 32 + b]];
+                    for (int l = 0; l < L; ++l) cnt[l] = 0;
+                    int dc = 0;
+                    for (int64_t w = 0; w < nwh; ++w) {
+                        uint32_t m = g.row[rb + i * nwh + w];
+                        dc += __popc(m);
+                        while (m) {
+                            const int bb = __ffs(m) - 1;
+                            m &= m - 1;
+                            const int xl = x_in[g.hood[hb + w * 32 + bb]];
 #pragma unroll
-                                for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
-                            }
+                            for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
                         }
-                        s_emin[threadIdx.x] = hood_emin<L>(Dtab, v, cnt, dc, beta);
                     }
-                    __syncthreads();
-                    if (threadIdx.x == 0) {
-                        const int64_t n = min((int64_t)blockDim.x, k - i0);
-                        for (int64_t j = 0; j < n; ++j) S += s_emin[j];
-                    }
-                    __syncthreads();
+                    part += hood_emin_fix<L>(Dfix, v, cnt, dc, beta_fix);
                 }
+                // exact integer sums: the reduction order does not matter
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) part += shfl_xor_i128(part, o);
+                __syncthreads();
+                if (lane_id() == 0) s_wsum[warp_id()] = part;
+                __syncthreads();
                 if (threadIdx.x == 0) {
+                    __int128 sd = 0;
+                    for (int w = 0; w < HT_THREADS / 32; ++w) sd += s_wsum[w];
+                    const double S = unfix80(sd);
                     if (mode == MODE_SWEEP) {
                         if (S_out) S_out[c] = S;
                     } else {
-                        my_unconv += (double)hood_history(S, c, g.C, t, cf, hist);
-                        my_S += S;
+                        my_unconv += hood_history(S, c, g.C, t, cf, hist);
+                        my_T += sd;
                     }
                 }
             }
         }
     }
     if (mode == MODE_SWEEP) return;
-    // per-tile partials: sum of hood sums, number of unconverged hoods
-    my_S = warp_sum(my_S);
-    my_unconv = warp_sum(my_unconv);
-    if (lane_id() == 0) { s_red[0][warp_id()] = my_S; s_red[1][warp_id()] = my_unconv; }
+    // per-tile partials: the exact sum of the tile's hood sums and the number
+    // of unconverged hoods (integer sums: any order gives the same result)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) my_T += shfl_xor_i128(my_T, o);
     __syncthreads();
-    if (threadIdx.x < 2) {
-        double acc = 0.0;
-        for (int w = 0; w < HT_THREADS / 32; ++w) acc += s_red[threadIdx.x][w];
-        hpart[(int64_t)tile.part * 2 + threadIdx.x] = acc;
+    if (lane_id() == 0) s_wsum[warp_id()] = my_T;
+    if (my_unconv) atomicAdd(&s_unconv, my_unconv);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __int128 a = 0;
+        for (int w = 0; w < HT_THREADS / 32; ++w) a += s_wsum[w];
+        hpart[(int64_t)tile.part * 2 + 0] = unfix80(a);
+        hpart[(int64_t)tile.part * 2 + 1] = (double)s_unconv;
     }
 }
 
@@ -599,7 +630,8 @@ __global__ void k_label_image(const int32_t* __restrict__ ids, const int64_t* __
 
 // tile table: vertex tiles then hood tiles, each grouped by slice
 __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const int64_t* __restrict__ hood_slice_off,
-                                  const int64_t* __restrict__ row_off, const int64_t* __restrict__ ht_first,
+                                  const int64_t* __restrict__ row_off, const int32_t* __restrict__ hood,
+                                  const int64_t* __restrict__ adj_off, const int64_t* __restrict__ ht_first,
                                   int32_t S, int64_t n_htiles, int32_t te, Tile* __restrict__ tiles,
                                   int64_t tile_base) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -618,10 +650,15 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
     t.a0 = (int32_t)c0;
     t.a1 = (int32_t)c1;
     t.part = (int32_t)k;
-    // fast when every hood has <= 32 members and the elements fit in shared memory
+    // fast when the elements fit in shared memory, every hood has <= 32
+    // members (one row word each) and every element's vertex has degree <= 32
     const int64_t ne = hood_off[c1] - hood_off[c0];
     bool fast = ne <= HT_CAP;
     if (fast && (row_off[c1] - row_off[c0]) != ne) fast = false;  // some hood needs > 1 word per row
+    for (int64_t e = hood_off[c0]; fast && e < hood_off[c1]; ++e) {
+        const int32_t v = hood[e];
+        if (adj_off[v + 1] - adj_off[v] > 32) fast = false;
+    }
     t.pad = fast ? 1 : 0;
     tiles[tile_base + k] = t;
 }
@@ -665,7 +702,7 @@ int free_plans(pmrf_graph* g) {
 int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
     void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_Dtab,
-                  w.d_kappa, w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
+                  w.d_lm, w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFree(p);
     g->em = EMWork();
@@ -678,7 +715,7 @@ int free_em(pmrf_graph* g) {
 namespace {
 
 int effective_tiles(const pmrf_graph* g, int* te, int* vt) {
-    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : 2048;
+    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : 1024;
     *vt = VT_THREADS;  // one vertex per thread
     (void)g;
     return PMRF_OK;
@@ -729,7 +766,8 @@ int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
     }
     if (p.n_htiles > 0) {
         k_make_hood_tiles<<<(unsigned)ceil_div(p.n_htiles, 256), 256, 0, s>>>(
-            g->d_hood_off, g->d_hood_slice_off, g->d_row_off, p.d_slice_ht0, S, p.n_htiles, te, p.d_tiles,
+            g->d_hood_off, g->d_hood_slice_off, g->d_row_off, g->d_hood, g->d_adj_off, p.d_slice_ht0, S, p.n_htiles,
+            te, p.d_tiles,
             p.n_vtiles);
         ::pmrf::note_launch(1);
     }
@@ -802,8 +840,8 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p) {
     if (!rc2) rc2 = walloc(&w.d_iters, S);
     if (!rc2) rc2 = walloc(&w.d_conv, S);
     if (!rc2) rc2 = walloc(&w.d_nactive, 1);
-    if (!rc2) rc2 = walloc(&w.d_Dtab, g->V * rc.L);  // data-term table D[v][l]
-    if (!rc2) rc2 = walloc(&w.d_kappa, g->V);        // integer label thresholds per vertex
+    if (!rc2) rc2 = walloc(&w.d_Dtab, g->V * rc.L);  // data term D[v][l], exact fixed point
+    if (!rc2) rc2 = walloc(&w.d_lm, g->V * rc.L);    // neighbour-label masks
     if (!rc2) rc2 = walloc((char**)&w.d_cfg, (int64_t)(sizeof(RunCfg) + sizeof(OutPtrs)));
     if (rc2) free_em(g);
     return rc2;
@@ -836,7 +874,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     EMWork& w = g->em;
     Launch z{g, p, view(g), p->d_tiles + 0, p->d_tiles + p->n_vtiles, (RunCfg*)w.d_cfg,
              (OutPtrs*)((char*)w.d_cfg + sizeof(RunCfg))};
-    double* Dtab = w.d_Dtab;
+    __int128* Dtab = w.d_Dtab;
     const int32_t S = g->S;
     // every slice active for INIT; nactive = S
     k_set_active_all<<<(unsigned)ceil_div(S, 256), 256, 0, s>>>(w.d_active, S); ::pmrf::note_launch(1);
@@ -860,13 +898,13 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (p->n_vtiles > 0) {
             k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
                                                                     xout, w.d_theta, Dtab, nullptr, nullptr,
-                                                                    w.d_vpart, g->d_status, w.d_kappa);
+                                                                    w.d_vpart, g->d_status, w.d_lm);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
         if (p->n_htiles > 0) {
             k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(z.dg, z.ht, MODE_EM, t, z.d_cfg, w.d_active, xin,
-                                                                  Dtab, w.d_hist, nullptr, w.d_hpart, w.d_kappa);
+                                                                  Dtab, w.d_hist, nullptr, w.d_hpart, w.d_lm);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
@@ -992,18 +1030,18 @@ namespace {
 
 template <int L>
 int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, const uint8_t* xin, const double* theta,
-               uint8_t* xout, double* Eout, double* Sout, double* Dtab, uint32_t* kap) {
+               uint8_t* xout, double* Eout, double* Sout, __int128* Dtab, uint32_t* lm) {
     DevGraph dg = view(g);
     const Tile* vt = p->d_tiles;
     const Tile* ht = p->d_tiles + p->n_vtiles;
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
-                                                                Dtab, nullptr, Eout, nullptr, g->d_status, kap);
+                                                                Dtab, nullptr, Eout, nullptr, g->d_status, lm);
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
         k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(dg, ht, MODE_SWEEP, 1, d_cfg, nullptr, xin, Dtab,
-                                                              nullptr, Sout, nullptr, kap);
+                                                              nullptr, Sout, nullptr, lm);
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
@@ -1061,7 +1099,7 @@ int sweep_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* xin, const d
     PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
     int r = PMRF_OK;
     DISPATCH_L(rc.L, r = sweep_body<L>(g, p, s, (const RunCfg*)w.d_cfg, xin, theta, xout, Eout, Sout,
-                                       w.d_Dtab, w.d_kappa));
+                                       w.d_Dtab, w.d_lm));
     PMRF_CUDA(cudaStreamSynchronize(s));  // the host RunCfg copy is a stack value
     return r;
 }
@@ -1130,7 +1168,7 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
         rc = fail(PMRF_ERR_CUDA, "event creation failed");
     pmrf_tuning keep = g->tuning, win = g->tuning;
     float best_ms = 1e30f;
-    const int cands[] = {1024, 2048, 4096};
+    const int cands[] = {512, 768, 1024};
     for (int c = 0; c < 3 && !rc; ++c) {
         pmrf_tuning t = keep;
         t.hood_tile = cands[c];

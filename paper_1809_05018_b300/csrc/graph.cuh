@@ -38,8 +38,8 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     double* d_hpart = nullptr;     // [n_htiles][2] (T partial, unconverged count)
     double* d_theta = nullptr;     // [S][L][4] current parameters
     double* d_Thist = nullptr;     // [S][W] ring of totals
-    double* d_Dtab = nullptr;      // [V][L] data term of the current iteration
-    uint32_t* d_kappa = nullptr;   // [V] packed int8 label-pair thresholds (L <= 3)
+    __int128* d_Dtab = nullptr;    // [V][L] data term of the current iteration, units of 2^-80
+    uint32_t* d_lm = nullptr;      // [V][L] neighbour-label masks over each vertex's adjacency slots
     int32_t* d_active = nullptr;   // [S] slice still iterating
     int32_t* d_iters = nullptr;    // [S]
     int32_t* d_conv = nullptr;     // [S]
@@ -80,6 +80,7 @@ struct pmrf_graph {
     uint32_t* d_rep_el = nullptr;        // [N_el] element of each replica (ascending per vertex)
     int64_t* d_rep_woff = nullptr;       // [V+1] word offsets of replica slot masks
     uint32_t* d_rep_mask = nullptr;      // [n_rep_words]
+    uint32_t* d_el_slot = nullptr;       // [N_el] slot mask of each hood element (degree <= 32), hood-major
     pmrf::DevStatus* d_status = nullptr;
 
     pmrf_tuning tuning{0, 0, 0, 1, 0};
