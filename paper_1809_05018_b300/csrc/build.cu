@@ -70,53 +70,113 @@ __global__ void k_vert_off(const int64_t* __restrict__ ex, const int64_t* __rest
     if (s <= S) vert_off[s] = ex[rank_off[s]];
 }
 
-// per-pixel vertex with warp-aggregated counting: lanes holding the same
-// vertex add once
-__global__ void k_count_pix(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
-                            const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
-                            int32_t* __restrict__ npix) {
+// pixel counts and bounding boxes (rows and columns inside the slice) of
+// every region, warp-aggregated: lanes holding the same vertex combine first
+__global__ void k_count_bbox(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                             const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
+                             const int32_t* __restrict__ rank, int32_t* __restrict__ npix, int4* __restrict__ bbox) {
     const int s = blockIdx.y;
-    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s];
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
         const int64_t p = base + threadIdx.x;
         const bool ok = p < e;
         const int32_t v = ok ? vertex_of(ids, rank, rb, p) : -1 - lane_id();
         const unsigned grp = __match_any_sync(0xffffffffu, v);
-        if (ok && lane_id() == __ffs(grp) - 1) atomicAdd(&npix[v], __popc(grp));
+        const int64_t q = p - b;
+        const unsigned r = ok ? (unsigned)(q / W) : 0u, c = ok ? (unsigned)(q - (q / W) * W) : 0u;
+        const unsigned rmin = __reduce_min_sync(grp, r), rmax = __reduce_max_sync(grp, r);
+        const unsigned cmin = __reduce_min_sync(grp, c), cmax = __reduce_max_sync(grp, c);
+        if (ok && lane_id() == __ffs(grp) - 1) {
+            atomicAdd(&npix[v], __popc(grp));
+            atomicMin(&bbox[v].x, (int)rmin);
+            atomicMax(&bbox[v].y, (int)rmax);
+            atomicMin(&bbox[v].z, (int)cmin);
+            atomicMax(&bbox[v].w, (int)cmax);
+        }
     }
+}
+
+__global__ void k_init_bbox(int4* __restrict__ bbox, int64_t V) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V) bbox[v] = make_int4(0x7fffffff, -1, 0x7fffffff, -1);
+}
+
+// raw id of every vertex (inverse of the compaction map)
+__global__ void k_inv_rank(const int32_t* __restrict__ rank, const int64_t* __restrict__ rank_off, int32_t S,
+                           int64_t n, int32_t* __restrict__ inv) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int32_t v = rank[i];
+    if (v < 0) return;
+    const int s = (int)(upper_bound_dev<int64_t>(rank_off, 0, S + 1, i) - 1);
+    inv[v] = (int32_t)(i - rank_off[s]);
+}
+
+// y_v for compact regions: the region's bounding box scanned in row-major
+// order, adding the pixels that carry its id -- the same additions, in the
+// same order, as a serial row-major accumulation.  Regions whose box is much
+// larger than their pixel count are flagged for the pixel-list path.
+__global__ void k_means_bbox(const double* __restrict__ img, const int32_t* __restrict__ ids,
+                             const int64_t* __restrict__ pix_off, const int64_t* __restrict__ Wd,
+                             const int64_t* __restrict__ vert_off, int32_t S, const int32_t* __restrict__ inv,
+                             const int4* __restrict__ bbox, const int32_t* __restrict__ npix, int64_t V,
+                             double* __restrict__ y, int32_t* __restrict__ fb_pix) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int4 bb = bbox[v];
+    const int64_t n = npix[v];
+    const int64_t area = (int64_t)(bb.y - bb.x + 1) * (int64_t)(bb.w - bb.z + 1);
+    if (area > 4 * n + 64) {
+        fb_pix[v] = (int32_t)n;
+        return;
+    }
+    fb_pix[v] = 0;
+    const int s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
+    const int64_t b = pix_off[s], W = Wd[s];
+    const int32_t id = inv[v];
+    double acc = 0.0;
+    for (int r = bb.x; r <= bb.y; ++r) {
+        const int64_t row = b + (int64_t)r * W;
+        for (int c = bb.z; c <= bb.w; ++c)
+            if (ids[row + c] == id) acc += img[row + c];
+    }
+    y[v] = acc / (double)n;
 }
 
 __global__ void k_fill_pix(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
                            const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
                            const int64_t* __restrict__ vpix_off, int32_t* __restrict__ cursor,
-                           uint32_t* __restrict__ pixlist) {
+                           uint32_t* __restrict__ pixlist, const int32_t* __restrict__ only) {
     const int s = blockIdx.y;
     const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
         const int64_t p = base + threadIdx.x;
         const bool ok = p < e;
-        const int32_t v = ok ? vertex_of(ids, rank, rb, p) : -1 - lane_id();
+        int32_t v = ok ? vertex_of(ids, rank, rb, p) : -1 - lane_id();
+        const bool take = ok && (only == nullptr || only[v] != 0);
+        if (!take) v = -1 - lane_id();
         const unsigned grp = __match_any_sync(0xffffffffu, v);
         const int leader = __ffs(grp) - 1;
         int slot = 0;
-        if (ok && lane_id() == leader) slot = atomicAdd(&cursor[v], __popc(grp));
+        if (take && lane_id() == leader) slot = atomicAdd(&cursor[v], __popc(grp));
         slot = __shfl_sync(grp, slot, leader);
-        if (ok) {
+        if (take) {
             const int rk = __popc(grp & ((1u << lane_id()) - 1u));
             pixlist[vpix_off[v] + slot + rk] = (uint32_t)p;
         }
     }
 }
 
-// y_v: the region's pixels added one by one in row-major order, then divided
-// by the count (the same sequence of IEEE operations as a serial row-major
-// accumulation).
+// y_v from a region's sorted pixel list: the pixels added one by one in
+// row-major order, then divided by the count (the same sequence of IEEE
+// operations as a serial row-major accumulation).
 __global__ void k_means(const double* __restrict__ img, const uint32_t* __restrict__ pixlist,
                         const int64_t* __restrict__ vpix_off, int64_t V, double* __restrict__ y) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
+    if (vpix_off[v + 1] == vpix_off[v]) return;  // region summed by k_means_bbox
     double acc = 0.0;
     const int64_t b = vpix_off[v], e = vpix_off[v + 1];
     for (int64_t i = b; i < e; ++i) acc += img[pixlist[i]];
@@ -439,31 +499,44 @@ __global__ void k_list_general(const int64_t* __restrict__ adj_off, int64_t V, i
 }
 
 // ---------------------------------------------------------------------------
-// hoods: candidates = every member plus all its neighbours; sort+unique per clique
+// hoods: H_c = K_c plus the neighbours of its members.  For a clique of two or
+// more members every member is a neighbour of another member, so H_c is the
+// union of the members' (sorted) adjacency lists: a k-way merge per clique.  A
+// one-member maximal clique is an isolated vertex, whose hood is itself.
 
-__global__ void k_hood_count(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
-                             const int64_t* __restrict__ adj_off, int64_t C, int64_t* __restrict__ cnt) {
+template <bool FILL>
+__global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
+                             const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t C,
+                             int32_t* __restrict__ hsize, const int64_t* __restrict__ hood_off,
+                             int32_t* __restrict__ hood) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
-    int64_t n = 0;
-    for (int64_t i = clq_off[c]; i < clq_off[c + 1]; ++i) {
-        int32_t u = clq[i];
-        n += 1 + adj_off[u + 1] - adj_off[u];
+    const int64_t m0 = clq_off[c];
+    const int m = (int)(clq_off[c + 1] - m0);
+    int32_t* out = FILL ? hood + hood_off[c] : nullptr;
+    if (m == 1) {
+        if (FILL) out[0] = clq[m0];
+        else hsize[c] = 1;
+        return;
     }
-    cnt[c] = n;
-}
-
-__global__ void k_hood_fill(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
-                            const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t C,
-                            const int64_t* __restrict__ hc_off, uint32_t* __restrict__ hc) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    int64_t o = hc_off[c];
-    for (int64_t i = clq_off[c]; i < clq_off[c + 1]; ++i) {
-        int32_t u = clq[i];
-        hc[o++] = (uint32_t)u;
-        for (int64_t j = adj_off[u]; j < adj_off[u + 1]; ++j) hc[o++] = (uint32_t)adj[j];
+    int64_t p[MAX_CLIQUE + 1], e[MAX_CLIQUE + 1];
+    for (int i = 0; i < m; ++i) {
+        const int32_t u = clq[m0 + i];
+        p[i] = adj_off[u];
+        e[i] = adj_off[u + 1];
     }
+    int32_t n = 0;
+    while (true) {
+        int32_t cur = 0x7fffffff;
+        for (int i = 0; i < m; ++i)
+            if (p[i] < e[i]) cur = min(cur, adj[p[i]]);
+        if (cur == 0x7fffffff) break;
+        if (FILL) out[n] = cur;
+        ++n;
+        for (int i = 0; i < m; ++i)
+            if (p[i] < e[i] && adj[p[i]] == cur) ++p[i];
+    }
+    if (!FILL) hsize[c] = n;
 }
 
 // ---------------------------------------------------------------------------
@@ -653,29 +726,44 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     g->V = V;
     if (V >= 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "more than 2^31-1 regions");
 
-    // 3. region means (row-major order per region)
+    // 3. region means (row-major order per region): bounding-box scan for
+    //    compact regions, sorted pixel lists for the rest
     PMRF_TRY(dalloc(&g->d_npix, V, s));
     PMRF_TRY(dalloc(&g->d_y, V, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_npix, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     int64_t* d_vpix_off = nullptr;
     int32_t* d_cursor = nullptr;
-    uint32_t* d_pixlist = nullptr;
+    int4* d_bbox = nullptr;
+    int32_t *d_inv = nullptr, *d_fbpix = nullptr;
     PMRF_TRY(tmp.get(&d_vpix_off, V + 1));
     PMRF_TRY(tmp.get(&d_cursor, V));
-    PMRF_TRY(tmp.get(&d_pixlist, g->n_pix));
+    PMRF_TRY(tmp.get(&d_bbox, V));
+    PMRF_TRY(tmp.get(&d_inv, V));
+    PMRF_TRY(tmp.get(&d_fbpix, V));
+    LAUNCH_1D(k_init_bbox, V, d_bbox, V);
     if (g->n_pix > 0) {
-        k_count_pix<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_rank_off, g->d_rank, g->d_npix); ::pmrf::note_launch(1);
+        k_count_bbox<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank, g->d_npix,
+                                                   d_bbox);
+        ::pmrf::note_launch(1);
         PMRF_CUDA(cudaGetLastError());
     }
-    PMRF_TRY(exclusive_scan_i32_to_i64(g->d_npix, d_vpix_off, V, s));
-    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-    if (g->n_pix > 0) {
+    LAUNCH_1D(k_inv_rank, g->n_rank, g->d_rank, g->d_rank_off, S, g->n_rank, d_inv);
+    LAUNCH_1D(k_means_bbox, V, d_img, d_ids, g->d_pix_off, g->d_W, g->d_vert_off, S, d_inv, d_bbox, g->d_npix, V,
+              g->d_y, d_fbpix);
+    PMRF_TRY(exclusive_scan_i32_to_i64(d_fbpix, d_vpix_off, V, s));
+    int64_t nfb = 0;
+    PMRF_TRY(read_i64(d_vpix_off + V, &nfb, s));
+    if (nfb > 0) {
+        uint32_t* d_pixlist = nullptr;
+        PMRF_TRY(tmp.get(&d_pixlist, nfb));
+        PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
         k_fill_pix<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_rank_off, g->d_rank, d_vpix_off, d_cursor,
-                                                 d_pixlist); ::pmrf::note_launch(1);
+                                                 d_pixlist, d_fbpix);
+        ::pmrf::note_launch(1);
         PMRF_CUDA(cudaGetLastError());
+        PMRF_TRY(segmented_sort_u32(d_pixlist, d_vpix_off, V, nfb, false, nullptr, g->d_status, s));
+        LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y);
     }
-    PMRF_TRY(segmented_sort_u32(d_pixlist, d_vpix_off, V, g->n_pix, false, nullptr, g->d_status, s));
-    LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y);
 
     // 4. adjacency
     int32_t* d_cnt = nullptr;
@@ -796,27 +884,17 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(check_status(g, s));
 
     // 6. hoods
-    int64_t *d_hc_cnt = nullptr, *d_hc_off = nullptr;
-    PMRF_TRY(tmp.get(&d_hc_cnt, C));
-    PMRF_TRY(tmp.get(&d_hc_off, C + 1));
-    LAUNCH_1D(k_hood_count, C, g->d_clq_off, g->d_clq, g->d_adj_off, C, d_hc_cnt);
-    PMRF_TRY(exclusive_scan_i64(d_hc_cnt, d_hc_off, C, s));
-    int64_t nhc = 0;
-    PMRF_TRY(read_i64(d_hc_off + C, &nhc, s));
-    if (nhc >= 4294967295ll) return fail(PMRF_ERR_UNSUPPORTED, "hood candidate list longer than 2^32");
-    uint32_t* d_hc = nullptr;
-    PMRF_TRY(tmp.get(&d_hc, nhc));
-    LAUNCH_1D(k_hood_fill, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, d_hc_off, d_hc);
     int32_t* d_hsize = nullptr;
     PMRF_TRY(tmp.get(&d_hsize, C));
-    PMRF_TRY(segmented_sort_u32(d_hc, d_hc_off, C, nhc, true, d_hsize, g->d_status, s));
+    LAUNCH_1D(k_hood_merge<false>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, d_hsize, nullptr, nullptr);
     PMRF_TRY(dalloc(&g->d_hood_off, C + 1, s));
     PMRF_TRY(exclusive_scan_i32_to_i64(d_hsize, g->d_hood_off, C, s));
     PMRF_TRY(read_i64(g->d_hood_off + C, &g->N_el, s));
     const int64_t N_el = g->N_el;
     if (N_el >= 4294967295ll) return fail(PMRF_ERR_UNSUPPORTED, "more than 2^32-1 hood elements");
     PMRF_TRY(dalloc(&g->d_hood, N_el, s));
-    LAUNCH_1D(k_compact, C, d_hc, d_hc_off, g->d_hood_off, C, g->d_hood);
+    LAUNCH_1D(k_hood_merge<true>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, nullptr, g->d_hood_off,
+              g->d_hood);
 
     // 7. replica structures and masks
     int32_t *d_el_hood = nullptr, *d_rcount = nullptr, *d_hmax = nullptr;

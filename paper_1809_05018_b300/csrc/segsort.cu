@@ -20,9 +20,7 @@ namespace pmrf {
 namespace {
 
 constexpr int SORT_THREADS = 512;
-constexpr int SORT_CAP = 4096;       // keys per shared-memory group
 constexpr int SMALL_MAX = 2048;      // longest segment sorted in shared memory
-constexpr int WINDOW = 2048;         // segment starts per tile window
 constexpr int WARP_MAX = 256;        // longest segment sorted by one warp in registers
 
 __device__ __forceinline__ void bitonic_sort_smem(uint64_t* key, int npow2) {
@@ -44,42 +42,28 @@ __device__ __forceinline__ void bitonic_sort_smem(uint64_t* key, int npow2) {
     }
 }
 
-// One CTA per window of segment starts.  Sorts the window's medium segments
-// (WARP_MAX < length <= SMALL_MAX) one at a time in shared memory; short ones
-// belong to k_sort_warp and long ones to the bitmap kernels.
-__global__ void __launch_bounds__(SORT_THREADS) k_sort_small(uint32_t* __restrict__ vals,
-                                                             const int64_t* __restrict__ off, int64_t nseg,
-                                                             int64_t n, int unique, int32_t* __restrict__ ucount) {
-    __shared__ uint64_t key[SORT_CAP];
-    __shared__ int64_t s_k0, s_k1;
-    const int64_t wlo = (int64_t)blockIdx.x * WINDOW, whi = wlo + WINDOW;
-    if (threadIdx.x == 0) {
-        // segments with start in [wlo, whi); empty segments at the same start
-        // are included by the first window whose range holds that start.
-        s_k0 = lower_bound_dev<int64_t>(off, 0, nseg, wlo);
-        s_k1 = lower_bound_dev<int64_t>(off, 0, nseg, whi);
-        if (whi > n) s_k1 = nseg;  // last window takes the trailing (empty) segments
-    }
+// One CTA per listed medium segment (WARP_MAX < length <= SMALL_MAX): bitonic
+// sort of the segment in shared memory.
+__global__ void __launch_bounds__(SORT_THREADS) k_sort_medium(uint32_t* __restrict__ vals,
+                                                              const int64_t* __restrict__ off,
+                                                              const int64_t* __restrict__ list, int unique,
+                                                              int32_t* __restrict__ ucount) {
+    __shared__ uint64_t key[SMALL_MAX];
+    const int64_t k = list[blockIdx.x];
+    const int64_t gstart = off[k];
+    const int cnt = (int)(off[k + 1] - gstart);
+    int npow2 = 1;
+    while (npow2 < cnt) npow2 <<= 1;
+    for (int i = threadIdx.x; i < npow2; i += blockDim.x) key[i] = (i < cnt) ? (uint64_t)vals[gstart + i] : ~0ull;
     __syncthreads();
-    const int64_t k0 = s_k0, k1 = s_k1;
-    for (int64_t k = k0; k < k1; ++k) {
-        const int64_t gstart = off[k];
-        const int cnt = (int)(off[k + 1] - gstart);
-        if (cnt <= WARP_MAX || cnt > SMALL_MAX) continue;  // warp kernel / bitmap path
-        int npow2 = 1;
-        while (npow2 < cnt) npow2 <<= 1;
-        for (int i = threadIdx.x; i < npow2; i += blockDim.x) key[i] = (i < cnt) ? (uint64_t)vals[gstart + i] : ~0ull;
-        __syncthreads();
-        bitonic_sort_smem(key, npow2);
-        if (!unique) {
-            for (int i = threadIdx.x; i < cnt; i += blockDim.x) vals[gstart + i] = (uint32_t)key[i];
-        } else if (threadIdx.x == 0) {
-            int u = 0;
-            for (int i = 0; i < cnt; ++i)
-                if (i == 0 || key[i] != key[i - 1]) vals[gstart + u++] = (uint32_t)key[i];
-            ucount[k] = u;
-        }
-        __syncthreads();
+    bitonic_sort_smem(key, npow2);
+    if (!unique) {
+        for (int i = threadIdx.x; i < cnt; i += blockDim.x) vals[gstart + i] = (uint32_t)key[i];
+    } else if (threadIdx.x == 0) {
+        int u = 0;
+        for (int i = 0; i < cnt; ++i)
+            if (i == 0 || key[i] != key[i - 1]) vals[gstart + u++] = (uint32_t)key[i];
+        ucount[k] = u;
     }
 }
 
@@ -179,14 +163,13 @@ __global__ void __launch_bounds__(256) k_sort_warp(uint32_t* __restrict__ vals, 
     }
 }
 
-__global__ void k_mark_big(const int64_t* __restrict__ off, int64_t nseg, int64_t* __restrict__ list,
-                           int32_t* __restrict__ nlist) {
+__global__ void k_mark_long(const int64_t* __restrict__ off, int64_t nseg, int64_t* __restrict__ mlist,
+                            int32_t* __restrict__ nm, int64_t* __restrict__ blist, int32_t* __restrict__ nb) {
     int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= nseg) return;
-    if (off[k + 1] - off[k] > SMALL_MAX) {
-        int slot = atomicAdd(nlist, 1);
-        list[slot] = k;
-    }
+    const int64_t len = off[k + 1] - off[k];
+    if (len > SMALL_MAX) blist[atomicAdd(nb, 1)] = k;
+    else if (len > WARP_MAX) mlist[atomicAdd(nm, 1)] = k;
 }
 
 __global__ void __launch_bounds__(1024) k_big_minmax(const uint32_t* __restrict__ vals,
@@ -275,8 +258,8 @@ __global__ void __launch_bounds__(1024) k_big_bitmap(uint32_t* __restrict__ vals
 
 int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t n, bool unique, int32_t* ucount,
                        DevStatus* st, cudaStream_t s) {
+    (void)n;
     if (nseg <= 0) return PMRF_OK;
-    const int64_t nwin = ceil_div(n > 0 ? n : 1, WINDOW);
     {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
@@ -285,21 +268,28 @@ int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t
         k_sort_warp<<<(unsigned)blocks, 256, 0, s>>>(vals, off, nseg, unique ? 1 : 0, ucount);
         ::pmrf::note_launch(1);
     }
-    k_sort_small<<<(unsigned)nwin, SORT_THREADS, 0, s>>>(vals, off, nseg, n, unique ? 1 : 0, ucount); ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
 
-    // big segments
-    int64_t* list = nullptr;
-    int32_t* nlist = nullptr;
-    PMRF_TRY(dalloc(&nlist, 1, s));
-    int rc = dalloc(&list, nseg, s);
-    if (rc) { dfree(nlist, s); return rc; }
-    cudaMemsetAsync(nlist, 0, sizeof(int32_t), s);
-    k_mark_big<<<(unsigned)ceil_div(nseg, 256), 256, 0, s>>>(off, nseg, list, nlist); ::pmrf::note_launch(1);
-    int32_t nbig = 0;
-    cudaMemcpyAsync(&nbig, nlist, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    // medium and long segments: listed first (order of the lists does not
+    // matter: each segment is sorted on its own)
+    int64_t *mlist = nullptr, *list = nullptr;
+    int32_t* cnts = nullptr;
+    PMRF_TRY(dalloc(&cnts, 2, s));
+    int rc = dalloc(&mlist, nseg, s);
+    if (!rc) rc = dalloc(&list, nseg, s);
+    if (rc) { dfree(cnts, s); dfree(mlist, s); dfree(list, s); return rc; }
+    cudaMemsetAsync(cnts, 0, 2 * sizeof(int32_t), s);
+    k_mark_long<<<(unsigned)ceil_div(nseg, 256), 256, 0, s>>>(off, nseg, mlist, cnts, list, cnts + 1);
+    ::pmrf::note_launch(1);
+    int32_t hc[2] = {0, 0};
+    cudaMemcpyAsync(hc, cnts, sizeof(hc), cudaMemcpyDeviceToHost, s);
     cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) { dfree(nlist, s); dfree(list, s); return cuda_fail(e, "segmented sort"); }
+    if (e != cudaSuccess) { dfree(cnts, s); dfree(mlist, s); dfree(list, s); return cuda_fail(e, "segmented sort"); }
+    const int32_t nmed = hc[0], nbig = hc[1];
+    if (nmed > 0) {
+        k_sort_medium<<<nmed, SORT_THREADS, 0, s>>>(vals, off, mlist, unique ? 1 : 0, ucount);
+        ::pmrf::note_launch(1);
+    }
     if (nbig > 0) {
         uint32_t *mn = nullptr, *mx = nullptr;
         int64_t* bmo = nullptr;
@@ -308,12 +298,13 @@ int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t
         if (!rc) rc = dalloc(&mx, nbig, s);
         if (!rc) rc = dalloc(&bmo, nbig + 1, s);
         if (!rc) {
-            k_big_minmax<<<nbig, 1024, 0, s>>>(vals, off, list, mn, mx); ::pmrf::note_launch(1);
+            k_big_minmax<<<nbig, 1024, 0, s>>>(vals, off, list, mn, mx);
+            ::pmrf::note_launch(1);
             std::vector<uint32_t> hmn(nbig), hmx(nbig);
             cudaMemcpyAsync(hmn.data(), mn, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, s);
             cudaMemcpyAsync(hmx.data(), mx, sizeof(uint32_t) * nbig, cudaMemcpyDeviceToHost, s);
             e = cudaStreamSynchronize(s);
-            if (e != cudaSuccess) rc = cuda_fail(e, "segmented sort (big)");
+            if (e != cudaSuccess) rc = cuda_fail(e, "segmented sort (long)");
             if (!rc) {
                 std::vector<int64_t> hbo(nbig + 1, 0);
                 for (int i = 0; i < nbig; ++i) hbo[i + 1] = hbo[i] + ceil_div((int64_t)hmx[i] - hmn[i] + 1, 32);
@@ -321,19 +312,22 @@ int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t
                 rc = dalloc(&bm, hbo[nbig], s);
                 if (!rc) {
                     cudaMemsetAsync(bm, 0, sizeof(uint32_t) * hbo[nbig], s);
-                    k_big_bitmap<<<nbig, 1024, 0, s>>>(vals, off, list, mn, bmo, bm, unique ? 1 : 0, ucount, st); ::pmrf::note_launch(1);
+                    k_big_bitmap<<<nbig, 1024, 0, s>>>(vals, off, list, mn, bmo, bm, unique ? 1 : 0, ucount, st);
+                    ::pmrf::note_launch(1);
                     e = cudaGetLastError();
                     if (e != cudaSuccess) rc = cuda_fail(e, "k_big_bitmap");
                     // the host vector hbo must outlive the async copy
                     cudaError_t e2 = cudaStreamSynchronize(s);
-                    if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "segmented sort (big)");
+                    if (!rc && e2 != cudaSuccess) rc = cuda_fail(e2, "segmented sort (long)");
                 }
             }
         }
         dfree(mn, s); dfree(mx, s); dfree(bmo, s); dfree(bm, s);
     }
-    dfree(nlist, s);
+    dfree(cnts, s);
+    dfree(mlist, s);
     dfree(list, s);
+    PMRF_CUDA(cudaGetLastError());
     return rc;
 }
 

@@ -63,7 +63,13 @@ def test_graph_edge_cases():
     img = np.random.default_rng(0).random((H, W))
     big = (img, ids)
     empty = (np.zeros((0, 5)), np.zeros((0, 5), np.int32))
-    cases = [one, big, empty]
+    # a diagonal region (40 pixels spread over a 40x40 box) takes the sorted
+    # pixel-list path for its mean; a few scattered pixels of a third id too
+    did = np.full((40, 40), 3, np.int32)
+    did[np.arange(40), np.arange(40)] = 7
+    did[[0, 39, 5, 33], [39, 0, 20, 2]] = 11
+    diag = (np.random.default_rng(1).random((40, 40)), did)
+    cases = [one, big, empty, diag]
     imgs = [torch.from_numpy(a).cuda() for a, _ in cases]
     idt = [torch.from_numpy(b).cuda() for _, b in cases]
     g = pmrf.build_graph(imgs, idt)
