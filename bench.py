@@ -122,6 +122,30 @@ def load_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
+STACKS = ("stack512", "grad64")
+
+
+def shard_workload(name: str, n: int | None, rank: int):
+    """Rank `rank`'s batch.  Stacks are split into consecutive runs of n slices,
+    one run per rank (disjoint: every rank adds n new slices -- weak scaling);
+    single-slice workloads are replicated on every rank."""
+    base = synth.workload(name)
+    if name not in STACKS:
+        return base
+    n = n or len(base.slices)
+    return synth.workload(name, n_slices=n, first_slice=rank * n)
+
+
+def max_over_ranks(x: float, world: int, device):
+    """The largest value over all ranks (the step time of the slowest rank)."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    if world > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t)
+
+
 def host_inputs(wl, threads=None):
     sl = synth.make_stack(wl.slices, threads=threads or os.cpu_count())
     img = np.stack([s.image for s in sl])
@@ -169,10 +193,7 @@ def run_ours(a):
         if world > 1:
             dist.barrier()
 
-    base = synth.workload(a.workload)
-    n = a.slices or len(base.slices)
-    wl = synth.workload(a.workload, n_slices=n, first_slice=rank * n) if a.workload in ("stack512", "grad64") \
-        else base
+    wl = shard_workload(a.workload, a.slices, rank)
     t0 = time.time()
     sl, img_np, ids_np = host_inputs(wl)
     gen_s = time.time() - t0
@@ -212,11 +233,7 @@ def run_ours(a):
         torch.cuda.synchronize()
     barrier()
     launches = pmrf.launch_count() - n0
-    ms = e0.elapsed_time(e1) / a.steps
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms = float(ms_t)
+    ms = max_over_ranks(e0.elapsed_time(e1) / a.steps, world, "cuda")
     value = S * world / (ms / 1e3)
 
     # ---- the EM loop alone, profiled per kernel (same graph, same inputs)
@@ -294,10 +311,8 @@ def run_ours(a):
         x1.record()
         torch.cuda.synchronize()
         barrier()
-        ems = torch.tensor([x0.elapsed_time(x1) / a.steps], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(ems, op=dist.ReduceOp.MAX)
-        e2e = {"value": S * world / (float(ems) / 1e3), "unit": "slices/s",
+        ems = max_over_ranks(x0.elapsed_time(x1) / a.steps, world, "cuda")
+        e2e = {"value": S * world / (ems / 1e3), "unit": "slices/s",
                "h2d_bytes_per_step": int(img_np.nbytes + ids_np.nbytes), "d2h_bytes_per_step": int(img_np.size)}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
@@ -357,7 +372,7 @@ def run_reference(a):
     import oracle
     base = synth.workload(a.workload)
     n = max(1, min(a.steps + a.warmup, len(base.slices)))
-    wl = synth.workload(a.workload, n_slices=n) if a.workload in ("stack512", "grad64") else base
+    wl = shard_workload(a.workload, n, 0)
     sl = synth.make_stack(wl.slices)
     cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters)
 
