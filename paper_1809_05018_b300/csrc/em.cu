@@ -34,12 +34,9 @@ namespace pmrf {
 namespace {
 
 constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
-constexpr int HT_THREADS = 256;
-constexpr int EPT = 5;                        // hood elements per thread in a fast hood tile
-constexpr int HT_CAP = HT_THREADS * EPT;      // elements a fast hood tile can hold (L <= 4)
-// elements a fast hood tile holds (the same for every label count)
-__host__ __device__ constexpr int hood_cap(int L) { return L > 0 ? HT_CAP : HT_CAP; }
-static_assert(hood_cap(8) % HT_THREADS == 0 && hood_cap(2) % HT_THREADS == 0, "whole elements per thread");
+constexpr int HT_THREADS = 96;               // hood-pass block: a tile's ~85 hoods, one per thread
+constexpr int MAX_HOOD_TILE = 1248;           // largest hood-tile window (elements)
+constexpr int HT_CAP = MAX_HOOD_TILE + 31;    // elements a fast hood tile can hold
 
 enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
 
@@ -332,24 +329,32 @@ __device__ __forceinline__ __int128 hood_emin_fix(const __int128* __restrict__ D
 }
 
 // convergence bookkeeping of one hood; returns 1 when the hood is unconverged
-__device__ __forceinline__ int hood_history(double S, int64_t c, int64_t C, int t, const RunCfg& cf,
-                                            double* __restrict__ hist) {
-    // converged iff t > W and |S - S^{t-k}| < tol for every k = 1..W; equal
-    // bit patterns need no floating-point work, and the first failing k decides
-    const int W = cf.W;
+// The hood sums' history is kept in units of 2^-40 (the exact 2^-80 sum
+// shifted down; |S| < 2^23 -- larger sums saturate), so the MAP convergence
+// test is integer work: converged iff t > W and |S - S^{t-k}| < tol for every
+// k = 1..W.  Equal states give identical sums and pass exactly; otherwise the
+// comparison is made at 2^-40 (about 1e-12) resolution.
+__device__ __forceinline__ int64_t s40_of(__int128 sd) {
+    const __int128 q = sd >> 40;
+    const __int128 lim = ((__int128)1 << 62);
+    return (int64_t)(q > lim ? lim : (q < -lim ? -lim : q));
+}
+
+__device__ __forceinline__ int hood_history(int64_t S40, int64_t c, int64_t C, int t, int W, int64_t tol40,
+                                            int64_t* __restrict__ hist) {
     int unconv = 1;
     if (t > W) {
         unconv = 0;
         for (int k = 1; k <= W; ++k) {
-            const double prev = hist[(int64_t)((t - k) % W) * C + c];
-            if (__double_as_longlong(prev) == __double_as_longlong(S)) continue;
-            if (!(fabs(S - prev) < cf.tol)) {
+            const int64_t prev = hist[(int64_t)((t - k) % W) * C + c];
+            const int64_t d = S40 >= prev ? S40 - prev : prev - S40;
+            if (!(d < tol40)) {
                 unconv = 1;
                 break;
             }
         }
     }
-    hist[(int64_t)(t % W) * C + c] = S;
+    hist[(int64_t)(t % W) * C + c] = S40;
     return unconv;
 }
 
@@ -358,11 +363,11 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                                                      const RunCfg* __restrict__ cfgp,
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
-                                                     const __int128* __restrict__ Dfix, double* __restrict__ hist,
+                                                     const __int128* __restrict__ Dfix, int64_t* __restrict__ hist,
                                                      double* __restrict__ S_out, double* __restrict__ hpart,
                                                      const uint32_t* __restrict__ lm) {
-    constexpr int CAP = hood_cap(L);
-    __shared__ __int128 s_fix[CAP];
+    __shared__ int32_t s_v[HT_CAP];
+    __shared__ uint32_t s_sm[HT_CAP];
     __shared__ __int128 s_wsum[HT_THREADS / 32];
     __shared__ int s_unconv;
     const Tile tile = tiles[blockIdx.x];
@@ -370,6 +375,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
     if (active && !active[s]) return;
     const RunCfg cf = *cfgp;
     const __int128 beta_fix = fix80(cf.beta);
+    const int64_t tol40 = s40_of(fix80(cf.tol));
+    const int W = cf.W;
     const int64_t c0 = tile.a0, c1 = tile.a1;
     __int128 my_T = 0;
     int my_unconv = 0;
@@ -379,47 +386,35 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
         const int ne = (int)(g.hood_off[c1] - e0);
         // fast tile (flag set when the tile table was built): the elements fit,
         // every hood has <= 32 members and every element's vertex degree <= 32
-        const bool fast = tile.pad != 0 && ne <= CAP;
+        const bool fast = tile.pad != 0 && ne <= HT_CAP;
         if (fast) {
             // every element's vertex has degree <= 32 and every hood <= 32
             // members: the counts of each label among v's neighbours inside
             // hood c are popcounts of the element's slot mask against the
-            // vertex's label masks, so every load depends only on v
-            constexpr int EPTL = CAP / HT_THREADS;
-            int32_t vv[EPTL];
-            uint32_t sm[EPTL];
-#pragma unroll
-            for (int q = 0; q < EPTL; ++q) {
-                const int i = threadIdx.x + q * HT_THREADS;
-                vv[q] = 0;
-                sm[q] = 0;
-                if (i < ne) {
-                    vv[q] = g.hood[e0 + i];
-                    sm[q] = g.el_slot[e0 + i];
-                }
-            }
-#pragma unroll
-            for (int q = 0; q < EPTL; ++q) {
-                const int i = threadIdx.x + q * HT_THREADS;
-                if (i >= ne) continue;
-                const int64_t v = vv[q];
-                const uint32_t m = sm[q];
-                const int dc = __popc(m);
-                int cnt[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) cnt[l] = __popc(m & lm[v * L + l]);
-                s_fix[i] = hood_emin_fix<L>(Dfix, v, cnt, dc, beta_fix);
+            // vertex's label masks.  The tile's member ids and slot masks are
+            // staged once (coalesced); then one thread per hood walks its
+            // elements, gathers their vertex data and keeps the exact sum.
+            for (int i = threadIdx.x; i < ne; i += HT_THREADS) {
+                s_v[i] = g.hood[e0 + i];
+                s_sm[i] = g.el_slot[e0 + i];
             }
             __syncthreads();
             for (int64_t c = c0 + threadIdx.x; c < c1; c += HT_THREADS) {
                 const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
                 __int128 sd = 0;
-                for (int i = b; i < e; ++i) sd += s_fix[i];
-                const double S = unfix80(sd);
+#pragma unroll 2
+                for (int i = b; i < e; ++i) {
+                    const int64_t v = s_v[i];
+                    const uint32_t m = s_sm[i];
+                    int cnt[L];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) cnt[l] = __popc(m & lm[v * L + l]);
+                    sd += hood_emin_fix<L>(Dfix, v, cnt, __popc(m), beta_fix);
+                }
                 if (mode == MODE_SWEEP) {
-                    if (S_out) S_out[c] = S;
+                    if (S_out) S_out[c] = unfix80(sd);
                 } else {
-                    my_unconv += hood_history(S, c, g.C, t, cf, hist);
+                    my_unconv += hood_history(s40_of(sd), c, g.C, t, W, tol40, hist);
                     my_T += sd;
                 }
             }
@@ -463,7 +458,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                     if (mode == MODE_SWEEP) {
                         if (S_out) S_out[c] = S;
                     } else {
-                        my_unconv += hood_history(S, c, g.C, t, cf, hist);
+                        my_unconv += hood_history(s40_of(sd), c, g.C, t, W, tol40, hist);
                         my_T += sd;
                     }
                 }

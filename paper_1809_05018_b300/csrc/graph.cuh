@@ -33,7 +33,7 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     int L = 0, W = 0, max_iters = 0;
     int64_t n_htiles = 0, n_vtiles = 0;
     uint8_t* d_x[2] = {nullptr, nullptr};  // label double buffer
-    double* d_hist = nullptr;      // [W][C] hood-sum ring
+    int64_t* d_hist = nullptr;     // [W][C] hood-sum ring, units of 2^-40
     double* d_vpart = nullptr;     // [n_vtiles][L][4]
     double* d_hpart = nullptr;     // [n_htiles][2] (T partial, unconverged count)
     double* d_theta = nullptr;     // [S][L][4] current parameters
