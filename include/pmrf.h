@@ -115,6 +115,24 @@ PMRF_API int64_t pmrf_launch_count(void);
 PMRF_API const char* pmrf_version(void);
 
 /*
+ * Device memory.  Every device array the library allocates comes from one
+ * stream-ordered memory pool per device, owned by the library and created on
+ * first use.  Memory freed into it (a destroyed graph, build temporaries)
+ * stays mapped, so the next build of a batch of similar size reuses it.  The
+ * paper has no counterpart: this is memory management of this implementation.
+ *
+ * pmrf_trim_memory: synchronise the current device, then return the pool's
+ *   unused memory to the driver, keeping at least keep_bytes (>= 0; 0 returns
+ *   all of it) reserved.  Arrays of live graphs are not touched.
+ * pmrf_memory_usage: bytes the current device's pool has reserved from the
+ *   driver and bytes of it in use by live allocations (either pointer may be
+ *   NULL).
+ * Both return PMRF_OK or PMRF_ERR_CUDA (no device, pool creation failed).
+ */
+PMRF_API int pmrf_trim_memory(int64_t keep_bytes);
+PMRF_API int pmrf_memory_usage(int64_t* reserved_bytes, int64_t* used_bytes);
+
+/*
  * Build the region graph, maximal cliques, hoods and replica structures of a
  * batch of slices (Algorithm 2 steps 1, 2, 4 and 5; Sections 2.1, 3.1,
  * 3.2.1, 3.2.2 "Construction of Neighborhoods").

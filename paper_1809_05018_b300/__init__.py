@@ -21,7 +21,7 @@ import torch
 from . import _native as N
 from ._native import PmrfError
 
-__all__ = ["EMConfig", "Graph", "build_graph", "PmrfError", "lib_path", "PLL"]
+__all__ = ["EMConfig", "Graph", "build_graph", "PmrfError", "lib_path", "PLL", "memory_usage", "trim_memory"]
 
 
 def lib_path() -> str:
@@ -35,6 +35,20 @@ def _lib():
 def launch_count() -> int:
     """Kernels launched by the library in this process so far."""
     return int(_lib().pmrf_launch_count())
+
+
+def memory_usage() -> tuple[int, int]:
+    """(reserved, used) bytes of the library's device memory pool on the
+    current device."""
+    r, u = N._I64(0), N._I64(0)
+    N.check(_lib().pmrf_memory_usage(ctypes.byref(r), ctypes.byref(u)), "pmrf_memory_usage")
+    return int(r.value), int(u.value)
+
+
+def trim_memory(keep_bytes: int = 0) -> None:
+    """Return the pool's unused device memory to the driver, keeping at least
+    keep_bytes reserved."""
+    N.check(_lib().pmrf_trim_memory(int(keep_bytes)), "pmrf_trim_memory")
 
 
 def _stream_ptr(stream=None):

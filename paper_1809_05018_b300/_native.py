@@ -64,6 +64,8 @@ SIGNATURES = {
     "pmrf_autotune": [_GP, ctypes.POINTER(Config), _P, ctypes.POINTER(Tuning)],
     "pmrf_em_kernel_times": [_GP, _I32, _P, _P, ctypes.POINTER(_I32), _P],
     "pmrf_launch_count": [],
+    "pmrf_trim_memory": [_I64],
+    "pmrf_memory_usage": [ctypes.POINTER(_I64), ctypes.POINTER(_I64)],
     "pmrf_last_error": [],
     "pmrf_version": [],
 }

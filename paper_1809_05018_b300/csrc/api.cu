@@ -58,9 +58,9 @@ void destroy(pmrf_graph* g) {
     for (cudaEvent_t ev : g->prof_ev) cudaEventDestroy(ev);
     void* ps[] = {g->d_pix_off, g->d_vert_off, g->d_hood_slice_off, g->d_rank_off, g->d_W, g->d_rank, g->d_y,
                   g->d_npix, g->d_adj_off, g->d_adj, g->d_clq_off, g->d_clq, g->d_hood_off, g->d_hood, g->d_row_off,
-                  g->d_row, g->d_rep_off, g->d_rep_el, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_status};
+                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_status};
     for (void* p : ps)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);
     delete g;
 }
 
@@ -98,6 +98,16 @@ const char* pmrf_last_error(void) { return g_last_error.c_str(); }
 int64_t pmrf_launch_count(void) { return g_launches.load(); }
 
 const char* pmrf_version(void) { return "pmrf-b300 0.1 (sm_103a)"; }
+
+int pmrf_trim_memory(int64_t keep_bytes) {
+    g_last_error.clear();
+    return pool_trim(keep_bytes);
+}
+
+int pmrf_memory_usage(int64_t* reserved_bytes, int64_t* used_bytes) {
+    g_last_error.clear();
+    return pool_usage(reserved_bytes, used_bytes);
+}
 
 int pmrf_build_graph(const double* d_image, const int32_t* d_region_ids, int32_t n_slices, const int64_t* h_heights,
                      const int64_t* h_widths, pmrf_stream_t stream, pmrf_graph** out) {

@@ -507,63 +507,63 @@ __global__ void k_list_general(const int64_t* __restrict__ adj_off, int64_t V, i
 template <bool FILL>
 __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
                              const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t C,
-                             int32_t* __restrict__ hsize, const int64_t* __restrict__ hood_off,
-                             int32_t* __restrict__ hood) {
+                             int32_t* __restrict__ hsize, int32_t* __restrict__ hmax,
+                             const int64_t* __restrict__ hood_off, int32_t* __restrict__ hood,
+                             int32_t* __restrict__ el_hood, int32_t* __restrict__ rcount) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     const int64_t m0 = clq_off[c];
     const int m = (int)(clq_off[c + 1] - m0);
-    int32_t* out = FILL ? hood + hood_off[c] : nullptr;
-    if (m == 1) {
-        if (FILL) out[0] = clq[m0];
-        else hsize[c] = 1;
-        return;
-    }
-    int64_t p[MAX_CLIQUE + 1], e[MAX_CLIQUE + 1];
-    for (int i = 0; i < m; ++i) {
-        const int32_t u = clq[m0 + i];
-        p[i] = adj_off[u];
-        e[i] = adj_off[u + 1];
-    }
+    const int64_t h0 = FILL ? hood_off[c] : 0;
     int32_t n = 0;
-    while (true) {
-        int32_t cur = 0x7fffffff;
-        for (int i = 0; i < m; ++i)
-            if (p[i] < e[i]) cur = min(cur, adj[p[i]]);
-        if (cur == 0x7fffffff) break;
-        if (FILL) out[n] = cur;
+    // element n of hood c is `cur`: its vertex gains one replica
+    auto emit = [&](int32_t cur) {
+        if (FILL) {
+            hood[h0 + n] = cur;
+            el_hood[h0 + n] = (int32_t)c;
+            atomicAdd(&rcount[cur], 1);
+        }
         ++n;
-        for (int i = 0; i < m; ++i)
-            if (p[i] < e[i] && adj[p[i]] == cur) ++p[i];
+    };
+    if (m == 1) {
+        emit(clq[m0]);
+    } else {
+        int64_t p[MAX_CLIQUE + 1], e[MAX_CLIQUE + 1];
+        for (int i = 0; i < m; ++i) {
+            const int32_t u = clq[m0 + i];
+            p[i] = adj_off[u];
+            e[i] = adj_off[u + 1];
+        }
+        while (true) {
+            int32_t cur = 0x7fffffff;
+            for (int i = 0; i < m; ++i)
+                if (p[i] < e[i]) cur = min(cur, adj[p[i]]);
+            if (cur == 0x7fffffff) break;
+            emit(cur);
+            for (int i = 0; i < m; ++i)
+                if (p[i] < e[i] && adj[p[i]] == cur) ++p[i];
+        }
     }
-    if (!FILL) hsize[c] = n;
+    if (!FILL) {
+        hsize[c] = n;
+        // largest hood: one atomic per group of converged lanes
+        const unsigned act = __activemask();
+        const int32_t wmax = (int32_t)__reduce_max_sync(act, (unsigned)n);
+        if ((threadIdx.x & 31) == __ffs(act) - 1) atomicMax(hmax, wmax);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // replica structures
 
-__global__ void k_el_hood(const int64_t* __restrict__ hood_off, int64_t C, int32_t* __restrict__ el_hood,
-                          const int32_t* __restrict__ hood, int32_t* __restrict__ rcount, int32_t* __restrict__ hmax) {
-    int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= C) return;
-    for (int64_t e = hood_off[c]; e < hood_off[c + 1]; ++e) {
-        el_hood[e] = (int32_t)c;
-        atomicAdd(&rcount[hood[e]], 1);
-    }
-    atomicMax(hmax, (int32_t)(hood_off[c + 1] - hood_off[c]));
-}
-
+// replica lists in element order (filled in any order, then sorted): only the
+// export of each vertex's hoods needs them
 __global__ void k_rep_fill(const int32_t* __restrict__ hood, int64_t N_el, const int64_t* __restrict__ rep_off,
                            int32_t* __restrict__ cursor, uint32_t* __restrict__ rep_el) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N_el) return;
     const int32_t v = hood[e];
     rep_el[rep_off[v] + atomicAdd(&cursor[v], 1)] = (uint32_t)e;
-}
-
-__global__ void k_rep_pos(const uint32_t* __restrict__ rep_el, int64_t N_el, uint32_t* __restrict__ rep_pos) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q < N_el) rep_pos[rep_el[q]] = (uint32_t)q;
 }
 
 __global__ void k_row_words(const int64_t* __restrict__ hood_off, int64_t C, int64_t* __restrict__ nwords) {
@@ -584,13 +584,14 @@ __global__ void k_rep_words(const int64_t* __restrict__ adj_off, const int32_t* 
 
 // For element e (vertex v in hood c at position i): row bits j where hood[j]
 // is a neighbour of v, and slot bits s where N(v)[s] lies in the hood (stored
-// vertex-major with the replicas and, for degrees <= 32, element-major too).
+// vertex-major, one record per replica of v, and, for degrees <= 32,
+// element-major too).
 __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
                         const int32_t* __restrict__ el_hood, const int64_t* __restrict__ adj_off,
                         const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
-                        uint32_t* __restrict__ row, const int64_t* __restrict__ rep_off,
-                        const uint32_t* __restrict__ rep_pos, const int64_t* __restrict__ rep_woff,
-                        uint32_t* __restrict__ rep_mask, uint32_t* __restrict__ el_slot, int64_t N_el) {
+                        uint32_t* __restrict__ row, int32_t* __restrict__ cursor,
+                        const int64_t* __restrict__ rep_woff, uint32_t* __restrict__ rep_mask,
+                        uint32_t* __restrict__ el_slot, int64_t N_el) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N_el) return;
     const int32_t c = el_hood[e];
@@ -603,7 +604,9 @@ __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __r
     const int64_t nwh = ceil_div(k, 32);
     const int64_t nwv = d > 32 ? ceil_div(d, 32) : 1;
     uint32_t* rw = row + row_off[c] + i * nwh;
-    uint32_t* sw = rep_mask + rep_woff[v] + (int64_t)(rep_pos[e] - rep_off[v]) * nwv;
+    // the replica's place among v's replicas is arbitrary: the vertex pass only
+    // takes a minimum over them
+    uint32_t* sw = rep_mask + rep_woff[v] + (int64_t)atomicAdd(&cursor[v], 1) * nwv;
     uint32_t rcur = 0, scur = 0;
     int64_t rwi = 0, swi = 0;
     int64_t a = 0, j = 0;
@@ -631,6 +634,13 @@ __global__ void k_slice_hoods(const int64_t* __restrict__ cq_off, const int64_t*
                               int64_t* __restrict__ hood_slice_off) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s <= S) hood_slice_off[s] = cq_off[vert_off[s]];
+}
+
+// first hood element of each slice (entries S+1 .. 2S+1 of the host copy)
+__global__ void k_slice_elems(const int64_t* __restrict__ hood_slice_off, const int64_t* __restrict__ hood_off,
+                              int32_t S, int64_t* __restrict__ el_slice_off) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s <= S) el_slice_off[s] = hood_off[hood_slice_off[s]];
 }
 
 struct Scratch {  // frees every temporary on scope exit
@@ -674,6 +684,18 @@ int check_status(pmrf_graph* g, cudaStream_t s) {
     } while (0)
 
 }  // namespace
+
+int rep_elements(pmrf_graph* g, uint32_t* d_rep_el, cudaStream_t s) {
+    const int64_t V = g->V, N_el = g->N_el;
+    if (N_el == 0) return PMRF_OK;
+    Scratch tmp{s, {}};
+    int32_t* d_cursor = nullptr;
+    PMRF_TRY(tmp.get(&d_cursor, V));
+    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    LAUNCH_1D(k_rep_fill, N_el, g->d_hood, N_el, g->d_rep_off, d_cursor, d_rep_el);
+    PMRF_TRY(segmented_sort_u32(d_rep_el, g->d_rep_off, V, N_el, false, nullptr, g->d_status, s));
+    return PMRF_OK;
+}
 
 int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, cudaStream_t s) {
     const int32_t S = g->S;
@@ -883,36 +905,30 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_CUDA(cudaGetLastError());
     PMRF_TRY(check_status(g, s));
 
-    // 6. hoods
-    int32_t* d_hsize = nullptr;
+    // 6. hoods (and, while filling them, each element's hood and each vertex's
+    //    number of replicas)
+    int32_t *d_hsize = nullptr, *d_hmax = nullptr;
     PMRF_TRY(tmp.get(&d_hsize, C));
-    LAUNCH_1D(k_hood_merge<false>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, d_hsize, nullptr, nullptr);
+    PMRF_TRY(tmp.get(&d_hmax, 1));
+    PMRF_CUDA(cudaMemsetAsync(d_hmax, 0, sizeof(int32_t), s));
+    LAUNCH_1D(k_hood_merge<false>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, d_hsize, d_hmax, nullptr,
+              nullptr, nullptr, nullptr);
     PMRF_TRY(dalloc(&g->d_hood_off, C + 1, s));
     PMRF_TRY(exclusive_scan_i32_to_i64(d_hsize, g->d_hood_off, C, s));
     PMRF_TRY(read_i64(g->d_hood_off + C, &g->N_el, s));
     const int64_t N_el = g->N_el;
     if (N_el >= 4294967295ll) return fail(PMRF_ERR_UNSUPPORTED, "more than 2^32-1 hood elements");
     PMRF_TRY(dalloc(&g->d_hood, N_el, s));
-    LAUNCH_1D(k_hood_merge<true>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, nullptr, g->d_hood_off,
-              g->d_hood);
-
-    // 7. replica structures and masks
-    int32_t *d_el_hood = nullptr, *d_rcount = nullptr, *d_hmax = nullptr;
+    int32_t *d_el_hood = nullptr, *d_rcount = nullptr;
     PMRF_TRY(tmp.get(&d_el_hood, N_el));
     PMRF_TRY(tmp.get(&d_rcount, V));
-    PMRF_TRY(tmp.get(&d_hmax, 1));
     PMRF_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-    PMRF_CUDA(cudaMemsetAsync(d_hmax, 0, sizeof(int32_t), s));
-    LAUNCH_1D(k_el_hood, C, g->d_hood_off, C, d_el_hood, g->d_hood, d_rcount, d_hmax);
+    LAUNCH_1D(k_hood_merge<true>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, nullptr, nullptr,
+              g->d_hood_off, g->d_hood, d_el_hood, d_rcount);
+
+    // 7. replica offsets and masks
     PMRF_TRY(dalloc(&g->d_rep_off, V + 1, s));
     PMRF_TRY(exclusive_scan_i32_to_i64(d_rcount, g->d_rep_off, V, s));
-    PMRF_TRY(dalloc(&g->d_rep_el, N_el, s));
-    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-    LAUNCH_1D(k_rep_fill, N_el, g->d_hood, N_el, g->d_rep_off, d_cursor, g->d_rep_el);
-    PMRF_TRY(segmented_sort_u32(g->d_rep_el, g->d_rep_off, V, N_el, false, nullptr, g->d_status, s));
-    uint32_t* d_rep_pos = nullptr;
-    PMRF_TRY(tmp.get(&d_rep_pos, N_el));
-    LAUNCH_1D(k_rep_pos, N_el, g->d_rep_el, N_el, d_rep_pos);
     int64_t* d_nw = nullptr;
     PMRF_TRY(tmp.get(&d_nw, std::max(C, V)));
     PMRF_TRY(dalloc(&g->d_row_off, C + 1, s));
@@ -928,21 +944,22 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(dalloc(&g->d_el_slot, N_el, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
+    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     LAUNCH_1D(k_masks, N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off, g->d_row,
-              g->d_rep_off, d_rep_pos, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, N_el);
+              d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, N_el);
     PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
-    // slice offsets of hoods and elements (host copies)
-    g->h_hood_slice_off.assign(S + 1, 0);
-    PMRF_CUDA(cudaMemcpyAsync(g->h_hood_slice_off.data(), g->d_hood_slice_off, sizeof(int64_t) * (S + 1),
+    // slice offsets of hoods and elements (host copies, one transfer)
+    int64_t* d_el_slice_off = nullptr;
+    PMRF_TRY(tmp.get(&d_el_slice_off, S + 1));
+    LAUNCH_1D(k_slice_elems, S + 1, g->d_hood_slice_off, g->d_hood_off, S, d_el_slice_off);
+    std::vector<int64_t> both(2 * (size_t)(S + 1));
+    PMRF_CUDA(cudaMemcpyAsync(both.data(), g->d_hood_slice_off, sizeof(int64_t) * (S + 1), cudaMemcpyDeviceToHost, s));
+    PMRF_CUDA(cudaMemcpyAsync(both.data() + (S + 1), d_el_slice_off, sizeof(int64_t) * (S + 1),
                               cudaMemcpyDeviceToHost, s));
-    PMRF_CUDA(cudaStreamSynchronize(s));
-    g->h_el_slice_off.assign(S + 1, 0);
-    for (int i = 0; i <= S; ++i) {
-        int64_t c = g->h_hood_slice_off[i];
-        PMRF_CUDA(cudaMemcpyAsync(&g->h_el_slice_off[i], g->d_hood_off + c, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
-    }
-    PMRF_TRY(check_status(g, s));
+    PMRF_TRY(check_status(g, s));  // synchronises the stream
+    g->h_hood_slice_off.assign(both.begin(), both.begin() + (S + 1));
+    g->h_el_slice_off.assign(both.begin() + (S + 1), both.end());
     return PMRF_OK;
 }
 

@@ -112,8 +112,8 @@ __device__ __forceinline__ int64_t upper_bound_dev(const T* a, int64_t lo, int64
 // primitives implemented in scan.cu / segsort.cu
 
 // out[i] = sum_{j<i} in[j] for i in [0, n]; out has n+1 entries (out[n] = total).
-// `in` may be int32 or int64 counts.  Scratch is allocated internally with
-// cudaMallocAsync on `s`.
+// `in` may be int32 or int64 counts.  Scratch is allocated internally from
+// the library pool on `s`.
 int exclusive_scan_i32_to_i64(const int32_t* in, int64_t* out, int64_t n, cudaStream_t s);
 int exclusive_scan_i64(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s);
 // read one device value (synchronous)
@@ -134,12 +134,21 @@ int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t
 void note_launch(int64_t n);
 void set_capture_counter(int64_t* counter);
 
-// Device allocation helpers (stream ordered).
+// The library's stream-ordered memory pool on the current device (pool.cu):
+// created on first use, it keeps the memory freed into it mapped for reuse.
+// NULL when it cannot be created.
+cudaMemPool_t lib_pool();
+int pool_trim(int64_t keep_bytes);
+int pool_usage(int64_t* reserved, int64_t* used);
+
+// Device allocation helpers (stream ordered, from lib_pool()).
 template <typename T>
 int dalloc(T** p, int64_t n, cudaStream_t s) {
     *p = nullptr;
     size_t bytes = (size_t)(n > 0 ? n : 1) * sizeof(T) + 16;  // +16: padded tail for vector reads
-    cudaError_t e = cudaMallocAsync((void**)p, bytes, s);
+    cudaMemPool_t pool = lib_pool();
+    if (!pool) return fail(PMRF_ERR_CUDA, "device memory pool unavailable");
+    cudaError_t e = cudaMallocFromPoolAsync((void**)p, bytes, pool, s);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(PMRF_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");

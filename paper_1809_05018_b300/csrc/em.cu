@@ -37,6 +37,9 @@ constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
 constexpr int HT_THREADS = 96;               // hood-pass block: a tile's ~85 hoods, one per thread
 constexpr int MAX_HOOD_TILE = 1248;           // largest hood-tile window (elements)
 constexpr int HT_CAP = MAX_HOOD_TILE + 31;    // elements a fast hood tile can hold
+// neighbour-label masks kept per vertex for the hood pass: labels 0..L-2 (the
+// last label's count follows from the slot mask); one word for L = 1
+__host__ __device__ constexpr int lm_stride(int L) { return L > 1 ? L - 1 : 1; }
 
 enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
 
@@ -192,6 +195,8 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
             if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
             Estar = E_in ? E_in[v] : 0.0;
         } else {
+            // a caller's labels (standalone sweep) must lie in [0, L)
+            if (mode == MODE_SWEEP && x_in[v] >= L) record_error(st, PMRF_ERR_ARG, SITE_LABEL, v);
             // data term D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l
             double D[L];
 #pragma unroll
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                 }
                 if (lm_out) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) lm_out[v * L + l] = lm[l];
+                    for (int l = 0; l < L - 1; ++l) lm_out[v * lm_stride(L) + l] = lm[l];
                 }
                 for (int64_t r = r0; r < r1; ++r) {
                     const uint32_t m = g.rep_mask[r];
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
             } else {
                 if (lm_out) {
 #pragma unroll
-                    for (int l = 0; l < L; ++l) lm_out[v * L + l] = 0u;  // not read: such vertices are in general tiles
+                    for (int l = 0; l < L - 1; ++l) lm_out[v * lm_stride(L) + l] = 0u;  // not read: general tiles
                 }
                 const int nw = (d + 31) >> 5;
                 for (int64_t r = r0; r < r1; r += nw) {
@@ -316,13 +321,42 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
 
 // exact min_l D_l(y_v) + beta * (dc - cnt_l) in units of 2^-80, ties to the
 // lower label
+// beta * m in the fixed point of the data terms (beta_fix >= 0, 0 <= m <= 2^31)
+__device__ __forceinline__ __int128 beta_times(__int128 beta_fix, int m) {
+    return (__int128)((unsigned __int128)beta_fix * (unsigned long long)(unsigned)m);
+}
+
+// the data terms D_l(y_v), l < L, of one vertex: one 256-bit load per label
+// pair when L is even (the table is 32-byte aligned and a vertex's L entries
+// are contiguous), else one 128-bit load per label
 template <int L>
-__device__ __forceinline__ __int128 hood_emin_fix(const __int128* __restrict__ Dfix, int64_t v, const int* cnt,
-                                                  int dc, __int128 beta_fix) {
-    __int128 e = Dfix[v * L + 0] + beta_fix * (__int128)(dc - cnt[0]);
+__device__ __forceinline__ void load_dfix(const __int128* __restrict__ Dfix, int64_t v, __int128 (&D)[L]) {
+    if constexpr ((L & 1) == 0) {
+        const unsigned long long* p = reinterpret_cast<const unsigned long long*>(Dfix + v * L);
+#pragma unroll
+        for (int l = 0; l < L; l += 2) {
+            unsigned long long a0, a1, b0, b1;
+            asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                : "=l"(a0), "=l"(a1), "=l"(b0), "=l"(b1)
+                : "l"(p + 2 * l));
+            D[l] = (__int128)(((unsigned __int128)a1 << 64) | a0);
+            D[l + 1] = (__int128)(((unsigned __int128)b1 << 64) | b0);
+        }
+    } else {
+#pragma unroll
+        for (int l = 0; l < L; ++l) D[l] = Dfix[v * L + l];
+    }
+}
+
+// min_l [D_l + beta * (dc - cnt_l)]: the element's energy at its best label
+// (Eq. 3 restricted to the hood), exact in fixed point; ties keep the lower
+// label
+template <int L>
+__device__ __forceinline__ __int128 hood_emin(const __int128 (&D)[L], const int* cnt, int dc, __int128 beta_fix) {
+    __int128 e = D[0] + beta_times(beta_fix, dc - cnt[0]);
 #pragma unroll
     for (int l = 1; l < L; ++l) {
-        const __int128 x = Dfix[v * L + l] + beta_fix * (__int128)(dc - cnt[l]);
+        const __int128 x = D[l] + beta_times(beta_fix, dc - cnt[l]);
         if (x < e) e = x;
     }
     return e;
@@ -366,6 +400,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                                                      const __int128* __restrict__ Dfix, int64_t* __restrict__ hist,
                                                      double* __restrict__ S_out, double* __restrict__ hpart,
                                                      const uint32_t* __restrict__ lm) {
+    constexpr int LM = lm_stride(L);
     __shared__ int32_t s_v[HT_CAP];
     __shared__ uint32_t s_sm[HT_CAP];
     __shared__ __int128 s_wsum[HT_THREADS / 32];
@@ -406,10 +441,20 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                 for (int i = b; i < e; ++i) {
                     const int64_t v = s_v[i];
                     const uint32_t m = s_sm[i];
+                    __int128 D[L];
+                    load_dfix<L>(Dfix, v, D);
+                    // every label is in [0, L): the last label's count is
+                    // what the other masks leave of the slot mask
+                    const int dc = __popc(m);
                     int cnt[L];
+                    int rest = dc;
 #pragma unroll
-                    for (int l = 0; l < L; ++l) cnt[l] = __popc(m & lm[v * L + l]);
-                    sd += hood_emin_fix<L>(Dfix, v, cnt, __popc(m), beta_fix);
+                    for (int l = 0; l < L - 1; ++l) {
+                        cnt[l] = __popc(m & lm[v * LM + l]);
+                        rest -= cnt[l];
+                    }
+                    cnt[L - 1] = rest;
+                    sd += hood_emin<L>(D, cnt, dc, beta_fix);
                 }
                 if (mode == MODE_SWEEP) {
                     if (S_out) S_out[c] = unfix80(sd);
@@ -443,7 +488,9 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                             for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
                         }
                     }
-                    part += hood_emin_fix<L>(Dfix, v, cnt, dc, beta_fix);
+                    __int128 D[L];
+                    load_dfix<L>(Dfix, v, D);
+                    part += hood_emin<L>(D, cnt, dc, beta_fix);
                 }
                 // exact integer sums: the reduction order does not matter
 #pragma unroll
@@ -623,14 +670,16 @@ __global__ void k_label_image(const int32_t* __restrict__ ids, const int64_t* __
     (void)maxid1;
 }
 
-// tile table: vertex tiles then hood tiles, each grouped by slice
+// tile table: vertex tiles then hood tiles, each grouped by slice; one warp
+// per hood tile
 __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const int64_t* __restrict__ hood_slice_off,
                                   const int64_t* __restrict__ row_off, const int32_t* __restrict__ hood,
                                   const int64_t* __restrict__ adj_off, const int64_t* __restrict__ ht_first,
                                   int32_t S, int64_t n_htiles, int32_t te, Tile* __restrict__ tiles,
                                   int64_t tile_base) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n_htiles) return;
+    const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (k >= n_htiles) return;  // whole warps leave together
     const int s = (int)(upper_bound_dev<int64_t>(ht_first, 0, S + 1, k) - 1);
     const int64_t j = k - ht_first[s];
     const int64_t cs = hood_slice_off[s], ce = hood_slice_off[s + 1];
@@ -639,23 +688,27 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
     int64_t c0 = lower_bound_dev<int64_t>(hood_off, cs, ce, lo);
     int64_t c1 = lower_bound_dev<int64_t>(hood_off, cs, ce, hi);
     if (j == ht_first[s + 1] - ht_first[s] - 1) c1 = ce;
-    Tile t;
-    t.kind = 0;
-    t.slice = s;
-    t.a0 = (int32_t)c0;
-    t.a1 = (int32_t)c1;
-    t.part = (int32_t)k;
     // fast when the elements fit in shared memory, every hood has <= 32
     // members (one row word each) and every element's vertex has degree <= 32
-    const int64_t ne = hood_off[c1] - hood_off[c0];
-    bool fast = ne <= HT_CAP;
-    if (fast && (row_off[c1] - row_off[c0]) != ne) fast = false;  // some hood needs > 1 word per row
-    for (int64_t e = hood_off[c0]; fast && e < hood_off[c1]; ++e) {
-        const int32_t v = hood[e];
-        if (adj_off[v + 1] - adj_off[v] > 32) fast = false;
+    const int64_t e0 = hood_off[c0], e1 = hood_off[c1];
+    bool fast = (e1 - e0) <= HT_CAP && (row_off[c1] - row_off[c0]) == (e1 - e0);
+    bool ok = true;
+    if (fast)
+        for (int64_t e = e0 + lane; e < e1; e += 32) {
+            const int32_t v = hood[e];
+            ok = ok && (adj_off[v + 1] - adj_off[v] <= 32);
+        }
+    fast = __all_sync(0xffffffffu, ok) && fast;
+    if (lane == 0) {
+        Tile t;
+        t.kind = 0;
+        t.slice = s;
+        t.a0 = (int32_t)c0;
+        t.a1 = (int32_t)c1;
+        t.part = (int32_t)k;
+        t.pad = fast ? 1 : 0;
+        tiles[tile_base + k] = t;
     }
-    t.pad = fast ? 1 : 0;
-    tiles[tile_base + k] = t;
 }
 
 __global__ void k_make_vert_tiles(const int64_t* __restrict__ vert_off, const int64_t* __restrict__ vt_first,
@@ -682,10 +735,10 @@ __global__ void k_make_vert_tiles(const int64_t* __restrict__ vert_off, const in
 int free_plans(pmrf_graph* g) {
     for (auto& kv : g->plans) {
         Plan& p = kv.second;
-        if (p.d_tiles) cudaFree(p.d_tiles);
-        if (p.d_slice_ntiles) cudaFree(p.d_slice_ntiles);
-        if (p.d_slice_vt0) cudaFree(p.d_slice_vt0);
-        if (p.d_slice_ht0) cudaFree(p.d_slice_ht0);
+        dfree(p.d_tiles, 0);
+        dfree(p.d_slice_ntiles, 0);
+        dfree(p.d_slice_vt0, 0);
+        dfree(p.d_slice_ht0, 0);
     }
     g->plans.clear();
     for (auto& e : g->execs)
@@ -699,7 +752,7 @@ int free_em(pmrf_graph* g) {
     void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_Dtab,
                   w.d_lm, w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
     for (void* p : ps)
-        if (p) cudaFree(p);
+        if (p) cudaFreeAsync(p, 0);
     g->em = EMWork();
     for (auto& e : g->execs)
         if (e.exec) cudaGraphExecDestroy(e.exec);
@@ -741,16 +794,14 @@ int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
     p.n_htiles = hfirst[S];
     p.n_tiles = p.n_vtiles + p.n_htiles;
     if (p.n_tiles >= 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "too many tiles");
-    cudaError_t e;
-    e = cudaMalloc(&p.d_tiles, sizeof(Tile) * std::max<int64_t>(p.n_tiles, 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p.d_slice_vt0, sizeof(int64_t) * (S + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&p.d_slice_ht0, sizeof(int64_t) * (S + 1));
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        if (p.d_tiles) cudaFree(p.d_tiles);
-        if (p.d_slice_vt0) cudaFree(p.d_slice_vt0);
-        if (p.d_slice_ht0) cudaFree(p.d_slice_ht0);
-        return fail(PMRF_ERR_OOM, "tile table allocation failed");
+    int ra = dalloc(&p.d_tiles, p.n_tiles, s);
+    if (!ra) ra = dalloc(&p.d_slice_vt0, S + 1, s);
+    if (!ra) ra = dalloc(&p.d_slice_ht0, S + 1, s);
+    if (ra) {
+        dfree(p.d_tiles, s);
+        dfree(p.d_slice_vt0, s);
+        dfree(p.d_slice_ht0, s);
+        return ra;
     }
     PMRF_CUDA(cudaMemcpyAsync(p.d_slice_vt0, vfirst.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
     PMRF_CUDA(cudaMemcpyAsync(p.d_slice_ht0, hfirst.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
@@ -760,7 +811,7 @@ int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
         ::pmrf::note_launch(1);
     }
     if (p.n_htiles > 0) {
-        k_make_hood_tiles<<<(unsigned)ceil_div(p.n_htiles, 256), 256, 0, s>>>(
+        k_make_hood_tiles<<<(unsigned)ceil_div(p.n_htiles, 8), 256, 0, s>>>(
             g->d_hood_off, g->d_hood_slice_off, g->d_row_off, g->d_hood, g->d_adj_off, p.d_slice_ht0, S, p.n_htiles,
             te, p.d_tiles,
             p.n_vtiles);
@@ -799,23 +850,14 @@ RunCfg to_run(const pmrf_config* c) {
     return r;
 }
 
-template <typename T>
-int walloc(T** p, int64_t n) {
-    cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (size_t)std::max<int64_t>(n, 1) + 16);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        *p = nullptr;
-        return fail(PMRF_ERR_OOM, "EM workspace allocation failed");
-    }
-    return PMRF_OK;
-}
 
 // (re)allocate the EM workspace for (L, W, max_iters, plan)
-int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p) {
+int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) {
     EMWork& w = g->em;
     if (w.d_x[0] && w.L == rc.L && w.W == rc.W && w.max_iters >= rc.max_iters && w.n_vtiles == p.n_vtiles &&
         w.n_htiles == p.n_htiles)
         return PMRF_OK;
+    if (w.d_x[0]) PMRF_CUDA(cudaDeviceSynchronize());  // the old workspace may be in use on any stream
     free_em(g);
     const int64_t S = g->S;
     w.L = rc.L;
@@ -824,20 +866,22 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p) {
     w.n_vtiles = p.n_vtiles;
     w.n_htiles = p.n_htiles;
     int rc2 = PMRF_OK;
-    if (!rc2) rc2 = walloc(&w.d_x[0], g->V);
-    if (!rc2) rc2 = walloc(&w.d_x[1], g->V);
-    if (!rc2) rc2 = walloc(&w.d_hist, (int64_t)rc.W * g->C);
-    if (!rc2) rc2 = walloc(&w.d_vpart, p.n_vtiles * 4 * rc.L);
-    if (!rc2) rc2 = walloc(&w.d_hpart, p.n_htiles * 2);
-    if (!rc2) rc2 = walloc(&w.d_theta, S * rc.L * 4);
-    if (!rc2) rc2 = walloc(&w.d_Thist, S * rc.W);
-    if (!rc2) rc2 = walloc(&w.d_active, S);
-    if (!rc2) rc2 = walloc(&w.d_iters, S);
-    if (!rc2) rc2 = walloc(&w.d_conv, S);
-    if (!rc2) rc2 = walloc(&w.d_nactive, 1);
-    if (!rc2) rc2 = walloc(&w.d_Dtab, g->V * rc.L);  // data term D[v][l], exact fixed point
-    if (!rc2) rc2 = walloc(&w.d_lm, g->V * rc.L);    // neighbour-label masks
-    if (!rc2) rc2 = walloc((char**)&w.d_cfg, (int64_t)(sizeof(RunCfg) + sizeof(OutPtrs)));
+    if (!rc2) rc2 = dalloc(&w.d_x[0], g->V, s);
+    if (!rc2) rc2 = dalloc(&w.d_x[1], g->V, s);
+    if (!rc2) rc2 = dalloc(&w.d_hist, (int64_t)rc.W * g->C, s);
+    if (!rc2) rc2 = dalloc(&w.d_vpart, p.n_vtiles * 4 * rc.L, s);
+    if (!rc2) rc2 = dalloc(&w.d_hpart, p.n_htiles * 2, s);
+    if (!rc2) rc2 = dalloc(&w.d_theta, S * rc.L * 4, s);
+    if (!rc2) rc2 = dalloc(&w.d_Thist, S * rc.W, s);
+    if (!rc2) rc2 = dalloc(&w.d_active, S, s);
+    if (!rc2) rc2 = dalloc(&w.d_iters, S, s);
+    if (!rc2) rc2 = dalloc(&w.d_conv, S, s);
+    if (!rc2) rc2 = dalloc(&w.d_nactive, 1, s);
+    if (!rc2) rc2 = dalloc(&w.d_Dtab, g->V * rc.L, s);              // data term D[v][l], exact fixed point
+    if (!rc2) rc2 = dalloc(&w.d_lm, g->V * lm_stride(rc.L), s);  // neighbour-label masks, labels < L-1
+    if (!rc2 && (reinterpret_cast<uintptr_t>(w.d_Dtab) & 31))  // the hood pass reads it 32 bytes at a time
+        rc2 = fail(PMRF_ERR_CUDA, "data-term table is not 32-byte aligned");
+    if (!rc2) rc2 = dalloc((char**)&w.d_cfg, (int64_t)(sizeof(RunCfg) + sizeof(OutPtrs)), s);
     if (rc2) free_em(g);
     return rc2;
 }
@@ -923,7 +967,7 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
     const RunCfg rc = to_run(cfg);
     Plan* p = nullptr;
     PMRF_TRY(get_plan(g, s, &p));
-    PMRF_TRY(ensure_work(g, rc, *p));
+    PMRF_TRY(ensure_work(g, rc, *p, s));
     EMWork& w = g->em;
     // constants and output pointers for this call
     struct {
@@ -1065,7 +1109,7 @@ int prepare(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, Plan** p, Run
     PMRF_TRY(check_cfg(g, cfg));
     *rc = to_run(cfg);
     PMRF_TRY(get_plan(g, s, p));
-    PMRF_TRY(ensure_work(g, *rc, **p));
+    PMRF_TRY(ensure_work(g, *rc, **p, s));
     return PMRF_OK;
 }
 
@@ -1154,10 +1198,10 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
     uint8_t* lab = nullptr;
     double* par = nullptr;
     int32_t *it = nullptr, *cv = nullptr;
-    int rc = walloc(&lab, g->V);
-    if (!rc) rc = walloc(&par, S * L * 4);
-    if (!rc) rc = walloc(&it, S);
-    if (!rc) rc = walloc(&cv, S);
+    int rc = dalloc(&lab, g->V, s);
+    if (!rc) rc = dalloc(&par, S * L * 4, s);
+    if (!rc) rc = dalloc(&it, S, s);
+    if (!rc) rc = dalloc(&cv, S, s);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (!rc && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess))
         rc = fail(PMRF_ERR_CUDA, "event creation failed");
@@ -1167,7 +1211,7 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
     for (int c = 0; c < 3 && !rc; ++c) {
         pmrf_tuning t = keep;
         t.hood_tile = cands[c];
-        cudaStreamSynchronize(s);
+        cudaDeviceSynchronize();
         free_plans(g);
         free_em(g);
         g->tuning = t;
@@ -1184,17 +1228,17 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
             win = t;
         }
     }
-    cudaStreamSynchronize(s);
+    cudaDeviceSynchronize();
     free_plans(g);
     free_em(g);
     g->tuning = rc ? keep : win;
     if (best && !rc) *best = win;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (lab) cudaFree(lab);
-    if (par) cudaFree(par);
-    if (it) cudaFree(it);
-    if (cv) cudaFree(cv);
+    dfree(lab, s);
+    dfree(par, s);
+    dfree(it, s);
+    dfree(cv, s);
     return rc;
 }
 

@@ -77,7 +77,6 @@ struct pmrf_graph {
     int64_t* d_row_off = nullptr;        // [C+1] word offsets of hood-local adjacency rows
     uint32_t* d_row = nullptr;           // [n_row_words]
     int64_t* d_rep_off = nullptr;        // [V+1]
-    uint32_t* d_rep_el = nullptr;        // [N_el] element of each replica (ascending per vertex)
     int64_t* d_rep_woff = nullptr;       // [V+1] word offsets of replica slot masks
     uint32_t* d_rep_mask = nullptr;      // [n_rep_words]
     uint32_t* d_el_slot = nullptr;       // [N_el] slot mask of each hood element (degree <= 32), hood-major
@@ -104,4 +103,7 @@ struct pmrf_graph {
 namespace pmrf {
 int free_plans(pmrf_graph* g);
 int free_em(pmrf_graph* g);
+// the hood-element index of every replica, ascending within each vertex's
+// range [rep_off[v], rep_off[v+1]) (N_el entries, into d_rep_el)
+int rep_elements(pmrf_graph* g, uint32_t* d_rep_el, cudaStream_t s);
 }  // namespace pmrf

@@ -138,8 +138,9 @@ __global__ void k_sum_slices(int32_t S, const double* __restrict__ in, double* _
     *out = t;
 }
 
-__global__ void k_rep_hood(const uint32_t* __restrict__ rep_el, const int64_t* __restrict__ hood_off, int64_t C,
-                           int64_t N_el, int32_t* __restrict__ dst) {
+// dst may alias rep_el: each thread reads its own entry before writing it
+__global__ void k_rep_hood(const uint32_t* rep_el, const int64_t* __restrict__ hood_off, int64_t C, int64_t N_el,
+                           int32_t* dst) {
     int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (q >= N_el) return;
     dst[q] = (int32_t)(upper_bound_dev<int64_t>(hood_off, 0, C + 1, (int64_t)rep_el[q]) - 1);
@@ -192,10 +193,14 @@ int pll_run(pmrf_graph* g, int32_t L, const uint8_t* x, const double* mu, const 
 }
 
 int export_rep_hood(pmrf_graph* g, int32_t* dst, cudaStream_t s) {
-    if (g->N_el > 0) {
-        k_rep_hood<<<(unsigned)ceil_div(g->N_el, 256), 256, 0, s>>>(g->d_rep_el, g->d_hood_off, g->C, g->N_el, dst);
-        ::pmrf::note_launch(1);
-    }
+    if (g->N_el == 0) return PMRF_OK;
+    // the sorted replica list is only needed here, so it is built on demand
+    // into dst's own storage (same size, 32-bit entries) and mapped in place
+    static_assert(sizeof(uint32_t) == sizeof(int32_t), "in-place mapping");
+    PMRF_TRY(rep_elements(g, reinterpret_cast<uint32_t*>(dst), s));
+    k_rep_hood<<<(unsigned)ceil_div(g->N_el, 256), 256, 0, s>>>(reinterpret_cast<const uint32_t*>(dst),
+                                                                 g->d_hood_off, g->C, g->N_el, dst);
+    ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;
 }
