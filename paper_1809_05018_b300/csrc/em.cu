@@ -37,15 +37,25 @@ constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
 constexpr int HT_THREADS = 96;               // hood-pass block: a tile's ~85 hoods, one per thread
 constexpr int MAX_HOOD_TILE = 1248;           // largest hood-tile window (elements)
 constexpr int HT_CAP = MAX_HOOD_TILE + 31;    // elements a fast hood tile can hold
-// neighbour-label masks kept per vertex for the hood pass: labels 0..L-2 (the
-// last label's count follows from the slot mask); one word for L = 1
-__host__ __device__ constexpr int lm_stride(int L) { return L > 1 ? L - 1 : 1; }
+// Per-vertex record of the hood pass, 32-byte chunks (one for L = 2), written
+// by the vertex pass of the same iteration:
+//   words 0-1   D_min(v) = min_l D_l(y_v), exact fixed point (units 2^-80)
+//   words 2..L  the excess D_l - D_min of every label l other than amin (the
+//               lowest label attaining D_min), ascending l, in units 2^-hq,
+//               rounded to nearest and saturated at DQ_MAX; bits 61-63 of
+//               word 2 hold amin
+//   then        L-1 u32 masks: which of v's adjacency slots hold label l, for
+//               l < L-1 (the last label's count follows from the slot mask)
+__host__ __device__ constexpr int vrec_words(int L) { return ((16 + 12 * (L - 1) + 31) / 32) * 4; }
+constexpr uint64_t DQ_MAX = (1ull << 60) - 1;
 
 enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
 
 struct RunCfg {
     int32_t L, W, max_iters, init_from_labels;
     double beta, tol, sigma_min, init_lo, init_hi;
+    int32_t hq, pad;  // unit 2^-hq of the hood pass's label excesses
+    int64_t beta_q;   // beta in those units (< 2^51)
 };
 
 struct OutPtrs {  // outputs of one pmrf_em call (read by the closing kernel)
@@ -148,15 +158,60 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
 // ---------------------------------------------------------------------------
 // vertex pass
 
+// the hood-pass record of vertex v (layout above) from its FP64 data terms
+template <int L>
+__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t v, const double (&D)[L],
+                                           const uint32_t (&lmw)[L], int hq) {
+    constexpr int NW = vrec_words(L);
+    __int128 F[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) F[l] = fix80(D[l]);
+    int amin = 0;
+    __int128 Fmin = F[0];
+#pragma unroll
+    for (int l = 1; l < L; ++l)
+        if (F[l] < Fmin) {
+            Fmin = F[l];
+            amin = l;
+        }
+    const int sh = 80 - hq;  // >= 29
+    uint64_t dq[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const unsigned __int128 dd = (unsigned __int128)F[l] - (unsigned __int128)Fmin;  // exact, >= 0
+        const unsigned __int128 q = (dd + ((unsigned __int128)1 << (sh - 1))) >> sh;
+        dq[l] = q > (unsigned __int128)DQ_MAX ? DQ_MAX : (uint64_t)q;
+    }
+    uint64_t w[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = 0ull;
+    w[0] = (uint64_t)(unsigned __int128)Fmin;
+    w[1] = (uint64_t)((unsigned __int128)Fmin >> 64);
+#pragma unroll
+    for (int k = 0; k < L - 1; ++k) w[2 + k] = k < amin ? dq[k] : dq[k + 1];
+    if (L > 1) w[2] |= (uint64_t)amin << 61;
+#pragma unroll
+    for (int k = 0; k < L - 1; ++k) {
+        const int u = 4 + 2 * (L - 1) + k;
+        w[u >> 1] |= (uint64_t)lmw[k] << (32 * (u & 1));
+    }
+    uint64_t* p = vrec + v * NW;
+#pragma unroll
+    for (int k = 0; k < NW; k += 4)
+        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p + k), "l"(w[k]), "l"(w[k + 1]),
+                     "l"(w[k + 2]), "l"(w[k + 3])
+                     : "memory");
+}
+
 template <int L>
 __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* __restrict__ tiles, int mode,
                                                        const RunCfg* __restrict__ cfgp,
                                                        const int32_t* __restrict__ active,
                                                        const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
-                                                       const double* __restrict__ theta, __int128* __restrict__ Dfix,
+                                                       const double* __restrict__ theta,
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
                                                        double* __restrict__ vpart, DevStatus* st,
-                                                       uint32_t* __restrict__ lm_out) {
+                                                       uint64_t* __restrict__ vrec) {
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
     __shared__ double s_vq[3][VT_THREADS];
     __shared__ double s_vc[3 * L][8];
@@ -204,30 +259,20 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                 const double dev = y - s_mu[l];
                 D[l] = dev * dev * s_inv[l] + s_lnsig[l];
             }
-            if (Dfix) {
-                // the hood pass works on these energies in exact fixed point
-#pragma unroll
-                for (int l = 0; l < L; ++l) Dfix[v * L + l] = fix80(D[l]);
-            }
             const int64_t a0 = g.adj_off[v];
             const int d = (int)(g.adj_off[v + 1] - a0);
             const int64_t r0 = g.rep_woff[v], r1 = g.rep_woff[v + 1];
             int M[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) M[l] = 0x7fffffff;
-            if (d <= 32) {
-                // label masks over v's adjacency slots
-                uint32_t lm[L];
+            uint32_t lm[L];  // label masks over v's adjacency slots (degree <= 32; else unused)
 #pragma unroll
-                for (int l = 0; l < L; ++l) lm[l] = 0;
+            for (int l = 0; l < L; ++l) lm[l] = 0;
+            if (d <= 32) {
                 for (int j = 0; j < d; ++j) {
                     const int xl = x_in[g.adj[a0 + j]];
 #pragma unroll
                     for (int l = 0; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
-                }
-                if (lm_out) {
-#pragma unroll
-                    for (int l = 0; l < L - 1; ++l) lm_out[v * lm_stride(L) + l] = lm[l];
                 }
                 for (int64_t r = r0; r < r1; ++r) {
                     const uint32_t m = g.rep_mask[r];
@@ -237,10 +282,6 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                         M[l] = min(M[l], dc - __popc(m & lm[l]));  // neighbours in the hood whose label is not l
                 }
             } else {
-                if (lm_out) {
-#pragma unroll
-                    for (int l = 0; l < L - 1; ++l) lm_out[v * lm_stride(L) + l] = 0u;  // not read: general tiles
-                }
                 const int nw = (d + 31) >> 5;
                 for (int64_t r = r0; r < r1; r += nw) {
                     int cnt[L];
@@ -262,6 +303,8 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                     for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - cnt[l]);
                 }
             }
+            // the hood pass of this iteration reads v's data terms and label masks
+            if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
             // every vertex lies in at least one hood, so M_l is set
             Estar = D[0] + c.beta * (double)M[0];
             lab = 0;
@@ -321,45 +364,69 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
 
 // exact min_l D_l(y_v) + beta * (dc - cnt_l) in units of 2^-80, ties to the
 // lower label
-// beta * m in the fixed point of the data terms (beta_fix >= 0, 0 <= m <= 2^31)
-__device__ __forceinline__ __int128 beta_times(__int128 beta_fix, int m) {
-    return (__int128)((unsigned __int128)beta_fix * (unsigned long long)(unsigned)m);
+// decoded hood-pass record of one vertex (dq[amin] = 0)
+template <int L>
+struct VRec {
+    __int128 Dmin;
+    uint64_t dq[L];
+    uint32_t lmv[L];  // lmv[L-1] unused
+};
+
+template <int L>
+__device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, int64_t v) {
+    constexpr int NW = vrec_words(L);
+    uint64_t w[NW];
+    const uint64_t* p = vrec + v * NW;
+#pragma unroll
+    for (int k = 0; k < NW; k += 4)
+        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+            : "=l"(w[k]), "=l"(w[k + 1]), "=l"(w[k + 2]), "=l"(w[k + 3])
+            : "l"(p + k));
+    VRec<L> R;
+    R.Dmin = (__int128)(((unsigned __int128)w[1] << 64) | w[0]);
+    const int amin = L > 1 ? (int)(w[2] >> 61) : 0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const uint64_t own = (l < L - 1) ? (w[2 + l] & DQ_MAX) : 0ull;  // stored slot l (labels below amin)
+        const uint64_t up = (l >= 1) ? (w[1 + l] & DQ_MAX) : 0ull;      // stored slot l-1 (labels above amin)
+        R.dq[l] = l == amin ? 0ull : (l < amin ? own : up);
+    }
+#pragma unroll
+    for (int k = 0; k < L; ++k) {
+        const int u = 4 + 2 * (L - 1) + k;  // u32 index of mask k
+        R.lmv[k] = k < L - 1 ? (uint32_t)(w[u >> 1] >> (32 * (u & 1))) : 0u;
+    }
+    return R;
 }
 
-// the data terms D_l(y_v), l < L, of one vertex: one 256-bit load per label
-// pair when L is even (the table is 32-byte aligned and a vertex's L entries
-// are contiguous), else one 128-bit load per label
+// the element's energy above D_min at its best label, in units 2^-hq:
+// min_l [dq_l + beta_q * (dc - cnt_l)]; every term is >= 0 and the minimum is
+// at most dc * beta_q (the amin term)
 template <int L>
-__device__ __forceinline__ void load_dfix(const __int128* __restrict__ Dfix, int64_t v, __int128 (&D)[L]) {
-    if constexpr ((L & 1) == 0) {
-        const unsigned long long* p = reinterpret_cast<const unsigned long long*>(Dfix + v * L);
+__device__ __forceinline__ int64_t vrec_excess(const VRec<L>& R, const int (&cnt)[L], int dc, int64_t beta_q) {
+    int64_t r = INT64_MAX;
 #pragma unroll
-        for (int l = 0; l < L; l += 2) {
-            unsigned long long a0, a1, b0, b1;
-            asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-                : "=l"(a0), "=l"(a1), "=l"(b0), "=l"(b1)
-                : "l"(p + 2 * l));
-            D[l] = (__int128)(((unsigned __int128)a1 << 64) | a0);
-            D[l + 1] = (__int128)(((unsigned __int128)b1 << 64) | b0);
-        }
-    } else {
-#pragma unroll
-        for (int l = 0; l < L; ++l) D[l] = Dfix[v * L + l];
+    for (int l = 0; l < L; ++l) {
+        const int64_t x = (int64_t)R.dq[l] + beta_q * (int64_t)(dc - cnt[l]);
+        r = x < r ? x : r;
     }
+    return r;
 }
 
-// min_l [D_l + beta * (dc - cnt_l)]: the element's energy at its best label
-// (Eq. 3 restricted to the hood), exact in fixed point; ties keep the lower
-// label
+// label counts among the element's in-hood neighbours, from its slot mask and
+// the vertex's label masks (every label is in [0, L): the last label's count is
+// what the other masks leave of the slot mask)
 template <int L>
-__device__ __forceinline__ __int128 hood_emin(const __int128 (&D)[L], const int* cnt, int dc, __int128 beta_fix) {
-    __int128 e = D[0] + beta_times(beta_fix, dc - cnt[0]);
+__device__ __forceinline__ int slot_counts(const VRec<L>& R, uint32_t m, int (&cnt)[L]) {
+    const int dc = __popc(m);
+    int rest = dc;
 #pragma unroll
-    for (int l = 1; l < L; ++l) {
-        const __int128 x = D[l] + beta_times(beta_fix, dc - cnt[l]);
-        if (x < e) e = x;
+    for (int l = 0; l < L - 1; ++l) {
+        cnt[l] = __popc(m & R.lmv[l]);
+        rest -= cnt[l];
     }
-    return e;
+    cnt[L - 1] = rest;
+    return dc;
 }
 
 // convergence bookkeeping of one hood; returns 1 when the hood is unconverged
@@ -397,10 +464,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                                                      const RunCfg* __restrict__ cfgp,
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
-                                                     const __int128* __restrict__ Dfix, int64_t* __restrict__ hist,
-                                                     double* __restrict__ S_out, double* __restrict__ hpart,
-                                                     const uint32_t* __restrict__ lm) {
-    constexpr int LM = lm_stride(L);
+                                                     const uint64_t* __restrict__ vrec, int64_t* __restrict__ hist,
+                                                     double* __restrict__ S_out, double* __restrict__ hpart) {
     __shared__ int32_t s_v[HT_CAP];
     __shared__ uint32_t s_sm[HT_CAP];
     __shared__ __int128 s_wsum[HT_THREADS / 32];
@@ -409,7 +474,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
     const int s = tile.slice;
     if (active && !active[s]) return;
     const RunCfg cf = *cfgp;
-    const __int128 beta_fix = fix80(cf.beta);
+    const int64_t beta_q = cf.beta_q;
+    const int rsh = 80 - cf.hq;  // excess units 2^-hq -> 2^-80
     const int64_t tol40 = s40_of(fix80(cf.tol));
     const int W = cf.W;
     const int64_t c0 = tile.a0, c1 = tile.a1;
@@ -436,26 +502,19 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
             __syncthreads();
             for (int64_t c = c0 + threadIdx.x; c < c1; c += HT_THREADS) {
                 const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
-                __int128 sd = 0;
+                // S_c = sum of D_min (exact) + sum of the excesses (<= 32
+                // elements of <= 32 beta_q each: no overflow)
+                __int128 sdD = 0;
+                int64_t sdR = 0;
 #pragma unroll 2
                 for (int i = b; i < e; ++i) {
-                    const int64_t v = s_v[i];
-                    const uint32_t m = s_sm[i];
-                    __int128 D[L];
-                    load_dfix<L>(Dfix, v, D);
-                    // every label is in [0, L): the last label's count is
-                    // what the other masks leave of the slot mask
-                    const int dc = __popc(m);
+                    const VRec<L> R = load_vrec<L>(vrec, s_v[i]);
                     int cnt[L];
-                    int rest = dc;
-#pragma unroll
-                    for (int l = 0; l < L - 1; ++l) {
-                        cnt[l] = __popc(m & lm[v * LM + l]);
-                        rest -= cnt[l];
-                    }
-                    cnt[L - 1] = rest;
-                    sd += hood_emin<L>(D, cnt, dc, beta_fix);
+                    const int dc = slot_counts<L>(R, s_sm[i], cnt);
+                    sdD += R.Dmin;
+                    sdR += vrec_excess<L>(R, cnt, dc, beta_q);
                 }
+                const __int128 sd = sdD + ((__int128)sdR << rsh);
                 if (mode == MODE_SWEEP) {
                     if (S_out) S_out[c] = unfix80(sd);
                 } else {
@@ -488,9 +547,8 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
                             for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
                         }
                     }
-                    __int128 D[L];
-                    load_dfix<L>(Dfix, v, D);
-                    part += hood_emin<L>(D, cnt, dc, beta_fix);
+                    const VRec<L> R = load_vrec<L>(vrec, v);
+                    part += R.Dmin + ((__int128)vrec_excess<L>(R, cnt, dc, beta_q) << rsh);
                 }
                 // exact integer sums: the reduction order does not matter
 #pragma unroll
@@ -749,8 +807,8 @@ int free_plans(pmrf_graph* g) {
 
 int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
-    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_Dtab,
-                  w.d_lm, w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
+    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_vrec,
+                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
     g->em = EMWork();
@@ -828,7 +886,7 @@ int check_cfg(const pmrf_graph* g, const pmrf_config* cfg) {
     if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
     if (!cfg) return fail(PMRF_ERR_ARG, "config is NULL");
     if (cfg->n_labels < 1 || cfg->n_labels > PMRF_MAX_LABELS) return fail(PMRF_ERR_ARG, "n_labels must be in [1, 8]");
-    if (!(cfg->beta >= 0.0) || !std::isfinite(cfg->beta)) return fail(PMRF_ERR_ARG, "beta must be finite and >= 0");
+    if (!(cfg->beta >= 0.0) || !(cfg->beta < 0x1p40)) return fail(PMRF_ERR_ARG, "beta must be in [0, 2^40)");
     if (!(cfg->sigma_min > 0.0)) return fail(PMRF_ERR_ARG, "sigma_min must be > 0");
     if (!(cfg->init_hi > cfg->init_lo)) return fail(PMRF_ERR_ARG, "init_hi must exceed init_lo");
     if (cfg->conv_window < 1) return fail(PMRF_ERR_ARG, "conv_window must be >= 1");
@@ -847,6 +905,14 @@ RunCfg to_run(const pmrf_config* c) {
     r.sigma_min = c->sigma_min;
     r.init_lo = c->init_lo;
     r.init_hi = c->init_hi;
+    // units 2^-hq of the hood pass's label excesses: beta_q = beta * 2^hq stays
+    // below 2^51, so a fast hood's 32 elements of <= 32 beta_q each sum below
+    // 2^61 (beta < 2^e with frexp's exponent e)
+    int e = 0;
+    if (r.beta > 0.0) std::frexp(r.beta, &e);
+    r.hq = std::max(0, std::min(51, 51 - e));
+    r.pad = 0;
+    r.beta_q = (int64_t)std::llrint(std::ldexp(r.beta, r.hq));
     return r;
 }
 
@@ -877,10 +943,9 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) 
     if (!rc2) rc2 = dalloc(&w.d_iters, S, s);
     if (!rc2) rc2 = dalloc(&w.d_conv, S, s);
     if (!rc2) rc2 = dalloc(&w.d_nactive, 1, s);
-    if (!rc2) rc2 = dalloc(&w.d_Dtab, g->V * rc.L, s);              // data term D[v][l], exact fixed point
-    if (!rc2) rc2 = dalloc(&w.d_lm, g->V * lm_stride(rc.L), s);  // neighbour-label masks, labels < L-1
-    if (!rc2 && (reinterpret_cast<uintptr_t>(w.d_Dtab) & 31))  // the hood pass reads it 32 bytes at a time
-        rc2 = fail(PMRF_ERR_CUDA, "data-term table is not 32-byte aligned");
+    if (!rc2) rc2 = dalloc(&w.d_vrec, g->V * vrec_words(rc.L), s);  // hood-pass vertex records
+    if (!rc2 && (reinterpret_cast<uintptr_t>(w.d_vrec) & 31))  // read and written 32 bytes at a time
+        rc2 = fail(PMRF_ERR_CUDA, "vertex record table is not 32-byte aligned");
     if (!rc2) rc2 = dalloc((char**)&w.d_cfg, (int64_t)(sizeof(RunCfg) + sizeof(OutPtrs)), s);
     if (rc2) free_em(g);
     return rc2;
@@ -913,7 +978,6 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     EMWork& w = g->em;
     Launch z{g, p, view(g), p->d_tiles + 0, p->d_tiles + p->n_vtiles, (RunCfg*)w.d_cfg,
              (OutPtrs*)((char*)w.d_cfg + sizeof(RunCfg))};
-    __int128* Dtab = w.d_Dtab;
     const int32_t S = g->S;
     // every slice active for INIT; nactive = S
     k_set_active_all<<<(unsigned)ceil_div(S, 256), 256, 0, s>>>(w.d_active, S); ::pmrf::note_launch(1);
@@ -922,7 +986,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     k_zero_T<<<64, 256, 0, s>>>(z.d_out, (int64_t)S * rc.max_iters); ::pmrf::note_launch(1);
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
-                                                                w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
+                                                                w.d_x[1], w.d_x[0], nullptr, nullptr,
                                                                 nullptr, w.d_vpart, g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
@@ -936,14 +1000,14 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
         if (p->n_vtiles > 0) {
             k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
-                                                                    xout, w.d_theta, Dtab, nullptr, nullptr,
-                                                                    w.d_vpart, g->d_status, w.d_lm);
+                                                                    xout, w.d_theta, nullptr, nullptr,
+                                                                    w.d_vpart, g->d_status, w.d_vrec);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
         if (p->n_htiles > 0) {
             k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(z.dg, z.ht, MODE_EM, t, z.d_cfg, w.d_active, xin,
-                                                                  Dtab, w.d_hist, nullptr, w.d_hpart, w.d_lm);
+                                                                  w.d_vrec, w.d_hist, nullptr, w.d_hpart);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
@@ -1069,18 +1133,18 @@ namespace {
 
 template <int L>
 int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, const uint8_t* xin, const double* theta,
-               uint8_t* xout, double* Eout, double* Sout, __int128* Dtab, uint32_t* lm) {
+               uint8_t* xout, double* Eout, double* Sout, uint64_t* vrec) {
     DevGraph dg = view(g);
     const Tile* vt = p->d_tiles;
     const Tile* ht = p->d_tiles + p->n_vtiles;
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
-                                                                Dtab, nullptr, Eout, nullptr, g->d_status, lm);
+                                                                nullptr, Eout, nullptr, g->d_status, vrec);
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
-        k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(dg, ht, MODE_SWEEP, 1, d_cfg, nullptr, xin, Dtab,
-                                                              nullptr, Sout, nullptr, lm);
+        k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(dg, ht, MODE_SWEEP, 1, d_cfg, nullptr, xin, vrec,
+                                                              nullptr, Sout, nullptr);
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
@@ -1094,7 +1158,7 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     EMWork& w = g->em;
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
-                                                                nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
+                                                                nullptr, prev, Ein, nullptr, w.d_vpart,
                                                                 g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
@@ -1138,7 +1202,7 @@ int sweep_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* xin, const d
     PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
     int r = PMRF_OK;
     DISPATCH_L(rc.L, r = sweep_body<L>(g, p, s, (const RunCfg*)w.d_cfg, xin, theta, xout, Eout, Sout,
-                                       w.d_Dtab, w.d_lm));
+                                       w.d_vrec));
     PMRF_CUDA(cudaStreamSynchronize(s));  // the host RunCfg copy is a stack value
     return r;
 }

@@ -38,8 +38,7 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     double* d_hpart = nullptr;     // [n_htiles][2] (T partial, unconverged count)
     double* d_theta = nullptr;     // [S][L][4] current parameters
     double* d_Thist = nullptr;     // [S][W] ring of totals
-    __int128* d_Dtab = nullptr;    // [V][L] data term of the current iteration, units of 2^-80
-    uint32_t* d_lm = nullptr;      // [V][L] neighbour-label masks over each vertex's adjacency slots
+    uint64_t* d_vrec = nullptr;    // [V][vrec_words(L)] hood-pass vertex records (em.cu)
     int32_t* d_active = nullptr;   // [S] slice still iterating
     int32_t* d_iters = nullptr;    // [S]
     int32_t* d_conv = nullptr;     // [S]
