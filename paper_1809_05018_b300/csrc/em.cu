@@ -158,6 +158,9 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
 // ---------------------------------------------------------------------------
 // vertex pass
 
+// 1 / (2 sigma^2) of the Gaussian data term (one expression for every caller)
+__device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * sg * sg); }
+
 // the hood-pass record of vertex v (layout above) from its FP64 data terms
 template <int L>
 __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t v, const double (&D)[L],
@@ -209,6 +212,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
                                                        const int32_t* __restrict__ active,
                                                        const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
                                                        const double* __restrict__ theta,
+                                                       const double* __restrict__ dterm,
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
                                                        double* __restrict__ vpart, DevStatus* st,
                                                        uint64_t* __restrict__ vrec) {
@@ -216,6 +220,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     __shared__ double s_vq[3][VT_THREADS];
     __shared__ double s_vc[3 * L][8];
     __shared__ uint8_t s_vl[VT_THREADS];
+    __shared__ int s_cnt[VT_THREADS / 32][L];
     const Tile tile = tiles[blockIdx.x];
     const int s = tile.slice;
     if (active && !active[s]) return;
@@ -226,11 +231,16 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
             s_K[l] = bin_centre(c, l);
         } else {
             const double mu = theta[((int64_t)s * L + l) * 4 + 1];
-            const double sg = theta[((int64_t)s * L + l) * 4 + 2];
             s_mu[l] = mu;
-            s_inv[l] = 1.0 / (2.0 * sg * sg);
-            s_lnsig[l] = log(sg);
             s_K[l] = mu;
+            if (dterm) {  // the finaliser's per-slice values (EM loop)
+                s_inv[l] = dterm[((int64_t)s * L + l) * 2 + 0];
+                s_lnsig[l] = dterm[((int64_t)s * L + l) * 2 + 1];
+            } else {
+                const double sg = theta[((int64_t)s * L + l) * 4 + 2];
+                s_inv[l] = inv_two_var(sg);
+                s_lnsig[l] = log(sg);
+            }
         }
     }
     __syncthreads();
@@ -238,6 +248,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     const bool ok = v < tile.a1;
     int vlab = 0;
     double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
+    bool have_dev = false;                   // EM/sweep: y - mu_lab and its square already known
     if (ok) {
         const double y = g.y[v];
         int lab = 0;
@@ -253,11 +264,12 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
             // a caller's labels (standalone sweep) must lie in [0, L)
             if (mode == MODE_SWEEP && x_in[v] >= L) record_error(st, PMRF_ERR_ARG, SITE_LABEL, v);
             // data term D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l
-            double D[L];
+            double D[L], dev[L], dev2[L];
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                const double dev = y - s_mu[l];
-                D[l] = dev * dev * s_inv[l] + s_lnsig[l];
+                dev[l] = y - s_mu[l];
+                dev2[l] = dev[l] * dev[l];
+                D[l] = dev2[l] * s_inv[l] + s_lnsig[l];
             }
             const int64_t a0 = g.adj_off[v];
             const int d = (int)(g.adj_off[v + 1] - a0);
@@ -315,13 +327,23 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
             }
             x_out[v] = (uint8_t)lab;
             if (E_out) E_out[v] = Estar;
+            // K = mu here: the moments reuse y - mu_lab and its square
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+                if (l == lab) {
+                    vq0 = dev[l];
+                    vq1 = dev2[l];
+                }
+            have_dev = true;
         }
         if (mode == MODE_INIT) x_out[v] = (uint8_t)lab;
         if (mode != MODE_SWEEP) {
-            const double dv = y - s_K[lab];
+            if (!have_dev) {
+                const double dv = y - s_K[lab];
+                vq0 = dv;
+                vq1 = dv * dv;
+            }
             vlab = lab;
-            vq0 = dv;
-            vq1 = dv * dv;
             vq2 = Estar;
         }
     }
@@ -331,6 +353,12 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     // order, then one thread adds the 8 results (no shuffle trees: the FP64
     // pipe is the scarce unit)
     s_vl[threadIdx.x] = ok ? (uint8_t)vlab : (uint8_t)0xff;
+    // label counts of the tile by warp ballots
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const unsigned b = __ballot_sync(0xffffffffu, ok && vlab == l);
+        if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5][l] = __popc(b);
+    }
     s_vq[0][threadIdx.x] = vq0;
     s_vq[1][threadIdx.x] = vq1;
     s_vq[2][threadIdx.x] = vq2;
@@ -347,7 +375,7 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     } else if (threadIdx.x >= 3 * L * 8 && threadIdx.x < 3 * L * 8 + L) {
         const int l = threadIdx.x - 3 * L * 8;
         int n = 0;
-        for (int i = 0; i < VT_THREADS; ++i) n += (s_vl[i] == l);
+        for (int w = 0; w < VT_THREADS / 32; ++w) n += s_cnt[w][l];
         vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
     }
     __syncthreads();
@@ -362,8 +390,6 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
 // ---------------------------------------------------------------------------
 // hood pass
 
-// exact min_l D_l(y_v) + beta * (dc - cnt_l) in units of 2^-80, ties to the
-// lower label
 // decoded hood-pass record of one vertex (dq[amin] = 0)
 template <int L>
 struct VRec {
@@ -597,7 +623,8 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
                            const double* __restrict__ theta_prev, double* __restrict__ theta,
                            const int64_t* __restrict__ vert_off, int32_t* __restrict__ active,
                            int32_t* __restrict__ iters, int32_t* __restrict__ conv, double* __restrict__ Thist,
-                           int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op) {
+                           int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op,
+                           double* __restrict__ dterm) {
     const int s = blockIdx.x;
     if (s >= S) return;
     const RunCfg cf = *cfgp;
@@ -648,6 +675,10 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
             th[1] = mu_prev;
             th[2] = sg_prev;
             th[3] = 0.0;
+        }
+        if (dterm) {  // read by the next vertex pass instead of recomputing them per block
+            dterm[((int64_t)s * L + l) * 2 + 0] = inv_two_var(th[2]);
+            dterm[((int64_t)s * L + l) * 2 + 1] = log(th[2]);
         }
     }
     if (mode == MODE_INIT) {
@@ -807,7 +838,7 @@ int free_plans(pmrf_graph* g) {
 
 int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
-    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_Thist, w.d_vrec,
+    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_dterm, w.d_Thist, w.d_vrec,
                   w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
@@ -938,6 +969,7 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) 
     if (!rc2) rc2 = dalloc(&w.d_vpart, p.n_vtiles * 4 * rc.L, s);
     if (!rc2) rc2 = dalloc(&w.d_hpart, p.n_htiles * 2, s);
     if (!rc2) rc2 = dalloc(&w.d_theta, S * rc.L * 4, s);
+    if (!rc2) rc2 = dalloc(&w.d_dterm, S * rc.L * 2, s);
     if (!rc2) rc2 = dalloc(&w.d_Thist, S * rc.W, s);
     if (!rc2) rc2 = dalloc(&w.d_active, S, s);
     if (!rc2) rc2 = dalloc(&w.d_iters, S, s);
@@ -986,13 +1018,14 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     k_zero_T<<<64, 256, 0, s>>>(z.d_out, (int64_t)S * rc.max_iters); ::pmrf::note_launch(1);
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
-                                                                w.d_x[1], w.d_x[0], nullptr, nullptr,
+                                                                w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
                                                                 nullptr, w.d_vpart, g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                             w.d_hpart, nullptr, w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
-                                            w.d_conv, w.d_Thist, w.d_nactive, z.d_out); ::pmrf::note_launch(1);
+                                            w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
+    ::pmrf::note_launch(1);
     const bool prof = g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
     for (int t = 1; t <= rc.max_iters; ++t) {
         const uint8_t* xin = w.d_x[(t - 1) & 1];
@@ -1000,7 +1033,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
         if (p->n_vtiles > 0) {
             k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
-                                                                    xout, w.d_theta, nullptr, nullptr,
+                                                                    xout, w.d_theta, w.d_dterm, nullptr, nullptr,
                                                                     w.d_vpart, g->d_status, w.d_vrec);
             ::pmrf::note_launch(1);
         }
@@ -1013,7 +1046,8 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
         k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                                 w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off, w.d_active,
-                                                w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out); ::pmrf::note_launch(1);
+                                                w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
+        ::pmrf::note_launch(1);
     }
     k_close<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->V, 256), 4096)), 256, 0, s>>>(
         z.dg, rc.L, w.d_x[0], w.d_x[1], w.d_iters, w.d_conv, w.d_theta, z.d_out); ::pmrf::note_launch(1);
@@ -1139,7 +1173,7 @@ int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, cons
     const Tile* ht = p->d_tiles + p->n_vtiles;
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
-                                                                nullptr, Eout, nullptr, g->d_status, vrec);
+                                                                nullptr, nullptr, Eout, nullptr, g->d_status, vrec);
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
@@ -1158,13 +1192,14 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     EMWork& w = g->em;
     if (p->n_vtiles > 0) {
         k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
-                                                                nullptr, prev, Ein, nullptr, w.d_vpart,
+                                                                nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
                                                                 g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
                                                w.d_vpart, w.d_hpart, prev, out, g->d_vert_off, nullptr, nullptr,
-                                               nullptr, nullptr, nullptr, nullptr); ::pmrf::note_launch(1);
+                                               nullptr, nullptr, nullptr, nullptr, nullptr);
+    ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;
 }

@@ -37,6 +37,7 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     double* d_vpart = nullptr;     // [n_vtiles][L][4]
     double* d_hpart = nullptr;     // [n_htiles][2] (T partial, unconverged count)
     double* d_theta = nullptr;     // [S][L][4] current parameters
+    double* d_dterm = nullptr;     // [S][L][2] 1/(2 sigma^2) and ln sigma of the current parameters
     double* d_Thist = nullptr;     // [S][W] ring of totals
     uint64_t* d_vrec = nullptr;    // [V][vrec_words(L)] hood-pass vertex records (em.cu)
     int32_t* d_active = nullptr;   // [S] slice still iterating
