@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import argparse
 import csv
+import hashlib
 import io
 import json
 import os
@@ -37,6 +38,33 @@ import synth  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
+
+# DRAM traffic of the dominant kernel from one ncu capture (the command and the
+# counters are in profiles/k_hood_stack512.md): dram__bytes_read.sum +
+# dram__bytes_write.sum of the first hood-pass launch of this bench's first step
+# (every slice active), with the SHA-1 of the sources it was taken on.  It is
+# reported, scaled to the average launch by its algorithmic bytes, only while
+# those sources are unchanged; otherwise the field is null.
+TRAFFIC_CAPTURE = {"kernel": "k_hood", "workload": "stack512", "bytes_all_active": 3488676864.0,
+                   "sources_sha1": "6b57c39fae3e23fae6cd193aad8f7fa98f3e17be"}
+TRAFFIC_SOURCES = ("paper_1809_05018_b300/csrc/em.cu", "paper_1809_05018_b300/csrc/graph.cuh",
+                   "paper_1809_05018_b300/csrc/common.cuh")
+
+
+def sources_sha1() -> str:
+    h = hashlib.sha1()
+    for rel in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
+def captured_traffic(kernel: str, workload: str, per_launch: float, all_active: float):
+    c = TRAFFIC_CAPTURE
+    if (c["bytes_all_active"] is None or kernel != c["kernel"] or workload != c["workload"]
+            or c["sources_sha1"] != sources_sha1() or all_active <= 0):
+        return None
+    return round(c["bytes_all_active"] * per_launch / all_active, 1)
 
 
 def parse():
@@ -264,6 +292,8 @@ def run_ours(a):
     dom = "k_hood" if sum(msh) >= sum(msv) else "k_vertex"
     ach = bw_h if dom == "k_hood" else bw_v
     per_launch = (sum(tb_h) / len(tb_h)) if dom == "k_hood" else (sum(tb_v) / len(tb_v))
+    all_active = float(hb.sum()) if dom == "k_hood" else float(vb.sum())
+    traffic = captured_traffic(dom, wl.name, per_launch, all_active)
 
     # ---- plain: one call per slice on a sample of slices
     ps = min(a.plain_sample, S)
@@ -335,8 +365,9 @@ def run_ours(a):
             "plain_slices_per_s": round(plain, 3), "plain_sample": ps,
             "iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
-                         "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": None,
+                         "unit": "GB/s", "frac": round(ach / hbm, 4), "traffic": traffic,
                          "peak_source": peak_kind, "bytes_per_launch": per_launch,
+                         "bytes_per_launch_all_active": all_active, "sources_sha1": sources_sha1(),
                          "k_vertex_GBs": round(bw_v, 1), "k_hood_GBs": round(bw_h, 1),
                          "k_vertex_ms": round(sum(msv), 3), "k_hood_ms": round(sum(msh), 3)},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
