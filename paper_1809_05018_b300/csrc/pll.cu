@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
                                                      const double* __restrict__ mu, const double* __restrict__ sigma,
                                                      double beta, int64_t nchunk, double* __restrict__ part) {
     constexpr int NP = 2 * L + 2;  // pll, gmu[L], gsigma[L], gbeta
-    __shared__ double s_mu[L], s_sg[L], s_inv[L], s_ln[L];
+    __shared__ double s_mu[L], s_inv[L], s_ln[L], s_isg[L], s_isg2[L], s_isg3[L];
     __shared__ double s_red[PLL_THREADS / 32][NP];
     const int s = blockIdx.y;
     const int64_t vb = vert_off[s], ve = vert_off[s + 1];
@@ -36,9 +36,13 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
     if (threadIdx.x < L) {
         const double m = mu[(int64_t)s * L + threadIdx.x], sg = sigma[(int64_t)s * L + threadIdx.x];
         s_mu[threadIdx.x] = m;
-        s_sg[threadIdx.x] = sg;
         s_inv[threadIdx.x] = 1.0 / (2.0 * sg * sg);
         s_ln[threadIdx.x] = log(sg);
+        // reciprocals for the adjoint: per-vertex divisions become products
+        const double isg = 1.0 / sg;
+        s_isg[threadIdx.x] = isg;
+        s_isg2[threadIdx.x] = isg * isg;
+        s_isg3[threadIdx.x] = isg * isg * isg;
     }
     __syncthreads();
     double acc[NP];
@@ -57,35 +61,48 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
             for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
         }
         const int d = (int)(a1 - a0);
-        double E[L], emin = 0.0;
+        double E[L], dev[L], dev2[L], emin = 0.0;
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            const double dev = yv - s_mu[l];
-            E[l] = dev * dev * s_inv[l] + s_ln[l] + beta * (double)(d - cnt[l]);
+            dev[l] = yv - s_mu[l];
+            dev2[l] = dev[l] * dev[l];
+            E[l] = dev2[l] * s_inv[l] + s_ln[l] + beta * (double)(d - cnt[l]);
             emin = (l == 0 || E[l] < emin) ? E[l] : emin;
         }
-        double z = 0.0, p[L];
+        // p = softmax(-E) with the minimum shifted out; log z of the same sum
+        double p[L], logz;
+        if constexpr (L == 2) {
+            // one exponential: z = 1 + exp(-|E_0 - E_1|)
+            const double e = exp(-fabs(E[0] - E[1]));
+            const double inv_z = 1.0 / (1.0 + e);
+            const bool zero_min = E[0] <= E[1];
+            p[0] = zero_min ? inv_z : e * inv_z;
+            p[L - 1] = zero_min ? e * inv_z : inv_z;
+            logz = log1p(e);
+        } else {
+            double z = 0.0;
 #pragma unroll
-        for (int l = 0; l < L; ++l) {
-            p[l] = exp(-(E[l] - emin));
-            z += p[l];
+            for (int l = 0; l < L; ++l) {
+                p[l] = exp(-(E[l] - emin));
+                z += p[l];
+            }
+            const double inv_z = 1.0 / z;
+#pragma unroll
+            for (int l = 0; l < L; ++l) p[l] *= inv_z;
+            logz = log(z);
         }
-        const double inv_z = 1.0 / z;
         double Ex = 0.0, mx = 0.0, eb = 0.0;
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            p[l] *= inv_z;
             if (l == xv) { Ex = E[l]; mx = (double)(d - cnt[l]); }
             eb += p[l] * (double)(d - cnt[l]);
         }
-        acc[0] = -Ex - (-emin + log(z));
+        acc[0] = -Ex - (-emin + logz);
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             const double w = p[l] - (l == xv ? 1.0 : 0.0);
-            const double sg = s_sg[l];
-            const double dev = yv - s_mu[l];
-            acc[1 + l] = w * (s_mu[l] - yv) / (sg * sg);
-            acc[1 + L + l] = w * (1.0 / sg - dev * dev / (sg * sg * sg));
+            acc[1 + l] = -w * dev[l] * s_isg2[l];
+            acc[1 + L + l] = w * (s_isg[l] - dev2[l] * s_isg3[l]);
         }
         acc[1 + 2 * L] = eb - mx;
     }
