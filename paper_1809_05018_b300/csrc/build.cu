@@ -113,15 +113,26 @@ __global__ void k_inv_rank(const int32_t* __restrict__ rank, const int64_t* __re
     inv[v] = (int32_t)(i - rank_off[s]);
 }
 
-// y_v for compact regions: the region's bounding box scanned in row-major
-// order, adding the pixels that carry its id -- the same additions, in the
-// same order, as a serial row-major accumulation.  Regions whose box is much
-// larger than their pixel count are flagged for the pixel-list path.
-__global__ void k_means_bbox(const double* __restrict__ img, const int32_t* __restrict__ ids,
-                             const int64_t* __restrict__ pix_off, const int64_t* __restrict__ Wd,
-                             const int64_t* __restrict__ vert_off, int32_t S, const int32_t* __restrict__ inv,
-                             const int4* __restrict__ bbox, const int32_t* __restrict__ npix, int64_t V,
-                             double* __restrict__ y, int32_t* __restrict__ fb_pix) {
+// One thread per region with a compact bounding box (area <= 4 n + 64): the
+// box is scanned in row-major order, adding the pixels that carry the region's
+// id -- the same additions, in the same order, as a serial row-major
+// accumulation -- and, for each of those pixels, reading its 4-neighbours: every
+// other id met is a neighbouring region (4-connectivity), kept in a small
+// sorted set of raw ids (raw ids and vertex ids sort alike within a slice).
+// Outputs: y_v; the region's neighbour vertex ids, ascending, at
+// nbr[v * NB_CAP ...) and their number in deg[v].  Regions whose box is too
+// sparse (their mean then comes from a sorted pixel list: fb_pix[v] = n) or
+// that have more than NB_CAP neighbours get fb_adj[v] = 1: their adjacency
+// comes from the pixel-pair path.
+constexpr int NB_CAP = 32;
+
+__global__ void k_region_scan(const double* __restrict__ img, const int32_t* __restrict__ ids,
+                              const int64_t* __restrict__ pix_off, const int64_t* __restrict__ Wd,
+                              const int64_t* __restrict__ vert_off, const int64_t* __restrict__ rank_off,
+                              const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv,
+                              const int4* __restrict__ bbox, const int32_t* __restrict__ npix, int64_t V,
+                              double* __restrict__ y, int32_t* __restrict__ fb_pix, int32_t* __restrict__ fb_adj,
+                              int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int4 bb = bbox[v];
@@ -129,19 +140,56 @@ __global__ void k_means_bbox(const double* __restrict__ img, const int32_t* __re
     const int64_t area = (int64_t)(bb.y - bb.x + 1) * (int64_t)(bb.w - bb.z + 1);
     if (area > 4 * n + 64) {
         fb_pix[v] = (int32_t)n;
+        fb_adj[v] = 1;
+        deg[v] = 0;
         return;
     }
     fb_pix[v] = 0;
     const int s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
     const int64_t b = pix_off[s], W = Wd[s];
+    const int64_t H = (pix_off[s + 1] - b) / W;
     const int32_t id = inv[v];
+    int32_t nb[NB_CAP];
+    int nn = 0;
+    bool over = false;
+    int32_t last = id;
     double acc = 0.0;
     for (int r = bb.x; r <= bb.y; ++r) {
         const int64_t row = b + (int64_t)r * W;
-        for (int c = bb.z; c <= bb.w; ++c)
-            if (ids[row + c] == id) acc += img[row + c];
+        for (int c = bb.z; c <= bb.w; ++c) {
+            if (ids[row + c] != id) continue;
+            acc += img[row + c];
+            int32_t q[4];
+            q[0] = c + 1 < W ? ids[row + c + 1] : id;
+            q[1] = r + 1 < H ? ids[row + W + c] : id;
+            q[2] = c > 0 ? ids[row + c - 1] : id;
+            q[3] = r > 0 ? ids[row - W + c] : id;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int32_t u = q[k];
+                if (u == id || u == last) continue;
+                last = u;
+                int pos = 0;
+                while (pos < nn && nb[pos] < u) ++pos;
+                if (pos < nn && nb[pos] == u) continue;
+                if (nn == NB_CAP) {
+                    over = true;
+                    continue;
+                }
+                for (int j = nn; j > pos; --j) nb[j] = nb[j - 1];
+                nb[pos] = u;
+                ++nn;
+            }
+        }
     }
     y[v] = acc / (double)n;
+    fb_adj[v] = over ? 1 : 0;
+    deg[v] = over ? 0 : nn;
+    if (!over) {
+        const int64_t rb = rank_off[s];
+        int32_t* out = nbr + v * NB_CAP;
+        for (int k = 0; k < nn; ++k) out[k] = rank[rb + nb[k]];
+    }
 }
 
 __global__ void k_fill_pix(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
@@ -176,7 +224,7 @@ __global__ void k_means(const double* __restrict__ img, const uint32_t* __restri
                         const int64_t* __restrict__ vpix_off, int64_t V, double* __restrict__ y) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    if (vpix_off[v + 1] == vpix_off[v]) return;  // region summed by k_means_bbox
+    if (vpix_off[v + 1] == vpix_off[v]) return;  // region summed by k_region_scan
     double acc = 0.0;
     const int64_t b = vpix_off[v], e = vpix_off[v + 1];
     for (int64_t i = b; i < e; ++i) acc += img[pixlist[i]];
@@ -184,17 +232,18 @@ __global__ void k_means(const double* __restrict__ img, const uint32_t* __restri
 }
 
 // ---------------------------------------------------------------------------
-// edges: 4-connected pixel pairs with different regions.  A pair that repeats
-// the same (left/top, right/bottom) vertex pair as its neighbour along the
-// boundary is skipped (the earlier one stands for it); the final sort+unique
-// gives the same set either way.
+// edges of the regions the scan could not take (only[v] != 0): 4-connected
+// pixel pairs with different regions, each delivered to its flagged endpoints.
+// A pair that repeats the same (left/top, right/bottom) vertex pair as its
+// neighbour along the boundary is skipped (the earlier one stands for it); the
+// final sort+unique gives the same set either way.
 
 template <bool FILL>
 __global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
                              const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
-                             const int32_t* __restrict__ rank, int32_t* __restrict__ cnt,
-                             const int64_t* __restrict__ cand_off, int32_t* __restrict__ cursor,
-                             uint32_t* __restrict__ cand) {
+                             const int32_t* __restrict__ rank, const int32_t* __restrict__ only,
+                             int32_t* __restrict__ cnt, const int64_t* __restrict__ cand_off,
+                             int32_t* __restrict__ cursor, uint32_t* __restrict__ cand) {
     const int s = blockIdx.y;
     const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
     if (W <= 0) return;
@@ -219,13 +268,15 @@ __global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __r
                 if (!dup) { pa[np] = a; pb[np] = bb; ++np; }
             }
         }
+        // each endpoint that takes the pixel-pair path receives the other one
         for (int k = 0; k < np; ++k) {
+            const bool ta = only[pa[k]] != 0, tb = only[pb[k]] != 0;
             if (!FILL) {
-                atomicAdd(&cnt[pa[k]], 1);
-                atomicAdd(&cnt[pb[k]], 1);
+                if (ta) atomicAdd(&cnt[pa[k]], 1);
+                if (tb) atomicAdd(&cnt[pb[k]], 1);
             } else {
-                cand[cand_off[pa[k]] + atomicAdd(&cursor[pa[k]], 1)] = (uint32_t)pb[k];
-                cand[cand_off[pb[k]] + atomicAdd(&cursor[pb[k]], 1)] = (uint32_t)pa[k];
+                if (ta) cand[cand_off[pa[k]] + atomicAdd(&cursor[pa[k]], 1)] = (uint32_t)pb[k];
+                if (tb) cand[cand_off[pb[k]] + atomicAdd(&cursor[pb[k]], 1)] = (uint32_t)pa[k];
             }
         }
     }
@@ -239,13 +290,28 @@ __global__ void k_check_degree(const int32_t* __restrict__ deg, int64_t V, int32
     atomicMax(dmax, deg[v]);
 }
 
-// copy the first cnt[k] values of segment k (at src_off[k]) to dst_off[k]
-__global__ void k_compact(const uint32_t* __restrict__ src, const int64_t* __restrict__ src_off,
-                          const int64_t* __restrict__ dst_off, int64_t nseg, int32_t* __restrict__ dst) {
-    int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= nseg) return;
-    const int64_t b = src_off[k], o = dst_off[k], n = dst_off[k + 1] - o;
-    for (int64_t i = 0; i < n; ++i) dst[o + i] = (int32_t)src[b + i];
+// flagged vertices take their de-duplicated candidate count as degree
+__global__ void k_take_counts(const int32_t* __restrict__ fb_adj, const int32_t* __restrict__ ucnt, int64_t V,
+                              int32_t* __restrict__ deg) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v < V && fb_adj[v]) deg[v] = ucnt[v];
+}
+
+// adjacency of every vertex: from its region scan, or (flagged vertices) from
+// its sorted, de-duplicated pixel-pair candidates
+__global__ void k_adj_fill(const int32_t* __restrict__ fb_adj, const int32_t* __restrict__ nbr,
+                           const uint32_t* __restrict__ cand, const int64_t* __restrict__ cand_off,
+                           const int64_t* __restrict__ adj_off, int64_t V, int32_t* __restrict__ adj) {
+    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (v >= V) return;
+    const int64_t o = adj_off[v], n = adj_off[v + 1] - o;
+    if (fb_adj[v]) {
+        const int64_t b = cand_off[v];
+        for (int64_t i = 0; i < n; ++i) adj[o + i] = (int32_t)cand[b + i];
+    } else {
+        const int32_t* src = nbr + v * NB_CAP;
+        for (int64_t i = 0; i < n; ++i) adj[o + i] = src[i];
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -748,20 +814,24 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     g->V = V;
     if (V >= 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "more than 2^31-1 regions");
 
-    // 3. region means (row-major order per region): bounding-box scan for
-    //    compact regions, sorted pixel lists for the rest
+    // 3. region means (row-major order per region) and neighbours: one
+    //    bounding-box scan per compact region; sorted pixel lists (means) and
+    //    pixel-pair candidates (adjacency) for the regions it cannot take
     PMRF_TRY(dalloc(&g->d_npix, V, s));
     PMRF_TRY(dalloc(&g->d_y, V, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_npix, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     int64_t* d_vpix_off = nullptr;
     int32_t* d_cursor = nullptr;
     int4* d_bbox = nullptr;
-    int32_t *d_inv = nullptr, *d_fbpix = nullptr;
+    int32_t *d_inv = nullptr, *d_fbpix = nullptr, *d_fbadj = nullptr, *d_deg = nullptr, *d_nbr = nullptr;
     PMRF_TRY(tmp.get(&d_vpix_off, V + 1));
     PMRF_TRY(tmp.get(&d_cursor, V));
     PMRF_TRY(tmp.get(&d_bbox, V));
     PMRF_TRY(tmp.get(&d_inv, V));
     PMRF_TRY(tmp.get(&d_fbpix, V));
+    PMRF_TRY(tmp.get(&d_fbadj, V));
+    PMRF_TRY(tmp.get(&d_deg, V));
+    PMRF_TRY(tmp.get(&d_nbr, V * NB_CAP));
     LAUNCH_1D(k_init_bbox, V, d_bbox, V);
     if (g->n_pix > 0) {
         k_count_bbox<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank, g->d_npix,
@@ -770,8 +840,8 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         PMRF_CUDA(cudaGetLastError());
     }
     LAUNCH_1D(k_inv_rank, g->n_rank, g->d_rank, g->d_rank_off, S, g->n_rank, d_inv);
-    LAUNCH_1D(k_means_bbox, V, d_img, d_ids, g->d_pix_off, g->d_W, g->d_vert_off, S, d_inv, d_bbox, g->d_npix, V,
-              g->d_y, d_fbpix);
+    LAUNCH_1D(k_region_scan, V, d_img, d_ids, g->d_pix_off, g->d_W, g->d_vert_off, g->d_rank_off, g->d_rank, S, d_inv,
+              d_bbox, g->d_npix, V, g->d_y, d_fbpix, d_fbadj, d_deg, d_nbr);
     PMRF_TRY(exclusive_scan_i32_to_i64(d_fbpix, d_vpix_off, V, s));
     int64_t nfb = 0;
     PMRF_TRY(read_i64(d_vpix_off + V, &nfb, s));
@@ -787,30 +857,34 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y);
     }
 
-    // 4. adjacency
-    int32_t* d_cnt = nullptr;
+    // 4. adjacency: the scans' neighbour lists, and for the flagged regions the
+    //    4-connected pixel pairs they take part in, sorted and de-duplicated
     int64_t* d_cand_off = nullptr;
-    PMRF_TRY(tmp.get(&d_cnt, V));
-    PMRF_TRY(tmp.get(&d_cand_off, V + 1));
-    PMRF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-    if (g->n_pix > 0) {
-        k_edge_pairs<false><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank, d_cnt,
-                                                         nullptr, nullptr, nullptr); ::pmrf::note_launch(1);
-        PMRF_CUDA(cudaGetLastError());
-    }
-    PMRF_TRY(exclusive_scan_i32_to_i64(d_cnt, d_cand_off, V, s));
-    int64_t ncand = 0;
-    PMRF_TRY(read_i64(d_cand_off + V, &ncand, s));
     uint32_t* d_cand = nullptr;
-    PMRF_TRY(tmp.get(&d_cand, ncand));
-    PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-    if (g->n_pix > 0) {
-        k_edge_pairs<true><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank,
-                                                        nullptr, d_cand_off, d_cursor, d_cand); ::pmrf::note_launch(1);
+    PMRF_TRY(tmp.get(&d_cand_off, V + 1));
+    PMRF_TRY(exclusive_scan_i32_to_i64(d_fbadj, d_cand_off, V, s));
+    int64_t nfa = 0;
+    PMRF_TRY(read_i64(d_cand_off + V, &nfa, s));
+    if (nfa > 0 && g->n_pix > 0) {
+        int32_t* d_cnt = nullptr;
+        PMRF_TRY(tmp.get(&d_cnt, V));
+        PMRF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+        k_edge_pairs<false><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank,
+                                                         d_fbadj, d_cnt, nullptr, nullptr, nullptr);
+        ::pmrf::note_launch(1);
         PMRF_CUDA(cudaGetLastError());
+        PMRF_TRY(exclusive_scan_i32_to_i64(d_cnt, d_cand_off, V, s));
+        int64_t ncand = 0;
+        PMRF_TRY(read_i64(d_cand_off + V, &ncand, s));
+        PMRF_TRY(tmp.get(&d_cand, ncand));
+        PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+        k_edge_pairs<true><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank,
+                                                        d_fbadj, nullptr, d_cand_off, d_cursor, d_cand);
+        ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaGetLastError());
+        PMRF_TRY(segmented_sort_u32(d_cand, d_cand_off, V, ncand, true, d_cnt, g->d_status, s));
+        LAUNCH_1D(k_take_counts, V, d_fbadj, d_cnt, V, d_deg);
     }
-    int32_t* d_deg = d_cnt;  // reused: unique counts
-    PMRF_TRY(segmented_sort_u32(d_cand, d_cand_off, V, ncand, true, d_deg, g->d_status, s));
     int32_t* d_dmax = nullptr;
     PMRF_TRY(tmp.get(&d_dmax, 1));
     PMRF_CUDA(cudaMemsetAsync(d_dmax, 0, sizeof(int32_t), s));
@@ -821,7 +895,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(read_i64(g->d_adj_off + V, &g->E2, s));
     PMRF_CUDA(cudaMemcpyAsync(&g->max_deg, d_dmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
     PMRF_TRY(dalloc(&g->d_adj, g->E2, s));
-    LAUNCH_1D(k_compact, V, d_cand, d_cand_off, g->d_adj_off, V, g->d_adj);
+    LAUNCH_1D(k_adj_fill, V, d_fbadj, d_nbr, d_cand, d_cand_off, g->d_adj_off, V, g->d_adj);
 
     // 5. maximal cliques
     int64_t *d_ncl = nullptr, *d_nmem = nullptr, *d_cq_off = nullptr, *d_mem_off = nullptr;
