@@ -26,6 +26,11 @@ struct SliceGeo {  // per-slice geometry for the pixel kernels
     const int64_t* rank_off;
 };
 
+// finite double, from its exponent bits (no floating-point instruction)
+__device__ __forceinline__ bool finite_bits(double x) {
+    return ((__double_as_longlong(x) >> 52) & 0x7ff) != 0x7ff;
+}
+
 __device__ __forceinline__ int32_t vertex_of(const int32_t* ids, const int32_t* rank, int64_t rank_base, int64_t p) {
     return rank[rank_base + ids[p]];
 }
@@ -33,6 +38,8 @@ __device__ __forceinline__ int32_t vertex_of(const int32_t* ids, const int32_t* 
 // ---------------------------------------------------------------------------
 // regions
 
+// ids must be non-negative (they index the per-slice rank table) and the
+// intensities finite (checked on their exponent bits)
 __global__ void k_validate(const double* __restrict__ img, const int32_t* __restrict__ ids,
                            const int64_t* __restrict__ pix_off, int32_t* __restrict__ maxid, DevStatus* st) {
     const int s = blockIdx.y;
@@ -40,9 +47,8 @@ __global__ void k_validate(const double* __restrict__ img, const int32_t* __rest
     int32_t m = -1;
     for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
         const int32_t id = ids[p];
-        const double v = img[p];
         if (id < 0) record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
-        if (!isfinite(v)) record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
+        if (!finite_bits(img[p])) record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
         m = max(m, id);
     }
 #pragma unroll
@@ -50,12 +56,39 @@ __global__ void k_validate(const double* __restrict__ img, const int32_t* __rest
     if (lane_id() == 0 && m >= 0) atomicMax(&maxid[s], m);
 }
 
-__global__ void k_mark_present(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
-                               const int64_t* __restrict__ rank_off, int32_t* __restrict__ flags) {
+// pixel counts and bounding boxes (rows and columns inside the slice) of every
+// raw id present, indexed by its slot in the slice's rank table (so they need
+// no vertex numbering yet); lanes holding the same id combine first
+__global__ void k_count_raw(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                            const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
+                            int32_t* __restrict__ npix_raw, int4* __restrict__ bbox_raw) {
     const int s = blockIdx.y;
-    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s];
-    for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x)
-        flags[rb + ids[p]] = 1;
+    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
+        const int64_t p = base + threadIdx.x;
+        const bool ok = p < e;
+        const int32_t id = ok ? ids[p] : -1 - lane_id();
+        const unsigned grp = __match_any_sync(0xffffffffu, id);
+        const int64_t q = p - b;
+        const unsigned r = ok ? (unsigned)(q / W) : 0u, c = ok ? (unsigned)(q - (q / W) * W) : 0u;
+        const unsigned rmin = __reduce_min_sync(grp, r), rmax = __reduce_max_sync(grp, r);
+        const unsigned cmin = __reduce_min_sync(grp, c), cmax = __reduce_max_sync(grp, c);
+        if (ok && lane_id() == __ffs(grp) - 1) {
+            const int64_t k = rb + id;
+            atomicAdd(&npix_raw[k], __popc(grp));
+            atomicMin(&bbox_raw[k].x, (int)rmin);
+            atomicMax(&bbox_raw[k].y, (int)rmax);
+            atomicMin(&bbox_raw[k].z, (int)cmin);
+            atomicMax(&bbox_raw[k].w, (int)cmax);
+        }
+    }
+}
+
+// presence flags of the rank table: an id is present when it has pixels
+__global__ void k_present(const int32_t* __restrict__ npix_raw, int64_t n, int32_t* __restrict__ flags) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) flags[i] = npix_raw[i] > 0 ? 1 : 0;
 }
 
 // flags -> global vertex ids (in place), -1 for absent ids
@@ -68,33 +101,6 @@ __global__ void k_vert_off(const int64_t* __restrict__ ex, const int64_t* __rest
                            int64_t* __restrict__ vert_off) {
     int s = blockIdx.x * blockDim.x + threadIdx.x;
     if (s <= S) vert_off[s] = ex[rank_off[s]];
-}
-
-// pixel counts and bounding boxes (rows and columns inside the slice) of
-// every region, warp-aggregated: lanes holding the same vertex combine first
-__global__ void k_count_bbox(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
-                             const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
-                             const int32_t* __restrict__ rank, int32_t* __restrict__ npix, int4* __restrict__ bbox) {
-    const int s = blockIdx.y;
-    const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
-        const int64_t p = base + threadIdx.x;
-        const bool ok = p < e;
-        const int32_t v = ok ? vertex_of(ids, rank, rb, p) : -1 - lane_id();
-        const unsigned grp = __match_any_sync(0xffffffffu, v);
-        const int64_t q = p - b;
-        const unsigned r = ok ? (unsigned)(q / W) : 0u, c = ok ? (unsigned)(q - (q / W) * W) : 0u;
-        const unsigned rmin = __reduce_min_sync(grp, r), rmax = __reduce_max_sync(grp, r);
-        const unsigned cmin = __reduce_min_sync(grp, c), cmax = __reduce_max_sync(grp, c);
-        if (ok && lane_id() == __ffs(grp) - 1) {
-            atomicAdd(&npix[v], __popc(grp));
-            atomicMin(&bbox[v].x, (int)rmin);
-            atomicMax(&bbox[v].y, (int)rmax);
-            atomicMin(&bbox[v].z, (int)cmin);
-            atomicMax(&bbox[v].w, (int)cmax);
-        }
-    }
 }
 
 __global__ void k_init_bbox(int4* __restrict__ bbox, int64_t V) {
@@ -116,27 +122,49 @@ __global__ void k_inv_rank(const int32_t* __restrict__ rank, const int64_t* __re
 // One thread per region with a compact bounding box (area <= 4 n + 64): the
 // box is scanned in row-major order, adding the pixels that carry the region's
 // id -- the same additions, in the same order, as a serial row-major
-// accumulation -- and, for each of those pixels, reading its 4-neighbours: every
-// other id met is a neighbouring region (4-connectivity), kept in a small
-// sorted set of raw ids (raw ids and vertex ids sort alike within a slice).
-// Outputs: y_v; the region's neighbour vertex ids, ascending, at
+// accumulation.  The same scan, widened by one pixel above and to the left,
+// visits every horizontal and vertical 4-connected pixel pair that touches the
+// region: a pair with exactly one pixel in the region names a neighbouring
+// region, kept in a small sorted set of raw ids (raw ids and vertex ids sort
+// alike within a slice).  Each pixel's right neighbour is the next step's
+// pixel, so a step loads one new id (and the one below).
+// Outputs: y_v, n_v; the region's neighbour vertex ids, ascending, at
 // nbr[v * NB_CAP ...) and their number in deg[v].  Regions whose box is too
 // sparse (their mean then comes from a sorted pixel list: fb_pix[v] = n) or
 // that have more than NB_CAP neighbours get fb_adj[v] = 1: their adjacency
 // comes from the pixel-pair path.
 constexpr int NB_CAP = 32;
 
+__device__ __forceinline__ void nb_insert(int32_t (&nb)[NB_CAP], int& nn, bool& over, int32_t& last, int32_t u) {
+    if (u == last) return;
+    last = u;
+    int pos = 0;
+    while (pos < nn && nb[pos] < u) ++pos;
+    if (pos < nn && nb[pos] == u) return;
+    if (nn == NB_CAP) {
+        over = true;
+        return;
+    }
+    for (int j = nn; j > pos; --j) nb[j] = nb[j - 1];
+    nb[pos] = u;
+    ++nn;
+}
+
 __global__ void k_region_scan(const double* __restrict__ img, const int32_t* __restrict__ ids,
                               const int64_t* __restrict__ pix_off, const int64_t* __restrict__ Wd,
                               const int64_t* __restrict__ vert_off, const int64_t* __restrict__ rank_off,
                               const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv,
-                              const int4* __restrict__ bbox, const int32_t* __restrict__ npix, int64_t V,
-                              double* __restrict__ y, int32_t* __restrict__ fb_pix, int32_t* __restrict__ fb_adj,
-                              int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
+                              const int4* __restrict__ bbox_raw, const int32_t* __restrict__ npix_raw, int64_t V,
+                              double* __restrict__ y, int32_t* __restrict__ npix, int32_t* __restrict__ fb_pix,
+                              int32_t* __restrict__ fb_adj, int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
-    const int4 bb = bbox[v];
-    const int64_t n = npix[v];
+    const int s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
+    const int32_t id = inv[v];
+    const int64_t slot = rank_off[s] + id;
+    const int4 bb = bbox_raw[slot];
+    const int64_t n = npix_raw[slot];
+    npix[v] = (int32_t)n;
     const int64_t area = (int64_t)(bb.y - bb.x + 1) * (int64_t)(bb.w - bb.z + 1);
     if (area > 4 * n + 64) {
         fb_pix[v] = (int32_t)n;
@@ -145,41 +173,30 @@ __global__ void k_region_scan(const double* __restrict__ img, const int32_t* __r
         return;
     }
     fb_pix[v] = 0;
-    const int s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
     const int64_t b = pix_off[s], W = Wd[s];
-    const int64_t H = (pix_off[s + 1] - b) / W;
-    const int32_t id = inv[v];
+    const int H = (int)((pix_off[s + 1] - b) / W);
     int32_t nb[NB_CAP];
     int nn = 0;
     bool over = false;
     int32_t last = id;
     double acc = 0.0;
-    for (int r = bb.x; r <= bb.y; ++r) {
+    const int r0 = bb.x > 0 ? bb.x - 1 : 0, c0 = bb.z > 0 ? bb.z - 1 : 0;
+    for (int r = r0; r <= bb.y; ++r) {
         const int64_t row = b + (int64_t)r * W;
-        for (int c = bb.z; c <= bb.w; ++c) {
-            if (ids[row + c] != id) continue;
-            acc += img[row + c];
-            int32_t q[4];
-            q[0] = c + 1 < W ? ids[row + c + 1] : id;
-            q[1] = r + 1 < H ? ids[row + W + c] : id;
-            q[2] = c > 0 ? ids[row + c - 1] : id;
-            q[3] = r > 0 ? ids[row - W + c] : id;
-#pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int32_t u = q[k];
-                if (u == id || u == last) continue;
-                last = u;
-                int pos = 0;
-                while (pos < nn && nb[pos] < u) ++pos;
-                if (pos < nn && nb[pos] == u) continue;
-                if (nn == NB_CAP) {
-                    over = true;
-                    continue;
-                }
-                for (int j = nn; j > pos; --j) nb[j] = nb[j - 1];
-                nb[pos] = u;
-                ++nn;
+        const bool in_r = r >= bb.x, down = r + 1 < H;
+        int32_t cur = ids[row + c0];
+        for (int c = c0; c <= bb.w; ++c) {
+            const int32_t right = c + 1 < W ? ids[row + c + 1] : cur;
+            const int32_t below = down ? ids[row + W + c] : cur;
+            if (cur == id) {
+                if (in_r && c >= bb.z) acc += img[row + c];
+                if (right != id) nb_insert(nb, nn, over, last, right);
+                if (below != id) nb_insert(nb, nn, over, last, below);
+            } else {
+                if (right == id) nb_insert(nb, nn, over, last, cur);
+                if (below == id) nb_insert(nb, nn, over, last, cur);
             }
+            cur = right;
         }
     }
     y[v] = acc / (double)n;
@@ -795,11 +812,20 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(dalloc(&g->d_rank_off, S + 1, s));
     PMRF_CUDA(cudaMemcpyAsync(g->d_rank_off, g->h_rank_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
 
-    // 2. compact ids -> global vertex ids
-    PMRF_TRY(dalloc(&g->d_rank, g->n_rank, s));
-    PMRF_CUDA(cudaMemsetAsync(g->d_rank, 0, sizeof(int32_t) * std::max<int64_t>(g->n_rank, 1), s));
-    if (g->n_pix > 0) { k_mark_present<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_rank_off, g->d_rank); ::pmrf::note_launch(1); }
+    // 2. pixel counts and boxes per raw id; compact ids -> global vertex ids
+    int32_t* d_npix_raw = nullptr;
+    int4* d_bbox_raw = nullptr;
+    PMRF_TRY(tmp.get(&d_npix_raw, g->n_rank));
+    PMRF_TRY(tmp.get(&d_bbox_raw, g->n_rank));
+    PMRF_CUDA(cudaMemsetAsync(d_npix_raw, 0, sizeof(int32_t) * std::max<int64_t>(g->n_rank, 1), s));
+    LAUNCH_1D(k_init_bbox, g->n_rank, d_bbox_raw, g->n_rank);
+    if (g->n_pix > 0) {
+        k_count_raw<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, d_npix_raw, d_bbox_raw);
+        ::pmrf::note_launch(1);
+    }
     PMRF_CUDA(cudaGetLastError());
+    PMRF_TRY(dalloc(&g->d_rank, g->n_rank, s));
+    LAUNCH_1D(k_present, g->n_rank, d_npix_raw, g->n_rank, g->d_rank);
     int64_t* d_ex = nullptr;
     PMRF_TRY(tmp.get(&d_ex, g->n_rank + 1));
     PMRF_TRY(exclusive_scan_i32_to_i64(g->d_rank, d_ex, g->n_rank, s));
@@ -819,29 +845,19 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     //    pixel-pair candidates (adjacency) for the regions it cannot take
     PMRF_TRY(dalloc(&g->d_npix, V, s));
     PMRF_TRY(dalloc(&g->d_y, V, s));
-    PMRF_CUDA(cudaMemsetAsync(g->d_npix, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     int64_t* d_vpix_off = nullptr;
     int32_t* d_cursor = nullptr;
-    int4* d_bbox = nullptr;
     int32_t *d_inv = nullptr, *d_fbpix = nullptr, *d_fbadj = nullptr, *d_deg = nullptr, *d_nbr = nullptr;
     PMRF_TRY(tmp.get(&d_vpix_off, V + 1));
     PMRF_TRY(tmp.get(&d_cursor, V));
-    PMRF_TRY(tmp.get(&d_bbox, V));
     PMRF_TRY(tmp.get(&d_inv, V));
     PMRF_TRY(tmp.get(&d_fbpix, V));
     PMRF_TRY(tmp.get(&d_fbadj, V));
     PMRF_TRY(tmp.get(&d_deg, V));
     PMRF_TRY(tmp.get(&d_nbr, V * NB_CAP));
-    LAUNCH_1D(k_init_bbox, V, d_bbox, V);
-    if (g->n_pix > 0) {
-        k_count_bbox<<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank, g->d_npix,
-                                                   d_bbox);
-        ::pmrf::note_launch(1);
-        PMRF_CUDA(cudaGetLastError());
-    }
     LAUNCH_1D(k_inv_rank, g->n_rank, g->d_rank, g->d_rank_off, S, g->n_rank, d_inv);
     LAUNCH_1D(k_region_scan, V, d_img, d_ids, g->d_pix_off, g->d_W, g->d_vert_off, g->d_rank_off, g->d_rank, S, d_inv,
-              d_bbox, g->d_npix, V, g->d_y, d_fbpix, d_fbadj, d_deg, d_nbr);
+              d_bbox_raw, d_npix_raw, V, g->d_y, g->d_npix, d_fbpix, d_fbadj, d_deg, d_nbr);
     PMRF_TRY(exclusive_scan_i32_to_i64(d_fbpix, d_vpix_off, V, s));
     int64_t nfb = 0;
     PMRF_TRY(read_i64(d_vpix_off + V, &nfb, s));

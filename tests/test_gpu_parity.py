@@ -103,6 +103,19 @@ def test_build_rejects_bad_input():
     img[2, 2] = 0.5
     g = pmrf.build_graph(img, ids)
     assert g.V == 1
+    # a non-finite pixel of a region whose box is too sparse for a box scan
+    # (its mean comes from a sorted pixel list) is rejected as well
+    img2 = torch.rand(16, 16, dtype=torch.float64, device="cuda")
+    ids2 = torch.zeros(16, 16, dtype=torch.int32, device="cuda")
+    ids2[0, 0] = 1
+    ids2[15, 15] = 1
+    img2[15, 15] = float("inf")
+    with pytest.raises(pmrf.PmrfError) as e:
+        pmrf.build_graph(img2, ids2)
+    assert e.value.code == 4
+    img2[15, 15] = 0.25
+    g2 = pmrf.build_graph(img2, ids2)
+    assert g2.V == 2 and abs(float(g2.array("Y")[1]) - (float(img2[0, 0]) + 0.25) / 2) < 1e-15
 
 
 # --------------------------------------------------------------------------
