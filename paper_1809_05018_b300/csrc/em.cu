@@ -19,7 +19,7 @@
 //     labels of the hood's members, staged in shared memory), Emin(c,v), and
 //     S_c = sum over the hood in ascending v; the hood convergence test over
 //     the last W sums (ring buffer).
-//   k_finalize<L> (one warp per slice) -- label moments -> (n, mu, sigma, U),
+//   k_finalize<L> (one block per slice) -- label moments -> (n, mu, sigma, U),
 //     the total T^t, the MAP and EM convergence tests, per-slice stop flags.
 // Slices that have stopped skip all work.  The loop for t = 1..max_iters is
 // captured once into a CUDA graph and replayed.
@@ -33,7 +33,8 @@ namespace pmrf {
 
 namespace {
 
-constexpr int VT_THREADS = 256;     // vertices per vertex tile = threads
+constexpr int VT_THREADS = 256;
+constexpr int FIN_THREADS = 256;     // finaliser block (one per slice)     // vertices per vertex tile = threads
 constexpr int HT_THREADS = 96;               // hood-pass block: a tile's ~85 hoods, one per thread
 constexpr int MAX_HOOD_TILE = 1248;           // largest hood-tile window (elements)
 constexpr int HT_CAP = MAX_HOOD_TILE + 31;    // elements a fast hood tile can hold
@@ -614,7 +615,7 @@ __global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __r
 }
 
 // ---------------------------------------------------------------------------
-// per-slice finalisation: parameters and convergence (one warp per slice)
+// per-slice finalisation: parameters and convergence (one block per slice)
 
 template <int L>
 __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict__ cfgp,
@@ -625,32 +626,43 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
                            int32_t* __restrict__ iters, int32_t* __restrict__ conv, double* __restrict__ Thist,
                            int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op,
                            double* __restrict__ dterm) {
+    constexpr int NQ = 4 * L + 2;  // label moments, T, unconverged hoods
+    __shared__ double s_q[FIN_THREADS / 32][NQ];
     const int s = blockIdx.x;
     if (s >= S) return;
     const RunCfg cf = *cfgp;
     const bool em = (mode == MODE_EM);
     if (em && !active[s]) return;
-    const int lane = threadIdx.x;
-    // label moments
-    double tot[4 * L];
+    // the slice's tile partials: a fixed thread per partial, then fixed-order
+    // warp and block sums (deterministic)
+    double tot[NQ];
 #pragma unroll
-    for (int k = 0; k < 4 * L; ++k) tot[k] = 0.0;
-    for (int64_t p = vt0[s] + lane; p < vt0[s + 1]; p += 32) {
+    for (int k = 0; k < NQ; ++k) tot[k] = 0.0;
+    for (int64_t p = vt0[s] + threadIdx.x; p < vt0[s + 1]; p += FIN_THREADS) {
 #pragma unroll
         for (int k = 0; k < 4 * L; ++k) tot[k] += vpart[p * 4 * L + k];
     }
-#pragma unroll
-    for (int k = 0; k < 4 * L; ++k) tot[k] = warp_sum(tot[k]);
-    double Tsum = 0.0, unconv = 0.0;
     if (em) {
-        for (int64_t p = ht0[s] + lane; p < ht0[s + 1]; p += 32) {
-            Tsum += hpart[p * 2 + 0];
-            unconv += hpart[p * 2 + 1];
+        for (int64_t p = ht0[s] + threadIdx.x; p < ht0[s + 1]; p += FIN_THREADS) {
+            tot[4 * L + 0] += hpart[p * 2 + 0];
+            tot[4 * L + 1] += hpart[p * 2 + 1];
         }
-        Tsum = warp_sum(Tsum);
-        unconv = warp_sum(unconv);
     }
-    if (lane != 0) return;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) tot[k] = warp_sum(tot[k]);
+    if (lane_id() == 0) {
+#pragma unroll
+        for (int k = 0; k < NQ; ++k) s_q[warp_id()][k] = tot[k];
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
+#pragma unroll
+    for (int k = 0; k < NQ; ++k) {
+        double a = 0.0;
+        for (int w = 0; w < FIN_THREADS / 32; ++w) a += s_q[w][k];
+        tot[k] = a;
+    }
+    const double Tsum = tot[4 * L + 0], unconv = tot[4 * L + 1];
     for (int l = 0; l < L; ++l) {
         const double n = tot[4 * l + 0];
         double* th = theta + ((int64_t)s * L + l) * 4;
@@ -1022,7 +1034,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
                                                                 nullptr, w.d_vpart, g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
-    k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
+    k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                             w.d_hpart, nullptr, w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
                                             w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
     ::pmrf::note_launch(1);
@@ -1044,7 +1056,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
-        k_finalize<L><<<(unsigned)S, 32, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
+        k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                                 w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off, w.d_active,
                                                 w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
         ::pmrf::note_launch(1);
@@ -1196,7 +1208,7 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
                                                                 g->d_status, nullptr);
         ::pmrf::note_launch(1);
     }
-    k_finalize<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
+    k_finalize<L><<<(unsigned)g->S, FIN_THREADS, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
                                                w.d_vpart, w.d_hpart, prev, out, g->d_vert_off, nullptr, nullptr,
                                                nullptr, nullptr, nullptr, nullptr, nullptr);
     ::pmrf::note_launch(1);
