@@ -42,18 +42,38 @@ __device__ __forceinline__ int32_t vertex_of(const int32_t* ids, const int32_t* 
 // intensities finite (checked on their exponent bits)
 __global__ void k_validate(const double* __restrict__ img, const int32_t* __restrict__ ids,
                            const int64_t* __restrict__ pix_off, int32_t* __restrict__ maxid, DevStatus* st) {
+    __shared__ int32_t s_m[PIX_THREADS / 32];
     const int s = blockIdx.y;
     const int64_t b = pix_off[s], e = pix_off[s + 1];
+    const int64_t step = (int64_t)gridDim.x * blockDim.x;
     int32_t m = -1;
-    for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t id = ids[p];
-        if (id < 0) record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
-        if (!finite_bits(img[p])) record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
-        m = max(m, id);
+    for (int64_t p0 = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < e; p0 += 4 * step) {
+        // four pixels' loads issued together
+        int32_t id[4];
+        long long bits[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t p = p0 + k * step;
+            id[k] = p < e ? ids[p] : 0;
+            bits[k] = p < e ? __double_as_longlong(img[p]) : 0ll;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t p = p0 + k * step;
+            if (id[k] < 0) record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
+            if (((bits[k] >> 52) & 0x7ff) == 0x7ff) record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
+            m = max(m, id[k]);
+        }
     }
+    // one atomic per block on the slice's word
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if (lane_id() == 0 && m >= 0) atomicMax(&maxid[s], m);
+    if (lane_id() == 0) s_m[warp_id()] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < PIX_THREADS / 32; ++w) m = max(m, s_m[w]);
+        if (m >= 0) atomicMax(&maxid[s], m);
+    }
 }
 
 // pixel counts and bounding boxes (rows and columns inside the slice) of every
@@ -70,8 +90,10 @@ __global__ void k_count_raw(const int32_t* __restrict__ ids, const int64_t* __re
         const bool ok = p < e;
         const int32_t id = ok ? ids[p] : -1 - lane_id();
         const unsigned grp = __match_any_sync(0xffffffffu, id);
-        const int64_t q = p - b;
-        const unsigned r = ok ? (unsigned)(q / W) : 0u, c = ok ? (unsigned)(q - (q / W) * W) : 0u;
+        // row and column within the slice in 32-bit arithmetic (a batch has
+        // fewer than 2^32 pixels)
+        const unsigned q = (unsigned)(p - b), w32 = (unsigned)W;
+        const unsigned r = ok ? q / w32 : 0u, c = ok ? q - r * w32 : 0u;
         const unsigned rmin = __reduce_min_sync(grp, r), rmax = __reduce_max_sync(grp, r);
         const unsigned cmin = __reduce_min_sync(grp, c), cmax = __reduce_max_sync(grp, c);
         if (ok && lane_id() == __ffs(grp) - 1) {
@@ -135,6 +157,8 @@ __global__ void k_inv_rank(const int32_t* __restrict__ rank, const int64_t* __re
 // comes from the pixel-pair path.
 constexpr int NB_CAP = 32;
 
+// `last` is the caller's cache of the id it inserted before (boundaries come
+// in runs of the same neighbour)
 __device__ __forceinline__ void nb_insert(int32_t (&nb)[NB_CAP], int& nn, bool& over, int32_t& last, int32_t u) {
     if (u == last) return;
     last = u;
@@ -178,23 +202,25 @@ __global__ void k_region_scan(const double* __restrict__ img, const int32_t* __r
     int32_t nb[NB_CAP];
     int nn = 0;
     bool over = false;
-    int32_t last = id;
+    int32_t last_h = id, last_v = id;  // per pair direction
     double acc = 0.0;
     const int r0 = bb.x > 0 ? bb.x - 1 : 0, c0 = bb.z > 0 ? bb.z - 1 : 0;
+    const int w = (int)W;
     for (int r = r0; r <= bb.y; ++r) {
-        const int64_t row = b + (int64_t)r * W;
-        const bool in_r = r >= bb.x, down = r + 1 < H;
-        int32_t cur = ids[row + c0];
+        const int32_t* irow = ids + b + (int64_t)r * W;
+        const double* vrow = img + b + (int64_t)r * W;
+        const bool down = r + 1 < H;
+        int32_t cur = irow[c0];
         for (int c = c0; c <= bb.w; ++c) {
-            const int32_t right = c + 1 < W ? ids[row + c + 1] : cur;
-            const int32_t below = down ? ids[row + W + c] : cur;
+            const int32_t right = c + 1 < w ? irow[c + 1] : cur;
+            const int32_t below = down ? irow[w + c] : cur;
             if (cur == id) {
-                if (in_r && c >= bb.z) acc += img[row + c];
-                if (right != id) nb_insert(nb, nn, over, last, right);
-                if (below != id) nb_insert(nb, nn, over, last, below);
+                acc += vrow[c];  // region pixels lie inside the box: row-major order
+                if (right != id) nb_insert(nb, nn, over, last_h, right);
+                if (below != id) nb_insert(nb, nn, over, last_v, below);
             } else {
-                if (right == id) nb_insert(nb, nn, over, last, cur);
-                if (below == id) nb_insert(nb, nn, over, last, cur);
+                if (right == id) nb_insert(nb, nn, over, last_h, cur);
+                if (below == id) nb_insert(nb, nn, over, last_v, cur);
             }
             cur = right;
         }
@@ -682,14 +708,44 @@ __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __r
     const int64_t k = hood_off[c + 1] - h0;
     const int64_t i = e - h0;
     const int32_t v = hood[e];
-    const int32_t* N = adj + adj_off[v];
-    const int64_t d = adj_off[v + 1] - adj_off[v];
+    const int64_t av = adj_off[v];
+    const int32_t* N = adj + av;
+    const int64_t d = adj_off[v + 1] - av;
     const int64_t nwh = ceil_div(k, 32);
     const int64_t nwv = d > 32 ? ceil_div(d, 32) : 1;
     uint32_t* rw = row + row_off[c] + i * nwh;
     // the replica's place among v's replicas is arbitrary: the vertex pass only
     // takes a minimum over them
     uint32_t* sw = rep_mask + rep_woff[v] + (int64_t)atomicAdd(&cursor[v], 1) * nwv;
+    if (k <= 32 && d <= 32) {
+        // one word each: a two-pointer merge with both heads in registers
+        const int32_t* Hc = hood + h0;
+        const int dk = (int)d, kk = (int)k;
+        uint32_t rbits = 0, sbits = 0;
+        if (dk > 0 && kk > 0) {
+            int a = 0, j = 0;
+            int32_t x = N[0], y = Hc[0];
+            while (true) {
+                if (x < y) {
+                    if (++a == dk) break;
+                    x = N[a];
+                } else if (x > y) {
+                    if (++j == kk) break;
+                    y = Hc[j];
+                } else {
+                    rbits |= 1u << j;
+                    sbits |= 1u << a;
+                    if (++a == dk || ++j == kk) break;
+                    x = N[a];
+                    y = Hc[j];
+                }
+            }
+        }
+        rw[0] = rbits;
+        sw[0] = sbits;
+        el_slot[e] = sbits;
+        return;
+    }
     uint32_t rcur = 0, scur = 0;
     int64_t rwi = 0, swi = 0;
     int64_t a = 0, j = 0;
