@@ -220,7 +220,6 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
     __shared__ double s_vq[3][VT_THREADS];
     __shared__ double s_vc[3 * L][8];
-    __shared__ uint8_t s_vl[VT_THREADS];
     __shared__ int s_cnt[VT_THREADS / 32][L];
     const Tile tile = tiles[blockIdx.x];
     const int s = tile.slice;
@@ -350,34 +349,46 @@ __global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* _
     }
     if (mode == MODE_SWEEP) return;
     // deterministic per-label sums of the tile: each vertex contributes to the
-    // label it carries; 8 threads per (label, quantity) add 32 entries each in
-    // order, then one thread adds the 8 results (no shuffle trees: the FP64
-    // pipe is the scarce unit)
-    s_vl[threadIdx.x] = ok ? (uint8_t)vlab : (uint8_t)0xff;
-    // label counts of the tile by warp ballots
+    // label it carries (no shuffle trees: the FP64 pipe is the scarce unit).
+    // Label counts of the tile by warp ballots; each vertex's place in its
+    // label's run (tile order kept) so the sums below add only that label's
+    // values
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned mine = 0u;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         const unsigned b = __ballot_sync(0xffffffffu, ok && vlab == l);
-        if ((threadIdx.x & 31) == 0) s_cnt[threadIdx.x >> 5][l] = __popc(b);
+        if (lane == 0) s_cnt[warp][l] = __popc(b);
+        if (ok && vlab == l) mine = b;
     }
-    s_vq[0][threadIdx.x] = vq0;
-    s_vq[1][threadIdx.x] = vq1;
-    s_vq[2][threadIdx.x] = vq2;
     __syncthreads();
+    if (ok) {
+        int pos = __popc(mine & ((1u << lane) - 1u));
+        for (int l = 0; l < vlab; ++l)
+            for (int w = 0; w < VT_THREADS / 32; ++w) pos += s_cnt[w][l];
+        for (int w = 0; w < warp; ++w) pos += s_cnt[w][vlab];
+        s_vq[0][pos] = vq0;
+        s_vq[1][pos] = vq1;
+        s_vq[2][pos] = vq2;
+    }
+    __syncthreads();
+    // 8 threads per (label, quantity) add fixed consecutive chunks of the
+    // label's run in order, then one thread adds the 8 results in order
     if (threadIdx.x < 3 * L * 8) {
-        const int lq = threadIdx.x >> 3, w = threadIdx.x & 7;
+        const int lq = threadIdx.x >> 3, k = threadIdx.x & 7;
         const int l = lq / 3, q = lq % 3;
+        int base = 0, n = 0;
+        for (int m = 0; m < L; ++m)
+            for (int w = 0; w < VT_THREADS / 32; ++w) {
+                const int cw = s_cnt[w][m];
+                if (m < l) base += cw;
+                if (m == l) n += cw;
+            }
+        const int lo = base + (k * n) / 8, hi = base + ((k + 1) * n) / 8;
         double a = 0.0;
-        for (int j = 0; j < 32; ++j) {
-            const int i = w * 32 + j;
-            if (s_vl[i] == l) a += s_vq[q][i];
-        }
-        s_vc[lq][w] = a;
-    } else if (threadIdx.x >= 3 * L * 8 && threadIdx.x < 3 * L * 8 + L) {
-        const int l = threadIdx.x - 3 * L * 8;
-        int n = 0;
-        for (int w = 0; w < VT_THREADS / 32; ++w) n += s_cnt[w][l];
-        vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
+        for (int i = lo; i < hi; ++i) a += s_vq[q][i];
+        s_vc[lq][k] = a;
+        if (q == 0 && k == 0) vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
     }
     __syncthreads();
     if (threadIdx.x < 3 * L) {
