@@ -33,11 +33,12 @@ namespace pmrf {
 
 namespace {
 
-constexpr int VT_THREADS = 256;
-constexpr int FIN_THREADS = 256;     // finaliser block (one per slice)     // vertices per vertex tile = threads
-constexpr int HT_THREADS = 96;               // hood-pass block: a tile's ~85 hoods, one per thread
-constexpr int MAX_HOOD_TILE = 1248;           // largest hood-tile window (elements)
-constexpr int HT_CAP = MAX_HOOD_TILE + 31;    // elements a fast hood tile can hold
+constexpr int VT_THREADS = 256;             // vertices per vertex tile = threads
+constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
+constexpr int LI_THREADS = 256;             // label-image block
+constexpr int HT_THREADS = 96;              // hood-pass block: a tile's ~85 hoods, one per thread
+constexpr int MAX_HOOD_TILE = 1248;         // largest hood-tile window (elements)
+constexpr int HT_CAP = MAX_HOOD_TILE + 31;  // elements a fast hood tile can hold
 // Per-vertex record of the hood pass, 32-byte chunks (one for L = 2), written
 // by the vertex pass of the same iteration:
 //   words 0-1   D_min(v) = min_l D_l(y_v), exact fixed point (units 2^-80)
@@ -767,16 +768,30 @@ __global__ void k_label_image(const int32_t* __restrict__ ids, const int64_t* __
                               const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
                               const uint8_t* __restrict__ labels, uint8_t* __restrict__ out,
                               const int64_t* __restrict__ maxid1, DevStatus* st) {
+    // four pixels a thread (256 apart, each access coalesced), their
+    // id -> vertex -> label chains in flight together
     const int s = blockIdx.y;
     const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], nr = rank_off[s + 1] - rb;
-    for (int64_t p = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < e; p += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t id = ids[p];
-        int32_t v = (id >= 0 && id < nr) ? rank[rb + id] : -1;
-        if (v < 0) {
-            record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
-            out[p] = 0;
-        } else {
-            out[p] = labels[v];
+    constexpr int CHUNK = 4 * LI_THREADS;
+    for (int64_t base = b + (int64_t)blockIdx.x * CHUNK + threadIdx.x; base < e; base += (int64_t)gridDim.x * CHUNK) {
+        int32_t id[4], v[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t p = base + k * LI_THREADS;
+            id[k] = p < e ? ids[p] : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = (id[k] >= 0 && id[k] < nr) ? rank[rb + id[k]] : -1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t p = base + k * LI_THREADS;
+            if (p >= e) continue;
+            if (v[k] < 0) {
+                record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
+                out[p] = 0;
+            } else {
+                out[p] = labels[v[k]];
+            }
         }
     }
     (void)maxid1;
@@ -1299,8 +1314,8 @@ int label_image_run(pmrf_graph* g, const int32_t* ids, const uint8_t* labels, ui
     int64_t maxpix = 0;
     for (int i = 0; i < g->S; ++i) maxpix = std::max(maxpix, g->h_pix_off[i + 1] - g->h_pix_off[i]);
     if (maxpix == 0) return PMRF_OK;
-    const dim3 grid((unsigned)std::min<int64_t>(ceil_div(maxpix, 1024), 65535), (unsigned)g->S);
-    k_label_image<<<grid, 256, 0, s>>>(ids, g->d_pix_off, g->d_rank_off, g->d_rank, labels, out, nullptr,
+    const dim3 grid((unsigned)std::min<int64_t>(ceil_div(maxpix, 4 * LI_THREADS), 65535), (unsigned)g->S);
+    k_label_image<<<grid, LI_THREADS, 0, s>>>(ids, g->d_pix_off, g->d_rank_off, g->d_rank, labels, out, nullptr,
                                        g->d_status); ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;
