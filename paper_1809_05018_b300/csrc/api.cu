@@ -58,7 +58,7 @@ void destroy(pmrf_graph* g) {
     for (cudaEvent_t ev : g->prof_ev) cudaEventDestroy(ev);
     void* ps[] = {g->d_pix_off, g->d_vert_off, g->d_hood_slice_off, g->d_rank_off, g->d_W, g->d_rank, g->d_y,
                   g->d_npix, g->d_adj_off, g->d_adj, g->d_clq_off, g->d_clq, g->d_hood_off, g->d_hood, g->d_row_off,
-                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_status};
+                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, g->d_status};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
     delete g;

@@ -700,7 +700,7 @@ __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __r
                         const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
                         uint32_t* __restrict__ row, int32_t* __restrict__ cursor,
                         const int64_t* __restrict__ rep_woff, uint32_t* __restrict__ rep_mask,
-                        uint32_t* __restrict__ el_slot, int64_t N_el) {
+                        uint32_t* __restrict__ el_slot, uint8_t* __restrict__ hood_gen, int64_t N_el) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N_el) return;
     const int32_t c = el_hood[e];
@@ -746,6 +746,7 @@ __global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __r
         el_slot[e] = sbits;
         return;
     }
+    hood_gen[c] = 1;  // the hood needs the general path of the hood pass
     uint32_t rcur = 0, scur = 0;
     int64_t rwi = 0, swi = 0;
     int64_t a = 0, j = 0;
@@ -1091,8 +1092,10 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    PMRF_TRY(dalloc(&g->d_hood_gen, C, s));
+    PMRF_CUDA(cudaMemsetAsync(g->d_hood_gen, 0, std::max<int64_t>(C, 1), s));
     LAUNCH_1D(k_masks, N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off, g->d_row,
-              d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, N_el);
+              d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, N_el);
     PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
     // slice offsets of hoods and elements (host copies, one transfer)

@@ -800,8 +800,7 @@ __global__ void k_label_image(const int32_t* __restrict__ ids, const int64_t* __
 // tile table: vertex tiles then hood tiles, each grouped by slice; one warp
 // per hood tile
 __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const int64_t* __restrict__ hood_slice_off,
-                                  const int64_t* __restrict__ row_off, const int32_t* __restrict__ hood,
-                                  const int64_t* __restrict__ adj_off, const int64_t* __restrict__ ht_first,
+                                  const uint8_t* __restrict__ hood_gen, const int64_t* __restrict__ ht_first,
                                   int32_t S, int64_t n_htiles, int32_t te, Tile* __restrict__ tiles,
                                   int64_t tile_base) {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -816,15 +815,13 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
     int64_t c1 = lower_bound_dev<int64_t>(hood_off, cs, ce, hi);
     if (j == ht_first[s + 1] - ht_first[s] - 1) c1 = ce;
     // fast when the elements fit in shared memory, every hood has <= 32
-    // members (one row word each) and every element's vertex has degree <= 32
+    // members and every element's vertex has degree <= 32 (the build flags
+    // the hoods that do not)
     const int64_t e0 = hood_off[c0], e1 = hood_off[c1];
-    bool fast = (e1 - e0) <= HT_CAP && (row_off[c1] - row_off[c0]) == (e1 - e0);
+    bool fast = (e1 - e0) <= HT_CAP;
     bool ok = true;
     if (fast)
-        for (int64_t e = e0 + lane; e < e1; e += 32) {
-            const int32_t v = hood[e];
-            ok = ok && (adj_off[v + 1] - adj_off[v] <= 32);
-        }
+        for (int64_t c = c0 + lane; c < c1; c += 32) ok = ok && hood_gen[c] == 0;
     fast = __all_sync(0xffffffffu, ok) && fast;
     if (lane == 0) {
         Tile t;
@@ -939,7 +936,7 @@ int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
     }
     if (p.n_htiles > 0) {
         k_make_hood_tiles<<<(unsigned)ceil_div(p.n_htiles, 8), 256, 0, s>>>(
-            g->d_hood_off, g->d_hood_slice_off, g->d_row_off, g->d_hood, g->d_adj_off, p.d_slice_ht0, S, p.n_htiles,
+            g->d_hood_off, g->d_hood_slice_off, g->d_hood_gen, p.d_slice_ht0, S, p.n_htiles,
             te, p.d_tiles,
             p.n_vtiles);
         ::pmrf::note_launch(1);
