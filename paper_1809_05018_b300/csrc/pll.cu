@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
                                                      double beta, int64_t nchunk, double* __restrict__ part) {
     constexpr int NP = 2 * L + 2;  // pll, gmu[L], gsigma[L], gbeta
     __shared__ double s_mu[L], s_inv[L], s_ln[L], s_isg[L], s_isg2[L], s_isg3[L];
-    __shared__ double s_red[PLL_THREADS / 32][NP];
+    __shared__ double s_acc[NP][PLL_THREADS];
+    __shared__ double s_red[NP][8];
     const int s = blockIdx.y;
     const int64_t vb = vert_off[s], ve = vert_off[s + 1];
     const int64_t v = vb + (int64_t)blockIdx.x * PLL_THREADS + threadIdx.x;
@@ -106,16 +107,22 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
         }
         acc[1 + 2 * L] = eb - mx;
     }
+    // block sums in a fixed order without shuffle trees (the FP64 pipe is the
+    // scarce unit): 8 threads per quantity add 32 consecutive entries each,
+    // then one thread adds the 8 results
 #pragma unroll
-    for (int k = 0; k < NP; ++k) acc[k] = warp_sum(acc[k]);
-    if (lane_id() == 0) {
-#pragma unroll
-        for (int k = 0; k < NP; ++k) s_red[warp_id()][k] = acc[k];
+    for (int k = 0; k < NP; ++k) s_acc[k][threadIdx.x] = acc[k];
+    __syncthreads();
+    if (threadIdx.x < NP * 8) {
+        const int k = threadIdx.x >> 3, w = threadIdx.x & 7;
+        double t = 0.0;
+        for (int j = 0; j < PLL_THREADS / 8; ++j) t += s_acc[k][w * (PLL_THREADS / 8) + j];
+        s_red[k][w] = t;
     }
     __syncthreads();
     if (threadIdx.x < NP) {
         double t = 0.0;
-        for (int w = 0; w < PLL_THREADS / 32; ++w) t += s_red[w][threadIdx.x];
+        for (int w = 0; w < 8; ++w) t += s_red[threadIdx.x][w];
         part[((int64_t)s * nchunk + blockIdx.x) * NP + threadIdx.x] = t;
     }
 }
