@@ -34,6 +34,11 @@ namespace pmrf {
 namespace {
 
 constexpr int VT_THREADS = 256;             // vertices per vertex tile = threads
+// resident blocks per SM the register budget of the EM kernels must allow
+// (measured on the two-label stack: the vertex pass gains from 8 blocks at 32
+// registers; the hood pass is best at 40; more labels need more registers)
+__host__ __device__ constexpr int vt_min_blocks(int L) { return L <= 2 ? 8 : (L <= 4 ? 5 : 2); }
+__host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 16 : 12; }
 constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
 constexpr int LI_THREADS = 256;             // label-image block
 constexpr int HT_THREADS = 96;              // hood-pass block: a tile's ~85 hoods, one per thread
@@ -209,7 +214,7 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
 }
 
 template <int L>
-__global__ void __launch_bounds__(VT_THREADS) k_vertex(DevGraph g, const Tile* __restrict__ tiles, int mode,
+__global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGraph g, const Tile* __restrict__ tiles, int mode,
                                                        const RunCfg* __restrict__ cfgp,
                                                        const int32_t* __restrict__ active,
                                                        const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
@@ -499,7 +504,7 @@ __device__ __forceinline__ int hood_history(int64_t S40, int64_t c, int64_t C, i
 }
 
 template <int L>
-__global__ void __launch_bounds__(HT_THREADS) k_hood(DevGraph g, const Tile* __restrict__ tiles, int mode, int t,
+__global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph g, const Tile* __restrict__ tiles, int mode, int t,
                                                      const RunCfg* __restrict__ cfgp,
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
