@@ -18,6 +18,10 @@ namespace pmrf {
 namespace {
 
 constexpr int PIX_THREADS = 256;
+// the region scan and the slot-mask pass wait mostly on scattered loads: 8
+// resident 256-thread blocks per SM (32 registers) hide more of that latency
+constexpr int RS_MIN_BLOCKS = 8;
+constexpr int MK_MIN_BLOCKS = 8;
 constexpr int MAX_CLIQUE = 64;  // deepest Bron-Kerbosch recursion (largest clique)
 
 struct SliceGeo {  // per-slice geometry for the pixel kernels
@@ -174,7 +178,7 @@ __device__ __forceinline__ void nb_insert(int32_t (&nb)[NB_CAP], int& nn, bool& 
     ++nn;
 }
 
-__global__ void k_region_scan(const double* __restrict__ img, const int32_t* __restrict__ ids,
+__global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(const double* __restrict__ img, const int32_t* __restrict__ ids,
                               const int64_t* __restrict__ pix_off, const int64_t* __restrict__ Wd,
                               const int64_t* __restrict__ vert_off, const int64_t* __restrict__ rank_off,
                               const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv,
@@ -695,7 +699,7 @@ __global__ void k_rep_words(const int64_t* __restrict__ adj_off, const int32_t* 
 // is a neighbour of v, and slot bits s where N(v)[s] lies in the hood (stored
 // vertex-major, one record per replica of v, and, for degrees <= 32,
 // element-major too).
-__global__ void k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
+__global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
                         const int32_t* __restrict__ el_hood, const int64_t* __restrict__ adj_off,
                         const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
                         uint32_t* __restrict__ row, int32_t* __restrict__ cursor,
