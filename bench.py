@@ -48,8 +48,8 @@ FALLBACK_HBM_GBS = 6400.0
 # the headers em.cu includes.  It is reported, scaled to the average
 # launch by its algorithmic bytes, only while those sources are unchanged;
 # otherwise the field is null.
-TRAFFIC_CAPTURE = {"kernel": "k_hood", "workload": "stack512", "bytes_all_active": 3487662592.0,
-                   "sources_sha1": "225773c83ff89971f641010294bb827ab319c407"}
+TRAFFIC_CAPTURE = {"kernel": "k_hood", "workload": "stack512", "bytes_all_active": 3487704064.0,
+                   "sources_sha1": "59828270d19de87e62a4123b8a00dd3e25d00086"}
 TRAFFIC_SECTION = ("paper_1809_05018_b300/csrc/em.cu", "// hood pass\n")
 TRAFFIC_SOURCES = ("paper_1809_05018_b300/csrc/graph.cuh", "paper_1809_05018_b300/csrc/common.cuh")
 
