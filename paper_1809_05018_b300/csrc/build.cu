@@ -151,40 +151,25 @@ __global__ void k_inv_rank(const int32_t* __restrict__ rank, const int64_t* __re
 // accumulation.  The same scan, widened by one pixel above and to the left,
 // visits every horizontal and vertical 4-connected pixel pair that touches the
 // region: a pair with exactly one pixel in the region names a neighbouring
-// region, kept in a small sorted set of raw ids (raw ids and vertex ids sort
-// alike within a slice).  Each pixel's right neighbour is the next step's
-// pixel, so a step loads one new id (and the one below).
+// region.  Those ids go to a small unsorted buffer (a run of the same
+// neighbour along a boundary is appended once), sorted and de-duplicated after
+// the scan; raw ids and vertex ids sort alike within a slice.  Each pixel's
+// right neighbour is the next step's pixel, so a step loads one new id (and
+// the one below).
 // Outputs: y_v, n_v; the region's neighbour vertex ids, ascending, at
 // nbr[v * NB_CAP ...) and their number in deg[v].  Regions whose box is too
-// sparse (their mean then comes from a sorted pixel list: fb_pix[v] = n) or
-// that have more than NB_CAP neighbours get fb_adj[v] = 1: their adjacency
-// comes from the pixel-pair path.
+// sparse (their mean then comes from a sorted pixel list: fb_pix[v] = n), whose
+// boundary buffer overflows or that have more than NB_CAP neighbours get
+// fb_adj[v] = 1: their adjacency comes from the pixel-pair path.
 constexpr int NB_CAP = 32;
+constexpr int NB_BUF = 64;
 
-// `last` is the caller's cache of the id it inserted before (boundaries come
-// in runs of the same neighbour)
-__device__ __forceinline__ void nb_insert(int32_t (&nb)[NB_CAP], int& nn, bool& over, int32_t& last, int32_t u) {
-    if (u == last) return;
-    last = u;
-    int pos = 0;
-    while (pos < nn && nb[pos] < u) ++pos;
-    if (pos < nn && nb[pos] == u) return;
-    if (nn == NB_CAP) {
-        over = true;
-        return;
-    }
-    for (int j = nn; j > pos; --j) nb[j] = nb[j - 1];
-    nb[pos] = u;
-    ++nn;
-}
-
-__global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(const double* __restrict__ img, const int32_t* __restrict__ ids,
-                              const int64_t* __restrict__ pix_off, const int64_t* __restrict__ Wd,
-                              const int64_t* __restrict__ vert_off, const int64_t* __restrict__ rank_off,
-                              const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv,
-                              const int4* __restrict__ bbox_raw, const int32_t* __restrict__ npix_raw, int64_t V,
-                              double* __restrict__ y, int32_t* __restrict__ npix, int32_t* __restrict__ fb_pix,
-                              int32_t* __restrict__ fb_adj, int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
+__global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
+    const double* __restrict__ img, const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+    const int64_t* __restrict__ Wd, const int64_t* __restrict__ vert_off, const int64_t* __restrict__ rank_off,
+    const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv, const int4* __restrict__ bbox_raw,
+    const int32_t* __restrict__ npix_raw, int64_t V, double* __restrict__ y, int32_t* __restrict__ npix,
+    int32_t* __restrict__ fb_pix, int32_t* __restrict__ fb_adj, int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
@@ -203,10 +188,9 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(const double
     fb_pix[v] = 0;
     const int64_t b = pix_off[s], W = Wd[s];
     const int H = (int)((pix_off[s + 1] - b) / W);
-    int32_t nb[NB_CAP];
-    int nn = 0;
-    bool over = false;
-    int32_t last_h = id, last_v = id;  // per pair direction
+    int32_t buf[NB_BUF];
+    int m = 0;
+    int32_t last_h = id, last_v = id;  // last neighbour appended per pair direction
     double acc = 0.0;
     const int r0 = bb.x > 0 ? bb.x - 1 : 0, c0 = bb.z > 0 ? bb.z - 1 : 0;
     const int w = (int)W;
@@ -218,24 +202,49 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(const double
         for (int c = c0; c <= bb.w; ++c) {
             const int32_t right = c + 1 < w ? irow[c + 1] : cur;
             const int32_t below = down ? irow[w + c] : cur;
-            if (cur == id) {
-                acc += vrow[c];  // region pixels lie inside the box: row-major order
-                if (right != id) nb_insert(nb, nn, over, last_h, right);
-                if (below != id) nb_insert(nb, nn, over, last_v, below);
-            } else {
-                if (right == id) nb_insert(nb, nn, over, last_h, cur);
-                if (below == id) nb_insert(nb, nn, over, last_v, cur);
+            const bool in = cur == id;
+            if (in) acc += vrow[c];  // region pixels lie inside the box: row-major order
+            // the other pixel of a pair with exactly one pixel in the region
+            const int32_t uh = in ? right : cur, uv = in ? below : cur;
+            const bool th = (in != (right == id)) && uh != last_h;
+            const bool tv = (in != (below == id)) && uv != last_v;
+            if (th) {
+                if (m < NB_BUF) buf[m] = uh;
+                ++m;
+                last_h = uh;
+            }
+            if (tv) {
+                if (m < NB_BUF) buf[m] = uv;
+                ++m;
+                last_v = uv;
             }
             cur = right;
         }
     }
     y[v] = acc / (double)n;
+    bool over = m > NB_BUF;
+    int nn = 0;
+    if (!over) {
+        // sort the buffer, keep distinct ids
+        for (int i = 1; i < m; ++i) {
+            const int32_t x = buf[i];
+            int j = i - 1;
+            while (j >= 0 && buf[j] > x) {
+                buf[j + 1] = buf[j];
+                --j;
+            }
+            buf[j + 1] = x;
+        }
+        for (int i = 0; i < m; ++i)
+            if (i == 0 || buf[i] != buf[i - 1]) buf[nn++] = buf[i];
+        over = nn > NB_CAP;
+    }
     fb_adj[v] = over ? 1 : 0;
     deg[v] = over ? 0 : nn;
     if (!over) {
         const int64_t rb = rank_off[s];
         int32_t* out = nbr + v * NB_CAP;
-        for (int k = 0; k < nn; ++k) out[k] = rank[rb + nb[k]];
+        for (int k = 0; k < nn; ++k) out[k] = rank[rb + buf[k]];
     }
 }
 
