@@ -408,12 +408,12 @@ __device__ void build_local_adj(const int64_t* __restrict__ adj_off, const int32
     }
 }
 
-// Runs the enumeration rooted at v.  mode 0: count (ncl, nmem); mode 1: store
-// masks (nw words each) at out_masks.  `stack` holds MAX_CLIQUE+1 frames of
-// 4*nw words; `tmp` holds 2*nw words.  Returns false when the recursion would
-// exceed MAX_CLIQUE.
+// Runs the enumeration rooted at v, counting cliques (ncl) and members (nmem)
+// and storing the first out_cap masks (nw words each) at out_masks (may be
+// NULL).  `stack` holds MAX_CLIQUE+1 frames of 4*nw words; `tmp` holds 2*nw
+// words.  Returns false when the recursion would exceed MAX_CLIQUE.
 __device__ bool bk_run(int64_t v, const int32_t* N, int d, int nw, const uint64_t* nbm, uint64_t* stack,
-                       uint64_t* tmp, int mode, int64_t* ncl, int64_t* nmem, uint64_t* out_masks) {
+                       uint64_t* tmp, int64_t* ncl, int64_t* nmem, uint64_t* out_masks, int64_t out_cap) {
     // slot of the first neighbour above v
     int hi = 0;
     while (hi < d && N[hi] < v) ++hi;
@@ -429,7 +429,7 @@ __device__ bool bk_run(int64_t v, const int32_t* N, int d, int nw, const uint64_
     auto emit = [&](const uint64_t* R) {
         int64_t sz = 1;
         for (int w = 0; w < nw; ++w) sz += __popcll(R[w]);
-        if (mode == 1) {
+        if (out_masks && *ncl < out_cap) {
             for (int w = 0; w < nw; ++w) out_masks[*ncl * nw + w] = R[w];
         }
         *ncl += 1;
@@ -511,26 +511,37 @@ __device__ __forceinline__ bool clique_less(const uint64_t* a, const uint64_t* b
 
 // Fast path: d <= 64, one word, stack in local memory.  mode 0 counts, mode 1
 // writes sorted cliques.  General vertices (d > 64) are skipped here.
+// The count pass keeps the first CQ_KEEP masks of each vertex in `kept`; the
+// fill pass copies them instead of enumerating again (vertices with more
+// cliques are enumerated twice).
+constexpr int CQ_KEEP = 8;
+
 __global__ void k_cliques_fast(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t V,
                                int mode, int64_t* __restrict__ ncl, int64_t* __restrict__ nmem,
                                const int64_t* __restrict__ cq_off, const int64_t* __restrict__ mem_off,
                                uint64_t* __restrict__ maskbuf, int64_t* __restrict__ clq_off,
-                               int32_t* __restrict__ clq, DevStatus* st) {
+                               int32_t* __restrict__ clq, DevStatus* st, uint64_t* __restrict__ kept) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     const int d = (int)(adj_off[v + 1] - adj_off[v]);
     if (d > 64) return;
-    uint64_t nbm[64];
-    uint64_t stack[(MAX_CLIQUE + 1) * 4];
-    uint64_t tmp[2];
     const int32_t* N = adj + adj_off[v];
-    build_local_adj(adj_off, adj, v, d, 1, nbm);
     int64_t nc = 0, nm = 0;
     uint64_t* out = (mode == 1) ? maskbuf + cq_off[v] : nullptr;
-    if (!bk_run(v, N, d, 1, nbm, stack, tmp, mode, &nc, &nm, out)) {
-        record_error(st, PMRF_ERR_UNSUPPORTED, SITE_MCE_STACK, v);
-        nc = 0;
-        nm = 0;
+    if (mode == 1 && ncl[v] <= CQ_KEEP) {
+        nc = ncl[v];
+        for (int64_t i = 0; i < nc; ++i) out[i] = kept[v * CQ_KEEP + i];
+    } else {
+        uint64_t nbm[64];
+        uint64_t stack[(MAX_CLIQUE + 1) * 4];
+        uint64_t tmp[2];
+        build_local_adj(adj_off, adj, v, d, 1, nbm);
+        uint64_t* dst = mode == 1 ? out : kept + v * CQ_KEEP;
+        if (!bk_run(v, N, d, 1, nbm, stack, tmp, &nc, &nm, dst, mode == 1 ? INT64_MAX : CQ_KEEP)) {
+            record_error(st, PMRF_ERR_UNSUPPORTED, SITE_MCE_STACK, v);
+            nc = 0;
+            nm = 0;
+        }
     }
     if (mode == 0) {
         ncl[v] = nc;
@@ -578,7 +589,7 @@ __global__ void k_cliques_general(const int64_t* __restrict__ adj_off, const int
     build_local_adj(adj_off, adj, v, d, nw, nbm);
     int64_t nc = 0, nm = 0;
     uint64_t* out = (mode == 1) ? gmask + gmask_off[k] : nullptr;
-    if (!bk_run(v, N, d, nw, nbm, stack, tmp, mode, &nc, &nm, out)) {
+    if (!bk_run(v, N, d, nw, nbm, stack, tmp, &nc, &nm, out, out ? INT64_MAX : 0)) {
         record_error(st, PMRF_ERR_UNSUPPORTED, SITE_MCE_STACK, v);
         nc = 0;
         nm = 0;
@@ -626,17 +637,36 @@ __global__ void k_list_general(const int64_t* __restrict__ adj_off, int64_t V, i
 // union of the members' (sorted) adjacency lists: a k-way merge per clique.  A
 // one-member maximal clique is an isolated vertex, whose hood is itself.
 
+// The count pass keeps hoods of up to HOOD_KEEP members in `kept`, element i
+// of hood c at kept[i * C + c] (a warp's stores and loads are adjacent); the
+// fill pass copies those and merges only the larger ones.
+constexpr int HOOD_KEEP = 32;
+
 template <bool FILL>
 __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
                              const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t C,
                              int32_t* __restrict__ hsize, int32_t* __restrict__ hmax,
                              const int64_t* __restrict__ hood_off, int32_t* __restrict__ hood,
-                             int32_t* __restrict__ el_hood, int32_t* __restrict__ rcount) {
+                             int32_t* __restrict__ el_hood, int32_t* __restrict__ rcount,
+                             int32_t* __restrict__ kept) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     const int64_t m0 = clq_off[c];
     const int m = (int)(clq_off[c + 1] - m0);
     const int64_t h0 = FILL ? hood_off[c] : 0;
+    int32_t* kc = kept + c;  // stride C
+    if (FILL) {
+        const int64_t k = hood_off[c + 1] - h0;
+        if (k <= HOOD_KEEP) {
+            for (int64_t i = 0; i < k; ++i) {
+                const int32_t cur = kc[i * C];
+                hood[h0 + i] = cur;
+                el_hood[h0 + i] = (int32_t)c;
+                atomicAdd(&rcount[cur], 1);
+            }
+            return;
+        }
+    }
     int32_t n = 0;
     // element n of hood c is `cur`: its vertex gains one replica
     auto emit = [&](int32_t cur) {
@@ -644,6 +674,8 @@ __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t*
             hood[h0 + n] = cur;
             el_hood[h0 + n] = (int32_t)c;
             atomicAdd(&rcount[cur], 1);
+        } else if (n < HOOD_KEEP) {
+            kc[(int64_t)n * C] = cur;
         }
         ++n;
     };
@@ -1025,8 +1057,10 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         hdeg.swap(so);  // keep the host vector alive until the copy has run
         PMRF_CUDA(cudaStreamSynchronize(s));
     }
+    uint64_t* d_cq_kept = nullptr;
+    PMRF_TRY(tmp.get(&d_cq_kept, V * CQ_KEEP));
     LAUNCH_1D(k_cliques_fast, V, g->d_adj_off, g->d_adj, V, 0, d_ncl, d_nmem, nullptr, nullptr, nullptr, nullptr,
-              nullptr, g->d_status);
+              nullptr, g->d_status, d_cq_kept);
     if (ng > 0)
         LAUNCH_1D(k_cliques_general, ng, g->d_adj_off, g->d_adj, d_glist, (int64_t)ng, d_gscr_off, d_gscr, 0, d_ncl,
                   d_nmem, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, g->d_status);
@@ -1055,7 +1089,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(dalloc(&g->d_clq_off, C + 1, s));
     PMRF_TRY(dalloc(&g->d_clq, g->n_clq, s));
     LAUNCH_1D(k_cliques_fast, V, g->d_adj_off, g->d_adj, V, 1, d_ncl, d_nmem, d_cq_off, d_mem_off, d_maskbuf,
-              g->d_clq_off, g->d_clq, g->d_status);
+              g->d_clq_off, g->d_clq, g->d_status, d_cq_kept);
     if (ng > 0)
         LAUNCH_1D(k_cliques_general, ng, g->d_adj_off, g->d_adj, d_glist, (int64_t)ng, d_gscr_off, d_gscr, 1, d_ncl,
                   d_nmem, d_cq_off, d_gmask_off, d_gmask, d_mem_off, g->d_clq_off, g->d_clq, g->d_status);
@@ -1071,8 +1105,10 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(tmp.get(&d_hsize, C));
     PMRF_TRY(tmp.get(&d_hmax, 1));
     PMRF_CUDA(cudaMemsetAsync(d_hmax, 0, sizeof(int32_t), s));
+    int32_t* d_hood_kept = nullptr;
+    PMRF_TRY(tmp.get(&d_hood_kept, C * HOOD_KEEP));
     LAUNCH_1D(k_hood_merge<false>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, d_hsize, d_hmax, nullptr,
-              nullptr, nullptr, nullptr);
+              nullptr, nullptr, nullptr, d_hood_kept);
     PMRF_TRY(dalloc(&g->d_hood_off, C + 1, s));
     PMRF_TRY(exclusive_scan_i32_to_i64(d_hsize, g->d_hood_off, C, s));
     PMRF_TRY(read_i64(g->d_hood_off + C, &g->N_el, s));
@@ -1084,7 +1120,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(tmp.get(&d_rcount, V));
     PMRF_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     LAUNCH_1D(k_hood_merge<true>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, nullptr, nullptr,
-              g->d_hood_off, g->d_hood, d_el_hood, d_rcount);
+              g->d_hood_off, g->d_hood, d_el_hood, d_rcount, d_hood_kept);
 
     // 7. replica offsets and masks
     PMRF_TRY(dalloc(&g->d_rep_off, V + 1, s));
