@@ -82,31 +82,39 @@ __global__ void k_validate(const double* __restrict__ img, const int32_t* __rest
 
 // pixel counts and bounding boxes (rows and columns inside the slice) of every
 // raw id present, indexed by its slot in the slice's rank table (so they need
-// no vertex numbering yet); lanes holding the same id combine first
+// no vertex numbering yet).  A warp's 32 consecutive pixels form runs of equal
+// ids within a row (one shuffle and one ballot find the run starts); the
+// first lane of each run updates the run's count and extent.
 __global__ void k_count_raw(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
                             const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
                             int32_t* __restrict__ npix_raw, int4* __restrict__ bbox_raw) {
     const int s = blockIdx.y;
     const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int lane = lane_id();
+    const unsigned w32 = (unsigned)W;
     for (int64_t base = b + (int64_t)blockIdx.x * blockDim.x; base < e; base += stride) {
         const int64_t p = base + threadIdx.x;
         const bool ok = p < e;
-        const int32_t id = ok ? ids[p] : -1 - lane_id();
-        const unsigned grp = __match_any_sync(0xffffffffu, id);
         // row and column within the slice in 32-bit arithmetic (a batch has
-        // fewer than 2^32 pixels)
-        const unsigned q = (unsigned)(p - b), w32 = (unsigned)W;
-        const unsigned r = ok ? q / w32 : 0u, c = ok ? q - r * w32 : 0u;
-        const unsigned rmin = __reduce_min_sync(grp, r), rmax = __reduce_max_sync(grp, r);
-        const unsigned cmin = __reduce_min_sync(grp, c), cmax = __reduce_max_sync(grp, c);
-        if (ok && lane_id() == __ffs(grp) - 1) {
+        // fewer than 2^32 pixels); lanes past the end get distinct ids
+        const int32_t id = ok ? ids[p] : -1 - lane;
+        const unsigned q = (unsigned)(p - b);
+        const unsigned r = q / w32, c = q - r * w32;
+        const int32_t pid = __shfl_up_sync(0xffffffffu, id, 1);
+        const unsigned pr = __shfl_up_sync(0xffffffffu, r, 1);
+        const bool start = lane == 0 || pid != id || pr != r;
+        const unsigned starts = __ballot_sync(0xffffffffu, start);
+        if (ok && start) {
+            const unsigned later = starts & ~((2u << lane) - 1u);  // starts above this lane
+            const int end = later ? __ffs(later) - 2 : 31;        // last lane of the run
+            const int len = end - lane + 1;
             const int64_t k = rb + id;
-            atomicAdd(&npix_raw[k], __popc(grp));
-            atomicMin(&bbox_raw[k].x, (int)rmin);
-            atomicMax(&bbox_raw[k].y, (int)rmax);
-            atomicMin(&bbox_raw[k].z, (int)cmin);
-            atomicMax(&bbox_raw[k].w, (int)cmax);
+            atomicAdd(&npix_raw[k], len);
+            atomicMin(&bbox_raw[k].x, (int)r);
+            atomicMax(&bbox_raw[k].y, (int)r);
+            atomicMin(&bbox_raw[k].z, (int)c);
+            atomicMax(&bbox_raw[k].w, (int)(c + len - 1));
         }
     }
 }
