@@ -1,6 +1,7 @@
 // api.cu -- the C ABI of include/pmrf.h: argument checks, graph lifetime,
 // error strings and the dispatch into the build / EM / PLL code.
 #include <atomic>
+#include <mutex>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -20,6 +21,51 @@ void note_launch(int64_t n) {
     else g_launches.fetch_add(n, std::memory_order_relaxed);
 }
 void set_capture_counter(int64_t* counter) { t_capture = counter; }
+
+// kernels counted on the device (the bodies of conditional graph nodes run
+// only when their condition holds): one counter per device, created on first
+// use
+namespace {
+std::mutex g_dev_counter_mu;
+unsigned long long* g_dev_counter[64] = {};
+}  // namespace
+
+unsigned long long* device_launch_counter() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_dev_counter_mu);
+    if (!g_dev_counter[dev]) {
+        unsigned long long* p = nullptr;
+        if (cudaMalloc(&p, sizeof(unsigned long long)) != cudaSuccess ||
+            cudaMemset(p, 0, sizeof(unsigned long long)) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        g_dev_counter[dev] = p;
+    }
+    return g_dev_counter[dev];
+}
+
+int64_t device_launches() {
+    int64_t total = 0;
+    std::lock_guard<std::mutex> lk(g_dev_counter_mu);
+    int cur = 0;
+    if (cudaGetDevice(&cur) != cudaSuccess) cudaGetLastError();
+    for (int d = 0; d < 64; ++d) {
+        if (!g_dev_counter[d]) continue;
+        unsigned long long v = 0;
+        if (cudaSetDevice(d) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+            cudaMemcpy(&v, g_dev_counter[d], sizeof(v), cudaMemcpyDeviceToHost) == cudaSuccess)
+            total += (int64_t)v;
+        else
+            cudaGetLastError();
+    }
+    cudaSetDevice(cur);
+    return total;
+}
 
 void set_error(const std::string& msg) { g_last_error = msg; }
 int fail(int code, const std::string& msg) {
@@ -95,7 +141,7 @@ int pmrf_config_default(pmrf_config* cfg) {
 
 const char* pmrf_last_error(void) { return g_last_error.c_str(); }
 
-int64_t pmrf_launch_count(void) { return g_launches.load(); }
+int64_t pmrf_launch_count(void) { return g_launches.load() + device_launches(); }
 
 const char* pmrf_version(void) { return "pmrf-b300 0.1 (sm_103a)"; }
 

@@ -133,6 +133,9 @@ int segmented_sort_u32(uint32_t* vals, const int64_t* off, int64_t nseg, int64_t
 // adds that count.
 void note_launch(int64_t n);
 void set_capture_counter(int64_t* counter);
+// a device word that kernels inside conditional graph bodies add their count
+// to (pmrf_launch_count adds it in); NULL when it cannot be created
+unsigned long long* device_launch_counter();
 
 // The library's stream-ordered memory pool on the current device (pool.cu):
 // created on first use, it keeps the memory freed into it mapped for reuse.

@@ -1040,13 +1040,67 @@ struct Launch {
 namespace {
 
 __global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
+
+// condition of the next EM iteration's graph body: run it while any slice is
+// still active; the kernels that body will run are added to the device-side
+// launch counter
+__global__ void k_set_cond(cudaGraphConditionalHandle h, const int32_t* __restrict__ nactive,
+                           unsigned long long* __restrict__ counter, unsigned int body_kernels) {
+    const unsigned int run = *nactive > 0 ? 1u : 0u;
+    cudaGraphSetConditional(h, run);
+    if (run) atomicAdd(counter, (unsigned long long)body_kernels);
+}
+
+// state of a capture that wraps each EM iteration in a conditional (IF) node
+struct CondCapture {
+    cudaStream_t body_stream = nullptr;        // captures the bodies
+    unsigned long long* counter = nullptr;     // device-side launch counter
+    std::vector<cudaGraphConditionalHandle> h;  // h[t-1] guards iteration t
+    int64_t* parent_nodes = nullptr;           // kernels outside the bodies
+    int64_t body_nodes = 0;                    // counted on the device instead
+};
 __global__ void k_set_active_all(int32_t* a, int32_t S) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < S) a[i] = 1;
 }
 
+// kernels one EM iteration body launches (the condition setter of the next
+// iteration included when there is one)
+int iter_kernels(const Plan* p, int t, int max_iters) {
+    return (p->n_vtiles > 0) + (p->n_htiles > 0) + 1 + (t < max_iters ? 1 : 0);
+}
+
+// open the IF node of iteration t on the capturing stream s and start
+// capturing its body on cc->body_stream
+int open_cond_body(CondCapture* cc, cudaStream_t s, int t) {
+    cudaStreamCaptureStatus st;
+    cudaGraph_t pg = nullptr;
+    const cudaGraphNode_t* deps = nullptr;
+    const cudaGraphEdgeData* ed = nullptr;
+    size_t nd = 0;
+    PMRF_CUDA(cudaStreamGetCaptureInfo(s, &st, nullptr, &pg, &deps, &ed, &nd));
+    if (st != cudaStreamCaptureStatusActive) return fail(PMRF_ERR_CUDA, "EM capture is not active");
+    cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
+    std::memset(&np, 0, sizeof(np));  // reserved fields must be zero
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cc->h[t - 1];
+    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    PMRF_CUDA(cudaGraphAddNode(&node, pg, deps, ed, nd, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    PMRF_CUDA(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    PMRF_CUDA(cudaStreamBeginCaptureToGraph(cc->body_stream, body, nullptr, nullptr, 0,
+                                            cudaStreamCaptureModeThreadLocal));
+    return PMRF_OK;
+}
+
+// with cc set (graph capture on s) every iteration is the body of an IF node
+// whose condition the previous iteration sets, so the iterations after all
+// slices converged cost one skipped node each; without it the loop is unrolled
 template <int L>
-int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_from_labels) {
+int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_from_labels,
+            CondCapture* cc = nullptr) {
     EMWork& w = g->em;
     Launch z{g, p, view(g), p->d_tiles + 0, p->d_tiles + p->n_vtiles, (RunCfg*)w.d_cfg,
              (OutPtrs*)((char*)w.d_cfg + sizeof(RunCfg))};
@@ -1066,10 +1120,21 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
                                             w.d_hpart, nullptr, w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
                                             w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
     ::pmrf::note_launch(1);
-    const bool prof = g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
+    if (cc) {
+        k_set_cond<<<1, 1, 0, s>>>(cc->h[0], w.d_nactive, cc->counter,
+                                   (unsigned)iter_kernels(p, 1, rc.max_iters));
+        ::pmrf::note_launch(1);
+    }
+    const bool prof = !cc && g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
+    const cudaStream_t s0 = s;
     for (int t = 1; t <= rc.max_iters; ++t) {
         const uint8_t* xin = w.d_x[(t - 1) & 1];
         uint8_t* xout = w.d_x[t & 1];
+        if (cc) {
+            PMRF_TRY(open_cond_body(cc, s0, t));
+            s = cc->body_stream;
+            set_capture_counter(&cc->body_nodes);
+        }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
         if (p->n_vtiles > 0) {
             k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
@@ -1088,6 +1153,18 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
                                                 w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off, w.d_active,
                                                 w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
         ::pmrf::note_launch(1);
+        if (cc) {
+            if (t < rc.max_iters) {
+                k_set_cond<<<1, 1, 0, s>>>(cc->h[t], w.d_nactive, cc->counter,
+                                           (unsigned)iter_kernels(p, t + 1, rc.max_iters));
+                ::pmrf::note_launch(1);
+            }
+            PMRF_CUDA(cudaGetLastError());
+            cudaGraph_t body = nullptr;
+            PMRF_CUDA(cudaStreamEndCapture(s, &body));
+            s = s0;
+            set_capture_counter(cc->parent_nodes);
+        }
     }
     k_close<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->V, 256), 4096)), 256, 0, s>>>(
         z.dg, rc.L, w.d_x[0], w.d_x[1], w.d_iters, w.d_conv, w.d_theta, z.d_out); ::pmrf::note_launch(1);
@@ -1095,6 +1172,79 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
 }
 
 }  // namespace
+
+// capture the whole EM loop into an executable graph; *nodes = the kernels
+// the capture launched outside conditional bodies
+int capture_em(pmrf_graph* g, Plan* p, const RunCfg& rc, bool init_from_labels, bool conditional,
+               cudaGraphExec_t* exec_out, int64_t* nodes) {
+    *exec_out = nullptr;
+    *nodes = 0;
+    CondCapture cc;
+    cc.parent_nodes = nodes;
+    if (conditional) {
+        cc.counter = device_launch_counter();
+        if (!cc.counter) return fail(PMRF_ERR_UNSUPPORTED, "no device launch counter");
+    }
+    cudaStream_t cs = nullptr;
+    PMRF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    if (conditional) {
+        cudaError_t e = cudaStreamCreateWithFlags(&cc.body_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(cs);
+            return cuda_fail(e, "body stream");
+        }
+    }
+    cudaGraph_t graph = nullptr;
+    int r = PMRF_OK;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess && conditional) {
+        cudaStreamCaptureStatus st;
+        cudaGraph_t pg = nullptr;
+        e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &pg);
+        cc.h.resize(rc.max_iters);
+        for (int t = 0; t < rc.max_iters && e == cudaSuccess; ++t)
+            e = cudaGraphConditionalHandleCreate(&cc.h[t], pg, 0, cudaGraphCondAssignDefault);
+    }
+    if (e == cudaSuccess) {
+        set_capture_counter(nodes);
+        CondCapture* c = conditional ? &cc : nullptr;
+        switch (rc.L) {
+            case 1: r = em_body<1>(g, p, rc, cs, init_from_labels, c); break;
+            case 2: r = em_body<2>(g, p, rc, cs, init_from_labels, c); break;
+            case 3: r = em_body<3>(g, p, rc, cs, init_from_labels, c); break;
+            case 4: r = em_body<4>(g, p, rc, cs, init_from_labels, c); break;
+            case 5: r = em_body<5>(g, p, rc, cs, init_from_labels, c); break;
+            case 6: r = em_body<6>(g, p, rc, cs, init_from_labels, c); break;
+            case 7: r = em_body<7>(g, p, rc, cs, init_from_labels, c); break;
+            default: r = em_body<8>(g, p, rc, cs, init_from_labels, c); break;
+        }
+        set_capture_counter(nullptr);
+    }
+    if (cc.body_stream) {  // a body capture left open by an error
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(cc.body_stream, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaGraph_t tmp = nullptr;
+            cudaStreamEndCapture(cc.body_stream, &tmp);
+        }
+    }
+    {
+        cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(cs, &st) == cudaSuccess && st != cudaStreamCaptureStatusNone) {
+            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+    }
+    if (e == cudaSuccess && r == PMRF_OK) e = cudaGraphInstantiate(exec_out, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (cc.body_stream) cudaStreamDestroy(cc.body_stream);
+    cudaStreamDestroy(cs);
+    if (r == PMRF_OK && e != cudaSuccess) r = cuda_fail(e, "EM graph capture");
+    if (r != PMRF_OK && *exec_out) {
+        cudaGraphExecDestroy(*exec_out);
+        *exec_out = nullptr;
+    }
+    return r;
+}
 
 // labels and T history destinations are passed through OutPtrs so a cached
 // CUDA graph can serve any caller buffers
@@ -1156,34 +1306,17 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
             e.vert_tile == p->vert_tile)
             ce = &e;
     if (!ce) {
-        cudaStream_t cs;
-        PMRF_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        cudaGraph_t graph = nullptr;
-        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-        int r = PMRF_OK;
         int64_t nodes = 0;
-        set_capture_counter(&nodes);
-        if (e == cudaSuccess) {
-            switch (rc.L) {
-                case 1: r = em_body<1>(g, p, rc, cs, cfg->init_from_labels); break;
-                case 2: r = em_body<2>(g, p, rc, cs, cfg->init_from_labels); break;
-                case 3: r = em_body<3>(g, p, rc, cs, cfg->init_from_labels); break;
-                case 4: r = em_body<4>(g, p, rc, cs, cfg->init_from_labels); break;
-                case 5: r = em_body<5>(g, p, rc, cs, cfg->init_from_labels); break;
-                case 6: r = em_body<6>(g, p, rc, cs, cfg->init_from_labels); break;
-                case 7: r = em_body<7>(g, p, rc, cs, cfg->init_from_labels); break;
-                default: r = em_body<8>(g, p, rc, cs, cfg->init_from_labels); break;
-            }
-            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
-            if (e == cudaSuccess) e = e2;
-        }
-        set_capture_counter(nullptr);
         cudaGraphExec_t exec = nullptr;
-        if (e == cudaSuccess && r == PMRF_OK) e = cudaGraphInstantiate(&exec, graph, 0);
-        if (graph) cudaGraphDestroy(graph);
-        cudaStreamDestroy(cs);
+        // conditional iteration bodies first (not with profiling: event
+        // records may not sit inside a conditional body), else the unrolled loop
+        int r = PMRF_ERR_UNSUPPORTED;
+        if (!g->tuning.profile) r = capture_em(g, p, rc, cfg->init_from_labels, true, &exec, &nodes);
+        if (r != PMRF_OK) {
+            cudaGetLastError();
+            r = capture_em(g, p, rc, cfg->init_from_labels, false, &exec, &nodes);
+        }
         if (r != PMRF_OK) return r;
-        if (e != cudaSuccess) return cuda_fail(e, "EM graph capture");
         pmrf_graph::CachedExec c;
         c.exec = exec;
         c.L = rc.L;

@@ -359,3 +359,39 @@ def test_large_regions_match_oracle():
         assert_graph_equal(oracle.Graph.from_image(one.image, one.region_ids), slice_view(arrs, s))
     cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=20)
     _em_compare(sl, oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20), cfg, g, g.em(cfg))
+
+
+def test_em_conditional_graph_equals_unrolled():
+    """The captured EM loop whose iterations sit in conditional graph nodes
+    gives exactly what the unrolled capture (profiling mode) and the direct
+    launches give, runs the same kernels as the unrolled loop cut at the last
+    active iteration plus one condition setter per run iteration and one after
+    the initial pass, and a repeated replay gives the same outputs."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(7, seed0=500))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+
+    def run(c, **tuning):
+        g.set_tuning(**tuning)
+        g.em(c, want_T=True)  # capture
+        torch.cuda.synchronize()
+        n0 = pmrf.launch_count()
+        out = g.em(c, want_T=True)
+        torch.cuda.synchronize()
+        return out, pmrf.launch_count() - n0
+
+    oc, nc = run(cfg)
+    ou, _ = run(cfg, profile=1)
+    od, _ = run(cfg, use_cuda_graph=0)
+    oc2, nc2 = run(cfg)
+    T = int(oc["iters"].max())
+    assert 1 <= T < cfg.max_iters
+    for o in (ou, od, oc2):
+        for k in ("labels", "params", "iters", "converged", "T_hist"):
+            assert torch.equal(oc[k], o[k]), k
+    assert nc == nc2
+    cut = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=T)
+    _, nu = run(cut, profile=1)
+    assert nc == nu + T + 1
