@@ -53,6 +53,11 @@ constexpr int HT_CAP = MAX_HOOD_TILE + 31;  // elements a fast hood tile can hol
 //               word 2 hold amin
 //   then        L-1 u32 masks: which of v's adjacency slots hold label l, for
 //               l < L-1 (the last label's count follows from the slot mask)
+// For L = 2 word 3 differs: it holds the mask of the slots that hold the
+// label other than amin.  With c_b the in-hood neighbours holding that label,
+// c_a the others and k = c_b - c_a, an element's excess
+// min(beta_q c_b, excess + beta_q c_a) is beta_q c_b, less beta_q k - excess
+// when that is positive, so a hood sum needs beta_q only once more.
 __host__ __device__ constexpr int vrec_words(int L) { return ((16 + 12 * (L - 1) + 31) / 32) * 4; }
 constexpr uint64_t DQ_MAX = (1ull << 60) - 1;
 
@@ -200,10 +205,16 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
 #pragma unroll
     for (int k = 0; k < L - 1; ++k) w[2 + k] = k < amin ? dq[k] : dq[k + 1];
     if (L > 1) w[2] |= (uint64_t)amin << 61;
+    if constexpr (L == 2) {
+        // slots holding the other label (the complement within v's slots of
+        // the label-0 mask when amin = 0)
+        w[3] = (uint64_t)(amin == 0 ? ~lmw[0] : lmw[0]);
+    } else {
 #pragma unroll
-    for (int k = 0; k < L - 1; ++k) {
-        const int u = 4 + 2 * (L - 1) + k;
-        w[u >> 1] |= (uint64_t)lmw[k] << (32 * (u & 1));
+        for (int k = 0; k < L - 1; ++k) {
+            const int u = 4 + 2 * (L - 1) + k;
+            w[u >> 1] |= (uint64_t)lmw[k] << (32 * (u & 1));
+        }
     }
     uint64_t* p = vrec + v * NW;
 #pragma unroll
@@ -435,10 +446,16 @@ __device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, 
         const uint64_t up = (l >= 1) ? (w[1 + l] & DQ_MAX) : 0ull;      // stored slot l-1 (labels above amin)
         R.dq[l] = l == amin ? 0ull : (l < amin ? own : up);
     }
+    if constexpr (L == 2) {
+        const uint32_t mb = (uint32_t)w[3];  // slots holding the label other than amin
+        R.lmv[0] = amin == 0 ? ~mb : mb;
+        R.lmv[1] = 0u;
+    } else {
 #pragma unroll
-    for (int k = 0; k < L; ++k) {
-        const int u = 4 + 2 * (L - 1) + k;  // u32 index of mask k
-        R.lmv[k] = k < L - 1 ? (uint32_t)(w[u >> 1] >> (32 * (u & 1))) : 0u;
+        for (int k = 0; k < L; ++k) {
+            const int u = 4 + 2 * (L - 1) + k;  // u32 index of mask k
+            R.lmv[k] = k < L - 1 ? (uint32_t)(w[u >> 1] >> (32 * (u & 1))) : 0u;
+        }
     }
     return R;
 }
@@ -550,13 +567,38 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                 // elements of <= 32 beta_q each: no overflow)
                 __int128 sdD = 0;
                 int64_t sdR = 0;
+                if constexpr (L == 2) {
+                    // sum of beta_q c_b, less beta_q k - excess where that is
+                    // positive (record layout above)
+                    int scb = 0, sk = 0;
+                    uint64_t sdq = 0;
 #pragma unroll 2
-                for (int i = b; i < e; ++i) {
-                    const VRec<L> R = load_vrec<L>(vrec, s_v[i]);
-                    int cnt[L];
-                    const int dc = slot_counts<L>(R, s_sm[i], cnt);
-                    sdD += R.Dmin;
-                    sdR += vrec_excess<L>(R, cnt, dc, beta_q);
+                    for (int i = b; i < e; ++i) {
+                        uint64_t w0, w1, w2, w3;
+                        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                            : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+                            : "l"(vrec + (int64_t)s_v[i] * 4));
+                        sdD += (__int128)(((unsigned __int128)w1 << 64) | w0);
+                        const uint32_t m = s_sm[i];
+                        const int cb = __popc(m & (uint32_t)w3);
+                        const int k = 2 * cb - __popc(m);
+                        scb += cb;
+                        const uint64_t dq = w2 & DQ_MAX;
+                        if (k > 0 && (uint64_t)beta_q * (uint32_t)k >= dq) {  // < 2^56
+                            sk += k;
+                            sdq += dq;
+                        }
+                    }
+                    sdR = beta_q * (int64_t)(scb - sk) + (int64_t)sdq;
+                } else {
+#pragma unroll 2
+                    for (int i = b; i < e; ++i) {
+                        const VRec<L> R = load_vrec<L>(vrec, s_v[i]);
+                        int cnt[L];
+                        const int dc = slot_counts<L>(R, s_sm[i], cnt);
+                        sdD += R.Dmin;
+                        sdR += vrec_excess<L>(R, cnt, dc, beta_q);
+                    }
                 }
                 const __int128 sd = sdD + ((__int128)sdR << rsh);
                 if (mode == MODE_SWEEP) {
