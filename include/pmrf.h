@@ -108,7 +108,9 @@ PMRF_API int pmrf_config_default(pmrf_config* cfg);
 PMRF_API const char* pmrf_last_error(void);
 
 /* Number of kernels this library has launched in this process so far (a
- * replay of a captured EM loop counts every kernel node it runs). */
+ * replay of a captured EM loop counts every kernel node it runs; the kernels
+ * inside its conditional iteration nodes are counted on the device, so this
+ * call synchronises every device on which an EM loop was captured). */
 PMRF_API int64_t pmrf_launch_count(void);
 
 /* Version string of the library build. */
