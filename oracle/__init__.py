@@ -21,6 +21,7 @@ per-slice functions and the readings they encode:
   step 3; G3, G8.
 * em                                 -- Algorithm 2 steps 6-11, EM step 5; G9.
 * pll                                -- the differentiable form (G10).
+* quality                            -- Section 4.2.1 evaluation metrics; G12.
 """
 from __future__ import annotations
 
@@ -90,6 +91,7 @@ def _get():
         lib.orc_em.argtypes = [GP, ctypes.POINTER(_Config), _P, _P, _P, _P, _P]
         lib.orc_pll.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P]
         lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
+        lib.orc_quality.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
         _lib = lib
     return _lib
 
@@ -285,6 +287,20 @@ def replicate(hood_off, hood, L):
     outs = [np.zeros(max(n, 1), np.int32) for _ in range(4)]
     _check(lib.orc_replicate(_ptr(hood_off), _ptr(hood), C, L, *[_ptr(o) for o in outs]), "replicate")
     return tuple(o[:n] for o in outs)
+
+
+def quality(pred, truth, L):
+    """Segmentation quality of one slice against its ground truth (Section
+    4.2.1; reading G12): the L x L confusion counts (truth-major) and, per
+    label, [precision, recall, accuracy, predicted fraction, true fraction]."""
+    pred = np.ascontiguousarray(pred, dtype=np.uint8).ravel()
+    truth = np.ascontiguousarray(truth, dtype=np.uint8).ravel()
+    if pred.size != truth.size:
+        raise ValueError("pred and truth differ in size")
+    conf = np.zeros((L, L), np.int64)
+    met = np.zeros((L, 5), np.float64)
+    _check(_get().orc_quality(_ptr(pred), _ptr(truth), pred.size, L, _ptr(conf), _ptr(met)), "quality")
+    return conf, met
 
 
 def segment_slices(images, region_ids, cfg: EMConfig):

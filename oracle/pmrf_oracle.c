@@ -731,3 +731,40 @@ int orc_label_image(const orc_graph* g, const int32_t* ids, int64_t npx, const u
     }
     return ORC_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Segmentation quality against a ground truth (Section 4.2.1, evaluation
+ * metrics).  The paper defines precision TP/(TP+FP), recall TP/(TP+FN),
+ * accuracy (TP+TN)/(TP+TN+FP+FN) for a two-phase segmentation and the
+ * porosity as the void volume over the total volume.  Reading G12: with L
+ * labels every label l is scored one-against-the-rest (TP: truth l and
+ * prediction l; FP: prediction l, truth other; FN: truth l, prediction other;
+ * TN: neither); the porosity of label l is the fraction of pixels carrying l
+ * (of the prediction and of the truth); a ratio whose denominator is 0 is NaN.
+ *
+ * conf[t*L + q] = number of pixels with truth t and prediction q;
+ * metrics[l*5 + k] = precision, recall, accuracy, predicted fraction, true
+ * fraction of label l.  Labels outside [0, L) are an argument error. */
+int orc_quality(const uint8_t* pred, const uint8_t* truth, int64_t npx, int32_t L, int64_t* conf, double* metrics) {
+    if (L < 1 || L > 255 || npx < 0) return ORC_ERR_ARG;
+    for (int64_t k = 0; k < (int64_t)L * L; ++k) conf[k] = 0;
+    for (int64_t p = 0; p < npx; ++p) {
+        if (pred[p] >= L || truth[p] >= L) return ORC_ERR_ARG;
+        conf[(int64_t)truth[p] * L + pred[p]] += 1;
+    }
+    for (int32_t l = 0; l < L; ++l) {
+        int64_t tp = conf[(int64_t)l * L + l], fp = 0, fn = 0;
+        for (int32_t t = 0; t < L; ++t)
+            if (t != l) fp += conf[(int64_t)t * L + l];
+        for (int32_t q = 0; q < L; ++q)
+            if (q != l) fn += conf[(int64_t)l * L + q];
+        const int64_t tn = npx - tp - fp - fn;
+        double* m = metrics + (int64_t)l * 5;
+        m[0] = (tp + fp) > 0 ? (double)tp / (double)(tp + fp) : NAN;
+        m[1] = (tp + fn) > 0 ? (double)tp / (double)(tp + fn) : NAN;
+        m[2] = npx > 0 ? (double)(tp + tn) / (double)npx : NAN;
+        m[3] = npx > 0 ? (double)(tp + fp) / (double)npx : NAN;
+        m[4] = npx > 0 ? (double)(tp + fn) / (double)npx : NAN;
+    }
+    return ORC_OK;
+}
