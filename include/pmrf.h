@@ -321,6 +321,27 @@ PMRF_API int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const 
  * the first error a kernel recorded since the last call (the word is then
  * cleared).  *detail (may be NULL) receives a kernel-specific code.
  */
+/*
+ * Segmentation quality against a ground truth (Section 4.2.1, evaluation
+ * metrics: precision TP/(TP+FP), recall TP/(TP+FN), accuracy
+ * (TP+TN)/(TP+TN+FP+FN), porosity = void volume / total volume).
+ *   d_pred, d_truth  u8 per pixel, in the layout the graph was built from
+ *                    (slices back to back, row-major); labels in [0, n_labels).
+ *   d_confusion      i64 [S][n_labels][n_labels]: pixels with true label t
+ *                    and predicted label q at [s][t][q] (truth-major).
+ *   d_metrics        f64 [S][n_labels][5]: for label l scored against the
+ *                    rest, precision, recall, accuracy, the predicted fraction
+ *                    and the true fraction of the slice's pixels carrying l
+ *                    (the porosity when l is the void phase); NaN where a
+ *                    denominator is 0.
+ * Caller-owned device buffers, written on the stream.  A pixel label outside
+ * [0, n_labels) is not counted and sets the device status to PMRF_ERR_ARG
+ * (pmrf_sync_status reports it with the pixel index).  n_labels outside
+ * [1, PMRF_MAX_LABELS] or a NULL pointer: PMRF_ERR_ARG.
+ */
+PMRF_API int pmrf_quality(pmrf_graph* g, int32_t n_labels, const uint8_t* d_pred, const uint8_t* d_truth,
+                          int64_t* d_confusion, double* d_metrics, pmrf_stream_t stream);
+
 PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* detail);
 
 /* Tile sizes of the EM launches.  0 selects the autotuned / default value.

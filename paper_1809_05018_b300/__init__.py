@@ -102,6 +102,7 @@ class Graph:
         N.check(_lib().pmrf_graph_stats(self._h, ctypes.byref(S), ctypes.byref(V), ctypes.byref(E),
                                         ctypes.byref(C), ctypes.byref(Nel)), "pmrf_graph_stats")
         self.S, self.V, self.E, self.C, self.N_el = S.value, V.value, E.value, C.value, Nel.value
+        self.n_pix = sum(h * w for h, w in zip(self.heights, self.widths))
 
     # -- lifetime -------------------------------------------------------------
     def close(self):
@@ -228,6 +229,21 @@ class Graph:
         N.check(_lib().pmrf_label_image(self._handle(), _ptr(ids), _ptr(labels), _ptr(out), _stream_ptr()),
                 "pmrf_label_image")
         return out
+
+    def quality(self, n_labels, pred, truth):
+        """Segmentation quality of a pixel label image against a ground truth
+        (Section 4.2.1): (confusion i64 [S, L, L] truth-major, metrics f64
+        [S, L, 5] = precision, recall, accuracy, predicted and true fraction)."""
+        pred = pred.reshape(-1)
+        truth = truth.reshape(-1)
+        for t, name in ((pred, "pred"), (truth, "truth")):
+            if t.dtype != torch.uint8 or not t.is_cuda or not t.is_contiguous() or t.numel() != self.n_pix:
+                raise ValueError(f"{name} must be a contiguous CUDA uint8 tensor of {self.n_pix} pixels")
+        conf = torch.empty((self.S, n_labels, n_labels), dtype=torch.int64, device=self.device)
+        met = torch.empty((self.S, n_labels, 5), dtype=torch.float64, device=self.device)
+        N.check(_lib().pmrf_quality(self._handle(), n_labels, _ptr(pred), _ptr(truth), _ptr(conf), _ptr(met),
+                                    _stream_ptr()), "pmrf_quality")
+        return conf, met
 
     def pll(self, n_labels, labels, mu, sigma, beta) -> torch.Tensor:
         _need(labels, torch.uint8, "labels", self.V)

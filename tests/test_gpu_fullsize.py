@@ -26,7 +26,8 @@ def _stack_tensors(sl):
 
 def test_stack512_sampled_slices_match_oracle():
     """512 slices of 1024x1024 in one batch (the bench workload); three
-    sampled slices checked end to end against the oracle."""
+    sampled slices checked end to end against the oracle, segmentation quality
+    against the phase maps included."""
     pmrf = _pmrf()
     wl = synth.workload("stack512")
     sl = synth.make_stack(wl.slices)
@@ -34,7 +35,10 @@ def test_stack512_sampled_slices_match_oracle():
     g = pmrf.build_graph(img, ids)
     cfg = pmrf.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters)
     out = g.em(cfg)
-    seg = g.label_image(ids, out["labels"]).cpu().numpy().reshape(len(sl), -1)
+    segd = g.label_image(ids, out["labels"])
+    conf, met = g.quality(wl.n_labels, segd, torch.from_numpy(np.stack([s.truth for s in sl])).cuda())
+    seg = segd.cpu().numpy().reshape(len(sl), -1)
+    conf, met = conf.cpu().numpy(), met.cpu().numpy()
     g.sync_status()
     x = out["labels"].cpu().numpy()
     th = out["params"].cpu().numpy()
@@ -50,6 +54,8 @@ def test_stack512_sampled_slices_match_oracle():
         assert np.array_equal(x[vo[s]:vo[s + 1]], r["labels"]), s
         assert rel_close(th[s, :, 1:3], r["theta"][:, 1:3], PARAM_RTOL)
         assert np.array_equal(seg[s], og.label_image(sl[s].region_ids, r["labels"]).ravel())
+        oc, om = oracle.quality(seg[s], sl[s].truth, wl.n_labels)
+        assert np.array_equal(conf[s], oc) and np.array_equal(met[s], om)
 
 
 def test_slice2048_matches_oracle():
