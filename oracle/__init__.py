@@ -37,6 +37,8 @@ _LIBDIR = os.path.join(_HERE, "lib")
 _LIB = os.path.join(_LIBDIR, "libpmrf_oracle.so")
 
 ORC_OK, ORC_ERR_ARG, ORC_ERR_OOM = 0, 1, 3
+SCOPE_HOOD, SCOPE_FULL = 0, 1
+RULE_MIN, RULE_SUM, RULE_VOTE = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -66,7 +68,8 @@ class _Graph(ctypes.Structure):
 
 class _Config(ctypes.Structure):
     _fields_ = [("n_labels", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("conv_window", ctypes.c_int32),
-                ("pad", ctypes.c_int32), ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
+                ("potts_scope", ctypes.c_int32), ("replica_rule", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double)]
 
 
@@ -92,6 +95,8 @@ def _get():
         lib.orc_pll.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P]
         lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
         lib.orc_quality.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
+        lib.orc_map_sweep_v.argtypes = [GP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P, _P,
+                                        _P, _P, _P, _P, _P]
         _lib = lib
     return _lib
 
@@ -124,10 +129,12 @@ class EMConfig:
     sigma_min: float = 1e-6
     init_lo: float = 0.0
     init_hi: float = 1.0
+    potts_scope: int = 0   # SCOPE_HOOD (G4) or SCOPE_FULL (G13)
+    replica_rule: int = 0  # RULE_MIN (G6), RULE_SUM or RULE_VOTE (G14)
 
     def _c(self):
-        return _Config(self.n_labels, self.max_iters, self.conv_window, 0, self.beta, self.conv_tol,
-                       self.sigma_min, self.init_lo, self.init_hi)
+        return _Config(self.n_labels, self.max_iters, self.conv_window, self.potts_scope, self.replica_rule, 0,
+                       self.beta, self.conv_tol, self.sigma_min, self.init_lo, self.init_hi)
 
 
 class Graph:
@@ -218,6 +225,20 @@ class Graph:
             out.update(E_el=E_el, Emin_el=Emin_el, lab_el=lab_el)
         if want_second:
             out["E_second"] = E2
+        return out
+
+    def map_sweep_variant(self, L, beta, x, mu, sigma, scope=SCOPE_HOOD, rule=RULE_MIN):
+        """One MAP sweep with a Potts scope and a replica rule (G13, G14);
+        returns dict with x_new, E_star, S (per hood) and gap (per vertex:
+        the relative distance of its decision from a floating-point tie)."""
+        lib = _get()
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        out = dict(x_new=np.zeros(self.V, np.uint8), E_star=np.zeros(self.V), S=np.zeros(self.C),
+                   gap=np.zeros(self.V))
+        _check(lib.orc_map_sweep_v(self._h, L, beta, scope, rule, _ptr(x), _ptr(mu), _ptr(sigma), _ptr(out["x_new"]),
+                                   _ptr(out["E_star"]), _ptr(out["S"]), _ptr(out["gap"])), "map_sweep_v")
         return out
 
     def params(self, L, x, E_star, theta_prev, sigma_min=1e-6):

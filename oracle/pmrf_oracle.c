@@ -46,9 +46,19 @@ typedef struct {
 } orc_graph;
 
 typedef struct {
-    int32_t n_labels, max_iters, conv_window, pad;
+    int32_t n_labels, max_iters, conv_window;
+    int32_t potts_scope;  /* ORC_SCOPE_HOOD (G4) or ORC_SCOPE_FULL */
+    int32_t replica_rule; /* ORC_RULE_MIN (G6), ORC_RULE_SUM or ORC_RULE_VOTE */
+    int32_t pad;
     double beta, conv_tol, sigma_min, init_lo, init_hi;
 } orc_config;
+
+/* Variants of the energy and of the replica reduction (readings G13, G14). */
+#define ORC_SCOPE_HOOD 0
+#define ORC_SCOPE_FULL 1
+#define ORC_RULE_MIN 0
+#define ORC_RULE_SUM 1
+#define ORC_RULE_VOTE 2
 
 static int cmp_i32(const void* a, const void* b) {
     int32_t x = *(const int32_t*)a, y = *(const int32_t*)b;
@@ -518,6 +528,147 @@ int orc_map_sweep(const orc_graph* g, int32_t L, double beta, const uint8_t* x, 
     return ORC_OK;
 }
 
+/*
+ * The MAP sweep with the variants of the scope table's NEXT list: the Potts
+ * penalty's scope and the rule that turns the replicas' decisions into one
+ * label per vertex.  Readings (ours; the paper fixes neither):
+ *
+ * G13 scope: ORC_SCOPE_HOOD counts the neighbours of v inside hood c (G4);
+ *     ORC_SCOPE_FULL counts every neighbour of v, so all replicas of v carry
+ *     the same energies  E(c,v,l) = D_l(y_v) + beta * #{u in N(v): x_u != l}.
+ * G14 replica rule ("Update Output Labels" scatters one label per vertex from
+ *     its replicas, Section 3.2.2 step 3; the winner among replicas is not
+ *     specified):
+ *     ORC_RULE_MIN   lexicographic minimum of (Emin(c,v), lab(c,v))  (G6);
+ *     ORC_RULE_SUM   the mean over v's replicas of E(c,v,l), summed in
+ *                    ascending c and divided by the replica count R_v; the
+ *                    label of the smallest mean (lower label on ties), E*_v
+ *                    its mean;
+ *     ORC_RULE_VOTE  each replica votes for lab(c,v); the label with most votes
+ *                    (lower label on ties); E*_v = the smallest Emin(c,v) among
+ *                    the replicas that voted for it.
+ * The hood sums S_c = sum of Emin(c,v) do not depend on the rule.
+ *
+ * gap[v] (optional): how far the decision of v is from a floating-point tie,
+ * relative (g = (b - a) / max(|a|, |b|, 1e-300) for the best value a and the
+ * runner-up b): for MIN and SUM over the label values compared; for VOTE the
+ * smallest such gap over v's replicas' own argmins (a vote count is an
+ * integer: only the per-replica decisions can be near a tie).  INFINITY when
+ * nothing competes.
+ */
+static double rel_gap(double a, double b) {
+    double s = fabs(a) > fabs(b) ? fabs(a) : fabs(b);
+    if (s < 1e-300) s = 1e-300;
+    return (b - a) / s;
+}
+
+int orc_map_sweep_v(const orc_graph* g, int32_t L, double beta, int32_t scope, int32_t rule, const uint8_t* x,
+                    const double* mu, const double* sigma, uint8_t* x_new, double* E_star, double* S_hood,
+                    double* gap) {
+    if (!g || L < 1 || L > 255 || scope < 0 || scope > 1 || rule < 0 || rule > 2) return ORC_ERR_ARG;
+    const int32_t V = g->V;
+    const size_t VL = (size_t)V * (size_t)L + 1;
+    double* E = (double*)malloc(sizeof(double) * (size_t)L);
+    double* acc = (double*)malloc(sizeof(double) * VL);    /* SUM: sums; VOTE: best Emin per label */
+    int64_t* cnt = (int64_t*)malloc(sizeof(int64_t) * VL); /* SUM: replica count at [v*L]; VOTE: votes */
+    double* best_E = (double*)malloc(sizeof(double) * ((size_t)V + 1));
+    int32_t* best_lab = (int32_t*)malloc(sizeof(int32_t) * ((size_t)V + 1));
+    double* rgap = (double*)malloc(sizeof(double) * ((size_t)V + 1)); /* VOTE: smallest replica gap */
+    if (!E || !acc || !cnt || !best_E || !best_lab || !rgap) {
+        free(E); free(acc); free(cnt); free(best_E); free(best_lab); free(rgap);
+        return ORC_ERR_OOM;
+    }
+    for (size_t k = 0; k < VL; ++k) { acc[k] = rule == ORC_RULE_VOTE ? INFINITY : 0.0; cnt[k] = 0; }
+    for (int32_t v = 0; v < V; ++v) { best_E[v] = INFINITY; best_lab[v] = -1; rgap[v] = INFINITY; }
+    for (int64_t c = 0; c < g->C; ++c) {
+        const int32_t* Hc = g->hood + g->hood_off[c];
+        const int64_t nH = g->hood_off[c + 1] - g->hood_off[c];
+        double S = 0.0;
+        for (int64_t i = 0; i < nH; ++i) {
+            const int32_t v = Hc[i];
+            int32_t lab = 0;
+            for (int32_t l = 0; l < L; ++l) {
+                int64_t m = 0;
+                for (int64_t j = g->adj_off[v]; j < g->adj_off[v + 1]; ++j) {
+                    int32_t u = g->adj[j];
+                    if ((scope == ORC_SCOPE_FULL || contains(Hc, nH, u)) && x[u] != l) ++m;
+                }
+                E[l] = data_term(g->y[v], mu[l], sigma[l]) + beta * (double)m;
+                if (E[l] < E[lab]) lab = l;
+            }
+            const double Emin = E[lab];
+            S += Emin;
+            if (rule == ORC_RULE_MIN) {
+                if (Emin < best_E[v] || (Emin == best_E[v] && lab < best_lab[v])) {
+                    best_E[v] = Emin;
+                    best_lab[v] = lab;
+                }
+            } else if (rule == ORC_RULE_SUM) {
+                for (int32_t l = 0; l < L; ++l) acc[(size_t)v * L + l] += E[l];
+                cnt[(size_t)v * L] += 1;
+            } else {
+                cnt[(size_t)v * L + lab] += 1;
+                if (Emin < acc[(size_t)v * L + lab]) acc[(size_t)v * L + lab] = Emin;
+                for (int32_t l = 0; l < L; ++l)
+                    if (l != lab) {
+                        double gg = rel_gap(Emin, E[l]);
+                        if (gg < rgap[v]) rgap[v] = gg;
+                    }
+            }
+        }
+        if (S_hood) S_hood[c] = S;
+    }
+    for (int32_t v = 0; v < V; ++v) {
+        double gv = INFINITY;
+        if (rule == ORC_RULE_MIN) {
+            /* runner-up: the smallest energy of any other label in any replica */
+            double second = INFINITY;
+            for (int64_t c = 0; c < g->C && gap; ++c) {
+                const int32_t* Hc = g->hood + g->hood_off[c];
+                const int64_t nH = g->hood_off[c + 1] - g->hood_off[c];
+                if (!contains(Hc, nH, v)) continue;
+                for (int32_t l = 0; l < L; ++l) {
+                    if (l == best_lab[v]) continue;
+                    int64_t m = 0;
+                    for (int64_t j = g->adj_off[v]; j < g->adj_off[v + 1]; ++j) {
+                        int32_t u = g->adj[j];
+                        if ((scope == ORC_SCOPE_FULL || contains(Hc, nH, u)) && x[u] != l) ++m;
+                    }
+                    double e = data_term(g->y[v], mu[l], sigma[l]) + beta * (double)m;
+                    if (e < second) second = e;
+                }
+            }
+            if (second < INFINITY) gv = rel_gap(best_E[v], second);
+        } else if (rule == ORC_RULE_SUM) {
+            const double R = (double)cnt[(size_t)v * L];
+            int32_t lab = 0;
+            for (int32_t l = 0; l < L; ++l) {
+                E[l] = acc[(size_t)v * L + l] / R;
+                if (E[l] < E[lab]) lab = l;
+            }
+            best_lab[v] = lab;
+            best_E[v] = E[lab];
+            for (int32_t l = 0; l < L; ++l)
+                if (l != lab) {
+                    double gg = rel_gap(E[lab], E[l]);
+                    if (gg < gv) gv = gg;
+                }
+        } else {
+            int32_t lab = 0;
+            for (int32_t l = 1; l < L; ++l)
+                if (cnt[(size_t)v * L + l] > cnt[(size_t)v * L + lab]) lab = l;
+            best_lab[v] = lab;
+            best_E[v] = acc[(size_t)v * L + lab];
+            gv = rgap[v];
+        }
+        if (x_new) x_new[v] = (uint8_t)best_lab[v];
+        if (E_star) E_star[v] = best_E[v];
+        if (gap) gap[v] = gv;
+    }
+    free(E); free(acc); free(cnt); free(best_E); free(best_lab); free(rgap);
+    return ORC_OK;
+}
+
 /* ------------------------------------------------------------------------ */
 /*
  * Parameter update (Section 3.2.2, EM step 4, "Update Parameters": mu and sigma
@@ -596,7 +747,8 @@ int orc_init_params(const orc_graph* g, int32_t L, double lo, double hi, double 
 
 /* ------------------------------------------------------------------------ */
 /*
- * The EM loop (Algorithm 2, steps 6-11; Section 3.2.2, EM steps 2-5).
+ * The EM loop (Algorithm 2, steps 6-11; Section 3.2.2, EM steps 2-5), with the
+ * sweep variant cfg->potts_scope / cfg->replica_rule (G13, G14).
  *   x^0, theta^0: orc_init_labels / orc_init_params.
  *   for t = 1, 2, ...:
  *     (x^t, E*, S^t) = sweep(x^{t-1}, theta^{t-1});  theta^t = params(x^t, E*)
@@ -613,6 +765,8 @@ int orc_init_params(const orc_graph* g, int32_t L, double lo, double hi, double 
 int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta, int32_t* iters, int32_t* converged,
            double* T_hist) {
     if (!g || !cfg || cfg->n_labels < 1 || cfg->max_iters < 1 || cfg->conv_window < 1) return ORC_ERR_ARG;
+    if (cfg->potts_scope < 0 || cfg->potts_scope > 1 || cfg->replica_rule < 0 || cfg->replica_rule > 2)
+        return ORC_ERR_ARG;
     const int32_t L = cfg->n_labels, W = cfg->conv_window, V = g->V;
     const int64_t C = g->C;
     int rc = orc_init_labels(g, L, cfg->init_lo, cfg->init_hi, x);
@@ -632,7 +786,7 @@ int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta,
     for (int32_t t = 1; t <= cfg->max_iters; ++t) {
         for (int32_t l = 0; l < L; ++l) { mu[l] = theta[4 * l + 1]; sg[l] = theta[4 * l + 2]; }
         double* S = Shist + (size_t)(t % (W + 1)) * (size_t)C;
-        rc = orc_map_sweep(g, L, cfg->beta, x, mu, sg, xn, Es, S, NULL, NULL, NULL, NULL);
+        rc = orc_map_sweep_v(g, L, cfg->beta, cfg->potts_scope, cfg->replica_rule, x, mu, sg, xn, Es, S, NULL);
         if (rc) goto done;
         memcpy(x, xn, (size_t)V);
         rc = orc_params(g, L, x, Es, theta, cfg->sigma_min, th2);
