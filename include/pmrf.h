@@ -87,12 +87,33 @@ typedef struct pmrf_graph pmrf_graph;
  * The starting parameters are the label-conditional moments of the starting
  * labels; a label with no vertex starts at the centre of its threshold bin
  * with sigma equal to the bin width.
+ *
+ * Variants of the sweep (the paper fixes neither choice; default 0 = the
+ * reading used throughout, Section 3.2.2 EM steps 2-3):
+ * potts_scope  PMRF_SCOPE_HOOD: the Potts penalty of vertex v in hood c counts
+ *              the neighbours of v inside c; PMRF_SCOPE_FULL: all neighbours
+ *              of v (every replica of v then carries the same energies).
+ * replica_rule how the replicas of v (one per hood holding v) give v its
+ *              label and energy E*_v.  PMRF_RULE_MIN: the replica of least
+ *              energy (lower label on ties); PMRF_RULE_SUM: the label of least
+ *              mean energy over the replicas, E*_v that mean; PMRF_RULE_VOTE:
+ *              each replica votes for its least-energy label, the label with
+ *              most votes wins (lower label on ties), E*_v is the least energy
+ *              among the replicas that voted for it.
+ * The hood energy sums do not depend on the replica rule.
  */
+#define PMRF_SCOPE_HOOD 0
+#define PMRF_SCOPE_FULL 1
+#define PMRF_RULE_MIN 0
+#define PMRF_RULE_SUM 1
+#define PMRF_RULE_VOTE 2
 typedef struct {
     int32_t n_labels;
     int32_t max_iters;
     int32_t conv_window;
     int32_t init_from_labels;
+    int32_t potts_scope;
+    int32_t replica_rule;
     double beta;
     double conv_tol;
     double sigma_min;

@@ -84,10 +84,12 @@ class EMConfig:
     init_lo: float = 0.0
     init_hi: float = 1.0
     init_from_labels: int = 0
+    potts_scope: int = 0   # 0 hood, 1 full neighbourhood
+    replica_rule: int = 0  # 0 min, 1 mean energy, 2 vote
 
     def c(self) -> N.Config:
-        return N.Config(self.n_labels, self.max_iters, self.conv_window, self.init_from_labels, self.beta,
-                        self.conv_tol, self.sigma_min, self.init_lo, self.init_hi)
+        return N.Config(self.n_labels, self.max_iters, self.conv_window, self.init_from_labels, self.potts_scope,
+                        self.replica_rule, self.beta, self.conv_tol, self.sigma_min, self.init_lo, self.init_hi)
 
 
 class Graph:

@@ -30,7 +30,8 @@ class PmrfError(RuntimeError):
 
 class Config(ctypes.Structure):
     _fields_ = [("n_labels", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("conv_window", ctypes.c_int32),
-                ("init_from_labels", ctypes.c_int32), ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
+                ("init_from_labels", ctypes.c_int32), ("potts_scope", ctypes.c_int32),
+                ("replica_rule", ctypes.c_int32), ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double)]
 
 

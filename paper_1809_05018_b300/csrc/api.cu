@@ -133,6 +133,8 @@ int pmrf_config_default(pmrf_config* cfg) {
     cfg->max_iters = 20;
     cfg->conv_window = 3;
     cfg->init_from_labels = 0;
+    cfg->potts_scope = PMRF_SCOPE_HOOD;
+    cfg->replica_rule = PMRF_RULE_MIN;
     cfg->beta = 1.0;
     cfg->conv_tol = 1e-4;
     cfg->sigma_min = 1e-6;

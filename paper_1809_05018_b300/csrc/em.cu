@@ -66,8 +66,11 @@ enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 
 struct RunCfg {
     int32_t L, W, max_iters, init_from_labels;
     double beta, tol, sigma_min, init_lo, init_hi;
-    int32_t hq, pad;  // unit 2^-hq of the hood pass's label excesses
-    int64_t beta_q;   // beta in those units (< 2^51)
+    int32_t hq;      // unit 2^-hq of the hood pass's label excesses
+    int32_t scope;   // PMRF_SCOPE_*
+    int32_t rule;    // PMRF_RULE_*
+    int32_t pad;
+    int64_t beta_q;  // beta in units 2^-hq (< 2^51)
 };
 
 struct OutPtrs {  // outputs of one pmrf_em call (read by the closing kernel)
@@ -173,15 +176,15 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
 // 1 / (2 sigma^2) of the Gaussian data term (one expression for every caller)
 __device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * sg * sg); }
 
-// the hood-pass record of vertex v (layout above) from its FP64 data terms
+// the data terms in fixed point: D_min exact (units 2^-80), the lowest label
+// attaining it, and every label's excess over it in units 2^-hq (rounded to
+// nearest, saturated at DQ_MAX)
 template <int L>
-__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t v, const double (&D)[L],
-                                           const uint32_t (&lmw)[L], int hq) {
-    constexpr int NW = vrec_words(L);
+__device__ __forceinline__ __int128 data_excess(const double (&D)[L], int hq, uint64_t (&dq)[L], int& amin) {
     __int128 F[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) F[l] = fix80(D[l]);
-    int amin = 0;
+    amin = 0;
     __int128 Fmin = F[0];
 #pragma unroll
     for (int l = 1; l < L; ++l)
@@ -190,13 +193,44 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
             amin = l;
         }
     const int sh = 80 - hq;  // >= 29
-    uint64_t dq[L];
 #pragma unroll
     for (int l = 0; l < L; ++l) {
         const unsigned __int128 dd = (unsigned __int128)F[l] - (unsigned __int128)Fmin;  // exact, >= 0
         const unsigned __int128 q = (dd + ((unsigned __int128)1 << (sh - 1))) >> sh;
         dq[l] = q > (unsigned __int128)DQ_MAX ? DQ_MAX : (uint64_t)q;
     }
+    return Fmin;
+}
+
+__device__ __forceinline__ void store_vrec_words(uint64_t* __restrict__ p, const uint64_t* w, int nw) {
+    for (int k = 0; k < nw; k += 4)
+        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p + k), "l"(w[k]), "l"(w[k + 1]),
+                     "l"(w[k + 2]), "l"(w[k + 3])
+                     : "memory");
+}
+
+// a record whose element energy is E in every hood (the full-neighbourhood
+// Potts scope: every replica of v carries the same energies): D_min = E, no
+// excess and no label masks, so the hood pass adds E for each element
+template <int L>
+__device__ __forceinline__ void write_vrec_const(uint64_t* __restrict__ vrec, int64_t v, __int128 E) {
+    constexpr int NW = vrec_words(L);
+    uint64_t w[NW];
+#pragma unroll
+    for (int k = 0; k < NW; ++k) w[k] = 0ull;
+    w[0] = (uint64_t)(unsigned __int128)E;
+    w[1] = (uint64_t)((unsigned __int128)E >> 64);
+    store_vrec_words(vrec + v * NW, w, NW);
+}
+
+// the hood-pass record of vertex v (layout above) from its FP64 data terms
+template <int L>
+__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t v, const double (&D)[L],
+                                           const uint32_t (&lmw)[L], int hq) {
+    constexpr int NW = vrec_words(L);
+    uint64_t dq[L];
+    int amin;
+    const __int128 Fmin = data_excess<L>(D, hq, dq, amin);
     uint64_t w[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) w[k] = 0ull;
@@ -216,15 +250,163 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
             w[u >> 1] |= (uint64_t)lmw[k] << (32 * (u & 1));
         }
     }
-    uint64_t* p = vrec + v * NW;
-#pragma unroll
-    for (int k = 0; k < NW; k += 4)
-        asm volatile("st.global.v4.b64 [%0], {%1, %2, %3, %4};" ::"l"(p + k), "l"(w[k]), "l"(w[k + 1]),
-                     "l"(w[k + 2]), "l"(w[k + 3])
-                     : "memory");
+    store_vrec_words(vrec + v * NW, w, NW);
 }
 
+// label counts among the neighbours of v in one replica with a multi-word
+// slot mask (degree > 32): returns the replica's in-hood degree
 template <int L>
+__device__ __forceinline__ int slot_label_counts(const DevGraph& g, const uint8_t* __restrict__ x_in, int64_t a0,
+                                                 int64_t r, int nw, int (&cnt)[L]) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) cnt[l] = 0;
+    int dc = 0;
+    for (int w = 0; w < nw; ++w) {
+        uint32_t m = g.rep_mask[r + w];
+        dc += __popc(m);
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int xl = x_in[g.adj[a0 + w * 32 + b]];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+        }
+    }
+    return dc;
+}
+
+// The sweep variants for one vertex (scope and replica rule of RunCfg; the
+// same definitions as pmrf_config documents): returns the new label, sets
+// Estar, writes the hood-pass record.  k_l of a replica = its in-hood
+// neighbours whose label is not l (every neighbour for the full scope).
+template <int L>
+__device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, const uint8_t* __restrict__ x_in,
+                                           int64_t a0, int d, int64_t r0, int64_t r1, const uint32_t (&lm)[L],
+                                           const double (&D)[L], uint64_t* __restrict__ vrec, int64_t v,
+                                           double& Estar) {
+    int lab = 0;
+    if (c.scope == PMRF_SCOPE_FULL) {
+        // one set of energies for every replica: every rule picks its least label
+        int M[L];
+        if (d <= 32) {
+#pragma unroll
+            for (int l = 0; l < L; ++l) M[l] = d - __popc(lm[l]);
+        } else {
+            int cnt[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cnt[l] = 0;
+            for (int j = 0; j < d; ++j) {
+                const int xl = x_in[g.adj[a0 + j]];
+#pragma unroll
+                for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+            }
+#pragma unroll
+            for (int l = 0; l < L; ++l) M[l] = d - cnt[l];
+        }
+        Estar = D[0] + c.beta * (double)M[0];
+#pragma unroll
+        for (int l = 1; l < L; ++l) {
+            const double e = D[l] + c.beta * (double)M[l];
+            if (e < Estar) { Estar = e; lab = l; }
+        }
+        if (vrec) {
+            // the element energy min_l (D_l + beta M_l) in the hood pass's fixed point
+            const int sh = 80 - c.hq;
+            __int128 Emin = 0;
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                const __int128 e = fix80(D[l]) + (((__int128)c.beta_q * M[l]) << sh);
+                if (l == 0 || e < Emin) Emin = e;
+            }
+            write_vrec_const<L>(vrec, v, Emin);
+        }
+        return lab;
+    }
+    const int nw = d <= 32 ? 1 : (d + 31) >> 5;
+    if (c.rule == PMRF_RULE_SUM) {
+        // mean energy over the replicas: D_l + beta * (sum of k_l) / R
+        int64_t Ks[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) Ks[l] = 0;
+        int64_t R = 0;
+        for (int64_t r = r0; r < r1; r += nw, ++R) {
+            if (d <= 32) {
+                const uint32_t m = g.rep_mask[r];
+                const int dc = __popc(m);
+#pragma unroll
+                for (int l = 0; l < L; ++l) Ks[l] += dc - __popc(m & lm[l]);
+            } else {
+                int cnt[L];
+                const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+#pragma unroll
+                for (int l = 0; l < L; ++l) Ks[l] += dc - cnt[l];
+            }
+        }
+        const double inv_R = 1.0 / (double)R;  // every vertex lies in at least one hood
+        Estar = D[0] + c.beta * ((double)Ks[0] * inv_R);
+#pragma unroll
+        for (int l = 1; l < L; ++l) {
+            const double e = D[l] + c.beta * ((double)Ks[l] * inv_R);
+            if (e < Estar) { Estar = e; lab = l; }
+        }
+    } else {
+        // vote: each replica's least label, compared exactly in the hood
+        // pass's fixed point (excess_l + beta_q k_l, units 2^-hq)
+        uint64_t dq[L];
+        int amin;
+        (void)data_excess<L>(D, c.hq, dq, amin);
+        int votes[L], kmin[L];
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            votes[l] = 0;
+            kmin[l] = 0x7fffffff;
+        }
+        const uint64_t bq = (uint64_t)c.beta_q;
+        for (int64_t r = r0; r < r1; r += nw) {
+            int k[L];
+            if (d <= 32) {
+                const uint32_t m = g.rep_mask[r];
+                const int dc = __popc(m);
+#pragma unroll
+                for (int l = 0; l < L; ++l) k[l] = dc - __popc(m & lm[l]);
+            } else {
+                int cnt[L];
+                const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+#pragma unroll
+                for (int l = 0; l < L; ++l) k[l] = dc - cnt[l];
+            }
+            // < 2^60 + 2^51 * 2^12: no overflow in 64 bits
+            int b = 0;
+            uint64_t eb = dq[0] + bq * (uint64_t)k[0];
+#pragma unroll
+            for (int l = 1; l < L; ++l) {
+                const uint64_t e = dq[l] + bq * (uint64_t)k[l];
+                if (e < eb) { eb = e; b = l; }
+            }
+#pragma unroll
+            for (int l = 0; l < L; ++l)
+                if (l == b) {
+                    votes[l] += 1;
+                    kmin[l] = min(kmin[l], k[l]);
+                }
+        }
+        int best = votes[0];
+#pragma unroll
+        for (int l = 1; l < L; ++l)
+            if (votes[l] > best) { best = votes[l]; lab = l; }
+        Estar = 0.0;
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            if (l == lab) Estar = D[l] + c.beta * (double)kmin[l];
+    }
+    if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
+    return lab;
+}
+
+// VAR: the sweep variants of RunCfg (Potts scope, replica rule) read at run
+// time; without it the default (hood scope, least-energy replica) is compiled
+// alone, so the variants cost the default nothing
+template <int L, bool VAR>
 __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGraph g, const Tile* __restrict__ tiles, int mode,
                                                        const RunCfg* __restrict__ cfgp,
                                                        const int32_t* __restrict__ active,
@@ -303,44 +485,37 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
 #pragma unroll
                     for (int l = 0; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
                 }
-                for (int64_t r = r0; r < r1; ++r) {
-                    const uint32_t m = g.rep_mask[r];
-                    const int dc = __popc(m);
+            }
+            if (!VAR || (c.scope == PMRF_SCOPE_HOOD && c.rule == PMRF_RULE_MIN)) {
+                if (d <= 32) {
+                    for (int64_t r = r0; r < r1; ++r) {
+                        const uint32_t m = g.rep_mask[r];
+                        const int dc = __popc(m);
 #pragma unroll
-                    for (int l = 0; l < L; ++l)
-                        M[l] = min(M[l], dc - __popc(m & lm[l]));  // neighbours in the hood whose label is not l
+                        for (int l = 0; l < L; ++l)
+                            M[l] = min(M[l], dc - __popc(m & lm[l]));  // neighbours in the hood whose label is not l
+                    }
+                } else {
+                    const int nw = (d + 31) >> 5;
+                    for (int64_t r = r0; r < r1; r += nw) {
+                        int cnt[L];
+                        const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+#pragma unroll
+                        for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - cnt[l]);
+                    }
+                }
+                // the hood pass of this iteration reads v's data terms and label masks
+                if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
+                // every vertex lies in at least one hood, so M_l is set
+                Estar = D[0] + c.beta * (double)M[0];
+                lab = 0;
+#pragma unroll
+                for (int l = 1; l < L; ++l) {
+                    const double e = D[l] + c.beta * (double)M[l];
+                    if (e < Estar) { Estar = e; lab = l; }
                 }
             } else {
-                const int nw = (d + 31) >> 5;
-                for (int64_t r = r0; r < r1; r += nw) {
-                    int cnt[L];
-#pragma unroll
-                    for (int l = 0; l < L; ++l) cnt[l] = 0;
-                    int dc = 0;
-                    for (int w = 0; w < nw; ++w) {
-                        uint32_t m = g.rep_mask[r + w];
-                        dc += __popc(m);
-                        while (m) {
-                            const int b = __ffs(m) - 1;
-                            m &= m - 1;
-                            const int xl = x_in[g.adj[a0 + w * 32 + b]];
-#pragma unroll
-                            for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
-                        }
-                    }
-#pragma unroll
-                    for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - cnt[l]);
-                }
-            }
-            // the hood pass of this iteration reads v's data terms and label masks
-            if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
-            // every vertex lies in at least one hood, so M_l is set
-            Estar = D[0] + c.beta * (double)M[0];
-            lab = 0;
-#pragma unroll
-            for (int l = 1; l < L; ++l) {
-                const double e = D[l] + c.beta * (double)M[l];
-                if (e < Estar) { Estar = e; lab = l; }
+                lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar);
             }
             x_out[v] = (uint8_t)lab;
             if (E_out) E_out[v] = Estar;
@@ -634,7 +809,9 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                         }
                     }
                     const VRec<L> R = load_vrec<L>(vrec, v);
-                    part += R.Dmin + ((__int128)vrec_excess<L>(R, cnt, dc, beta_q) << rsh);
+                    // full scope: the record's D_min is already the element energy
+                    part += cf.scope == PMRF_SCOPE_FULL ? R.Dmin
+                                                        : R.Dmin + ((__int128)vrec_excess<L>(R, cnt, dc, beta_q) << rsh);
                 }
                 // exact integer sums: the reduction order does not matter
 #pragma unroll
@@ -1004,8 +1181,15 @@ int check_cfg(const pmrf_graph* g, const pmrf_config* cfg) {
     if (!(cfg->init_hi > cfg->init_lo)) return fail(PMRF_ERR_ARG, "init_hi must exceed init_lo");
     if (cfg->conv_window < 1) return fail(PMRF_ERR_ARG, "conv_window must be >= 1");
     if (cfg->max_iters < 1) return fail(PMRF_ERR_ARG, "max_iters must be >= 1");
+    if (cfg->potts_scope != PMRF_SCOPE_HOOD && cfg->potts_scope != PMRF_SCOPE_FULL)
+        return fail(PMRF_ERR_ARG, "potts_scope must be PMRF_SCOPE_HOOD or PMRF_SCOPE_FULL");
+    if (cfg->replica_rule < PMRF_RULE_MIN || cfg->replica_rule > PMRF_RULE_VOTE)
+        return fail(PMRF_ERR_ARG, "replica_rule must be PMRF_RULE_MIN, PMRF_RULE_SUM or PMRF_RULE_VOTE");
     return PMRF_OK;
 }
+
+// a sweep variant other than the default (hood scope, least-energy replica)
+bool is_variant(const RunCfg& r) { return r.scope != PMRF_SCOPE_HOOD || r.rule != PMRF_RULE_MIN; }
 
 RunCfg to_run(const pmrf_config* c) {
     RunCfg r;
@@ -1024,6 +1208,8 @@ RunCfg to_run(const pmrf_config* c) {
     int e = 0;
     if (r.beta > 0.0) std::frexp(r.beta, &e);
     r.hq = std::max(0, std::min(51, 51 - e));
+    r.scope = c->potts_scope;
+    r.rule = c->replica_rule;
     r.pad = 0;
     r.beta_q = (int64_t)std::llrint(std::ldexp(r.beta, r.hq));
     return r;
@@ -1153,7 +1339,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     (void)init_from_labels;  // the INIT pass reads buffer 1, which em_run fills from the caller
     k_zero_T<<<64, 256, 0, s>>>(z.d_out, (int64_t)S * rc.max_iters); ::pmrf::note_launch(1);
     if (p->n_vtiles > 0) {
-        k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
+        k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
                                                                 w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
                                                                 nullptr, w.d_vpart, g->d_status, nullptr);
         ::pmrf::note_launch(1);
@@ -1168,6 +1354,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         ::pmrf::note_launch(1);
     }
     const bool prof = !cc && g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
+    const auto kv = is_variant(rc) ? &k_vertex<L, true> : &k_vertex<L, false>;
     const cudaStream_t s0 = s;
     for (int t = 1; t <= rc.max_iters; ++t) {
         const uint8_t* xin = w.d_x[(t - 1) & 1];
@@ -1179,7 +1366,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
         if (p->n_vtiles > 0) {
-            k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
+            kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
                                                                     xout, w.d_theta, w.d_dterm, nullptr, nullptr,
                                                                     w.d_vpart, g->d_status, w.d_vrec);
             ::pmrf::note_launch(1);
@@ -1345,7 +1532,7 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
     pmrf_graph::CachedExec* ce = nullptr;
     for (auto& e : g->execs)
         if (e.L == rc.L && e.W == rc.W && e.max_iters == rc.max_iters && e.hood_tile == p->hood_tile &&
-            e.vert_tile == p->vert_tile)
+            e.vert_tile == p->vert_tile && e.var == (int)is_variant(rc))
             ce = &e;
     if (!ce) {
         int64_t nodes = 0;
@@ -1366,6 +1553,7 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
         c.max_iters = rc.max_iters;
         c.hood_tile = p->hood_tile;
         c.vert_tile = p->vert_tile;
+        c.var = (int)is_variant(rc);
         c.nkernels = nodes;
         g->execs.push_back(c);
         ce = &g->execs.back();
@@ -1382,12 +1570,13 @@ namespace {
 
 template <int L>
 int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, const uint8_t* xin, const double* theta,
-               uint8_t* xout, double* Eout, double* Sout, uint64_t* vrec) {
+               uint8_t* xout, double* Eout, double* Sout, uint64_t* vrec, bool var) {
     DevGraph dg = view(g);
     const Tile* vt = p->d_tiles;
     const Tile* ht = p->d_tiles + p->n_vtiles;
     if (p->n_vtiles > 0) {
-        k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
+        const auto kv = var ? &k_vertex<L, true> : &k_vertex<L, false>;
+        kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
                                                                 nullptr, nullptr, Eout, nullptr, g->d_status, vrec);
         ::pmrf::note_launch(1);
     }
@@ -1406,7 +1595,7 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     DevGraph dg = view(g);
     EMWork& w = g->em;
     if (p->n_vtiles > 0) {
-        k_vertex<L><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
+        k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
                                                                 nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
                                                                 g->d_status, nullptr);
         ::pmrf::note_launch(1);
@@ -1452,7 +1641,7 @@ int sweep_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* xin, const d
     PMRF_CUDA(cudaMemcpyAsync(w.d_cfg, &rc, sizeof(rc), cudaMemcpyHostToDevice, s));
     int r = PMRF_OK;
     DISPATCH_L(rc.L, r = sweep_body<L>(g, p, s, (const RunCfg*)w.d_cfg, xin, theta, xout, Eout, Sout,
-                                       w.d_vrec));
+                                       w.d_vrec, is_variant(rc)));
     PMRF_CUDA(cudaStreamSynchronize(s));  // the host RunCfg copy is a stack value
     return r;
 }

@@ -96,6 +96,7 @@ struct pmrf_graph {
     struct CachedExec {
         cudaGraphExec_t exec = nullptr;
         int L = 0, W = 0, max_iters = 0, hood_tile = 0, vert_tile = 0;
+        int var = 0;  // vertex pass compiled with the sweep variants
         int64_t nkernels = 0;  // kernel nodes per replay
     };
     std::vector<CachedExec> execs;

@@ -1,0 +1,112 @@
+"""Sweep variants on the GPU (Potts scope, replica rule; readings G13, G14)
+against the oracle: one sweep lock-step (labels at the gap rule, vertex and
+hood energies), and whole EM runs (iterations, labels, parameters)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from pmrf_testutil import ENERGY_RTOL, PARAM_RTOL, assert_labels_match, dev_tensors, gpu_arrays, rel_close, small_specs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+VARIANTS = [(0, 1), (0, 2), (1, 0), (1, 1), (1, 2)]
+
+
+def _pmrf():
+    import paper_1809_05018_b300 as pmrf
+    return pmrf
+
+
+def _wide_slice():
+    """A background region touching 70 small cells (degree > 32, hoods wider
+    than 32): the multi-word paths of the vertex and hood passes."""
+    H, W = 24, 140
+    ids = np.zeros((H, W), np.int32)
+    ids[1:, :] = 1000
+    for k in range(70):
+        ids[0, 2 * k:2 * k + 2] = 7 + 3 * k
+    img = np.random.default_rng(0).random((H, W))
+    img[0, :] *= 0.5
+    return img, ids
+
+
+def _slices(seed0):
+    sl = synth.make_stack(small_specs(4, seed0=seed0))
+    pairs = [(s.image, s.region_ids) for s in sl]
+    pairs.append(_wide_slice())
+    return pairs
+
+
+@pytest.mark.parametrize("L", [2, 3])
+@pytest.mark.parametrize("scope,rule", VARIANTS)
+def test_sweep_variant_lockstep(scope, rule, L):
+    pmrf = _pmrf()
+    pairs = _slices(800 + L)
+    g = pmrf.build_graph([torch.from_numpy(a).cuda() for a, _ in pairs],
+                         [torch.from_numpy(b).cuda() for _, b in pairs])
+    rng = np.random.default_rng(10 * scope + rule + L)
+    x = rng.integers(0, L, g.V).astype(np.uint8)
+    theta = np.zeros((g.S, L, 4))
+    theta[:, :, 1] = np.sort(rng.uniform(0.2, 0.8, (g.S, L)), axis=1)
+    theta[:, :, 2] = rng.uniform(0.05, 0.3, (g.S, L))
+    cfg = pmrf.EMConfig(n_labels=L, beta=0.8, potts_scope=scope, replica_rule=rule)
+    xo, ev, eh = g.map_sweep(cfg, torch.from_numpy(x).cuda(), torch.from_numpy(theta).cuda())
+    xo, ev, eh = xo.cpu().numpy(), ev.cpu().numpy(), eh.cpu().numpy()
+    g.sync_status()
+    arrs = gpu_arrays(g)
+    for s, (a, b) in enumerate(pairs):
+        og = oracle.Graph.from_image(a, b)
+        v0, v1 = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        c0, c1 = arrs["HOOD_SLICE_OFF"][s], arrs["HOOD_SLICE_OFF"][s + 1]
+        r = og.map_sweep_variant(L, cfg.beta, x[v0:v1], theta[s, :, 1], theta[s, :, 2], scope, rule)
+        assert_labels_match(xo[v0:v1], r["x_new"], r["gap"], f"slice {s}")
+        ok = r["gap"] >= 1e-9
+        assert rel_close(ev[v0:v1][ok], r["E_star"][ok], 1e-12, 1e-13), s
+        assert rel_close(eh[c0:c1], r["S"], ENERGY_RTOL, 1e-12), s
+
+
+@pytest.mark.parametrize("scope,rule", VARIANTS)
+def test_em_variant_matches_oracle(scope, rule):
+    pmrf = _pmrf()
+    pairs = _slices(820)
+    g = pmrf.build_graph([torch.from_numpy(a).cuda() for a, _ in pairs],
+                         [torch.from_numpy(b).cuda() for _, b in pairs])
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=30, potts_scope=scope, replica_rule=rule)
+    out = g.em(cfg, want_T=True)
+    g.sync_status()
+    x = out["labels"].cpu().numpy()
+    th = out["params"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    T = out["T_hist"].cpu().numpy()
+    vo = g.array("VERT_OFF").numpy()
+    ocfg = oracle.EMConfig(n_labels=2, beta=1.0, max_iters=30, potts_scope=scope, replica_rule=rule)
+    for s, (a, b) in enumerate(pairs):
+        og = oracle.Graph.from_image(a, b)
+        r = og.em(ocfg)
+        assert it[s] == r["iters"], (s, it[s], r["iters"])
+        assert np.array_equal(x[vo[s]:vo[s + 1]], r["labels"]), s
+        assert np.array_equal(th[s, :, 0], r["theta"][:, 0])
+        assert rel_close(th[s, :, 1:3], r["theta"][:, 1:3], PARAM_RTOL)
+        assert rel_close(th[s, :, 3], r["theta"][:, 3], 1e-11, 1e-11)
+        assert rel_close(T[s, :r["iters"]], r["T_hist"], ENERGY_RTOL)
+
+
+def test_default_variant_unchanged_and_graph_cache_keyed():
+    """The same graph runs the default and a variant back to back: each result
+    equals a fresh run of its own, so the captured loops are not mixed up."""
+    pmrf = _pmrf()
+    pairs = _slices(840)
+    mk = lambda: pmrf.build_graph([torch.from_numpy(a).cuda() for a, _ in pairs],
+                                  [torch.from_numpy(b).cuda() for _, b in pairs])
+    g = mk()
+    base = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=30)
+    var = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=30, replica_rule=2)
+    a1 = g.em(base)
+    b1 = g.em(var)
+    a2 = g.em(base)
+    b2 = mk().em(var)
+    for k in ("labels", "params", "iters", "converged"):
+        assert torch.equal(a1[k], a2[k]), k
+        assert torch.equal(b1[k], b2[k]), k
