@@ -68,7 +68,7 @@ class _Graph(ctypes.Structure):
 
 class _Config(ctypes.Structure):
     _fields_ = [("n_labels", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("conv_window", ctypes.c_int32),
-                ("potts_scope", ctypes.c_int32), ("replica_rule", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("potts_scope", ctypes.c_int32), ("replica_rule", ctypes.c_int32), ("init_mode", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double)]
 
@@ -95,6 +95,10 @@ def _get():
         lib.orc_pll.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P]
         lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
         lib.orc_quality.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
+        lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
+        lib.orc_splitmix64.restype = ctypes.c_uint64
+        lib.orc_random_init.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
+                                        ctypes.c_double, ctypes.c_double, _P, _P]
         lib.orc_map_sweep_v.argtypes = [GP, ctypes.c_int32, ctypes.c_double, ctypes.c_int32, ctypes.c_int32, _P, _P,
                                         _P, _P, _P, _P, _P]
         _lib = lib
@@ -131,10 +135,11 @@ class EMConfig:
     init_hi: float = 1.0
     potts_scope: int = 0   # SCOPE_HOOD (G4) or SCOPE_FULL (G13)
     replica_rule: int = 0  # RULE_MIN (G6), RULE_SUM or RULE_VOTE (G14)
+    init_mode: int = 0     # 0 threshold (G3), 1 given labels, 2 given labels and parameters
 
     def _c(self):
-        return _Config(self.n_labels, self.max_iters, self.conv_window, self.potts_scope, self.replica_rule, 0,
-                       self.beta, self.conv_tol, self.sigma_min, self.init_lo, self.init_hi)
+        return _Config(self.n_labels, self.max_iters, self.conv_window, self.potts_scope, self.replica_rule,
+                       self.init_mode, self.beta, self.conv_tol, self.sigma_min, self.init_lo, self.init_hi)
 
 
 class Graph:
@@ -261,12 +266,13 @@ class Graph:
         _check(_get().orc_init_params(self._h, L, lo, hi, sigma_min, _ptr(x), _ptr(th)), "init_params")
         return th
 
-    def em(self, cfg: EMConfig):
-        """Full EM loop from the threshold initialisation.  Returns dict with
-        labels, theta [L,4] (n, mu, sigma, U), iters, converged, T_hist."""
+    def em(self, cfg: EMConfig, x0=None, theta0=None):
+        """Full EM loop from the start cfg.init_mode selects (threshold; the
+        labels x0; the labels x0 and parameters theta0 [L,4]).  Returns dict
+        with labels, theta [L,4] (n, mu, sigma, U), iters, converged, T_hist."""
         lib = _get()
-        x = np.zeros(self.V, np.uint8)
-        th = np.zeros((cfg.n_labels, 4))
+        x = np.zeros(self.V, np.uint8) if x0 is None else np.array(x0, dtype=np.uint8)
+        th = np.zeros((cfg.n_labels, 4)) if theta0 is None else np.array(theta0, dtype=np.float64).reshape(-1, 4)
         it = ctypes.c_int32(0)
         cv = ctypes.c_int32(0)
         Th = np.zeros(cfg.max_iters)
@@ -322,6 +328,20 @@ def quality(pred, truth, L):
     met = np.zeros((L, 5), np.float64)
     _check(_get().orc_quality(_ptr(pred), _ptr(truth), pred.size, L, _ptr(conf), _ptr(met)), "quality")
     return conf, met
+
+
+def splitmix64(key, i):
+    """Output of the (i+1)-th SplitMix64 step from state key."""
+    return int(_get().orc_splitmix64(key, i))
+
+
+def random_init(V, L, seed, slice_index, lo=0.0, hi=255.0):
+    """Random start of one slice (Algorithm 2 step 3; reading G15): labels
+    [V] and theta [L,4] = (0, mu, sigma, 0)."""
+    x = np.zeros(max(V, 1), np.uint8)
+    th = np.zeros((L, 4))
+    _check(_get().orc_random_init(V, L, seed, slice_index, lo, hi, _ptr(x), _ptr(th)), "random_init")
+    return x[:V], th
 
 
 def segment_slices(images, region_ids, cfg: EMConfig):

@@ -49,7 +49,7 @@ typedef struct {
     int32_t n_labels, max_iters, conv_window;
     int32_t potts_scope;  /* ORC_SCOPE_HOOD (G4) or ORC_SCOPE_FULL */
     int32_t replica_rule; /* ORC_RULE_MIN (G6), ORC_RULE_SUM or ORC_RULE_VOTE */
-    int32_t pad;
+    int32_t init_mode;    /* 0 threshold (G3), 1 labels given in x, 2 labels in x and parameters in theta */
     double beta, conv_tol, sigma_min, init_lo, init_hi;
 } orc_config;
 
@@ -748,7 +748,11 @@ int orc_init_params(const orc_graph* g, int32_t L, double lo, double hi, double 
 /* ------------------------------------------------------------------------ */
 /*
  * The EM loop (Algorithm 2, steps 6-11; Section 3.2.2, EM steps 2-5), with the
- * sweep variant cfg->potts_scope / cfg->replica_rule (G13, G14).
+ * sweep variant cfg->potts_scope / cfg->replica_rule (G13, G14).  The start
+ * (Algorithm 2 step 3): cfg->init_mode 0 thresholds the region means (G3);
+ * 1 takes the labels in x and the moments of them; 2 takes the labels in x
+ * and mu, sigma in theta (sigma floored at sigma_min), e.g. the random draw
+ * of orc_random_init.
  *   x^0, theta^0: orc_init_labels / orc_init_params.
  *   for t = 1, 2, ...:
  *     (x^t, E*, S^t) = sweep(x^{t-1}, theta^{t-1});  theta^t = params(x^t, E*)
@@ -769,8 +773,18 @@ int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta,
         return ORC_ERR_ARG;
     const int32_t L = cfg->n_labels, W = cfg->conv_window, V = g->V;
     const int64_t C = g->C;
-    int rc = orc_init_labels(g, L, cfg->init_lo, cfg->init_hi, x);
-    if (!rc) rc = orc_init_params(g, L, cfg->init_lo, cfg->init_hi, cfg->sigma_min, x, theta);
+    if (cfg->init_mode < 0 || cfg->init_mode > 2) return ORC_ERR_ARG;
+    int rc = ORC_OK;
+    if (cfg->init_mode == 0) rc = orc_init_labels(g, L, cfg->init_lo, cfg->init_hi, x);
+    for (int32_t v = 0; v < V && !rc; ++v)
+        if (x[v] >= L) rc = ORC_ERR_ARG;
+    if (!rc && cfg->init_mode < 2) rc = orc_init_params(g, L, cfg->init_lo, cfg->init_hi, cfg->sigma_min, x, theta);
+    if (!rc && cfg->init_mode == 2)  /* given parameters: sigma floored, counts and energies cleared */
+        for (int32_t l = 0; l < L; ++l) {
+            theta[4 * l + 0] = 0.0;
+            if (!(theta[4 * l + 2] > cfg->sigma_min)) theta[4 * l + 2] = cfg->sigma_min;
+            theta[4 * l + 3] = 0.0;
+        }
     if (rc) return rc;
     *iters = 0; *converged = 1;
     if (V == 0) return ORC_OK;
@@ -919,6 +933,42 @@ int orc_quality(const uint8_t* pred, const uint8_t* truth, int64_t npx, int32_t 
         m[2] = npx > 0 ? (double)(tp + tn) / (double)npx : NAN;
         m[3] = npx > 0 ? (double)(tp + fp) / (double)npx : NAN;
         m[4] = npx > 0 ? (double)(tp + fn) / (double)npx : NAN;
+    }
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Random start (Algorithm 2 step 3; Section 3.2.2: the label means and
+ * deviations are drawn between 0 and 255 and every vertex label is drawn at
+ * random).  The draws come from SplitMix64 (Steele, Lea, Flood, "Fast
+ * splittable pseudorandom number generators", OOPSLA 2014), used as a
+ * counter-based generator: splitmix64(key, i) is the output of the (i+1)-th
+ * step from state key.  Reading G15: for slice s, key_x = splitmix64(seed, 2s)
+ * and key_t = splitmix64(seed, 2s+1); label of vertex v = the high 32 bits of
+ * splitmix64(key_x, v) times L, shifted down 32 (uniform over [0, L));
+ * mu_l = lo + (hi - lo) * u(splitmix64(key_t, 2l)), sigma_l = lo + (hi - lo) *
+ * u(splitmix64(key_t, 2l+1)), u(r) = (r >> 11) * 2^-53 in [0, 1). */
+uint64_t orc_splitmix64(uint64_t key, uint64_t i) {
+    uint64_t z = key + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int orc_random_init(int32_t V, int32_t L, uint64_t seed, int64_t slice, double lo, double hi, uint8_t* x,
+                    double* theta) {
+    if (V < 0 || L < 1 || L > 255 || slice < 0 || !(hi >= lo)) return ORC_ERR_ARG;
+    const uint64_t kx = orc_splitmix64(seed, 2 * (uint64_t)slice);
+    const uint64_t kt = orc_splitmix64(seed, 2 * (uint64_t)slice + 1);
+    for (int32_t v = 0; v < V; ++v) x[v] = (uint8_t)(((orc_splitmix64(kx, (uint64_t)v) >> 32) * (uint64_t)L) >> 32);
+    const double w = hi - lo;
+    for (int32_t l = 0; l < L; ++l) {
+        const double u0 = (double)(orc_splitmix64(kt, 2 * (uint64_t)l) >> 11) * 0x1p-53;
+        const double u1 = (double)(orc_splitmix64(kt, 2 * (uint64_t)l + 1) >> 11) * 0x1p-53;
+        theta[4 * l + 0] = 0.0;
+        theta[4 * l + 1] = lo + w * u0;
+        theta[4 * l + 2] = lo + w * u1;
+        theta[4 * l + 3] = 0.0;
     }
     return ORC_OK;
 }
