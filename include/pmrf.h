@@ -84,9 +84,13 @@ typedef struct pmrf_graph pmrf_graph;
  *   (the paper draws random labels and parameters, Algorithm 2 step 3; the
  *   threshold start replaces that draw).
  * init_from_labels = 1: d_labels holds the starting labels (resume).
- * The starting parameters are the label-conditional moments of the starting
- * labels; a label with no vertex starts at the centre of its threshold bin
- * with sigma equal to the bin width.
+ * With 0 or 1 the starting parameters are the label-conditional moments of the
+ * starting labels; a label with no vertex starts at the centre of its
+ * threshold bin with sigma equal to the bin width.
+ * init_from_labels = 2: d_labels holds the starting labels and d_params the
+ *   starting parameters ([S][L][4]; mu and sigma at entries 1 and 2, sigma
+ *   floored at sigma_min), e.g. the paper's random start from
+ *   pmrf_random_init.
  *
  * Variants of the sweep (the paper fixes neither choice; default 0 = the
  * reading used throughout, Section 3.2.2 EM steps 2-3):
@@ -225,6 +229,24 @@ PMRF_API int pmrf_graph_get(const pmrf_graph* g, int32_t which, void* dst, size_
  * d_labels u8 [V].
  */
 PMRF_API int pmrf_init_labels(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, pmrf_stream_t stream);
+
+/*
+ * The paper's random start (Algorithm 2 step 3; Section 3.2.2: label means and
+ * deviations drawn between 0 and 255, every vertex label drawn at random),
+ * for pmrf_em with init_from_labels = 2.  Draws from SplitMix64 (Steele, Lea,
+ * Flood, OOPSLA 2014) used as a counter-based generator, sm(key, i) = the
+ * output of the (i+1)-th step from state key: for slice s, kx = sm(seed, 2s),
+ * kt = sm(seed, 2s+1); vertex v (index within its slice) gets label
+ * (hi32(sm(kx, v)) * n_labels) >> 32; label l gets mu = lo + (hi-lo)*u(sm(kt, 2l))
+ * and sigma = lo + (hi-lo)*u(sm(kt, 2l+1)) with u(r) = (r >> 11) * 2^-53
+ * (each operation rounded once).
+ *   d_labels u8 [V]; d_params f64 [S][n_labels][4] = (0, mu, sigma, 0).
+ * Caller-owned device buffers, written on the stream.  n_labels outside
+ * [1, PMRF_MAX_LABELS], lo > hi, a non-finite bound or a NULL pointer:
+ * PMRF_ERR_ARG.
+ */
+PMRF_API int pmrf_random_init(pmrf_graph* g, int32_t n_labels, uint64_t seed, double lo, double hi,
+                              uint8_t* d_labels, double* d_params, pmrf_stream_t stream);
 
 /*
  * Parameter update (Section 3.2.2, EM step 4 "Update Parameters"), per slice

@@ -201,10 +201,12 @@ class Graph:
                                       _ptr(e_v), _ptr(e_h), _stream_ptr()), "pmrf_map_sweep")
         return x_out, e_v, e_h
 
-    def em(self, cfg: EMConfig, labels=None, want_T=False, out=None):
+    def em(self, cfg: EMConfig, labels=None, want_T=False, out=None, params=None):
         """Run the EM loop on every slice.  Returns a dict of CUDA tensors:
         labels u8 [V], params f64 [S, L, 4] (n, mu, sigma, U), iters i32 [S],
-        converged i32 [S] and, with want_T, T_hist f64 [S, max_iters]."""
+        converged i32 [S] and, with want_T, T_hist f64 [S, max_iters].
+        labels: start from these labels (their moments as parameters);
+        labels and params [S, L, 4]: start from both (e.g. random_init)."""
         L = cfg.n_labels
         dev = self.device
         if out is None:
@@ -214,10 +216,16 @@ class Graph:
                        converged=torch.empty(self.S, dtype=torch.int32, device=dev))
             if want_T:
                 out["T_hist"] = torch.empty((self.S, cfg.max_iters), dtype=torch.float64, device=dev)
+        if params is not None and labels is None:
+            raise ValueError("a parameter start needs starting labels too")
         if labels is not None:
             _need(labels, torch.uint8, "labels", self.V)
             out["labels"].copy_(labels)
             cfg = EMConfig(**{**cfg.__dict__, "init_from_labels": 1})
+        if params is not None:
+            _need(params, torch.float64, "params", self.S * L * 4)
+            out["params"].copy_(params.reshape(self.S, L, 4))
+            cfg = EMConfig(**{**cfg.__dict__, "init_from_labels": 2})
         c = cfg.c()
         N.check(_lib().pmrf_em(self._handle(), ctypes.byref(c), _ptr(out["labels"]), _ptr(out["params"]),
                                _ptr(out["iters"]), _ptr(out["converged"]), _ptr(out.get("T_hist")), _stream_ptr()),
@@ -231,6 +239,15 @@ class Graph:
         N.check(_lib().pmrf_label_image(self._handle(), _ptr(ids), _ptr(labels), _ptr(out), _stream_ptr()),
                 "pmrf_label_image")
         return out
+
+    def random_init(self, n_labels, seed, lo=0.0, hi=255.0):
+        """The paper's random start (Algorithm 2 step 3): (labels u8 [V],
+        params f64 [S, L, 4] = (0, mu, sigma, 0)) for em(init_from_labels=2)."""
+        x = torch.empty(self.V, dtype=torch.uint8, device=self.device)
+        th = torch.empty((self.S, n_labels, 4), dtype=torch.float64, device=self.device)
+        N.check(_lib().pmrf_random_init(self._handle(), n_labels, seed, lo, hi, _ptr(x), _ptr(th), _stream_ptr()),
+                "pmrf_random_init")
+        return x, th
 
     def quality(self, n_labels, pred, truth):
         """Segmentation quality of a pixel label image against a ground truth

@@ -60,6 +60,7 @@ SIGNATURES = {
     "pmrf_pll_grad_noalloc": [_GP, _I32, _P, _P, _P, _D, _P, _P, _P, _P, _P],
     "pmrf_label_image": [_GP, _P, _P, _P, _P],
     "pmrf_quality": [_GP, ctypes.c_int32, _P, _P, _P, _P, _P],
+    "pmrf_random_init": [_GP, ctypes.c_int32, ctypes.c_uint64, ctypes.c_double, ctypes.c_double, _P, _P, _P],
     "pmrf_sync_status": [_GP, _P, ctypes.POINTER(_I64)],
     "pmrf_get_tuning": [_GP, ctypes.POINTER(Tuning)],
     "pmrf_set_tuning": [_GP, ctypes.POINTER(Tuning)],

@@ -86,6 +86,8 @@ int params_run(pmrf_graph* g, const pmrf_config* cfg, const uint8_t* x, const do
                double* out, cudaStream_t s);
 int init_labels_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* x, cudaStream_t s);
 int label_image_run(pmrf_graph* g, const int32_t* ids, const uint8_t* labels, uint8_t* out, cudaStream_t s);
+int random_init_run(pmrf_graph* g, int32_t L, uint64_t seed, double lo, double hi, uint8_t* x, double* params,
+                    cudaStream_t s);
 int quality_run(pmrf_graph* g, int32_t L, const uint8_t* pred, const uint8_t* truth, int64_t* conf, double* metrics,
                 cudaStream_t s);
 int pll_run(pmrf_graph* g, int32_t L, const uint8_t* x, const double* mu, const double* sigma, double beta,
@@ -357,6 +359,14 @@ int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const uint8_t* 
     if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
     PMRF_TRY(check_device(g));
     return label_image_run(g, d_region_ids, d_labels, d_out, (cudaStream_t)stream);
+}
+
+int pmrf_random_init(pmrf_graph* g, int32_t n_labels, uint64_t seed, double lo, double hi, uint8_t* d_labels,
+                     double* d_params, pmrf_stream_t stream) {
+    g_last_error.clear();
+    if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
+    PMRF_TRY(check_device(g));
+    return random_init_run(g, n_labels, seed, lo, hi, d_labels, d_params, (cudaStream_t)stream);
 }
 
 int pmrf_quality(pmrf_graph* g, int32_t n_labels, const uint8_t* d_pred, const uint8_t* d_truth, int64_t* d_confusion,

@@ -24,6 +24,7 @@
 // Slices that have stopped skip all work.  The loop for t = 1..max_iters is
 // captured once into a CUDA graph and replayed.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -910,7 +911,12 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
             mu_prev = theta_prev[((int64_t)s * L + l) * 4 + 1];
             sg_prev = theta_prev[((int64_t)s * L + l) * 4 + 2];
         }
-        if (n > 0.0) {
+        if (mode == MODE_INIT && cf.init_from_labels == 2) {
+            // the caller's starting mu and sigma (already in theta), sigma floored
+            th[0] = 0.0;
+            if (!(th[2] > cf.sigma_min)) th[2] = cf.sigma_min;
+            th[3] = 0.0;
+        } else if (n > 0.0) {
             const double m1 = tot[4 * l + 1] / n;
             const double var = fmax(tot[4 * l + 2] / n - m1 * m1, 0.0);
             const double sd = sqrt(var);
@@ -1181,6 +1187,7 @@ int check_cfg(const pmrf_graph* g, const pmrf_config* cfg) {
     if (!(cfg->init_hi > cfg->init_lo)) return fail(PMRF_ERR_ARG, "init_hi must exceed init_lo");
     if (cfg->conv_window < 1) return fail(PMRF_ERR_ARG, "conv_window must be >= 1");
     if (cfg->max_iters < 1) return fail(PMRF_ERR_ARG, "max_iters must be >= 1");
+    if (cfg->init_from_labels < 0 || cfg->init_from_labels > 2) return fail(PMRF_ERR_ARG, "init_from_labels must be 0, 1 or 2");
     if (cfg->potts_scope != PMRF_SCOPE_HOOD && cfg->potts_scope != PMRF_SCOPE_FULL)
         return fail(PMRF_ERR_ARG, "potts_scope must be PMRF_SCOPE_HOOD or PMRF_SCOPE_FULL");
     if (cfg->replica_rule < PMRF_RULE_MIN || cfg->replica_rule > PMRF_RULE_VOTE)
@@ -1502,6 +1509,11 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
         // the INIT pass reads x_in = buffer 1
         PMRF_CUDA(cudaMemcpyAsync(w.d_x[1], d_labels, (size_t)g->V, cudaMemcpyDeviceToDevice, s));
     }
+    if (cfg->init_from_labels == 2) {
+        // the finaliser's INIT step keeps these (sigma floored)
+        PMRF_CUDA(cudaMemcpyAsync(w.d_theta, d_params, sizeof(double) * (size_t)g->S * rc.L * 4,
+                                  cudaMemcpyDeviceToDevice, s));
+    }
     if (g->tuning.profile) {
         while ((int)g->prof_ev.size() < 3 * rc.max_iters) {
             cudaEvent_t ev;
@@ -1672,6 +1684,64 @@ int init_labels_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* x, cudaStrea
     if (g->V > 0) { k_init_labels<<<(unsigned)ceil_div(g->V, 256), 256, 0, s>>>(view(g), (const RunCfg*)w.d_cfg, x); ::pmrf::note_launch(1); }
     PMRF_CUDA(cudaGetLastError());
     PMRF_CUDA(cudaStreamSynchronize(s));
+    return PMRF_OK;
+}
+
+namespace {
+
+// SplitMix64 (Steele, Lea, Flood, OOPSLA 2014) as a counter-based generator:
+// the output of the (i+1)-th step from state key
+__device__ __forceinline__ uint64_t splitmix64(uint64_t key, uint64_t i) {
+    uint64_t z = key + (i + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// labels: vertex v of slice s draws from key_x = splitmix64(seed, 2s)
+__global__ void k_random_labels(const int64_t* __restrict__ vert_off, uint64_t seed, int L, uint8_t* __restrict__ x) {
+    const int s = blockIdx.y;
+    const int64_t v0 = vert_off[s], n = vert_off[s + 1] - v0;
+    const uint64_t kx = splitmix64(seed, 2 * (uint64_t)s);
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        x[v0 + v] = (uint8_t)(((splitmix64(kx, (uint64_t)v) >> 32) * (uint64_t)L) >> 32);
+}
+
+// parameters: label l of slice s draws mu and sigma from key_t = splitmix64(seed, 2s+1)
+__global__ void k_random_params(int S, int L, uint64_t seed, double lo, double hi, double* __restrict__ th) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S * L) return;
+    const int s = i / L, l = i % L;
+    const uint64_t kt = splitmix64(seed, 2 * (uint64_t)s + 1);
+    const double w = __dsub_rn(hi, lo);
+    const double u0 = (double)(splitmix64(kt, 2 * (uint64_t)l) >> 11) * 0x1p-53;
+    const double u1 = (double)(splitmix64(kt, 2 * (uint64_t)l + 1) >> 11) * 0x1p-53;
+    double* t = th + (int64_t)i * 4;
+    t[0] = 0.0;
+    t[1] = __dadd_rn(lo, __dmul_rn(w, u0));  // no contraction: one rounding per operation
+    t[2] = __dadd_rn(lo, __dmul_rn(w, u1));
+    t[3] = 0.0;
+}
+
+}  // namespace
+
+int random_init_run(pmrf_graph* g, int32_t L, uint64_t seed, double lo, double hi, uint8_t* x, double* params,
+                    cudaStream_t s) {
+    if (!x || !params) return fail(PMRF_ERR_ARG, "null pointer");
+    if (L < 1 || L > PMRF_MAX_LABELS) return fail(PMRF_ERR_ARG, "n_labels must be in [1, 8]");
+    if (!(hi >= lo) || !std::isfinite(lo) || !std::isfinite(hi)) return fail(PMRF_ERR_ARG, "need finite lo <= hi");
+    const int32_t S = g->S;
+    if (S == 0) return PMRF_OK;
+    int64_t maxv = 0;
+    for (int i = 0; i < S; ++i) maxv = std::max(maxv, g->h_vert_off[i + 1] - g->h_vert_off[i]);
+    if (maxv > 0) {
+        const dim3 grid((unsigned)std::min<int64_t>(ceil_div(maxv, 256), 65535), (unsigned)S);
+        k_random_labels<<<grid, 256, 0, s>>>(g->d_vert_off, seed, L, x);
+        ::pmrf::note_launch(1);
+    }
+    k_random_params<<<(unsigned)ceil_div((int64_t)S * L, 128), 128, 0, s>>>(S, L, seed, lo, hi, params);
+    ::pmrf::note_launch(1);
+    PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;
 }
 
