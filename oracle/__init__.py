@@ -95,6 +95,7 @@ def _get():
         lib.orc_pll.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P]
         lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
         lib.orc_quality.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
+        lib.orc_graph_set_hood_depth.argtypes = [GP, ctypes.c_int32]
         lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.orc_splitmix64.restype = ctypes.c_uint64
         lib.orc_random_init.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
@@ -174,7 +175,7 @@ class Graph:
 
     # -- constructors --------------------------------------------------------
     @classmethod
-    def from_image(cls, image: np.ndarray, region_ids: np.ndarray) -> "Graph":
+    def from_image(cls, image: np.ndarray, region_ids: np.ndarray, hood_depth: int = 1) -> "Graph":
         lib = _get()
         img = np.ascontiguousarray(image, dtype=np.float64)
         ids = np.ascontiguousarray(region_ids, dtype=np.int32)
@@ -182,10 +183,12 @@ class Graph:
             raise ValueError("image and region_ids must be 2-D of the same shape")
         h = ctypes.POINTER(_Graph)()
         _check(lib.orc_build_graph(_ptr(img), _ptr(ids), img.shape[0], img.shape[1], ctypes.byref(h)), "build_graph")
+        if hood_depth != 1:
+            _check(lib.orc_graph_set_hood_depth(h, hood_depth), "set_hood_depth")
         return cls(h)
 
     @classmethod
-    def from_adjacency(cls, y, neighbours) -> "Graph":
+    def from_adjacency(cls, y, neighbours, hood_depth: int = 1) -> "Graph":
         """neighbours: list of iterables (symmetric, no self loops)."""
         lib = _get()
         V = len(neighbours)
@@ -199,6 +202,8 @@ class Graph:
         yy = np.ascontiguousarray(y, dtype=np.float64)
         h = ctypes.POINTER(_Graph)()
         _check(lib.orc_graph_from_adjacency(V, _ptr(yy), _ptr(off), _ptr(adj), ctypes.byref(h)), "from_adjacency")
+        if hood_depth != 1:
+            _check(lib.orc_graph_set_hood_depth(h, hood_depth), "set_hood_depth")
         return cls(h)
 
     # -- method steps --------------------------------------------------------

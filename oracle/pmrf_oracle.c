@@ -362,6 +362,60 @@ oom:
     return ORC_ERR_OOM;
 }
 
+/* k-neighbourhoods (Section 3.1: a k-neighbourhood holds the vertices of a
+ * maximal clique and every vertex within k edges of any of them; the study
+ * uses k = 1).  Replaces the graph's hoods by those of depth k >= 1: for each
+ * clique a breadth-first search from all members at once, k levels deep, the
+ * reached vertices sorted ascending. */
+int orc_graph_set_hood_depth(orc_graph* g, int32_t k) {
+    if (!g || k < 1) return ORC_ERR_ARG;
+    const int32_t V = g->V;
+    int32_t* seen = (int32_t*)malloc(sizeof(int32_t) * ((size_t)V + 1)); /* clique index + 1 that reached v */
+    int64_t* off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)g->C + 1));
+    ivec out; memset(&out, 0, sizeof(out));
+    ivec cur; memset(&cur, 0, sizeof(cur));
+    ivec nxt; memset(&nxt, 0, sizeof(nxt));
+    if (!seen || !off) goto oom;
+    for (int32_t v = 0; v < V; ++v) seen[v] = 0;
+    off[0] = 0;
+    for (int64_t c = 0; c < g->C; ++c) {
+        const int32_t mark = (int32_t)(c + 1);
+        const int64_t start = out.n;
+        cur.n = 0;
+        for (int64_t i = g->clq_off[c]; i < g->clq_off[c + 1]; ++i) {
+            const int32_t u = g->clq[i];
+            if (seen[u] != mark) {
+                seen[u] = mark;
+                if (iv_push(&cur, u) || iv_push(&out, u)) goto oom;
+            }
+        }
+        for (int32_t level = 1; level <= k; ++level) {
+            nxt.n = 0;
+            for (int64_t i = 0; i < cur.n; ++i) {
+                const int32_t u = cur.a[i];
+                for (int64_t j = g->adj_off[u]; j < g->adj_off[u + 1]; ++j) {
+                    const int32_t w = g->adj[j];
+                    if (seen[w] == mark) continue;
+                    seen[w] = mark;
+                    if (iv_push(&nxt, w) || iv_push(&out, w)) goto oom;
+                }
+            }
+            ivec t = cur; cur = nxt; nxt = t;
+        }
+        qsort(out.a + start, (size_t)(out.n - start), sizeof(int32_t), cmp_i32);
+        off[c + 1] = out.n;
+    }
+    free(g->hood_off); free(g->hood);
+    g->hood_off = off;
+    g->hood = out.a ? out.a : (int32_t*)malloc(sizeof(int32_t));
+    g->N_el = out.n;
+    free(seen); free(cur.a); free(nxt.a);
+    return ORC_OK;
+oom:
+    free(seen); free(off); free(out.a); free(cur.a); free(nxt.a);
+    return ORC_ERR_OOM;
+}
+
 /* ------------------------------------------------------------------------ */
 /* Build everything for one slice: regions, adjacency, cliques, hoods. */
 int orc_build_graph(const double* image, const int32_t* ids, int64_t H, int64_t W, orc_graph** out) {
