@@ -184,6 +184,30 @@ PMRF_API int pmrf_memory_usage(int64_t* reserved_bytes, int64_t* used_bytes);
  * than PMRF_MAX_DEGREE neighbours, or a limit above), PMRF_ERR_OOM,
  * PMRF_ERR_CUDA.  On error *out is left NULL and nothing is leaked.
  */
+/*
+ * Build options (pmrf_build_graph_ex).
+ * hood_depth  k of the k-neighbourhoods (Section 3.1: a neighbourhood holds
+ *             the vertices of a maximal clique and every vertex within k edges
+ *             of any of them; the paper's study uses k = 1, the default).  In
+ *             [1, PMRF_MAX_HOOD_DEPTH].  With k > 1, "hood" everywhere below
+ *             means the k-neighbourhood (energies, replicas, sums).
+ * reserved    must be 0.
+ */
+#define PMRF_MAX_HOOD_DEPTH 8
+typedef struct {
+    int32_t hood_depth;
+    int32_t reserved;
+} pmrf_build_options;
+
+/* Fill *opt with the defaults (hood_depth 1).  PMRF_ERR_ARG on NULL. */
+PMRF_API int pmrf_build_options_default(pmrf_build_options* opt);
+
+/* pmrf_build_graph with options (NULL = the defaults); the same arguments,
+ * ownership and errors, plus PMRF_ERR_ARG for an option out of range. */
+PMRF_API int pmrf_build_graph_ex(const double* d_image, const int32_t* d_region_ids, int32_t n_slices,
+                                 const int64_t* h_heights, const int64_t* h_widths, const pmrf_build_options* opt,
+                                 pmrf_stream_t stream, pmrf_graph** out);
+
 PMRF_API int pmrf_build_graph(const double* d_image, const int32_t* d_region_ids, int32_t n_slices,
                      const int64_t* h_heights, const int64_t* h_widths, pmrf_stream_t stream,
                      pmrf_graph** out);

@@ -292,10 +292,11 @@ def _flat_ids(region_ids):
     return _need(region_ids, torch.int32, "region_ids").reshape(-1)
 
 
-def build_graph(images, region_ids, stream=None) -> Graph:
+def build_graph(images, region_ids, stream=None, hood_depth=1) -> Graph:
     """Build the graph of one slice (2-D tensors), a stack (3-D tensors) or a
     list of slices of different sizes (lists of 2-D tensors).  images: CUDA
-    float64, region_ids: CUDA int32 of the same shapes."""
+    float64, region_ids: CUDA int32 of the same shapes; hood_depth: k of the
+    k-neighbourhoods (Section 3.1; 1 in the paper's study)."""
     lib = _lib()
     if isinstance(images, (list, tuple)):
         shapes = [tuple(t.shape) for t in images]
@@ -319,8 +320,9 @@ def build_graph(images, region_ids, stream=None) -> Graph:
     H = (ctypes.c_int64 * S)(*hs)
     W = (ctypes.c_int64 * S)(*ws)
     h = ctypes.c_void_p()
-    N.check(lib.pmrf_build_graph(_ptr(img), _ptr(ids), S, H, W, _stream_ptr(stream), ctypes.byref(h)),
-            "pmrf_build_graph")
+    opt = N.BuildOptions(hood_depth, 0)
+    N.check(lib.pmrf_build_graph_ex(_ptr(img), _ptr(ids), S, H, W, ctypes.byref(opt), _stream_ptr(stream),
+                                    ctypes.byref(h)), "pmrf_build_graph_ex")
     return Graph(h, hs, ws, img.device)
 
 

@@ -35,6 +35,10 @@ class Config(ctypes.Structure):
                 ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double)]
 
 
+class BuildOptions(ctypes.Structure):
+    _fields_ = [("hood_depth", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 class Tuning(ctypes.Structure):
     _fields_ = [("hood_tile", ctypes.c_int32), ("vert_tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
                 ("use_cuda_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
@@ -47,6 +51,8 @@ _GP = ctypes.c_void_p
 SIGNATURES = {
     "pmrf_config_default": [ctypes.POINTER(Config)],
     "pmrf_build_graph": [_P, _P, _I32, _P, _P, _P, ctypes.POINTER(_GP)],
+    "pmrf_build_graph_ex": [_P, _P, _I32, _P, _P, _P, _P, ctypes.POINTER(_GP)],
+    "pmrf_build_options_default": [_P],
     "pmrf_graph_destroy": [_GP],
     "pmrf_graph_stats": [_GP, _P, _P, _P, _P, _P],
     "pmrf_graph_len": [_GP, _I32, ctypes.POINTER(_I64)],

@@ -161,16 +161,36 @@ int pmrf_memory_usage(int64_t* reserved_bytes, int64_t* used_bytes) {
     return pool_usage(reserved_bytes, used_bytes);
 }
 
+int pmrf_build_options_default(pmrf_build_options* opt) {
+    if (!opt) return fail(PMRF_ERR_ARG, "opt is NULL");
+    opt->hood_depth = 1;
+    opt->reserved = 0;
+    return PMRF_OK;
+}
+
 int pmrf_build_graph(const double* d_image, const int32_t* d_region_ids, int32_t n_slices, const int64_t* h_heights,
                      const int64_t* h_widths, pmrf_stream_t stream, pmrf_graph** out) {
+    return pmrf_build_graph_ex(d_image, d_region_ids, n_slices, h_heights, h_widths, nullptr, stream, out);
+}
+
+int pmrf_build_graph_ex(const double* d_image, const int32_t* d_region_ids, int32_t n_slices,
+                        const int64_t* h_heights, const int64_t* h_widths, const pmrf_build_options* opt,
+                        pmrf_stream_t stream, pmrf_graph** out) {
     g_last_error.clear();
     if (!out) return fail(PMRF_ERR_ARG, "out is NULL");
     *out = nullptr;
+    pmrf_build_options o;
+    pmrf_build_options_default(&o);
+    if (opt) o = *opt;
+    if (o.hood_depth < 1 || o.hood_depth > PMRF_MAX_HOOD_DEPTH)
+        return fail(PMRF_ERR_ARG, "hood_depth must be in [1, PMRF_MAX_HOOD_DEPTH]");
+    if (o.reserved != 0) return fail(PMRF_ERR_ARG, "reserved must be 0");
     if (n_slices < 1 || n_slices > 65535) return fail(PMRF_ERR_ARG, "n_slices must be in [1, 65535]");
     if (!h_heights || !h_widths) return fail(PMRF_ERR_ARG, "h_heights / h_widths is NULL");
     pmrf_graph* g = new (std::nothrow) pmrf_graph();
     if (!g) return fail(PMRF_ERR_OOM, "host allocation failed");
     g->S = n_slices;
+    g->hood_depth = o.hood_depth;
     g->h_H.assign(h_heights, h_heights + n_slices);
     g->h_W.assign(h_widths, h_widths + n_slices);
     g->h_pix_off.assign(n_slices + 1, 0);

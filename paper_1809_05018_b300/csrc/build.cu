@@ -716,6 +716,59 @@ __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t*
 }
 
 // ---------------------------------------------------------------------------
+// k-neighbourhoods (Section 3.1: the vertices within k edges of a clique's
+// members).  Level j+1 of a hood is the union of the closed neighbourhoods of
+// its level-j members: per hood, every member and its adjacency as candidates,
+// then a segmented sort with de-duplication.
+
+__global__ void k_expand_count(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
+                               const int64_t* __restrict__ adj_off, int64_t C, int64_t* __restrict__ cnt) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int64_t n = 0;
+    for (int64_t i = hood_off[c]; i < hood_off[c + 1]; ++i) {
+        const int32_t u = hood[i];
+        n += 1 + adj_off[u + 1] - adj_off[u];
+    }
+    cnt[c] = n;
+}
+
+__global__ void k_expand_fill(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
+                              const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj,
+                              const int64_t* __restrict__ cand_off, int64_t C, uint32_t* __restrict__ cand) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    int64_t o = cand_off[c];
+    for (int64_t i = hood_off[c]; i < hood_off[c + 1]; ++i) {
+        const int32_t u = hood[i];
+        cand[o++] = (uint32_t)u;
+        for (int64_t j = adj_off[u]; j < adj_off[u + 1]; ++j) cand[o++] = (uint32_t)adj[j];
+    }
+}
+
+// the de-duplicated head of each sorted candidate segment becomes the hood
+__global__ void k_take_unique(const uint32_t* __restrict__ cand, const int64_t* __restrict__ cand_off,
+                              const int64_t* __restrict__ new_off, int64_t C, int32_t* __restrict__ hood) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int64_t o = cand_off[c], h = new_off[c], n = new_off[c + 1] - h;
+    for (int64_t i = 0; i < n; ++i) hood[h + i] = (int32_t)cand[o + i];
+}
+
+// each element's hood, each vertex's replica count, the largest hood
+__global__ void k_el_hood(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood, int64_t C,
+                          int32_t* __restrict__ el_hood, int32_t* __restrict__ rcount, int32_t* __restrict__ hmax) {
+    const int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    const int64_t h0 = hood_off[c], h1 = hood_off[c + 1];
+    for (int64_t i = h0; i < h1; ++i) {
+        el_hood[i] = (int32_t)c;
+        atomicAdd(&rcount[hood[i]], 1);
+    }
+    atomicMax(hmax, (int32_t)(h1 - h0 < 0x7fffffff ? h1 - h0 : 0x7fffffff));
+}
+
+// ---------------------------------------------------------------------------
 // replica structures
 
 // replica lists in element order (filled in any order, then sorted): only the
@@ -887,6 +940,51 @@ int rep_elements(pmrf_graph* g, uint32_t* d_rep_el, cudaStream_t s) {
     PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     LAUNCH_1D(k_rep_fill, N_el, g->d_hood, N_el, g->d_rep_off, d_cursor, d_rep_el);
     PMRF_TRY(segmented_sort_u32(d_rep_el, g->d_rep_off, V, N_el, false, nullptr, g->d_status, s));
+    return PMRF_OK;
+}
+
+// hoods of depth g->hood_depth from the 1-hoods in g->d_hood_off / g->d_hood
+// (replaced); el_hood (a new scratch array), rcount and hmax recomputed
+int deepen_hoods(pmrf_graph* g, Scratch* tmp, int32_t** el_hood, int32_t* rcount, int32_t* hmax, cudaStream_t s) {
+    const int64_t C = g->C, V = g->V;
+    for (int level = 2; level <= g->hood_depth; ++level) {
+        int64_t *d_cnt = nullptr, *d_coff = nullptr, *d_noff = nullptr;
+        int32_t* d_ucnt = nullptr;
+        uint32_t* d_cand = nullptr;
+        int32_t* d_new = nullptr;
+        Scratch lv{s, {}};
+        PMRF_TRY(lv.get(&d_cnt, std::max<int64_t>(C, 1)));
+        PMRF_TRY(lv.get(&d_coff, C + 1));
+        PMRF_TRY(lv.get(&d_ucnt, std::max<int64_t>(C, 1)));
+        LAUNCH_1D(k_expand_count, C, g->d_hood_off, g->d_hood, g->d_adj_off, C, d_cnt);
+        PMRF_TRY(exclusive_scan_i64(d_cnt, d_coff, C, s));
+        int64_t ncand = 0;
+        PMRF_TRY(read_i64(d_coff + C, &ncand, s));
+        PMRF_TRY(lv.get(&d_cand, std::max<int64_t>(ncand, 1)));
+        LAUNCH_1D(k_expand_fill, C, g->d_hood_off, g->d_hood, g->d_adj_off, g->d_adj, d_coff, C, d_cand);
+        PMRF_TRY(segmented_sort_u32(d_cand, d_coff, C, ncand, true, d_ucnt, g->d_status, s));
+        PMRF_TRY(dalloc(&d_noff, C + 1, s));
+        int rc = exclusive_scan_i32_to_i64(d_ucnt, d_noff, C, s);
+        int64_t n_el = 0;
+        if (!rc) rc = read_i64(d_noff + C, &n_el, s);
+        if (!rc && n_el >= 4294967295ll) rc = fail(PMRF_ERR_UNSUPPORTED, "more than 2^32-1 hood elements");
+        if (!rc) rc = dalloc(&d_new, std::max<int64_t>(n_el, 1), s);
+        if (rc) {
+            dfree(d_noff, s);
+            return rc;
+        }
+        LAUNCH_1D(k_take_unique, C, d_cand, d_coff, d_noff, C, d_new);
+        dfree(g->d_hood_off, s);
+        dfree(g->d_hood, s);
+        g->d_hood_off = d_noff;
+        g->d_hood = d_new;
+        g->N_el = n_el;
+    }
+    PMRF_TRY(tmp->get(el_hood, std::max<int64_t>(g->N_el, 1)));
+    PMRF_CUDA(cudaMemsetAsync(rcount, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
+    PMRF_CUDA(cudaMemsetAsync(hmax, 0, sizeof(int32_t), s));
+    LAUNCH_1D(k_el_hood, C, g->d_hood_off, g->d_hood, C, *el_hood, rcount, hmax);
+    PMRF_TRY(check_status(g, s));
     return PMRF_OK;
 }
 
@@ -1129,6 +1227,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_CUDA(cudaMemsetAsync(d_rcount, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     LAUNCH_1D(k_hood_merge<true>, C, g->d_clq_off, g->d_clq, g->d_adj_off, g->d_adj, C, nullptr, nullptr,
               g->d_hood_off, g->d_hood, d_el_hood, d_rcount, d_hood_kept);
+    if (g->hood_depth > 1) PMRF_TRY(deepen_hoods(g, &tmp, &d_el_hood, d_rcount, d_hmax, s));
 
     // 7. replica offsets and masks
     PMRF_TRY(dalloc(&g->d_rep_off, V + 1, s));
@@ -1145,14 +1244,14 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(read_i64(g->d_rep_woff + V, &g->n_rep_words, s));
     PMRF_TRY(dalloc(&g->d_row, g->n_row_words, s));
     PMRF_TRY(dalloc(&g->d_rep_mask, g->n_rep_words, s));
-    PMRF_TRY(dalloc(&g->d_el_slot, N_el, s));
+    PMRF_TRY(dalloc(&g->d_el_slot, g->N_el, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     PMRF_TRY(dalloc(&g->d_hood_gen, C, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_hood_gen, 0, std::max<int64_t>(C, 1), s));
-    LAUNCH_1D(k_masks, N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off, g->d_row,
-              d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, N_el);
+    LAUNCH_1D(k_masks, g->N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off,
+              g->d_row, d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, g->N_el);
     PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
     // slice offsets of hoods and elements (host copies, one transfer)

@@ -55,6 +55,7 @@ struct pmrf_graph {
     int device = 0;
     int32_t S = 0;
     int64_t V = 0, E2 = 0, C = 0, n_clq = 0, N_el = 0, n_rank = 0, n_pix = 0;
+    int32_t hood_depth = 1;  // k of the k-neighbourhoods (Section 3.1)
     int64_t n_row_words = 0, n_rep_words = 0;
     int32_t max_deg = 0, max_hood = 0;
 
