@@ -96,6 +96,7 @@ def _get():
         lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
         lib.orc_quality.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
         lib.orc_graph_set_hood_depth.argtypes = [GP, ctypes.c_int32]
+        lib.orc_build_volume.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.POINTER(GP)]
         lib.orc_splitmix64.argtypes = [ctypes.c_uint64, ctypes.c_uint64]
         lib.orc_splitmix64.restype = ctypes.c_uint64
         lib.orc_random_init.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64, ctypes.c_int64,
@@ -183,6 +184,21 @@ class Graph:
             raise ValueError("image and region_ids must be 2-D of the same shape")
         h = ctypes.POINTER(_Graph)()
         _check(lib.orc_build_graph(_ptr(img), _ptr(ids), img.shape[0], img.shape[1], ctypes.byref(h)), "build_graph")
+        if hood_depth != 1:
+            _check(lib.orc_graph_set_hood_depth(h, hood_depth), "set_hood_depth")
+        return cls(h)
+
+    @classmethod
+    def from_volume(cls, volume: np.ndarray, region_ids: np.ndarray, hood_depth: int = 1) -> "Graph":
+        """3-D region graph of one volume [D, H, W] (reading G16: 6-connected
+        voxels, means in storage order)."""
+        lib = _get()
+        img = np.ascontiguousarray(volume, dtype=np.float64)
+        ids = np.ascontiguousarray(region_ids, dtype=np.int32)
+        if img.shape != ids.shape or img.ndim != 3:
+            raise ValueError("volume and region_ids must be 3-D of the same shape")
+        h = ctypes.POINTER(_Graph)()
+        _check(lib.orc_build_volume(_ptr(img), _ptr(ids), *img.shape, ctypes.byref(h)), "build_volume")
         if hood_depth != 1:
             _check(lib.orc_graph_set_hood_depth(h, hood_depth), "set_hood_depth")
         return cls(h)

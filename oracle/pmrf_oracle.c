@@ -417,6 +417,85 @@ oom:
 }
 
 /* ------------------------------------------------------------------------ */
+/* 3-D region graphs (the paper's future work, Section 6: graphs built from
+ * whole volumes instead of slices).  Reading G16: a volume of D layers of
+ * H x W voxels, stored layer by layer, each layer row-major; two regions are
+ * adjacent when some pair of 6-connected voxels (neighbours along x, y or z)
+ * carries their two ids; a region's value is the mean of its voxels summed in
+ * storage order.  Same bucketing, sorting and de-duplication as the 2-D
+ * adjacency. */
+static int edges_volume(const int32_t* ids, int64_t D, int64_t H, int64_t W, orc_graph* g) {
+    const int32_t V = g->V;
+    const int64_t layer = H * W;
+    int64_t* cnt = (int64_t*)calloc((size_t)V + 1, sizeof(int64_t));
+    if (!cnt) return ORC_ERR_OOM;
+    for (int pass = 0; pass < 2; ++pass) {
+        int64_t* off = NULL;
+        int32_t* bucket = NULL;
+        if (pass == 1) {
+            off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+            if (!off) { free(cnt); return ORC_ERR_OOM; }
+            off[0] = 0;
+            for (int32_t v = 0; v < V; ++v) off[v + 1] = off[v] + cnt[v];
+            bucket = (int32_t*)malloc(sizeof(int32_t) * (size_t)(off[V] + 1));
+            if (!bucket) { free(cnt); free(off); return ORC_ERR_OOM; }
+            for (int32_t v = 0; v < V; ++v) cnt[v] = 0;
+        }
+        for (int64_t z = 0; z < D; ++z)
+            for (int64_t r = 0; r < H; ++r)
+                for (int64_t c = 0; c < W; ++c) {
+                    const int64_t p = z * layer + r * W + c;
+                    const int32_t a = g->rank[ids[p]];
+                    int64_t q[3];
+                    int nq = 0;
+                    if (c + 1 < W) q[nq++] = p + 1;
+                    if (r + 1 < H) q[nq++] = p + W;
+                    if (z + 1 < D) q[nq++] = p + layer;
+                    for (int k = 0; k < nq; ++k) {
+                        const int32_t b = g->rank[ids[q[k]]];
+                        if (a == b) continue;
+                        if (pass == 0) { cnt[a]++; cnt[b]++; }
+                        else { bucket[off[a] + cnt[a]++] = b; bucket[off[b] + cnt[b]++] = a; }
+                    }
+                }
+        if (pass == 1) {
+            g->adj_off = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+            g->adj = (int32_t*)malloc(sizeof(int32_t) * (size_t)(off[V] + 1));
+            if (!g->adj_off || !g->adj) { free(cnt); free(off); free(bucket); return ORC_ERR_OOM; }
+            int64_t n = 0;
+            g->adj_off[0] = 0;
+            for (int32_t v = 0; v < V; ++v) {
+                int32_t* b = bucket + off[v];
+                const int64_t k = off[v + 1] - off[v];
+                qsort(b, (size_t)k, sizeof(int32_t), cmp_i32);
+                for (int64_t i = 0; i < k; ++i)
+                    if (i == 0 || b[i] != b[i - 1]) g->adj[n++] = b[i];
+                g->adj_off[v + 1] = n;
+            }
+            g->n_adj = n;
+            free(off); free(bucket);
+        }
+    }
+    free(cnt);
+    return ORC_OK;
+}
+
+/* Build everything for one volume of D layers (G16): regions (voxel means in
+ * storage order), 6-connected adjacency, cliques, hoods. */
+int orc_build_volume(const double* image, const int32_t* ids, int64_t D, int64_t H, int64_t W, orc_graph** out) {
+    if (!out || D < 1 || H < 0 || W < 0 || ((D * H * W) > 0 && (!image || !ids))) return ORC_ERR_ARG;
+    orc_graph* g = (orc_graph*)calloc(1, sizeof(orc_graph));
+    if (!g) return ORC_ERR_OOM;
+    int rc = regions(image, ids, D * H * W, g);
+    if (!rc) rc = edges_volume(ids, D, H, W, g);
+    if (!rc) rc = cliques(g);
+    if (!rc) rc = hoods(g);
+    if (rc) { orc_graph_free(g); return rc; }
+    *out = g;
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Build everything for one slice: regions, adjacency, cliques, hoods. */
 int orc_build_graph(const double* image, const int32_t* ids, int64_t H, int64_t W, orc_graph** out) {
     if (!out || H < 0 || W < 0 || ((H * W) > 0 && (!image || !ids))) return ORC_ERR_ARG;
