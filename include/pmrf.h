@@ -191,15 +191,24 @@ PMRF_API int pmrf_memory_usage(int64_t* reserved_bytes, int64_t* used_bytes);
  *             of any of them; the paper's study uses k = 1, the default).  In
  *             [1, PMRF_MAX_HOOD_DEPTH].  With k > 1, "hood" everywhere below
  *             means the k-neighbourhood (energies, replicas, sums).
- * reserved    must be 0.
+ * volume_depth D >= 1.  1 (default): every slice is its own 2-D image.
+ *             D > 1: every D consecutive slices (n_slices a multiple of D,
+ *             the D slices of equal height and width) are the layers of one
+ *             3-D volume (the paper's future work, Section 6): voxels are
+ *             6-connected (neighbours along x, y and z), a region may span
+ *             layers, its value is the mean of its voxels in storage order,
+ *             and the graph's "slices" are the volumes (S = n_slices / D; the
+ *             per-slice outputs of pmrf_em, pmrf_pll, pmrf_quality are per
+ *             volume).  Region ids are per volume.
  */
 #define PMRF_MAX_HOOD_DEPTH 8
 typedef struct {
     int32_t hood_depth;
-    int32_t reserved;
+    int32_t volume_depth;
 } pmrf_build_options;
 
-/* Fill *opt with the defaults (hood_depth 1).  PMRF_ERR_ARG on NULL. */
+/* Fill *opt with the defaults (hood_depth 1, volume_depth 1).  PMRF_ERR_ARG
+ * on NULL. */
 PMRF_API int pmrf_build_options_default(pmrf_build_options* opt);
 
 /* pmrf_build_graph with options (NULL = the defaults); the same arguments,

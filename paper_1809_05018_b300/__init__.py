@@ -292,11 +292,13 @@ def _flat_ids(region_ids):
     return _need(region_ids, torch.int32, "region_ids").reshape(-1)
 
 
-def build_graph(images, region_ids, stream=None, hood_depth=1) -> Graph:
+def build_graph(images, region_ids, stream=None, hood_depth=1, volume_depth=1) -> Graph:
     """Build the graph of one slice (2-D tensors), a stack (3-D tensors) or a
     list of slices of different sizes (lists of 2-D tensors).  images: CUDA
     float64, region_ids: CUDA int32 of the same shapes; hood_depth: k of the
-    k-neighbourhoods (Section 3.1; 1 in the paper's study)."""
+    k-neighbourhoods (Section 3.1; 1 in the paper's study); volume_depth D > 1:
+    every D consecutive slices are the layers of one 3-D volume (6-connected
+    voxels, region ids per volume), and the graph's slices are the volumes."""
     lib = _lib()
     if isinstance(images, (list, tuple)):
         shapes = [tuple(t.shape) for t in images]
@@ -320,7 +322,7 @@ def build_graph(images, region_ids, stream=None, hood_depth=1) -> Graph:
     H = (ctypes.c_int64 * S)(*hs)
     W = (ctypes.c_int64 * S)(*ws)
     h = ctypes.c_void_p()
-    opt = N.BuildOptions(hood_depth, 0)
+    opt = N.BuildOptions(hood_depth, volume_depth)
     N.check(lib.pmrf_build_graph_ex(_ptr(img), _ptr(ids), S, H, W, ctypes.byref(opt), _stream_ptr(stream),
                                     ctypes.byref(h)), "pmrf_build_graph_ex")
     return Graph(h, hs, ws, img.device)

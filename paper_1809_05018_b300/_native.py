@@ -36,7 +36,7 @@ class Config(ctypes.Structure):
 
 
 class BuildOptions(ctypes.Structure):
-    _fields_ = [("hood_depth", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+    _fields_ = [("hood_depth", ctypes.c_int32), ("volume_depth", ctypes.c_int32)]
 
 
 class Tuning(ctypes.Structure):

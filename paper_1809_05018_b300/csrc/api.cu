@@ -108,7 +108,7 @@ void destroy(pmrf_graph* g) {
     for (cudaEvent_t ev : g->prof_ev) cudaEventDestroy(ev);
     void* ps[] = {g->d_pix_off, g->d_vert_off, g->d_hood_slice_off, g->d_rank_off, g->d_W, g->d_rank, g->d_y,
                   g->d_npix, g->d_adj_off, g->d_adj, g->d_clq_off, g->d_clq, g->d_hood_off, g->d_hood, g->d_row_off,
-                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, g->d_status};
+                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, g->d_status, g->d_layer};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
     delete g;
@@ -164,7 +164,7 @@ int pmrf_memory_usage(int64_t* reserved_bytes, int64_t* used_bytes) {
 int pmrf_build_options_default(pmrf_build_options* opt) {
     if (!opt) return fail(PMRF_ERR_ARG, "opt is NULL");
     opt->hood_depth = 1;
-    opt->reserved = 0;
+    opt->volume_depth = 1;
     return PMRF_OK;
 }
 
@@ -184,24 +184,37 @@ int pmrf_build_graph_ex(const double* d_image, const int32_t* d_region_ids, int3
     if (opt) o = *opt;
     if (o.hood_depth < 1 || o.hood_depth > PMRF_MAX_HOOD_DEPTH)
         return fail(PMRF_ERR_ARG, "hood_depth must be in [1, PMRF_MAX_HOOD_DEPTH]");
-    if (o.reserved != 0) return fail(PMRF_ERR_ARG, "reserved must be 0");
+    if (o.volume_depth < 1) return fail(PMRF_ERR_ARG, "volume_depth must be >= 1");
+    if (n_slices % o.volume_depth != 0) return fail(PMRF_ERR_ARG, "n_slices must be a multiple of volume_depth");
     if (n_slices < 1 || n_slices > 65535) return fail(PMRF_ERR_ARG, "n_slices must be in [1, 65535]");
     if (!h_heights || !h_widths) return fail(PMRF_ERR_ARG, "h_heights / h_widths is NULL");
     pmrf_graph* g = new (std::nothrow) pmrf_graph();
     if (!g) return fail(PMRF_ERR_OOM, "host allocation failed");
-    g->S = n_slices;
+    // the graph's slices are the volumes: D layers stacked row after row
+    const int32_t D = o.volume_depth, S = n_slices / D;
+    g->S = S;
     g->hood_depth = o.hood_depth;
-    g->h_H.assign(h_heights, h_heights + n_slices);
-    g->h_W.assign(h_widths, h_widths + n_slices);
-    g->h_pix_off.assign(n_slices + 1, 0);
+    g->volume_depth = D;
+    g->h_H.assign(S, 0);
+    g->h_W.assign(S, 0);
+    g->h_layer.assign(S, 0);
+    g->h_pix_off.assign(S + 1, 0);
     for (int i = 0; i < n_slices; ++i) {
         if (h_heights[i] < 0 || h_widths[i] < 0) {
             delete g;
             return fail(PMRF_ERR_ARG, "negative slice size");
         }
-        g->h_pix_off[i + 1] = g->h_pix_off[i] + h_heights[i] * h_widths[i];
+        const int v = i / D;
+        if (i % D != 0 && (h_heights[i] != h_heights[i - 1] || h_widths[i] != h_widths[i - 1])) {
+            delete g;
+            return fail(PMRF_ERR_ARG, "the layers of a volume must have equal sizes");
+        }
+        g->h_layer[v] = h_heights[i];
+        g->h_W[v] = h_widths[i];
+        g->h_H[v] += h_heights[i];
     }
-    g->n_pix = g->h_pix_off[n_slices];
+    for (int v = 0; v < S; ++v) g->h_pix_off[v + 1] = g->h_pix_off[v] + g->h_H[v] * g->h_W[v];
+    g->n_pix = g->h_pix_off[S];
     if (g->n_pix >= 4294967295ll) {
         delete g;
         return fail(PMRF_ERR_UNSUPPORTED, "more than 2^32-1 pixels in one batch");

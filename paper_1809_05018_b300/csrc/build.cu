@@ -304,7 +304,8 @@ __global__ void k_means(const double* __restrict__ img, const uint32_t* __restri
 
 template <bool FILL>
 __global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
-                             const int64_t* __restrict__ Wd, const int64_t* __restrict__ rank_off,
+                             const int64_t* __restrict__ Wd, const int64_t* __restrict__ layer_rows,
+                             const int64_t* __restrict__ rank_off,
                              const int32_t* __restrict__ rank, const int32_t* __restrict__ only,
                              int32_t* __restrict__ cnt, const int64_t* __restrict__ cand_off,
                              int32_t* __restrict__ cursor, uint32_t* __restrict__ cand) {
@@ -312,11 +313,15 @@ __global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __r
     const int64_t b = pix_off[s], e = pix_off[s + 1], rb = rank_off[s], W = Wd[s];
     if (W <= 0) return;
     const int64_t H = (e - b) / W;
+    // a 3-D volume is its layers' rows one after another: rows r and r+1 are
+    // neighbours inside a layer only, rows r and r+Hl (the next layer) are
+    // z-neighbours
+    const int64_t Hl = layer_rows ? layer_rows[s] : H;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < e - b; q += (int64_t)gridDim.x * blockDim.x) {
         const int64_t r = q / W, c = q - r * W;
         const int64_t p = b + q;
         const int32_t a = vertex_of(ids, rank, rb, p);
-        int32_t pa[2], pb[2];
+        int32_t pa[3], pb[3];
         int np = 0;
         if (c + 1 < W) {
             const int32_t bb = vertex_of(ids, rank, rb, p + 1);
@@ -325,10 +330,18 @@ __global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __r
                 if (!dup) { pa[np] = a; pb[np] = bb; ++np; }
             }
         }
-        if (r + 1 < H) {
+        if (r + 1 < H && (r + 1) % Hl != 0) {
             const int32_t bb = vertex_of(ids, rank, rb, p + W);
             if (a != bb) {
                 bool dup = (c > 0) && vertex_of(ids, rank, rb, p - 1) == a && vertex_of(ids, rank, rb, p + W - 1) == bb;
+                if (!dup) { pa[np] = a; pb[np] = bb; ++np; }
+            }
+        }
+        if (Hl < H && r + Hl < H) {
+            const int32_t bb = vertex_of(ids, rank, rb, p + Hl * W);
+            if (a != bb) {
+                bool dup = (c > 0) && vertex_of(ids, rank, rb, p - 1) == a &&
+                           vertex_of(ids, rank, rb, p + Hl * W - 1) == bb;
                 if (!dup) { pa[np] = a; pb[np] = bb; ++np; }
             }
         }
@@ -715,6 +728,11 @@ __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t*
     }
 }
 
+__global__ void k_flag_all(int32_t* __restrict__ f, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) f[i] = 1;
+}
+
 // ---------------------------------------------------------------------------
 // k-neighbourhoods (Section 3.1: the vertices within k edges of a clique's
 // members).  Level j+1 of a hood is the union of the closed neighbourhoods of
@@ -1001,6 +1019,10 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(dalloc(&g->d_W, S, s));
     PMRF_CUDA(cudaMemcpyAsync(g->d_pix_off, g->h_pix_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
     PMRF_CUDA(cudaMemcpyAsync(g->d_W, g->h_W.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, s));
+    if (g->volume_depth > 1) {
+        PMRF_TRY(dalloc(&g->d_layer, S, s));
+        PMRF_CUDA(cudaMemcpyAsync(g->d_layer, g->h_layer.data(), sizeof(int64_t) * S, cudaMemcpyHostToDevice, s));
+    }
     const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(maxpix, PIX_THREADS * 4), 65535));
     const dim3 pgrid(gx, (unsigned)S);
 
@@ -1081,6 +1103,10 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y);
     }
 
+    // a volume's z-neighbours lie outside the bounding-box scan: every region
+    // of a 3-D volume takes the pixel-pair path below
+    if (g->volume_depth > 1) LAUNCH_1D(k_flag_all, V, d_fbadj, V);
+
     // 4. adjacency: the scans' neighbour lists, and for the flagged regions the
     //    4-connected pixel pairs they take part in, sorted and de-duplicated
     int64_t* d_cand_off = nullptr;
@@ -1093,7 +1119,8 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         int32_t* d_cnt = nullptr;
         PMRF_TRY(tmp.get(&d_cnt, V));
         PMRF_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-        k_edge_pairs<false><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank,
+        k_edge_pairs<false><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_layer, g->d_rank_off,
+                                                         g->d_rank,
                                                          d_fbadj, d_cnt, nullptr, nullptr, nullptr);
         ::pmrf::note_launch(1);
         PMRF_CUDA(cudaGetLastError());
@@ -1102,7 +1129,8 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         PMRF_TRY(read_i64(d_cand_off + V, &ncand, s));
         PMRF_TRY(tmp.get(&d_cand, ncand));
         PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
-        k_edge_pairs<true><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_rank_off, g->d_rank,
+        k_edge_pairs<true><<<pgrid, PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, g->d_W, g->d_layer, g->d_rank_off,
+                                                        g->d_rank,
                                                         d_fbadj, nullptr, d_cand_off, d_cursor, d_cand);
         ::pmrf::note_launch(1);
         PMRF_CUDA(cudaGetLastError());

@@ -55,13 +55,16 @@ struct pmrf_graph {
     int device = 0;
     int32_t S = 0;
     int64_t V = 0, E2 = 0, C = 0, n_clq = 0, N_el = 0, n_rank = 0, n_pix = 0;
-    int32_t hood_depth = 1;  // k of the k-neighbourhoods (Section 3.1)
+    int32_t hood_depth = 1;    // k of the k-neighbourhoods (Section 3.1)
+    int32_t volume_depth = 1;  // layers per 3-D volume (1: 2-D slices)
     int64_t n_row_words = 0, n_rep_words = 0;
     int32_t max_deg = 0, max_hood = 0;
 
     std::vector<int64_t> h_H, h_W, h_pix_off, h_vert_off, h_hood_slice_off, h_el_slice_off, h_rank_off;
+    std::vector<int64_t> h_layer;  // rows per layer of each volume (= h_H for 2-D slices)
 
     int64_t* d_pix_off = nullptr;        // [S+1]
+    int64_t* d_layer = nullptr;          // [S] rows per layer (3-D volumes only; NULL for slices)
     int64_t* d_vert_off = nullptr;       // [S+1]
     int64_t* d_hood_slice_off = nullptr; // [S+1]
     int64_t* d_rank_off = nullptr;       // [S+1]
