@@ -90,7 +90,45 @@ def parse():
     ap.add_argument("--cpu-slices", type=int, default=2, help="slices the oracle baseline runs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    # the scope table's NEXT rows, measured on the same workload (default: the paper's form)
+    ap.add_argument("--hood-depth", type=int, default=1, help="k of the k-neighbourhoods")
+    ap.add_argument("--potts-scope", type=int, default=0, choices=[0, 1], help="0 hood, 1 full neighbourhood")
+    ap.add_argument("--replica-rule", type=int, default=0, choices=[0, 1, 2], help="0 min, 1 mean energy, 2 vote")
+    ap.add_argument("--volume-depth", type=int, default=1, help="layers per 3-D volume (1: 2-D slices)")
+    ap.add_argument("--slab", type=int, default=4, help="layers of a volume sharing one slice's partition")
     return ap.parse_args()
+
+
+def variant(a):
+    """The non-default build and sweep choices of this run (empty: the paper's form)."""
+    v = {}
+    if a.hood_depth != 1:
+        v["hood_depth"] = a.hood_depth
+    if a.potts_scope:
+        v["potts_scope"] = a.potts_scope
+    if a.replica_rule:
+        v["replica_rule"] = a.replica_rule
+    if a.volume_depth > 1:
+        v.update(volume_depth=a.volume_depth, slab=a.slab)
+    return v
+
+
+def volumize(img, ids, D, t):
+    """Stack the slices into volumes of D layers: layers of a slab of t share
+    the partition and intensities of the slab's first slice, ids offset per
+    slab (regions are prisms t layers tall; neighbouring slabs' partitions
+    differ, so regions touch several others across the slab boundary)."""
+    S = img.shape[0]
+    if S % D:
+        raise SystemExit(f"--volume-depth {D} must divide the {S} slices")
+    off = int(ids.max()) + 1
+    img2, ids2 = np.empty_like(img), np.empty_like(ids)
+    for v in range(S // D):
+        for z in range(D):
+            src = v * D + (z // t) * t
+            img2[v * D + z] = img[src]
+            ids2[v * D + z] = ids[src] + (z // t) * off
+    return img2, ids2
 
 
 def dist_env():
@@ -235,10 +273,15 @@ def run_ours(a):
     wl = shard_workload(a.workload, a.slices, rank)
     t0 = time.time()
     sl, img_np, ids_np = host_inputs(wl)
+    D = a.volume_depth
+    if D > 1:
+        img_np, ids_np = volumize(img_np, ids_np, D, a.slab)
     gen_s = time.time() - t0
     S = img_np.shape[0]
     L, beta = wl.n_labels, wl.beta
-    cfg = pmrf.EMConfig(n_labels=L, beta=beta, max_iters=wl.max_iters)
+    cfg = pmrf.EMConfig(n_labels=L, beta=beta, max_iters=wl.max_iters, potts_scope=a.potts_scope,
+                        replica_rule=a.replica_rule)
+    bopt = dict(hood_depth=a.hood_depth, volume_depth=D)
     img_h = torch.from_numpy(img_np).pin_memory()
     ids_h = torch.from_numpy(ids_np).pin_memory()
     img_d = img_h.cuda()
@@ -246,7 +289,7 @@ def run_ours(a):
     ones = torch.ones(S, dtype=torch.float64, device="cuda")
 
     def step(img, ids):
-        g = pmrf.build_graph(img, ids)
+        g = pmrf.build_graph(img, ids, **bopt)
         out = g.em(cfg)
         seg = g.label_image(ids, out["labels"])
         mu = out["params"][:, :, 1].contiguous()
@@ -317,7 +360,16 @@ def run_ours(a):
     ones1 = ones[:1]
 
     def step1(k):
-        g1 = pmrf.build_graph(img_d[k], ids_d[k])
+        if D > 1:  # one volume per call
+            g1 = pmrf.build_graph(img_d[k * D:(k + 1) * D], ids_d[k * D:(k + 1) * D], **bopt)
+            o1 = g1.em(cfg)
+            g1.label_image(ids_d[k * D:(k + 1) * D], o1["labels"])
+            mu1 = o1["params"][:, :, 1].contiguous()
+            sg1 = o1["params"][:, :, 2].contiguous()
+            g1.pll(L, o1["labels"], mu1, sg1, beta)
+            g1.pll_grad(L, o1["labels"], mu1, sg1, beta, ones1)
+            return
+        g1 = pmrf.build_graph(img_d[k], ids_d[k], **bopt)
         o1 = g1.em(cfg)
         g1.label_image(ids_d[k], o1["labels"])
         mu1 = o1["params"][:, :, 1].contiguous()
@@ -325,15 +377,16 @@ def run_ours(a):
         g1.pll(L, o1["labels"], mu1, sg1, beta)
         g1.pll_grad(L, o1["labels"], mu1, sg1, beta, ones1)
 
-    for k in range(min(2, ps)):  # warm the per-slice path
+    units = ps if D == 1 else max(1, ps // D)  # slices, or volumes of D slices
+    for k in range(min(2, units)):  # warm the per-slice path
         step1(k)
     torch.cuda.synchronize()
     p0.record()
-    for k in range(ps):
+    for k in range(units):
         step1(k)
     p1.record()
     torch.cuda.synchronize()
-    plain = ps / (p0.elapsed_time(p1) / 1e3)
+    plain = units * D / (p0.elapsed_time(p1) / 1e3)
 
     # ---- end to end: host buffers in, label image out, copies inside the timed region
     e2e = None
@@ -363,7 +416,10 @@ def run_ours(a):
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu:
-        cpu = cpu_baseline(sl[:a.cpu_slices], wl)
+        if D > 1:
+            cpu = cpu_baseline_volume(img_np[:D], ids_np[:D], wl, a)
+        else:
+            cpu = cpu_baseline(sl[:a.cpu_slices], wl, a)
 
     if rank == 0:
         line = {
@@ -374,7 +430,8 @@ def run_ours(a):
             "config": {"workload": wl.name, "slices_per_gpu": S, "height": int(img_np.shape[1]),
                        "width": int(img_np.shape[2]), "n_labels": L, "beta": beta, "max_iters": wl.max_iters,
                        "V": st["V"], "E": st["E"], "C": st["C"], "N_el": st["N_el"],
-                       "l2_policy": "inputs larger than L2 (6.4 GB per step)", "parallelism": f"replicas{world}"},
+                       "l2_policy": "inputs larger than L2 (6.4 GB per step)", "parallelism": f"replicas{world}",
+                       **({"variant": variant(a)} if variant(a) else {})},
             "energy_evals_per_s": round(evals / (em_ms / 1e3), 1),
             "em_ms": round(em_ms, 3), "em_slices_per_s": round(S / (em_ms / 1e3), 3),
             "plain_slices_per_s": round(plain, 3), "plain_sample": ps,
@@ -393,13 +450,15 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def cpu_baseline(slices, wl):
+def cpu_baseline(slices, wl, a=None):
     """The oracle as it stands (serial C), full per-slice pipeline."""
     import oracle
-    cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters)
+    k = a.hood_depth if a else 1
+    cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters,
+                          potts_scope=a.potts_scope if a else 0, replica_rule=a.replica_rule if a else 0)
     t0 = time.perf_counter()
     for s in slices:
-        g = oracle.Graph.from_image(s.image, s.region_ids)
+        g = oracle.Graph.from_image(s.image, s.region_ids, hood_depth=k)
         r = g.em(cfg)
         g.label_image(s.region_ids, r["labels"])
         g.pll(wl.n_labels, r["labels"], r["theta"][:, 1], r["theta"][:, 2], wl.beta)
@@ -407,6 +466,23 @@ def cpu_baseline(slices, wl):
     return {"value": round(len(slices) / dt, 4), "unit": "slices/s", "cores": 1, "kind": "oracle",
             "sample": f"{len(slices)} slices of {wl.name} ({slices[0].image.shape[0]}x{slices[0].image.shape[1]}), "
                       f"serial C oracle: graph, cliques, hoods, EM, label image, PLL"}
+
+
+def cpu_baseline_volume(img, ids, wl, a):
+    """The oracle on one volume of the run (serial C, full pipeline)."""
+    import oracle
+    cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters, potts_scope=a.potts_scope,
+                          replica_rule=a.replica_rule)
+    t0 = time.perf_counter()
+    g = oracle.Graph.from_volume(img, ids, hood_depth=a.hood_depth)
+    r = g.em(cfg)
+    g.label_image(ids.reshape(-1, ids.shape[-1]), r["labels"])
+    g.pll(wl.n_labels, r["labels"], r["theta"][:, 1], r["theta"][:, 2], wl.beta)
+    dt = time.perf_counter() - t0
+    D = img.shape[0]
+    return {"value": round(D / dt, 4), "unit": "slices/s", "cores": 1, "kind": "oracle",
+            "sample": f"one volume of {D} layers of {img.shape[1]}x{img.shape[2]}, serial C oracle: graph, "
+                      f"cliques, hoods, EM, label image, PLL"}
 
 
 def run_reference(a):

@@ -870,7 +870,7 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
         el_slot[e] = sbits;
         return;
     }
-    hood_gen[c] = 1;  // the hood needs the general path of the hood pass
+    if (d > 32 || k > HOOD_FAST_MAX) hood_gen[c] = 1;  // the hood needs the general path of the hood pass
     uint32_t rcur = 0, scur = 0;
     int64_t rwi = 0, swi = 0;
     int64_t a = 0, j = 0;

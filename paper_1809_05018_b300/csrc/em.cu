@@ -723,10 +723,11 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
         const int64_t e0 = g.hood_off[c0];
         const int ne = (int)(g.hood_off[c1] - e0);
         // fast tile (flag set when the tile table was built): the elements fit,
-        // every hood has <= 32 members and every element's vertex degree <= 32
+        // every hood has <= HOOD_FAST_MAX members and every element's vertex
+        // degree <= 32
         const bool fast = tile.pad != 0 && ne <= HT_CAP;
         if (fast) {
-            // every element's vertex has degree <= 32 and every hood <= 32
+            // every element's vertex has degree <= 32 and every hood <= 64
             // members: the counts of each label among v's neighbours inside
             // hood c are popcounts of the element's slot mask against the
             // vertex's label masks.  The tile's member ids and slot masks are
@@ -739,8 +740,8 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
             __syncthreads();
             for (int64_t c = c0 + threadIdx.x; c < c1; c += HT_THREADS) {
                 const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
-                // S_c = sum of D_min (exact) + sum of the excesses (<= 32
-                // elements of <= 32 beta_q each: no overflow)
+                // S_c = sum of D_min (exact) + sum of the excesses (<= 64
+                // elements of <= 32 beta_q each, below 2^62: no overflow)
                 __int128 sdD = 0;
                 int64_t sdR = 0;
                 if constexpr (L == 2) {
@@ -1044,8 +1045,8 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
     int64_t c0 = lower_bound_dev<int64_t>(hood_off, cs, ce, lo);
     int64_t c1 = lower_bound_dev<int64_t>(hood_off, cs, ce, hi);
     if (j == ht_first[s + 1] - ht_first[s] - 1) c1 = ce;
-    // fast when the elements fit in shared memory, every hood has <= 32
-    // members and every element's vertex has degree <= 32 (the build flags
+    // fast when the elements fit in shared memory, every hood has <=
+    // HOOD_FAST_MAX members and every element's vertex has degree <= 32 (the build flags
     // the hoods that do not)
     const int64_t e0 = hood_off[c0], e1 = hood_off[c1];
     bool fast = (e1 - e0) <= HT_CAP;
@@ -1210,8 +1211,8 @@ RunCfg to_run(const pmrf_config* c) {
     r.init_lo = c->init_lo;
     r.init_hi = c->init_hi;
     // units 2^-hq of the hood pass's label excesses: beta_q = beta * 2^hq stays
-    // below 2^51, so a fast hood's 32 elements of <= 32 beta_q each sum below
-    // 2^61 (beta < 2^e with frexp's exponent e)
+    // below 2^51, so a fast hood's <= 64 elements of <= 32 beta_q each sum
+    // below 2^62 (beta < 2^e with frexp's exponent e)
     int e = 0;
     if (r.beta > 0.0) std::frexp(r.beta, &e);
     r.hq = std::max(0, std::min(51, 51 - e));

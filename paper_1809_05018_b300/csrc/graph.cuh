@@ -7,6 +7,10 @@
 
 #include "common.cuh"
 
+// largest hood the hood pass takes on its fast path (every member of degree
+// <= 32): 64 elements of excess at most 32 beta_q (< 2^56) sum below 2^62
+constexpr int HOOD_FAST_MAX = 64;
+
 namespace pmrf {
 
 // Per-tile descriptor of the persistent EM launch.  kind 0 = hood tile (hoods
@@ -84,7 +88,7 @@ struct pmrf_graph {
     int64_t* d_rep_woff = nullptr;       // [V+1] word offsets of replica slot masks
     uint32_t* d_rep_mask = nullptr;      // [n_rep_words]
     uint32_t* d_el_slot = nullptr;       // [N_el] slot mask of each hood element (degree <= 32), hood-major
-    uint8_t* d_hood_gen = nullptr;       // [C] 1: the hood has > 32 members or a member of degree > 32
+    uint8_t* d_hood_gen = nullptr;       // [C] 1: the hood has > HOOD_FAST_MAX members or a member of degree > 32
     pmrf::DevStatus* d_status = nullptr;
 
     pmrf_tuning tuning{0, 0, 0, 1, 0};
