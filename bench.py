@@ -5,7 +5,7 @@ One step = the whole path on one batch of synthetic slices: region graph +
 maximal cliques + hoods + replica structures (pmrf_build_graph), the EM loop
 (pmrf_em: MAP sweeps, replica reduction, parameter update, convergence tests),
 the label image (pmrf_label_image) and one pseudo-log-likelihood value plus its
-adjoint at the final labels (pmrf_pll, pmrf_pll_grad).
+adjoint at the final labels (pmrf_pll_value_and_grad: both in one pass).
 
 Default workload: stack512 -- 512 slices of 1024x1024, per-slice seed and
 Voronoi pitch U[4,10] (10k-65k regions each), 2 labels, beta 1, <= 50 EM
@@ -294,8 +294,8 @@ def run_ours(a):
         seg = g.label_image(ids, out["labels"])
         mu = out["params"][:, :, 1].contiguous()
         sg = out["params"][:, :, 2].contiguous()
-        pll = g.pll(L, out["labels"], mu, sg, beta)
-        gm, gs, gb = g.pll_grad(L, out["labels"], mu, sg, beta, ones[:g.S])
+        # the pseudo-log-likelihood and its adjoint in one pass
+        pll, gm, gs, gb = g.pll_value_and_grad(L, out["labels"], mu, sg, beta, ones[:g.S])
         return g, out, seg, pll
 
     for _ in range(a.warmup):
@@ -366,16 +366,14 @@ def run_ours(a):
             g1.label_image(ids_d[k * D:(k + 1) * D], o1["labels"])
             mu1 = o1["params"][:, :, 1].contiguous()
             sg1 = o1["params"][:, :, 2].contiguous()
-            g1.pll(L, o1["labels"], mu1, sg1, beta)
-            g1.pll_grad(L, o1["labels"], mu1, sg1, beta, ones1)
+            g1.pll_value_and_grad(L, o1["labels"], mu1, sg1, beta, ones1)
             return
         g1 = pmrf.build_graph(img_d[k], ids_d[k], **bopt)
         o1 = g1.em(cfg)
         g1.label_image(ids_d[k], o1["labels"])
         mu1 = o1["params"][:, :, 1].contiguous()
         sg1 = o1["params"][:, :, 2].contiguous()
-        g1.pll(L, o1["labels"], mu1, sg1, beta)
-        g1.pll_grad(L, o1["labels"], mu1, sg1, beta, ones1)
+        g1.pll_value_and_grad(L, o1["labels"], mu1, sg1, beta, ones1)
 
     units = ps if D == 1 else max(1, ps // D)  # slices, or volumes of D slices
     for k in range(min(2, units)):  # warm the per-slice path

@@ -358,6 +358,16 @@ PMRF_API int pmrf_pll_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_lab
                   double* d_gbeta, pmrf_stream_t stream);
 
 /*
+ * pmrf_pll and pmrf_pll_grad in one pass over the vertices (the value is a
+ * by-product of the adjoint's softmax): d_pll as pmrf_pll, the gradients as
+ * pmrf_pll_grad, bit-identical to the two separate calls.  d_gout must not be
+ * NULL; d_pll and the gradient outputs may be.
+ */
+PMRF_API int pmrf_pll_value_and_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu,
+                                     const double* d_sigma, double beta, const double* d_gout, double* d_pll,
+                                     double* d_gmu, double* d_gsigma, double* d_gbeta, pmrf_stream_t stream);
+
+/*
  * Allocation-free variant of pmrf_pll_grad; the paper has no counterpart.
  * Same inputs, outputs and results as pmrf_pll_grad, but it allocates no
  * memory: no cudaMalloc, no stream-ordered allocation, no host allocation on

@@ -286,6 +286,22 @@ class Graph:
         return gmu, gsg, gb
 
 
+    def pll_value_and_grad(self, n_labels, labels, mu, sigma, beta, gout):
+        """pll() and pll_grad() in one pass: (pll [S], gmu, gsigma, gbeta)."""
+        _need(labels, torch.uint8, "labels", self.V)
+        _need(mu, torch.float64, "mu", self.S * n_labels)
+        _need(sigma, torch.float64, "sigma", self.S * n_labels)
+        _need(gout, torch.float64, "gout", self.S)
+        pll = torch.empty(self.S, dtype=torch.float64, device=self.device)
+        gmu = torch.empty((self.S, n_labels), dtype=torch.float64, device=self.device)
+        gsg = torch.empty((self.S, n_labels), dtype=torch.float64, device=self.device)
+        gb = torch.empty(1, dtype=torch.float64, device=self.device)
+        N.check(_lib().pmrf_pll_value_and_grad(self._handle(), n_labels, _ptr(labels), _ptr(mu), _ptr(sigma),
+                                               float(beta), _ptr(gout), _ptr(pll), _ptr(gmu), _ptr(gsg), _ptr(gb),
+                                               _stream_ptr()), "pmrf_pll_value_and_grad")
+        return pll, gmu, gsg, gb
+
+
 def _flat_ids(region_ids):
     if isinstance(region_ids, (list, tuple)):
         return torch.cat([_need(r, torch.int32, "region_ids").reshape(-1) for r in region_ids])

@@ -63,6 +63,7 @@ SIGNATURES = {
     "pmrf_em": [_GP, ctypes.POINTER(Config), _P, _P, _P, _P, _P, _P],
     "pmrf_pll": [_GP, _I32, _P, _P, _P, _D, _P, _P],
     "pmrf_pll_grad": [_GP, _I32, _P, _P, _P, _D, _P, _P, _P, _P, _P],
+    "pmrf_pll_value_and_grad": [_GP, _I32, _P, _P, _P, _D, _P, _P, _P, _P, _P, _P],
     "pmrf_pll_grad_noalloc": [_GP, _I32, _P, _P, _P, _D, _P, _P, _P, _P, _P],
     "pmrf_label_image": [_GP, _P, _P, _P, _P],
     "pmrf_quality": [_GP, ctypes.c_int32, _P, _P, _P, _P, _P],

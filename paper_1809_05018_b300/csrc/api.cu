@@ -376,6 +376,17 @@ int pmrf_pll_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, cons
                    (cudaStream_t)stream);
 }
 
+int pmrf_pll_value_and_grad(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu,
+                            const double* d_sigma, double beta, const double* d_gout, double* d_pll, double* d_gmu,
+                            double* d_gsigma, double* d_gbeta, pmrf_stream_t stream) {
+    g_last_error.clear();
+    if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
+    if (!d_gout) return fail(PMRF_ERR_ARG, "d_gout is NULL");
+    PMRF_TRY(check_device(g));
+    return pll_run(g, n_labels, d_labels, d_mu, d_sigma, beta, d_pll, d_gout, d_gmu, d_gsigma, d_gbeta,
+                   (cudaStream_t)stream);
+}
+
 int pmrf_pll_grad_noalloc(pmrf_graph* g, int32_t n_labels, const uint8_t* d_labels, const double* d_mu,
                           const double* d_sigma, double beta, const double* d_gout, double* d_gmu, double* d_gsigma,
                           double* d_gbeta, pmrf_stream_t stream) {

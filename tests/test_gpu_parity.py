@@ -395,3 +395,22 @@ def test_em_conditional_graph_equals_unrolled():
     cut = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=T)
     _, nu = run(cut, profile=1)
     assert nc == nu + T + 1
+
+
+def test_pll_value_and_grad_equals_separate_calls():
+    """The fused value-and-adjoint call gives bit for bit what pll() and
+    pll_grad() give."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(4, seed0=990))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    for L in (2, 3):
+        out = g.em(pmrf.EMConfig(n_labels=L, beta=1.0, max_iters=15))
+        mu = out["params"][:, :, 1].contiguous()
+        sg = out["params"][:, :, 2].contiguous()
+        gout = torch.linspace(0.5, 2.0, g.S, dtype=torch.float64, device="cuda")
+        p1 = g.pll(L, out["labels"], mu, sg, 0.8)
+        gm1, gs1, gb1 = g.pll_grad(L, out["labels"], mu, sg, 0.8, gout)
+        p2, gm2, gs2, gb2 = g.pll_value_and_grad(L, out["labels"], mu, sg, 0.8, gout)
+        for a, b in ((p1, p2), (gm1, gm2), (gs1, gs2), (gb1, gb2)):
+            assert torch.equal(a, b)
