@@ -603,6 +603,9 @@ struct VRec {
     uint32_t lmv[L];  // lmv[L-1] unused
 };
 
+// The records are gathered (one 32-byte record per element) without
+// allocating L1 lines: a tile's records are spread over many lines that are
+// rarely reused before eviction (measured 2 % faster on the two-label stack)
 template <int L>
 __device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, int64_t v) {
     constexpr int NW = vrec_words(L);
@@ -610,7 +613,7 @@ __device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, 
     const uint64_t* p = vrec + v * NW;
 #pragma unroll
     for (int k = 0; k < NW; k += 4)
-        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+        asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
             : "=l"(w[k]), "=l"(w[k + 1]), "=l"(w[k + 2]), "=l"(w[k + 3])
             : "l"(p + k));
     VRec<L> R;
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
 #pragma unroll 2
                     for (int i = b; i < e; ++i) {
                         uint64_t w0, w1, w2, w3;
-                        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                        asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
                             : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
                             : "l"(vrec + (int64_t)s_v[i] * 4));
                         sdD += (__int128)(((unsigned __int128)w1 << 64) | w0);
