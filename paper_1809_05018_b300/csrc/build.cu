@@ -178,22 +178,32 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
     const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv, const int4* __restrict__ bbox_raw,
     const int32_t* __restrict__ npix_raw, int64_t V, double* __restrict__ y, int32_t* __restrict__ npix,
     int32_t* __restrict__ fb_pix, int32_t* __restrict__ fb_adj, int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    const int s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
-    const int32_t id = inv[v];
-    const int64_t slot = rank_off[s] + id;
-    const int4 bb = bbox_raw[slot];
-    const int64_t n = npix_raw[slot];
-    npix[v] = (int32_t)n;
-    const int64_t area = (int64_t)(bb.y - bb.x + 1) * (int64_t)(bb.w - bb.z + 1);
-    if (area > 4 * n + 64) {
-        fb_pix[v] = (int32_t)n;
-        fb_adj[v] = 1;
-        deg[v] = 0;
-        return;
+    const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    // every lane reaches the ballot below (the warp's row range is shared)
+    bool scan = false;
+    int s = 0;
+    int32_t id = 0;
+    int4 bb = make_int4(0, -1, 0, -1);
+    int64_t n = 0;
+    if (v < V) {
+        s = (int)(upper_bound_dev<int64_t>(vert_off, 0, S + 1, v) - 1);
+        id = inv[v];
+        const int64_t slot = rank_off[s] + id;
+        bb = bbox_raw[slot];
+        n = npix_raw[slot];
+        npix[v] = (int32_t)n;
+        const int64_t area = (int64_t)(bb.y - bb.x + 1) * (int64_t)(bb.w - bb.z + 1);
+        if (area > 4 * n + 64) {
+            fb_pix[v] = (int32_t)n;
+            fb_adj[v] = 1;
+            deg[v] = 0;
+        } else {
+            fb_pix[v] = 0;
+            scan = true;
+        }
     }
-    fb_pix[v] = 0;
+    const unsigned lanes = __ballot_sync(0xffffffffu, scan);
+    if (!scan) return;
     const int64_t b = pix_off[s], W = Wd[s];
     const int H = (int)((pix_off[s + 1] - b) / W);
     int32_t buf[NB_BUF];
@@ -202,7 +212,15 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
     double acc = 0.0;
     const int r0 = bb.x > 0 ? bb.x - 1 : 0, c0 = bb.z > 0 ? bb.z - 1 : 0;
     const int w = (int)W;
-    for (int r = r0; r <= bb.y; ++r) {
+    // The warp's regions are consecutive ids: neighbours along a seed row of
+    // the oversegmentation, their boxes side by side.  The lanes step through
+    // the rows of the warp's joint row range together, each working on its own
+    // box's part of the row, so a row's loads of the warp fall on a few
+    // neighbouring cache lines; a lane's own rows still come in order.
+    const int rlo = (int)__reduce_min_sync(lanes, (unsigned)r0);
+    const int rhi = (int)__reduce_max_sync(lanes, (unsigned)bb.y);
+    for (int r = rlo; r <= rhi; ++r) {
+        if (r < r0 || r > bb.y) continue;
         const int32_t* irow = ids + b + (int64_t)r * W;
         const double* vrow = img + b + (int64_t)r * W;
         const bool down = r + 1 < H;
