@@ -432,8 +432,9 @@ PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* deta
 
 /* Tile sizes of the EM launches.  0 selects the autotuned / default value.
  * hood_tile: hood elements per tile window (multiple of 32, 128..1248; a tile
- * holds the hoods starting in its window, at most hood_tile + 31 elements when
- * every hood has <= 32 members, default 1024);
+ * holds the hoods starting in its window and takes the fast path when they
+ * fit 1279 elements, every hood has <= 64 members and every member <= 32
+ * neighbours; default 1024);
  * vert_tile: vertices per tile (multiple of 32, 32..4096); ctas_per_sm: 1..8. */
 typedef struct {
     int32_t hood_tile;
@@ -456,8 +457,9 @@ PMRF_API int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t);
 PMRF_API int pmrf_em_kernel_times(pmrf_graph* g, int32_t max_n, float* ms_vertex, float* ms_hood, int32_t* n,
                                   pmrf_stream_t stream);
 
-/* Time candidate tunings on this graph with `cfg` (runs EM several times;
- * synchronises `stream`) and keep the fastest.  *best may be NULL. */
+/* Time candidate tunings on this graph with `cfg` (hood_tile 512, 768, 1024
+ * and 1248; runs EM several times; synchronises `stream`) and keep the
+ * fastest.  *best may be NULL. */
 PMRF_API int pmrf_autotune(pmrf_graph* g, const pmrf_config* cfg, pmrf_stream_t stream, pmrf_tuning* best);
 
 #ifdef __cplusplus

@@ -705,7 +705,7 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
                                                      const uint64_t* __restrict__ vrec, int64_t* __restrict__ hist,
-                                                     double* __restrict__ S_out, double* __restrict__ hpart) {
+                                                     double* __restrict__ S_out, int64_t* __restrict__ hpart) {
     __shared__ int32_t s_v[HT_CAP];
     __shared__ uint32_t s_sm[HT_CAP];
     __shared__ __int128 s_wsum[HT_THREADS / 32];
@@ -850,8 +850,9 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
     if (threadIdx.x == 0) {
         __int128 a = 0;
         for (int w = 0; w < HT_THREADS / 32; ++w) a += s_wsum[w];
-        hpart[(int64_t)tile.part * 2 + 0] = unfix80(a);
-        hpart[(int64_t)tile.part * 2 + 1] = (double)s_unconv;
+        hpart[(int64_t)tile.part * 3 + 0] = (int64_t)(uint64_t)(unsigned __int128)a;
+        hpart[(int64_t)tile.part * 3 + 1] = (int64_t)(a >> 64);
+        hpart[(int64_t)tile.part * 3 + 2] = s_unconv;
     }
 }
 
@@ -861,14 +862,16 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
 template <int L>
 __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict__ cfgp,
                            const int64_t* __restrict__ vt0, const int64_t* __restrict__ ht0,
-                           const double* __restrict__ vpart, const double* __restrict__ hpart,
+                           const double* __restrict__ vpart, const int64_t* __restrict__ hpart,
                            const double* __restrict__ theta_prev, double* __restrict__ theta,
                            const int64_t* __restrict__ vert_off, int32_t* __restrict__ active,
                            int32_t* __restrict__ iters, int32_t* __restrict__ conv, double* __restrict__ Thist,
                            int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op,
                            double* __restrict__ dterm) {
-    constexpr int NQ = 4 * L + 2;  // label moments, T, unconverged hoods
+    constexpr int NQ = 4 * L;  // label moments
     __shared__ double s_q[FIN_THREADS / 32][NQ];
+    __shared__ __int128 s_T[FIN_THREADS / 32];
+    __shared__ int64_t s_u[FIN_THREADS / 32];
     const int s = blockIdx.x;
     if (s >= S) return;
     const RunCfg cf = *cfgp;
@@ -883,17 +886,28 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
 #pragma unroll
         for (int k = 0; k < 4 * L; ++k) tot[k] += vpart[p * 4 * L + k];
     }
+    // T: the exact sum of the tiles' exact partials (integers: independent
+    // of the tiling and of the order), rounded once
+    __int128 Tacc = 0;
+    int64_t uacc = 0;
     if (em) {
         for (int64_t p = ht0[s] + threadIdx.x; p < ht0[s + 1]; p += FIN_THREADS) {
-            tot[4 * L + 0] += hpart[p * 2 + 0];
-            tot[4 * L + 1] += hpart[p * 2 + 1];
+            Tacc += (__int128)(((unsigned __int128)(uint64_t)hpart[p * 3 + 1] << 64) | (uint64_t)hpart[p * 3 + 0]);
+            uacc += hpart[p * 3 + 2];
         }
     }
 #pragma unroll
     for (int k = 0; k < NQ; ++k) tot[k] = warp_sum(tot[k]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        Tacc += shfl_xor_i128(Tacc, o);
+        uacc += __shfl_xor_sync(0xffffffffu, uacc, o);
+    }
     if (lane_id() == 0) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) s_q[warp_id()][k] = tot[k];
+        s_T[warp_id()] = Tacc;
+        s_u[warp_id()] = uacc;
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
@@ -903,7 +917,13 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
         for (int w = 0; w < FIN_THREADS / 32; ++w) a += s_q[w][k];
         tot[k] = a;
     }
-    const double Tsum = tot[4 * L + 0], unconv = tot[4 * L + 1];
+    Tacc = 0;
+    uacc = 0;
+    for (int w = 0; w < FIN_THREADS / 32; ++w) {
+        Tacc += s_T[w];
+        uacc += s_u[w];
+    }
+    const double Tsum = unfix80(Tacc), unconv = (double)uacc;
     for (int l = 0; l < L; ++l) {
         const double n = tot[4 * l + 0];
         double* th = theta + ((int64_t)s * L + l) * 4;
@@ -1246,7 +1266,7 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) 
     if (!rc2) rc2 = dalloc(&w.d_x[1], g->V, s);
     if (!rc2) rc2 = dalloc(&w.d_hist, (int64_t)rc.W * g->C, s);
     if (!rc2) rc2 = dalloc(&w.d_vpart, p.n_vtiles * 4 * rc.L, s);
-    if (!rc2) rc2 = dalloc(&w.d_hpart, p.n_htiles * 2, s);
+    if (!rc2) rc2 = dalloc(&w.d_hpart, p.n_htiles * 3, s);
     if (!rc2) rc2 = dalloc(&w.d_theta, S * rc.L * 4, s);
     if (!rc2) rc2 = dalloc(&w.d_dterm, S * rc.L * 2, s);
     if (!rc2) rc2 = dalloc(&w.d_Thist, S * rc.W, s);
@@ -1784,8 +1804,8 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
         rc = fail(PMRF_ERR_CUDA, "event creation failed");
     pmrf_tuning keep = g->tuning, win = g->tuning;
     float best_ms = 1e30f;
-    const int cands[] = {512, 768, 1024};
-    for (int c = 0; c < 3 && !rc; ++c) {
+    const int cands[] = {512, 768, 1024, 1248};
+    for (int c = 0; c < 4 && !rc; ++c) {
         pmrf_tuning t = keep;
         t.hood_tile = cands[c];
         cudaDeviceSynchronize();

@@ -39,7 +39,8 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     uint8_t* d_x[2] = {nullptr, nullptr};  // label double buffer
     int64_t* d_hist = nullptr;     // [W][C] hood-sum ring, units of 2^-40
     double* d_vpart = nullptr;     // [n_vtiles][L][4]
-    double* d_hpart = nullptr;     // [n_htiles][2] (T partial, unconverged count)
+    int64_t* d_hpart = nullptr;    // [n_htiles][3]: the tile's exact T partial (low, high word, units
+                                   // 2^-80) and its unconverged-hood count
     double* d_theta = nullptr;     // [S][L][4] current parameters
     double* d_dterm = nullptr;     // [S][L][2] 1/(2 sigma^2) and ln sigma of the current parameters
     double* d_Thist = nullptr;     // [S][W] ring of totals
