@@ -435,7 +435,9 @@ PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* deta
  * holds the hoods starting in its window and takes the fast path when they
  * fit 1279 elements, every hood has <= 64 members and every member <= 32
  * neighbours; default 1024);
- * vert_tile: vertices per tile (multiple of 32, 32..4096); ctas_per_sm: 1..8. */
+ * vert_tile: accepted for compatibility (multiple of 32, 32..4096) but not
+ * used: the vertex pass always takes 256 vertices per block, one per thread;
+ * ctas_per_sm: accepted (0..8), not used. */
 typedef struct {
     int32_t hood_tile;
     int32_t vert_tile;
