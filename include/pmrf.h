@@ -105,6 +105,10 @@ typedef struct pmrf_graph pmrf_graph;
  *              most votes wins (lower label on ties), E*_v is the least energy
  *              among the replicas that voted for it.
  * The hood energy sums do not depend on the replica rule.
+ *
+ * Ranges (PMRF_ERR_ARG otherwise): 1 <= n_labels <= PMRF_MAX_LABELS,
+ * 0 <= beta < 2^32, sigma_min > 0, init_hi > init_lo, conv_window >= 1,
+ * max_iters >= 1, init_from_labels in {0, 1, 2}.
  */
 #define PMRF_SCOPE_HOOD 0
 #define PMRF_SCOPE_FULL 1
@@ -433,7 +437,7 @@ PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* deta
 /* Tile sizes of the EM launches.  0 selects the autotuned / default value.
  * hood_tile: hood elements per tile window (multiple of 32, 128..1248; a tile
  * holds the hoods starting in its window and takes the fast path when they
- * fit 1279 elements, every hood has <= 64 members and every member <= 32
+ * fit 1279 elements, every hood has <= 128 members and every member <= 32
  * neighbours; default 1024);
  * vert_tile: accepted for compatibility (multiple of 32, 32..4096) but not
  * used: the vertex pass always takes 256 vertices per block, one per thread;

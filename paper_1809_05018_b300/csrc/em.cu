@@ -730,7 +730,7 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
         // degree <= 32
         const bool fast = tile.pad != 0 && ne <= HT_CAP;
         if (fast) {
-            // every element's vertex has degree <= 32 and every hood <= 64
+            // every element's vertex has degree <= 32 and every hood <= 128
             // members: the counts of each label among v's neighbours inside
             // hood c are popcounts of the element's slot mask against the
             // vertex's label masks.  The tile's member ids and slot masks are
@@ -743,10 +743,10 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
             __syncthreads();
             for (int64_t c = c0 + threadIdx.x; c < c1; c += HT_THREADS) {
                 const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
-                // S_c = sum of D_min (exact) + sum of the excesses (<= 64
-                // elements of <= 32 beta_q each, below 2^62: no overflow)
+                // S_c = sum of D_min (exact) + sum of the excesses (<= 128
+                // elements of <= 32 beta_q each, below 2^63)
                 __int128 sdD = 0;
-                int64_t sdR = 0;
+                unsigned __int128 sdR = 0;
                 if constexpr (L == 2) {
                     // sum of beta_q c_b, less beta_q k - excess where that is
                     // positive (record layout above)
@@ -769,7 +769,8 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                             sdq += dq;
                         }
                     }
-                    sdR = beta_q * (int64_t)(scb - sk) + (int64_t)sdq;
+                    // scb - sk <= 128 * 32 and sdq <= sk beta_q: below 2^64
+                    sdR = (unsigned __int128)(uint64_t)beta_q * (uint32_t)(scb - sk) + sdq;
                 } else {
 #pragma unroll 2
                     for (int i = b; i < e; ++i) {
@@ -777,10 +778,10 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                         int cnt[L];
                         const int dc = slot_counts<L>(R, s_sm[i], cnt);
                         sdD += R.Dmin;
-                        sdR += vrec_excess<L>(R, cnt, dc, beta_q);
+                        sdR += (uint64_t)vrec_excess<L>(R, cnt, dc, beta_q);
                     }
                 }
-                const __int128 sd = sdD + ((__int128)sdR << rsh);
+                const __int128 sd = sdD + (__int128)(sdR << rsh);
                 if (mode == MODE_SWEEP) {
                     if (S_out) S_out[c] = unfix80(sd);
                 } else {
@@ -1206,7 +1207,9 @@ int check_cfg(const pmrf_graph* g, const pmrf_config* cfg) {
     if (!g) return fail(PMRF_ERR_ARG, "graph is NULL");
     if (!cfg) return fail(PMRF_ERR_ARG, "config is NULL");
     if (cfg->n_labels < 1 || cfg->n_labels > PMRF_MAX_LABELS) return fail(PMRF_ERR_ARG, "n_labels must be in [1, 8]");
-    if (!(cfg->beta >= 0.0) || !(cfg->beta < 0x1p40)) return fail(PMRF_ERR_ARG, "beta must be in [0, 2^40)");
+    // beta < 2^32 keeps a fast hood's excess sum (<= 128 * 32 beta, units
+    // 2^-80) inside 128 bits
+    if (!(cfg->beta >= 0.0) || !(cfg->beta < 0x1p32)) return fail(PMRF_ERR_ARG, "beta must be in [0, 2^32)");
     if (!(cfg->sigma_min > 0.0)) return fail(PMRF_ERR_ARG, "sigma_min must be > 0");
     if (!(cfg->init_hi > cfg->init_lo)) return fail(PMRF_ERR_ARG, "init_hi must exceed init_lo");
     if (cfg->conv_window < 1) return fail(PMRF_ERR_ARG, "conv_window must be >= 1");
@@ -1234,8 +1237,8 @@ RunCfg to_run(const pmrf_config* c) {
     r.init_lo = c->init_lo;
     r.init_hi = c->init_hi;
     // units 2^-hq of the hood pass's label excesses: beta_q = beta * 2^hq stays
-    // below 2^51, so a fast hood's <= 64 elements of <= 32 beta_q each sum
-    // below 2^62 (beta < 2^e with frexp's exponent e)
+    // below 2^51, so a fast hood's <= 128 elements of <= 32 beta_q each sum
+    // below 2^63 (beta < 2^e with frexp's exponent e)
     int e = 0;
     if (r.beta > 0.0) std::frexp(r.beta, &e);
     r.hq = std::max(0, std::min(51, 51 - e));

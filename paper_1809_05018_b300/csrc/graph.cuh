@@ -8,8 +8,8 @@
 #include "common.cuh"
 
 // largest hood the hood pass takes on its fast path (every member of degree
-// <= 32): 64 elements of excess at most 32 beta_q (< 2^56) sum below 2^62
-constexpr int HOOD_FAST_MAX = 64;
+// <= 32): 128 elements of excess at most 32 beta_q (< 2^56) sum below 2^63
+constexpr int HOOD_FAST_MAX = 128;
 
 namespace pmrf {
 
