@@ -1,28 +1,32 @@
 // em.cu -- the EM loop of DPP-PMRF on the device (Algorithm 2 steps 3, 6-11;
 // Section 3.2.2 EM steps 2-5), plus the standalone MAP sweep, parameter
-// update, threshold initialisation and label image.
+// update, starts (threshold, random) and label image.
 //
 // One EM iteration t is three kernels over a tile table:
-//   k_vertex<L> (vertex tiles) -- for every vertex v: the neighbour-label masks
-//     from x^{t-1}; for every replica (hood c containing v) the disagreement
-//     counts m(c,v,l) = #{u in N(v) n H_c : x_u != l} by popcount of the
-//     replica's slot mask against the label masks; their minimum over the
-//     replicas M_l(v); E*_v = min_l D_l(y_v) + beta * M_l(v) and x^t_v its
+//   k_vertex<L, VAR> (vertex tiles) -- for every vertex v: the neighbour-label
+//     masks from x^{t-1}; for every replica (hood c containing v) the
+//     disagreement counts m(c,v,l) = #{u in N(v) n H_c : x_u != l} by popcount
+//     of the replica's slot mask against the label masks; their minimum over
+//     the replicas M_l(v); E*_v = min_l D_l(y_v) + beta * M_l(v) and x^t_v its
 //     smallest minimising label.  Because beta >= 0 and rounding is monotone,
 //     min_c fl(D_l + beta*m(c,v,l)) = fl(D_l + beta*min_c m(c,v,l)), so this
 //     equals the lexicographic minimum of (Emin(c,v), label) over the replicas
 //     (Section 3.2.2 "Update Output Labels", reading G6) while keeping all
-//     per-replica work in integers.  Also writes D_l(y_v) for the hood pass
-//     and the per-tile moment partials of the parameter update.
-//   k_hood<L> (hood tiles) -- for every hood element (c,v): counts of each
-//     label among v's in-hood neighbours (hood-local adjacency row against the
-//     labels of the hood's members, staged in shared memory), Emin(c,v), and
-//     S_c = sum over the hood in ascending v; the hood convergence test over
-//     the last W sums (ring buffer).
+//     per-replica work in integers.  Also writes v's hood-pass record (its
+//     data terms in fixed point and its label masks) and the per-tile moment
+//     partials of the parameter update.  The VAR instantiation adds the sweep
+//     variants (full-neighbourhood Potts, mean-energy and vote replica rules).
+//   k_hood<L> (hood tiles) -- for every hood c: S_c = sum over its members v
+//     of Emin(c,v), from v's record and the element's slot mask (fast tiles:
+//     member ids and slot masks staged in shared memory, one thread per hood)
+//     or from the hood-local adjacency rows and the members' labels (general
+//     tiles); the sums are exact integers.  Also the hood convergence test
+//     over the last W sums (ring buffer) and the tile's exact partial of T.
 //   k_finalize<L> (one block per slice) -- label moments -> (n, mu, sigma, U),
 //     the total T^t, the MAP and EM convergence tests, per-slice stop flags.
-// Slices that have stopped skip all work.  The loop for t = 1..max_iters is
-// captured once into a CUDA graph and replayed.
+// Slices that have stopped skip all work.  The loop is captured once into a
+// CUDA graph whose iterations sit in conditional nodes: once every slice has
+// stopped, the remaining iterations are skipped.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
