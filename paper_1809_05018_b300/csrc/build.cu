@@ -1,13 +1,15 @@
 // build.cu -- device construction of the region graph, its maximal cliques,
-// the 1-neighbourhoods ("hoods") and the replica structures the EM sweep
-// streams (Algorithm 2 steps 1, 2, 4, 5; Sections 2.1, 3.1, 3.2.1, 3.2.2
-// "Construction of Neighborhoods" and "Replicate Neighborhoods By Label").
+// the 1-neighbourhoods ("hoods", or k-neighbourhoods) and the replica
+// structures the EM sweep streams (Algorithm 2 steps 1, 2, 4, 5; Sections 2.1,
+// 3.1, 3.2.1, 3.2.2 "Construction of Neighborhoods" and "Replicate
+// Neighborhoods By Label"); 2-D slices, or 3-D volumes of stacked layers.
 //
 // Everything is computed for a whole batch at once: the slices are disjoint
 // sub-graphs of one graph whose vertex ids are global (slice s owns vertices
 // [vert_off[s], vert_off[s+1])).  Integer results are deterministic and do not
-// depend on the order atomics land in: every list filled through atomics is
-// sorted afterwards.
+// depend on the order atomics land in: every list filled through atomics whose
+// order can reach a result is sorted afterwards (a vertex's replica masks are
+// left in fill order: only their minimum is used).
 #include <algorithm>
 #include <vector>
 
@@ -23,12 +25,6 @@ constexpr int PIX_THREADS = 256;
 constexpr int RS_MIN_BLOCKS = 8;
 constexpr int MK_MIN_BLOCKS = 8;
 constexpr int MAX_CLIQUE = 64;  // deepest Bron-Kerbosch recursion (largest clique)
-
-struct SliceGeo {  // per-slice geometry for the pixel kernels
-    const int64_t* pix_off;
-    const int64_t* W;
-    const int64_t* rank_off;
-};
 
 // finite double, from its exponent bits (no floating-point instruction)
 __device__ __forceinline__ bool finite_bits(double x) {
