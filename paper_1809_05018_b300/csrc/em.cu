@@ -714,6 +714,90 @@ __device__ __forceinline__ int hood_history(int64_t S40, int64_t c, int64_t C, i
     return unconv;
 }
 
+// The fast-tile hood sums: P adjacent lanes per hood (1, 2 or 4), each taking
+// every P-th element, their partial sums added across the group; S_c = the
+// exact sum of D_min plus the excesses (<= 128 elements of <= 32 beta_q
+// each, below 2^63)
+template <int P>
+__device__ __forceinline__ __int128 group_sum_i128(__int128 x, unsigned mask) {
+#pragma unroll
+    for (int o = 1; o < P; o <<= 1) {
+        const long long hi = __shfl_xor_sync(mask, (long long)(x >> 64), o);
+        const unsigned long long lo = __shfl_xor_sync(mask, (unsigned long long)x, o);
+        x += ((__int128)hi << 64) | (__int128)lo;
+    }
+    return x;
+}
+
+template <int L, int P>
+__device__ __forceinline__ void fast_hoods(const DevGraph& g, int64_t c0, int64_t c1, int64_t e0,
+                                           const int32_t* s_v, const uint32_t* s_sm,
+                                           const uint64_t* __restrict__ vrec, int64_t beta_q, int rsh, int mode,
+                                           int t, int W, int64_t tol40, int64_t* __restrict__ hist,
+                                           double* __restrict__ S_out, __int128& my_T, int& my_unconv) {
+    const int sub = threadIdx.x & (P - 1);
+    const unsigned gmask = P == 1 ? (1u << (threadIdx.x & 31))
+                                  : (((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1)));
+    for (int64_t c = c0 + threadIdx.x / P; c < c1; c += HT_THREADS / P) {
+        const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
+        __int128 sdD = 0;
+        unsigned __int128 sdR = 0;
+        if constexpr (L == 2) {
+            // sum of beta_q c_b, less beta_q k - excess where that is
+            // positive (record layout above)
+            int scb = 0, sk = 0;
+            uint64_t sdq = 0;
+#pragma unroll 2
+            for (int i = b + sub; i < e; i += P) {
+                uint64_t w0, w1, w2, w3;
+                asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
+                    : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+                    : "l"(vrec + (int64_t)s_v[i] * 4));
+                sdD += (__int128)(((unsigned __int128)w1 << 64) | w0);
+                const uint32_t m = s_sm[i];
+                const int cb = __popc(m & (uint32_t)w3);
+                const int k = 2 * cb - __popc(m);
+                scb += cb;
+                const uint64_t dq = w2 & DQ_MAX;
+                if (k > 0 && (uint64_t)beta_q * (uint32_t)k >= dq) {  // < 2^56
+                    sk += k;
+                    sdq += dq;
+                }
+            }
+#pragma unroll
+            for (int o = 1; o < P; o <<= 1) {
+                scb += __shfl_xor_sync(gmask, scb, o);
+                sk += __shfl_xor_sync(gmask, sk, o);
+                sdq += __shfl_xor_sync(gmask, sdq, o);
+            }
+            // scb - sk <= 128 * 32 and sdq <= sk beta_q: below 2^64
+            sdR = (unsigned __int128)(uint64_t)beta_q * (uint32_t)(scb - sk) + sdq;
+        } else {
+            uint64_t r = 0;  // <= 128 excesses of <= 32 beta_q each: below 2^63
+#pragma unroll 2
+            for (int i = b + sub; i < e; i += P) {
+                const VRec<L> R = load_vrec<L>(vrec, s_v[i]);
+                int cnt[L];
+                const int dc = slot_counts<L>(R, s_sm[i], cnt);
+                sdD += R.Dmin;
+                r += (uint64_t)vrec_excess<L>(R, cnt, dc, beta_q);
+            }
+#pragma unroll
+            for (int o = 1; o < P; o <<= 1) r += __shfl_xor_sync(gmask, r, o);
+            sdR = r;
+        }
+        sdD = group_sum_i128<P>(sdD, gmask);
+        if (sub != 0) continue;
+        const __int128 sd = sdD + (__int128)(sdR << rsh);
+        if (mode == MODE_SWEEP) {
+            if (S_out) S_out[c] = unfix80(sd);
+        } else {
+            my_unconv += hood_history(s40_of(sd), c, g.C, t, W, tol40, hist);
+            my_T += sd;
+        }
+    }
+}
+
 template <int L>
 __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph g, const Tile* __restrict__ tiles, int mode, int t,
                                                      const RunCfg* __restrict__ cfgp,
@@ -756,54 +840,18 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                 s_sm[i] = g.el_slot[e0 + i];
             }
             __syncthreads();
-            for (int64_t c = c0 + threadIdx.x; c < c1; c += HT_THREADS) {
-                const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
-                // S_c = sum of D_min (exact) + sum of the excesses (<= 128
-                // elements of <= 32 beta_q each, below 2^63)
-                __int128 sdD = 0;
-                unsigned __int128 sdR = 0;
-                if constexpr (L == 2) {
-                    // sum of beta_q c_b, less beta_q k - excess where that is
-                    // positive (record layout above)
-                    int scb = 0, sk = 0;
-                    uint64_t sdq = 0;
-#pragma unroll 2
-                    for (int i = b; i < e; ++i) {
-                        uint64_t w0, w1, w2, w3;
-                        asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
-                            : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
-                            : "l"(vrec + (int64_t)s_v[i] * 4));
-                        sdD += (__int128)(((unsigned __int128)w1 << 64) | w0);
-                        const uint32_t m = s_sm[i];
-                        const int cb = __popc(m & (uint32_t)w3);
-                        const int k = 2 * cb - __popc(m);
-                        scb += cb;
-                        const uint64_t dq = w2 & DQ_MAX;
-                        if (k > 0 && (uint64_t)beta_q * (uint32_t)k >= dq) {  // < 2^56
-                            sk += k;
-                            sdq += dq;
-                        }
-                    }
-                    // scb - sk <= 128 * 32 and sdq <= sk beta_q: below 2^64
-                    sdR = (unsigned __int128)(uint64_t)beta_q * (uint32_t)(scb - sk) + sdq;
-                } else {
-#pragma unroll 2
-                    for (int i = b; i < e; ++i) {
-                        const VRec<L> R = load_vrec<L>(vrec, s_v[i]);
-                        int cnt[L];
-                        const int dc = slot_counts<L>(R, s_sm[i], cnt);
-                        sdD += R.Dmin;
-                        sdR += (uint64_t)vrec_excess<L>(R, cnt, dc, beta_q);
-                    }
-                }
-                const __int128 sd = sdD + (__int128)(sdR << rsh);
-                if (mode == MODE_SWEEP) {
-                    if (S_out) S_out[c] = unfix80(sd);
-                } else {
-                    my_unconv += hood_history(s40_of(sd), c, g.C, t, W, tol40, hist);
-                    my_T += sd;
-                }
-            }
+            // tiles of few, large hoods (k-neighbourhoods) share each hood
+            // between 2 or 4 adjacent lanes, which split its elements
+            const int nh = (int)(c1 - c0);
+            if (nh * 4 <= HT_THREADS)
+                fast_hoods<L, 4>(g, c0, c1, e0, s_v, s_sm, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
+                                 my_unconv);
+            else if (nh * 2 <= HT_THREADS)
+                fast_hoods<L, 2>(g, c0, c1, e0, s_v, s_sm, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
+                                 my_unconv);
+            else
+                fast_hoods<L, 1>(g, c0, c1, e0, s_v, s_sm, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
+                                 my_unconv);
         } else {
             // general tile: hood by hood, labels read from global memory
             for (int64_t c = c0; c < c1; ++c) {

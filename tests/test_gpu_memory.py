@@ -15,6 +15,7 @@ pytestmark = pytest.mark.gpu
 
 def test_pool_keeps_and_trims_memory():
     import paper_1809_05018_b300 as pmrf
+    gc.collect()  # graphs that earlier tests left in reference cycles go back to the pool first
     sl = synth.make_stack(small_specs(3, seed0=2600))
     imgs, ids = dev_tensors(sl)
     g = pmrf.build_graph(imgs, ids)
