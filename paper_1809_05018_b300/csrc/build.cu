@@ -813,11 +813,15 @@ __global__ void k_rep_fill(const int32_t* __restrict__ hood, int64_t N_el, const
     rep_el[rep_off[v] + atomicAdd(&cursor[v], 1)] = (uint32_t)e;
 }
 
-__global__ void k_row_words(const int64_t* __restrict__ hood_off, int64_t C, int64_t* __restrict__ nwords) {
+// words of hood c's local adjacency rows: k rows of ceil(k/32) words, kept
+// only for hoods of at least rows_min_k members (the ones the hood pass's
+// general path reads)
+__global__ void k_row_words(const int64_t* __restrict__ hood_off, int64_t C, int64_t rows_min_k,
+                            int64_t* __restrict__ nwords) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= C) return;
     int64_t k = hood_off[c + 1] - hood_off[c];
-    nwords[c] = k * ceil_div(k, 32);
+    nwords[c] = k >= rows_min_k ? k * ceil_div(k, 32) : 0;
 }
 
 __global__ void k_rep_words(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ rcount, int64_t V,
@@ -829,16 +833,40 @@ __global__ void k_rep_words(const int64_t* __restrict__ adj_off, const int32_t* 
     nwords[v] = (int64_t)rcount[v] * nw;
 }
 
+// The intersection of two ascending lists of at most 32 ids (N(v), d ids, and
+// the hood, k ids): bit a of *sbits where N(v)[a] is in the hood and, with
+// ROWS, bit j of *rbits where hood[j] is in N(v).  Both heads are loaded every
+// step and the step advances them without branching (x <= y moves a, x >= y
+// moves j), so the lanes of a warp stay converged.
+template <bool ROWS>
+__device__ __forceinline__ void merge32(const int32_t* __restrict__ N, int d, const int32_t* __restrict__ Hc, int k,
+                                        uint32_t* rbits, uint32_t* sbits) {
+    uint32_t rb = 0, sb = 0;
+    int a = 0, j = 0;
+    while (a < d && j < k) {
+        const int32_t x = __ldg(N + a), y = __ldg(Hc + j);
+        const bool le = x <= y, ge = x >= y;
+        const uint32_t eq = (le && ge) ? 1u : 0u;
+        if (ROWS) rb |= eq << j;
+        sb |= eq << a;
+        a += le;
+        j += ge;
+    }
+    *rbits = rb;
+    *sbits = sb;
+}
+
 // For element e (vertex v in hood c at position i): row bits j where hood[j]
-// is a neighbour of v, and slot bits s where N(v)[s] lies in the hood (stored
-// vertex-major, one record per replica of v, and, for degrees <= 32,
-// element-major too).
+// is a neighbour of v (for hoods of at least rows_min_k members), and slot
+// bits s where N(v)[s] lies in the hood (stored vertex-major, one record per
+// replica of v, and, for degrees <= 32, element-major too).
 __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
                         const int32_t* __restrict__ el_hood, const int64_t* __restrict__ adj_off,
                         const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
                         uint32_t* __restrict__ row, int32_t* __restrict__ cursor,
                         const int64_t* __restrict__ rep_woff, uint32_t* __restrict__ rep_mask,
-                        uint32_t* __restrict__ el_slot, uint8_t* __restrict__ hood_gen, int64_t N_el) {
+                        uint32_t* __restrict__ el_slot, uint8_t* __restrict__ hood_gen, int64_t rows_min_k,
+                        int64_t N_el) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N_el) return;
     const int32_t c = el_hood[e];
@@ -851,35 +879,20 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
     const int64_t d = adj_off[v + 1] - av;
     const int64_t nwh = ceil_div(k, 32);
     const int64_t nwv = d > 32 ? ceil_div(d, 32) : 1;
-    uint32_t* rw = row + row_off[c] + i * nwh;
+    const bool keep_row = k >= rows_min_k;
+    uint32_t* rw = keep_row ? row + row_off[c] + i * nwh : nullptr;
     // the replica's place among v's replicas is arbitrary: the vertex pass only
     // takes a minimum over them
     uint32_t* sw = rep_mask + rep_woff[v] + (int64_t)atomicAdd(&cursor[v], 1) * nwv;
     if (k <= 32 && d <= 32) {
-        // one word each: a two-pointer merge with both heads in registers
-        const int32_t* Hc = hood + h0;
-        const int dk = (int)d, kk = (int)k;
-        uint32_t rbits = 0, sbits = 0;
-        if (dk > 0 && kk > 0) {
-            int a = 0, j = 0;
-            int32_t x = N[0], y = Hc[0];
-            while (true) {
-                if (x < y) {
-                    if (++a == dk) break;
-                    x = N[a];
-                } else if (x > y) {
-                    if (++j == kk) break;
-                    y = Hc[j];
-                } else {
-                    rbits |= 1u << j;
-                    sbits |= 1u << a;
-                    if (++a == dk || ++j == kk) break;
-                    x = N[a];
-                    y = Hc[j];
-                }
-            }
+        // one word each
+        uint32_t rbits, sbits;
+        if (keep_row) {
+            merge32<true>(N, (int)d, hood + h0, (int)k, &rbits, &sbits);
+            rw[0] = rbits;
+        } else {
+            merge32<false>(N, (int)d, hood + h0, (int)k, &rbits, &sbits);
         }
-        rw[0] = rbits;
         sw[0] = sbits;
         el_slot[e] = sbits;
         return;
@@ -893,7 +906,11 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
         if (x < y) ++a;
         else if (x > y) ++j;
         else {
-            if ((j >> 5) != rwi) { rw[rwi] = rcur; rcur = 0; rwi = j >> 5; }
+            if ((j >> 5) != rwi) {
+                if (keep_row) rw[rwi] = rcur;
+                rcur = 0;
+                rwi = j >> 5;
+            }
             rcur |= 1u << (j & 31);
             if ((a >> 5) != swi) { sw[swi] = scur; scur = 0; swi = a >> 5; }
             scur |= 1u << (a & 31);
@@ -901,7 +918,7 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
             ++j;
         }
     }
-    rw[rwi] = rcur;
+    if (keep_row) rw[rwi] = rcur;
     sw[swi] = scur;
     // the same slot mask in element (hood-major) order, for vertices of degree <= 32
     el_slot[e] = (d <= 32) ? scur : 0u;
@@ -1276,8 +1293,13 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(exclusive_scan_i32_to_i64(d_rcount, g->d_rep_off, V, s));
     int64_t* d_nw = nullptr;
     PMRF_TRY(tmp.get(&d_nw, std::max(C, V)));
+    // with every degree <= 32 only hoods above the fast path's size are read
+    // through their local adjacency rows, and every replica's slot mask is
+    // one word that k_masks writes in full
+    const bool deg32 = g->max_deg <= 32;
+    const int64_t rows_min_k = deg32 ? HOOD_FAST_MAX + 1 : 0;
     PMRF_TRY(dalloc(&g->d_row_off, C + 1, s));
-    LAUNCH_1D(k_row_words, C, g->d_hood_off, C, d_nw);
+    LAUNCH_1D(k_row_words, C, g->d_hood_off, C, rows_min_k, d_nw);
     PMRF_TRY(exclusive_scan_i64(d_nw, g->d_row_off, C, s));
     PMRF_TRY(read_i64(g->d_row_off + C, &g->n_row_words, s));
     PMRF_TRY(dalloc(&g->d_rep_woff, V + 1, s));
@@ -1288,12 +1310,13 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(dalloc(&g->d_rep_mask, g->n_rep_words, s));
     PMRF_TRY(dalloc(&g->d_el_slot, g->N_el, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
-    PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
+    if (!deg32)
+        PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
     PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
     PMRF_TRY(dalloc(&g->d_hood_gen, C, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_hood_gen, 0, std::max<int64_t>(C, 1), s));
     LAUNCH_1D(k_masks, g->N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off,
-              g->d_row, d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, g->N_el);
+              g->d_row, d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, rows_min_k, g->N_el);
     PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
     // slice offsets of hoods and elements (host copies, one transfer)
