@@ -716,6 +716,35 @@ __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t*
     };
     if (m == 1) {
         emit(clq[m0]);
+    } else if (m <= 4) {
+        // the common cliques (edges, triangles, 4-cliques): cursors and heads
+        // in registers, each head loaded once
+        constexpr int32_t END = 0x7fffffff;
+        const int32_t* q[4];
+        const int32_t* qe[4];
+        int32_t h[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            h[i] = END;
+            q[i] = qe[i] = nullptr;
+            if (i < m) {
+                const int32_t u = clq[m0 + i];
+                q[i] = adj + adj_off[u];
+                qe[i] = adj + adj_off[u + 1];
+                if (q[i] < qe[i]) h[i] = *q[i];
+            }
+        }
+        while (true) {
+            const int32_t cur = min(min(h[0], h[1]), min(h[2], h[3]));
+            if (cur == END) break;
+            emit(cur);
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (h[i] == cur) {
+                    ++q[i];
+                    h[i] = q[i] < qe[i] ? *q[i] : END;
+                }
+        }
     } else {
         int64_t p[MAX_CLIQUE + 1], e[MAX_CLIQUE + 1];
         for (int i = 0; i < m; ++i) {
