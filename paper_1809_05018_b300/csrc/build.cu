@@ -221,6 +221,8 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
         const double* vrow = img + b + (int64_t)r * W;
         const bool down = r + 1 < H;
         int32_t cur = irow[c0];
+        // two steps' id loads in flight per lane
+#pragma unroll 2
         for (int c = c0; c <= bb.w; ++c) {
             const int32_t right = c + 1 < w ? irow[c + 1] : cur;
             const int32_t below = down ? irow[w + c] : cur;
