@@ -676,8 +676,14 @@ __global__ void k_list_general(const int64_t* __restrict__ adj_off, int64_t V, i
 
 // The count pass keeps hoods of up to HOOD_KEEP members in `kept`, element i
 // of hood c at kept[i * C + c] (a warp's stores and loads are adjacent); the
-// fill pass copies those and merges only the larger ones.
+// fill pass copies those and merges only the larger ones.  A block of the fill
+// pass whose hoods are all kept and whose output range (contiguous: hood_off
+// is a prefix sum) fits FILL_STAGE elements assembles the range in shared
+// memory and writes it out with adjacent stores.
 constexpr int HOOD_KEEP = 32;
+constexpr int FILL_BLOCK = 256;
+constexpr int FILL_STAGE = 6144;
+static_assert(FILL_BLOCK == 256, "the fill pass is launched with 256 threads per block");
 
 template <bool FILL>
 __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t* __restrict__ clq,
@@ -687,6 +693,29 @@ __global__ void k_hood_merge(const int64_t* __restrict__ clq_off, const int32_t*
                              int32_t* __restrict__ el_hood, int32_t* __restrict__ rcount,
                              int32_t* __restrict__ kept) {
     int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if constexpr (FILL) {
+        __shared__ int32_t s_hood[FILL_STAGE];
+        __shared__ uint8_t s_cl[FILL_STAGE];  // hood of each element, less the block's first
+        const int64_t cb = (int64_t)blockIdx.x * FILL_BLOCK;
+        const int64_t ce = cb + FILL_BLOCK < C ? cb + FILL_BLOCK : C;
+        const int64_t H0 = hood_off[cb], n = hood_off[ce] - H0;
+        const int64_t h0 = c < C ? hood_off[c] : 0, k = c < C ? hood_off[c + 1] - h0 : 0;
+        if (__syncthreads_and(k <= HOOD_KEEP) && n <= FILL_STAGE) {
+            const int32_t* kc = kept + c;
+            for (int64_t i = 0; i < k; ++i) {
+                const int32_t cur = kc[i * C];
+                s_hood[h0 - H0 + i] = cur;
+                s_cl[h0 - H0 + i] = (uint8_t)threadIdx.x;
+                atomicAdd(&rcount[cur], 1);
+            }
+            __syncthreads();
+            for (int q = threadIdx.x; q < (int)n; q += FILL_BLOCK) {
+                hood[H0 + q] = s_hood[q];
+                el_hood[H0 + q] = (int32_t)(cb + s_cl[q]);
+            }
+            return;
+        }
+    }
     if (c >= C) return;
     const int64_t m0 = clq_off[c];
     const int m = (int)(clq_off[c + 1] - m0);
