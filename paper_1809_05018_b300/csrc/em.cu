@@ -731,7 +731,7 @@ __device__ __forceinline__ __int128 group_sum_i128(__int128 x, unsigned mask) {
 
 template <int L, int P>
 __device__ __forceinline__ void fast_hoods(const DevGraph& g, int64_t c0, int64_t c1, int64_t e0,
-                                           const int32_t* s_v, const uint32_t* s_sm,
+                                           const uint2* s_el,
                                            const uint64_t* __restrict__ vrec, int64_t beta_q, int rsh, int mode,
                                            int t, int W, int64_t tol40, int64_t* __restrict__ hist,
                                            double* __restrict__ S_out, __int128& my_T, int& my_unconv) {
@@ -749,12 +749,13 @@ __device__ __forceinline__ void fast_hoods(const DevGraph& g, int64_t c0, int64_
             uint64_t sdq = 0;
 #pragma unroll 2
             for (int i = b + sub; i < e; i += P) {
+                const uint2 q = s_el[i];
                 uint64_t w0, w1, w2, w3;
                 asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
                     : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
-                    : "l"(vrec + (int64_t)s_v[i] * 4));
+                    : "l"(vrec + (int64_t)(int32_t)q.x * 4));
                 sdD += (__int128)(((unsigned __int128)w1 << 64) | w0);
-                const uint32_t m = s_sm[i];
+                const uint32_t m = q.y;
                 const int cb = __popc(m & (uint32_t)w3);
                 const int k = 2 * cb - __popc(m);
                 scb += cb;
@@ -776,9 +777,10 @@ __device__ __forceinline__ void fast_hoods(const DevGraph& g, int64_t c0, int64_
             uint64_t r = 0;  // <= 128 excesses of <= 32 beta_q each: below 2^63
 #pragma unroll 2
             for (int i = b + sub; i < e; i += P) {
-                const VRec<L> R = load_vrec<L>(vrec, s_v[i]);
+                const uint2 q = s_el[i];
+                const VRec<L> R = load_vrec<L>(vrec, (int32_t)q.x);
                 int cnt[L];
-                const int dc = slot_counts<L>(R, s_sm[i], cnt);
+                const int dc = slot_counts<L>(R, q.y, cnt);
                 sdD += R.Dmin;
                 r += (uint64_t)vrec_excess<L>(R, cnt, dc, beta_q);
             }
@@ -805,8 +807,7 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                                                      const uint8_t* __restrict__ x_in,
                                                      const uint64_t* __restrict__ vrec, int64_t* __restrict__ hist,
                                                      double* __restrict__ S_out, int64_t* __restrict__ hpart) {
-    __shared__ int32_t s_v[HT_CAP];
-    __shared__ uint32_t s_sm[HT_CAP];
+    __shared__ uint2 s_el[HT_CAP];  // member id, slot mask: one 8-byte load per element
     __shared__ __int128 s_wsum[HT_THREADS / 32];
     __shared__ int s_unconv;
     const Tile tile = tiles[blockIdx.x];
@@ -836,21 +837,20 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
             // staged once (coalesced); then one thread per hood walks its
             // elements, gathers their vertex data and keeps the exact sum.
             for (int i = threadIdx.x; i < ne; i += HT_THREADS) {
-                s_v[i] = g.hood[e0 + i];
-                s_sm[i] = g.el_slot[e0 + i];
+                s_el[i] = make_uint2((uint32_t)g.hood[e0 + i], g.el_slot[e0 + i]);
             }
             __syncthreads();
             // tiles of few, large hoods (k-neighbourhoods) share each hood
             // between 2 or 4 adjacent lanes, which split its elements
             const int nh = (int)(c1 - c0);
             if (nh * 4 <= HT_THREADS)
-                fast_hoods<L, 4>(g, c0, c1, e0, s_v, s_sm, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
+                fast_hoods<L, 4>(g, c0, c1, e0, s_el, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
                                  my_unconv);
             else if (nh * 2 <= HT_THREADS)
-                fast_hoods<L, 2>(g, c0, c1, e0, s_v, s_sm, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
+                fast_hoods<L, 2>(g, c0, c1, e0, s_el, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
                                  my_unconv);
             else
-                fast_hoods<L, 1>(g, c0, c1, e0, s_v, s_sm, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
+                fast_hoods<L, 1>(g, c0, c1, e0, s_el, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
                                  my_unconv);
         } else {
             // general tile: hood by hood, labels read from global memory
