@@ -422,6 +422,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                                                        double* __restrict__ vpart, DevStatus* st,
                                                        uint64_t* __restrict__ vrec) {
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
+    __shared__ double s_Md[33];  // (double)m for m <= 32: no int-to-FP64 conversions on the common path
     __shared__ double s_vq[3][VT_THREADS];
     __shared__ double s_vc[3 * L][8];
     __shared__ int s_cnt[VT_THREADS / 32][L];
@@ -429,6 +430,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
     const int s = tile.slice;
     if (active && !active[s]) return;
     const RunCfg c = *cfgp;
+    if (threadIdx.x < 33) s_Md[threadIdx.x] = (double)threadIdx.x;
     if (threadIdx.x < L) {
         const int l = threadIdx.x;
         if (mode == MODE_INIT) {
@@ -522,12 +524,21 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                 }
                 // the hood pass of this iteration reads v's data terms and label masks
                 if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
-                // every vertex lies in at least one hood, so M_l is set
-                Estar = D[0] + c.beta * (double)M[0];
+                // every vertex lies in at least one hood, so M_l is set (and
+                // <= 32 when d <= 32)
+                double Md[L];
+                if (d <= 32) {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) Md[l] = s_Md[M[l]];
+                } else {
+#pragma unroll
+                    for (int l = 0; l < L; ++l) Md[l] = (double)M[l];
+                }
+                Estar = D[0] + c.beta * Md[0];
                 lab = 0;
 #pragma unroll
                 for (int l = 1; l < L; ++l) {
-                    const double e = D[l] + c.beta * (double)M[l];
+                    const double e = D[l] + c.beta * Md[l];
                     if (e < Estar) { Estar = e; lab = l; }
                 }
             } else {
