@@ -178,6 +178,15 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
 // ---------------------------------------------------------------------------
 // vertex pass
 
+// an integer with the order of the finite double x (x < y exactly when
+// key(x) < key(y); -0 and +0 share a key): the sign bit set flips the other
+// bits, so larger magnitudes of negative values map lower
+__device__ __forceinline__ long long ordered_key(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
 // 1 / (2 sigma^2) of the Gaussian data term (one expression for every caller)
 __device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * sg * sg); }
 
@@ -534,12 +543,17 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
 #pragma unroll
                     for (int l = 0; l < L; ++l) Md[l] = (double)M[l];
                 }
+                // the least energy compared on the integer pipes: finite
+                // doubles order like their bit patterns mapped to ordered
+                // integers (negative values' magnitude bits flipped, -0 as +0)
                 Estar = D[0] + c.beta * Md[0];
+                long long kbest = ordered_key(Estar);
                 lab = 0;
 #pragma unroll
                 for (int l = 1; l < L; ++l) {
                     const double e = D[l] + c.beta * Md[l];
-                    if (e < Estar) { Estar = e; lab = l; }
+                    const long long k = ordered_key(e);
+                    if (k < kbest) { Estar = e; kbest = k; lab = l; }
                 }
             } else {
                 lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar);
