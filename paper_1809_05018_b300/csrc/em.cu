@@ -1229,8 +1229,21 @@ int free_em(pmrf_graph* g) {
 
 namespace {
 
+// The default hood-tile window from the graph's mean hood size: about 94
+// hoods per tile when one thread takes a hood (a tile of HT_THREADS threads
+// then rarely needs a second round), else about 40 (two lanes per hood, at
+// most HT_THREADS / 2 hoods), to the nearest multiple of 32 within
+// [512, MAX_HOOD_TILE]
+int default_hood_tile(const pmrf_graph* g) {
+    const double mean = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
+    double w = mean * 94.0;
+    if (w > MAX_HOOD_TILE + 16) w = mean * 40.0;
+    int te = (int)((w + 16.0) / 32.0) * 32;
+    return te < 512 ? 512 : (te > MAX_HOOD_TILE ? MAX_HOOD_TILE : te);
+}
+
 int effective_tiles(const pmrf_graph* g, int* te, int* vt) {
-    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : 1024;
+    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : default_hood_tile(g);
     *vt = VT_THREADS;  // one vertex per thread
     (void)g;
     return PMRF_OK;
@@ -1895,8 +1908,8 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
         rc = fail(PMRF_ERR_CUDA, "event creation failed");
     pmrf_tuning keep = g->tuning, win = g->tuning;
     float best_ms = 1e30f;
-    const int cands[] = {512, 768, 1024, 1248};
-    for (int c = 0; c < 4 && !rc; ++c) {
+    const int cands[] = {0, 512, 768, 1024, 1248};  // 0: the window from the mean hood size
+    for (int c = 0; c < 5 && !rc; ++c) {
         pmrf_tuning t = keep;
         t.hood_tile = cands[c];
         cudaDeviceSynchronize();

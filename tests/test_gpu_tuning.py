@@ -42,7 +42,7 @@ def test_autotune_and_kernel_times():
     ref = g.em(cfg)
     ref = {k: v.clone() for k, v in ref.items()}
     best = g.autotune(cfg)
-    assert best["hood_tile"] in (512, 768, 1024, 1248)
+    assert best["hood_tile"] in (0, 512, 768, 1024, 1248)  # 0: the default from the mean hood size
     assert g.tuning()["hood_tile"] == best["hood_tile"]
     out = g.em(cfg)
     for k in ("labels", "params", "iters"):
