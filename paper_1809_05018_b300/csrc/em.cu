@@ -46,7 +46,7 @@ __host__ __device__ constexpr int vt_min_blocks(int L) { return L <= 2 ? 8 : (L 
 __host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 16 : 12; }
 constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
 constexpr int LI_THREADS = 256;             // label-image block
-constexpr int HT_THREADS = 96;              // hood-pass block: a tile's ~85 hoods, one per thread
+constexpr int HT_THREADS = 96;              // hood-pass block: a tile's ~94 hoods, one per thread
 constexpr int MAX_HOOD_TILE = 1248;         // largest hood-tile window (elements)
 constexpr int HT_CAP = MAX_HOOD_TILE + 31;  // elements a fast hood tile can hold
 // Per-vertex record of the hood pass, 32-byte chunks (one for L = 2), written
