@@ -289,6 +289,8 @@ __device__ __forceinline__ int slot_label_counts(const DevGraph& g, const uint8_
     return dc;
 }
 
+constexpr int RCP_N = 65;  // replica counts whose reciprocal the vertex pass takes from a table
+
 // The sweep variants for one vertex (scope and replica rule of RunCfg; the
 // same definitions as pmrf_config documents): returns the new label, sets
 // Estar, writes the hood-pass record.  k_l of a replica = its in-hood
@@ -297,7 +299,7 @@ template <int L>
 __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, const uint8_t* __restrict__ x_in,
                                            int64_t a0, int d, int64_t r0, int64_t r1, const uint32_t (&lm)[L],
                                            const double (&D)[L], uint64_t* __restrict__ vrec, int64_t v,
-                                           double& Estar) {
+                                           double& Estar, const double* __restrict__ rcp) {
     int lab = 0;
     if (c.scope == PMRF_SCOPE_FULL) {
         // one set of energies for every replica: every rule picks its least label
@@ -356,7 +358,9 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
                 for (int l = 0; l < L; ++l) Ks[l] += dc - cnt[l];
             }
         }
-        const double inv_R = 1.0 / (double)R;  // every vertex lies in at least one hood
+        // every vertex lies in at least one hood; 1/R from the block's table of
+        // the same correctly rounded quotients when R is small
+        const double inv_R = R < RCP_N ? rcp[R] : 1.0 / (double)R;
         Estar = D[0] + c.beta * ((double)Ks[0] * inv_R);
 #pragma unroll
         for (int l = 1; l < L; ++l) {
@@ -432,6 +436,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                                                        uint64_t* __restrict__ vrec) {
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
     __shared__ double s_Md[33];  // (double)m for m <= 32: no int-to-FP64 conversions on the common path
+    __shared__ double s_rcp[VAR ? RCP_N : 1];  // 1 / R for the mean-energy replica rule
     __shared__ double s_vq[3][VT_THREADS];
     __shared__ double s_vc[3 * L][8];
     __shared__ int s_cnt[VT_THREADS / 32][L];
@@ -440,6 +445,8 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
     if (active && !active[s]) return;
     const RunCfg c = *cfgp;
     if (threadIdx.x < 33) s_Md[threadIdx.x] = (double)threadIdx.x;
+    if (VAR && threadIdx.x < RCP_N && c.rule == PMRF_RULE_SUM)
+        s_rcp[threadIdx.x] = threadIdx.x > 0 ? 1.0 / (double)threadIdx.x : 0.0;
     if (threadIdx.x < L) {
         const int l = threadIdx.x;
         if (mode == MODE_INIT) {
@@ -556,7 +563,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                     if (k < kbest) { Estar = e; kbest = k; lab = l; }
                 }
             } else {
-                lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar);
+                lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar, s_rcp);
             }
             x_out[v] = (uint8_t)lab;
             if (E_out) E_out[v] = Estar;
