@@ -289,6 +289,22 @@ __device__ __forceinline__ int slot_label_counts(const DevGraph& g, const uint8_
     return dc;
 }
 
+// f(mask) for the one-word replica masks rm[r0 .. r1), read four at a time
+// once the address is 16-byte aligned (fewer load requests per warp)
+template <typename F>
+__device__ __forceinline__ void for_each_mask(const uint32_t* __restrict__ rm, int64_t r0, int64_t r1, F&& f) {
+    int64_t r = r0;
+    for (; r < r1 && (r & 3); ++r) f(rm[r]);
+    for (; r + 4 <= r1; r += 4) {
+        const uint4 q = __ldg(reinterpret_cast<const uint4*>(rm + r));
+        f(q.x);
+        f(q.y);
+        f(q.z);
+        f(q.w);
+    }
+    for (; r < r1; ++r) f(rm[r]);
+}
+
 constexpr int RCP_N = 65;  // replica counts whose reciprocal the vertex pass takes from a table
 
 // The sweep variants for one vertex (scope and replica rule of RunCfg; the
@@ -345,13 +361,15 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
 #pragma unroll
         for (int l = 0; l < L; ++l) Ks[l] = 0;
         int64_t R = 0;
-        for (int64_t r = r0; r < r1; r += nw, ++R) {
-            if (d <= 32) {
-                const uint32_t m = g.rep_mask[r];
+        if (d <= 32) {
+            R = r1 - r0;
+            for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
                 const int dc = __popc(m);
 #pragma unroll
                 for (int l = 0; l < L; ++l) Ks[l] += dc - __popc(m & lm[l]);
-            } else {
+            });
+        } else {
+            for (int64_t r = r0; r < r1; r += nw, ++R) {
                 int cnt[L];
                 const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
 #pragma unroll
@@ -380,19 +398,8 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
             kmin[l] = 0x7fffffff;
         }
         const uint64_t bq = (uint64_t)c.beta_q;
-        for (int64_t r = r0; r < r1; r += nw) {
-            int k[L];
-            if (d <= 32) {
-                const uint32_t m = g.rep_mask[r];
-                const int dc = __popc(m);
-#pragma unroll
-                for (int l = 0; l < L; ++l) k[l] = dc - __popc(m & lm[l]);
-            } else {
-                int cnt[L];
-                const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
-#pragma unroll
-                for (int l = 0; l < L; ++l) k[l] = dc - cnt[l];
-            }
+        // one replica's vote from its counts k_l of in-hood neighbours not labelled l
+        auto vote = [&](const int (&k)[L]) {
             // < 2^60 + 2^51 * 2^12: no overflow in 64 bits
             int b = 0;
             uint64_t eb = dq[0] + bq * (uint64_t)k[0];
@@ -407,6 +414,23 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
                     votes[l] += 1;
                     kmin[l] = min(kmin[l], k[l]);
                 }
+        };
+        if (d <= 32) {
+            for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
+                const int dc = __popc(m);
+                int k[L];
+#pragma unroll
+                for (int l = 0; l < L; ++l) k[l] = dc - __popc(m & lm[l]);
+                vote(k);
+            });
+        } else {
+            for (int64_t r = r0; r < r1; r += nw) {
+                int cnt[L], k[L];
+                const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+#pragma unroll
+                for (int l = 0; l < L; ++l) k[l] = dc - cnt[l];
+                vote(k);
+            }
         }
         int best = votes[0];
 #pragma unroll
@@ -514,21 +538,11 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                     // neighbours in the hood whose label is not l, minimised over
                     // the replicas; the masks are read four at a time once the
                     // address is 16-byte aligned (fewer load requests per warp)
-                    auto take = [&](uint32_t m) {
+                    for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
                         const int dc = __popc(m);
 #pragma unroll
                         for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - __popc(m & lm[l]));
-                    };
-                    int64_t r = r0;
-                    for (; r < r1 && (r & 3); ++r) take(g.rep_mask[r]);
-                    for (; r + 4 <= r1; r += 4) {
-                        const uint4 q = __ldg(reinterpret_cast<const uint4*>(g.rep_mask + r));
-                        take(q.x);
-                        take(q.y);
-                        take(q.z);
-                        take(q.w);
-                    }
-                    for (; r < r1; ++r) take(g.rep_mask[r]);
+                    });
                 } else {
                     const int nw = (d + 31) >> 5;
                     for (int64_t r = r0; r < r1; r += nw) {
