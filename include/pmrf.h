@@ -438,9 +438,9 @@ PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* deta
  * hood_tile: hood elements per tile window (multiple of 32, 128..1248; a tile
  * holds the hoods starting in its window and takes the fast path when they
  * fit 1279 elements, every hood has <= 128 members and every member <= 32
- * neighbours; default, 0: from the graph's mean hood size m, 94 m (one thread
- * per hood, 96 threads per tile) or, when that exceeds 1248, 40 m (two lanes
- * per hood), rounded to the nearest multiple of 32 and clamped to [512, 1248]);
+ * neighbours; default, 0: from the graph's mean hood size m, 94 m rounded to
+ * the nearest multiple of 32 (one thread per hood, 96 threads per tile) and at
+ * least 512, or 1152 when 94 m exceeds 1248);
  * vert_tile: accepted for compatibility (multiple of 32, 32..4096) but not
  * used: the vertex pass always takes 256 vertices per block, one per thread;
  * ctas_per_sm: accepted (0..8), not used. */

@@ -1250,17 +1250,16 @@ int free_em(pmrf_graph* g) {
 
 namespace {
 
-// The default hood-tile window from the graph's mean hood size: about 94
-// hoods per tile when one thread takes a hood (a tile of HT_THREADS threads
-// then rarely needs a second round), else about 40 (two lanes per hood, at
-// most HT_THREADS / 2 hoods), to the nearest multiple of 32 within
-// [512, MAX_HOOD_TILE]
+// The default hood-tile window from the graph's mean hood size m: 94 m, to the
+// nearest multiple of 32, so that a tile holds about 94 hoods and its
+// HT_THREADS threads, one per hood, rarely need a second round; when that
+// exceeds MAX_HOOD_TILE (larger hoods), 1152 elements, measured best on the
+// 2-neighbourhoods (m = 28.6) and the volumes (m = 22.1) of the stack
 int default_hood_tile(const pmrf_graph* g) {
     const double mean = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
-    double w = mean * 94.0;
-    if (w > MAX_HOOD_TILE + 16) w = mean * 40.0;
-    int te = (int)((w + 16.0) / 32.0) * 32;
-    return te < 512 ? 512 : (te > MAX_HOOD_TILE ? MAX_HOOD_TILE : te);
+    const int te = (int)((mean * 94.0 + 16.0) / 32.0) * 32;
+    if (te > MAX_HOOD_TILE) return 1152;
+    return te < 512 ? 512 : te;
 }
 
 int effective_tiles(const pmrf_graph* g, int* te, int* vt) {
