@@ -442,7 +442,7 @@ PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* deta
  * the nearest multiple of 32 (one thread per hood, 96 threads per tile) and at
  * least 512, or 1152 when 94 m exceeds 1248);
  * vert_tile: accepted for compatibility (multiple of 32, 32..4096) but not
- * used: the vertex pass always takes 256 vertices per block, one per thread;
+ * used: the vertex pass always takes 128 vertices per block, one per thread;
  * ctas_per_sm: accepted (0..8), not used. */
 typedef struct {
     int32_t hood_tile;

@@ -38,11 +38,11 @@ namespace pmrf {
 
 namespace {
 
-constexpr int VT_THREADS = 256;             // vertices per vertex tile = threads
+constexpr int VT_THREADS = 128;             // vertices per vertex tile = threads
 // resident blocks per SM the register budget of the EM kernels must allow
-// (measured on the two-label stack: the vertex pass gains from 8 blocks at 32
+// (measured on the two-label stack: the vertex pass gains from 16 blocks at 32
 // registers; the hood pass is best at 40; more labels need more registers)
-__host__ __device__ constexpr int vt_min_blocks(int L) { return L <= 2 ? 8 : (L <= 4 ? 5 : 2); }
+__host__ __device__ constexpr int vt_min_blocks(int L) { return L <= 2 ? 16 : (L <= 4 ? 10 : 4); }
 __host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 16 : 12; }
 constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
 constexpr int LI_THREADS = 256;             // label-image block
@@ -628,8 +628,8 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
     __syncthreads();
     // 8 threads per (label, quantity) add fixed consecutive chunks of the
     // label's run in order, then one thread adds the 8 results in order
-    if (threadIdx.x < 3 * L * 8) {
-        const int lq = threadIdx.x >> 3, k = threadIdx.x & 7;
+    for (int job = threadIdx.x; job < 3 * L * 8; job += VT_THREADS) {  // two jobs a thread when L > 5
+        const int lq = job >> 3, k = job & 7;
         const int l = lq / 3, q = lq % 3;
         int base = 0, n = 0;
         for (int m = 0; m < L; ++m)
@@ -1909,7 +1909,7 @@ int label_image_run(pmrf_graph* g, const int32_t* ids, const uint8_t* labels, ui
 
 // ---------------------------------------------------------------------------
 // autotuner: time the EM loop on this graph for a few hood-tile sizes and keep
-// the fastest (the vertex tile is one vertex per thread of a 256-thread CTA)
+// the fastest (the vertex tile is one vertex per thread of a 128-thread CTA)
 
 namespace pmrf {
 
