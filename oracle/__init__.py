@@ -19,8 +19,8 @@ per-slice functions and the readings they encode:
 * map_sweep                          -- Section 3.2.2 EM step 2-3; G4-G7.
 * params / init                      -- Section 3.2.2 EM step 4, Algorithm 2
   step 3; G3, G8.
-* em                                 -- Algorithm 2 steps 6-11, EM step 5; G9.
-* pll                                -- the differentiable form (G10).
+* em, stop_rule                     -- Algorithm 2 steps 6-11, EM step 5; G9.
+* pll, fit_beta                      -- the differentiable form (G10, G11).
 * quality                            -- Section 4.2.1 evaluation metrics; G12.
 """
 from __future__ import annotations
@@ -43,12 +43,13 @@ RULE_MIN, RULE_SUM, RULE_VOTE = 0, 1, 2
 
 def build(force: bool = False) -> str:
     """Compile the oracle with plain gcc -O2 (no fast-math: the C source fixes
-    the order of every floating-point operation)."""
+    the order of every floating-point operation; OpenMP for the optional
+    multi-core sweep only)."""
     src = os.path.join(_HERE, "pmrf_oracle.c")
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(src):
         os.makedirs(_LIBDIR, exist_ok=True)
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fno-fast-math", "-ffp-contract=off", "-fPIC",
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-fno-fast-math", "-ffp-contract=off", "-fopenmp", "-fPIC",
                                "-shared", "-o", tmp, src, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -70,7 +71,8 @@ class _Config(ctypes.Structure):
     _fields_ = [("n_labels", ctypes.c_int32), ("max_iters", ctypes.c_int32), ("conv_window", ctypes.c_int32),
                 ("potts_scope", ctypes.c_int32), ("replica_rule", ctypes.c_int32), ("init_mode", ctypes.c_int32),
                 ("beta", ctypes.c_double), ("conv_tol", ctypes.c_double),
-                ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double)]
+                ("sigma_min", ctypes.c_double), ("init_lo", ctypes.c_double), ("init_hi", ctypes.c_double),
+                ("n_threads", ctypes.c_int32)]
 
 
 _lib = None
@@ -92,6 +94,19 @@ def _get():
         lib.orc_init_labels.argtypes = [GP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, _P]
         lib.orc_init_params.argtypes = [GP, ctypes.c_int32, ctypes.c_double, ctypes.c_double, ctypes.c_double, _P, _P]
         lib.orc_em.argtypes = [GP, ctypes.POINTER(_Config), _P, _P, _P, _P, _P]
+        lib.orc_em_ex.argtypes = [GP, ctypes.POINTER(_Config), _P, _P, _P, _P, _P, _P]
+        lib.orc_stop_rule.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_double, ctypes.c_int64, _P, _P, _P,
+                                      _P]
+        lib.orc_replica_lists.argtypes = [GP, ctypes.POINTER(ctypes.POINTER(ctypes.c_int64)),
+                                          ctypes.POINTER(ctypes.POINTER(ctypes.c_int64))]
+        lib.orc_map_sweep_par.argtypes = [GP, ctypes.c_int32, ctypes.c_double, _P, _P, _P, _P, _P, ctypes.c_int32,
+                                          _P, _P, _P]
+        libc = ctypes.CDLL(None)
+        libc.free.argtypes = [ctypes.c_void_p]
+        lib._free = libc.free
+        lib.orc_fit_beta.argtypes = [ctypes.POINTER(GP), ctypes.c_int32, ctypes.c_int32,
+                                     ctypes.POINTER(ctypes.c_void_p), _P, _P, ctypes.c_double, ctypes.c_int32,
+                                     ctypes.c_double, _P]
         lib.orc_pll.argtypes = [GP, ctypes.c_int32, _P, _P, _P, ctypes.c_double, _P, _P, _P, _P]
         lib.orc_label_image.argtypes = [GP, _P, ctypes.c_int64, _P, _P]
         lib.orc_quality.argtypes = [_P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P]
@@ -138,10 +153,12 @@ class EMConfig:
     potts_scope: int = 0   # SCOPE_HOOD (G4) or SCOPE_FULL (G13)
     replica_rule: int = 0  # RULE_MIN (G6), RULE_SUM or RULE_VOTE (G14)
     init_mode: int = 0     # 0 threshold (G3), 1 given labels, 2 given labels and parameters
+    n_threads: int = 1     # > 1: the default sweep on that many threads (identical results)
 
     def _c(self):
         return _Config(self.n_labels, self.max_iters, self.conv_window, self.potts_scope, self.replica_rule,
-                       self.init_mode, self.beta, self.conv_tol, self.sigma_min, self.init_lo, self.init_hi)
+                       self.init_mode, self.beta, self.conv_tol, self.sigma_min, self.init_lo, self.init_hi,
+                       self.n_threads)
 
 
 class Graph:
@@ -253,6 +270,27 @@ class Graph:
             out["E_second"] = E2
         return out
 
+    def map_sweep_par(self, L, beta, x, mu, sigma, n_threads):
+        """The default sweep on n_threads threads (orc_map_sweep_par): x_new,
+        E_star, S -- identical to map_sweep's."""
+        lib = _get()
+        x = np.ascontiguousarray(x, dtype=np.uint8)
+        mu = np.ascontiguousarray(mu, dtype=np.float64)
+        sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+        ro = ctypes.POINTER(ctypes.c_int64)()
+        re = ctypes.POINTER(ctypes.c_int64)()
+        _check(lib.orc_replica_lists(self._h, ctypes.byref(ro), ctypes.byref(re)), "replica_lists")
+        out = dict(x_new=np.zeros(self.V, np.uint8), E_star=np.zeros(self.V), S=np.zeros(self.C))
+        try:
+            _check(lib.orc_map_sweep_par(self._h, L, beta, _ptr(x), _ptr(mu), _ptr(sigma),
+                                         ctypes.cast(ro, ctypes.c_void_p), ctypes.cast(re, ctypes.c_void_p),
+                                         n_threads, _ptr(out["x_new"]), _ptr(out["E_star"]), _ptr(out["S"])),
+                   "map_sweep_par")
+        finally:
+            lib._free(ctypes.cast(ro, ctypes.c_void_p))
+            lib._free(ctypes.cast(re, ctypes.c_void_p))
+        return out
+
     def map_sweep_variant(self, L, beta, x, mu, sigma, scope=SCOPE_HOOD, rule=RULE_MIN):
         """One MAP sweep with a Potts scope and a replica rule (G13, G14);
         returns dict with x_new, E_star, S (per hood) and gap (per vertex:
@@ -290,17 +328,22 @@ class Graph:
     def em(self, cfg: EMConfig, x0=None, theta0=None):
         """Full EM loop from the start cfg.init_mode selects (threshold; the
         labels x0; the labels x0 and parameters theta0 [L,4]).  Returns dict
-        with labels, theta [L,4] (n, mu, sigma, U), iters, converged, T_hist."""
+        with labels, theta [L,4] (n, mu, sigma, U), iters, converged, T_hist
+        and stop (which convergence tests held at the last iteration: bit 0 the
+        MAP check over every hood, bit 1 the EM check on the total; 0 when the
+        iteration cap ended the loop)."""
         lib = _get()
         x = np.zeros(self.V, np.uint8) if x0 is None else np.array(x0, dtype=np.uint8)
         th = np.zeros((cfg.n_labels, 4)) if theta0 is None else np.array(theta0, dtype=np.float64).reshape(-1, 4)
         it = ctypes.c_int32(0)
         cv = ctypes.c_int32(0)
+        why = ctypes.c_int32(0)
         Th = np.zeros(cfg.max_iters)
         c = cfg._c()
-        _check(lib.orc_em(self._h, ctypes.byref(c), _ptr(x), _ptr(th), ctypes.byref(it), ctypes.byref(cv), _ptr(Th)),
-               "em")
-        return dict(labels=x, theta=th, iters=int(it.value), converged=int(cv.value), T_hist=Th[:it.value].copy())
+        _check(lib.orc_em_ex(self._h, ctypes.byref(c), _ptr(x), _ptr(th), ctypes.byref(it), ctypes.byref(cv),
+                             _ptr(Th), ctypes.byref(why)), "em")
+        return dict(labels=x, theta=th, iters=int(it.value), converged=int(cv.value), T_hist=Th[:it.value].copy(),
+                    stop=int(why.value))
 
     def pll(self, L, x, mu, sigma, beta):
         """Pseudo-log-likelihood and its gradient: (pll, g_mu[L], g_sigma[L], g_beta)."""
@@ -322,6 +365,41 @@ class Graph:
         x = np.ascontiguousarray(x, dtype=np.uint8)
         _check(_get().orc_label_image(self._h, _ptr(ids), ids.size, _ptr(x), _ptr(out)), "label_image")
         return out
+
+
+def stop_rule(S_seq, T_seq, W=3, tol=1e-4):
+    """The two convergence tests (Section 3.2.2; reading G9) after the last
+    iteration of the given histories, as the EM loop applies them:
+    S_seq [t, C] the hood sums of iterations 1..t, T_seq [t] the totals.
+    Returns (hood_ok, total_ok)."""
+    S = np.ascontiguousarray(S_seq, dtype=np.float64)
+    T = np.ascontiguousarray(T_seq, dtype=np.float64)
+    if S.ndim != 2 or T.shape != (S.shape[0],):
+        raise ValueError("S_seq must be [t, C] and T_seq [t]")
+    h = ctypes.c_int32(0)
+    k = ctypes.c_int32(0)
+    _check(_get().orc_stop_rule(S.shape[0], W, tol, S.shape[1], _ptr(S), _ptr(T), ctypes.byref(h),
+                                ctypes.byref(k)), "stop_rule")
+    return bool(h.value), bool(k.value)
+
+
+def fit_beta(graphs, labels, mu, sigma, beta0=0.2, steps=30, lr=1.0):
+    """Fit of beta by gradient ascent on the summed pseudo-log-likelihood of a
+    batch (reading G11): beta <- max(0, beta + lr * sum_s dPLL_s/dbeta / sum_s
+    V_s), labels and per-slice (mu, sigma) [S, L] fixed.  Returns the
+    trajectory beta_0 .. beta_steps."""
+    lib = _get()
+    n = len(graphs)
+    mu = np.ascontiguousarray(mu, dtype=np.float64)
+    sigma = np.ascontiguousarray(sigma, dtype=np.float64)
+    L = mu.shape[1]
+    GP = ctypes.POINTER(_Graph)
+    gs = (GP * n)(*[g._h for g in graphs])
+    xs_np = [np.ascontiguousarray(x, dtype=np.uint8) for x in labels]
+    xs = (ctypes.c_void_p * n)(*[x.ctypes.data for x in xs_np])
+    traj = np.zeros(steps + 1)
+    _check(lib.orc_fit_beta(gs, n, L, xs, _ptr(mu), _ptr(sigma), beta0, steps, lr, _ptr(traj)), "fit_beta")
+    return traj
 
 
 def replicate(hood_off, hood, L):

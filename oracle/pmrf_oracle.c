@@ -9,8 +9,8 @@
  * library shares no code, header or table with it.
  *
  * Every function follows one passage of the paper; where the paper is silent
- * the reading used is stated at the function (labelled G1..G11; the same labels
- * are used in the design notes).  Floating point is IEEE double throughout,
+ * the reading used is stated at the function (labelled G1..G16).  Floating
+ * point is IEEE double throughout,
  * evaluated in the order written (no reassociation: build with -O2 and without
  * -ffast-math).
  *
@@ -19,6 +19,9 @@
  * (n_l, mu_l, sigma_l, U_l).
  */
 #include <math.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -51,6 +54,7 @@ typedef struct {
     int32_t replica_rule; /* ORC_RULE_MIN (G6), ORC_RULE_SUM or ORC_RULE_VOTE */
     int32_t init_mode;    /* 0 threshold (G3), 1 labels given in x, 2 labels in x and parameters in theta */
     double beta, conv_tol, sigma_min, init_lo, init_hi;
+    int32_t n_threads;    /* > 1: the default sweep runs on that many threads (orc_map_sweep_par) */
 } orc_config;
 
 /* Variants of the energy and of the replica reduction (readings G13, G14). */
@@ -662,9 +666,9 @@ int orc_map_sweep(const orc_graph* g, int32_t L, double beta, const uint8_t* x, 
 }
 
 /*
- * The MAP sweep with the variants of the scope table's NEXT list: the Potts
- * penalty's scope and the rule that turns the replicas' decisions into one
- * label per vertex.  Readings (ours; the paper fixes neither):
+ * The MAP sweep with two variants of the reading above: the Potts penalty's
+ * scope and the rule that turns the replicas' decisions into one label per
+ * vertex.  Readings (ours; the paper fixes neither):
  *
  * G13 scope: ORC_SCOPE_HOOD counts the neighbours of v inside hood c (G4);
  *     ORC_SCOPE_FULL counts every neighbour of v, so all replicas of v carry
@@ -804,6 +808,94 @@ int orc_map_sweep_v(const orc_graph* g, int32_t L, double beta, int32_t scope, i
 
 /* ------------------------------------------------------------------------ */
 /*
+ * Multi-core form of the default sweep (hood scope G4, least-energy replica
+ * G6), the analogue of the paper's multi-core CPU runs (Section 4.3.4, Table 1):
+ * the hoods are split over n_threads OpenMP threads.  Each hood's element
+ * energies, argmins and sum are computed by the same statements, in the same
+ * order, as orc_map_sweep_v computes them, and each vertex then takes the
+ * lexicographic minimum of (Emin(c,v), lab(c,v)) over its replicas, which does
+ * not depend on the order the replicas are visited: the outputs are identical
+ * to orc_map_sweep_v's (scope ORC_SCOPE_HOOD, rule ORC_RULE_MIN).  rep_off /
+ * rep_el: the elements of each vertex (orc_replica_lists).  Serial when the
+ * library is built without OpenMP.
+ */
+int orc_replica_lists(const orc_graph* g, int64_t** rep_off, int64_t** rep_el) {
+    if (!g || !rep_off || !rep_el) return ORC_ERR_ARG;
+    const int32_t V = g->V;
+    int64_t* off = (int64_t*)calloc((size_t)V + 1, sizeof(int64_t));
+    int64_t* el = (int64_t*)malloc(sizeof(int64_t) * ((size_t)g->N_el + 1));
+    int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * ((size_t)V + 1));
+    if (!off || !el || !cur) { free(off); free(el); free(cur); return ORC_ERR_OOM; }
+    for (int64_t e = 0; e < g->N_el; ++e) off[g->hood[e] + 1] += 1;
+    for (int32_t v = 0; v < V; ++v) off[v + 1] += off[v];
+    for (int32_t v = 0; v < V; ++v) cur[v] = off[v];
+    for (int64_t e = 0; e < g->N_el; ++e) el[cur[g->hood[e]]++] = e;
+    free(cur);
+    *rep_off = off;
+    *rep_el = el;
+    return ORC_OK;
+}
+
+int orc_map_sweep_par(const orc_graph* g, int32_t L, double beta, const uint8_t* x, const double* mu,
+                      const double* sigma, const int64_t* rep_off, const int64_t* rep_el, int32_t n_threads,
+                      uint8_t* x_new, double* E_star, double* S_hood) {
+    if (!g || L < 1 || L > 255 || !rep_off || !rep_el || n_threads < 1) return ORC_ERR_ARG;
+    double* Emin_el = (double*)malloc(sizeof(double) * ((size_t)g->N_el + 1));
+    int32_t* lab_el = (int32_t*)malloc(sizeof(int32_t) * ((size_t)g->N_el + 1));
+    if (!Emin_el || !lab_el) { free(Emin_el); free(lab_el); return ORC_ERR_OOM; }
+    int oom = 0;
+#pragma omp parallel num_threads(n_threads)
+    {
+        double* E = (double*)malloc(sizeof(double) * (size_t)L);
+        if (!E) {
+#pragma omp atomic write
+            oom = 1;
+        }
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t c = 0; c < g->C; ++c) {
+            if (!E) continue;
+            const int32_t* Hc = g->hood + g->hood_off[c];
+            const int64_t nH = g->hood_off[c + 1] - g->hood_off[c];
+            double S = 0.0;
+            for (int64_t i = 0; i < nH; ++i) {
+                const int32_t v = Hc[i];
+                int32_t lab = 0;
+                for (int32_t l = 0; l < L; ++l) {
+                    int64_t m = 0;
+                    for (int64_t j = g->adj_off[v]; j < g->adj_off[v + 1]; ++j) {
+                        int32_t u = g->adj[j];
+                        if (contains(Hc, nH, u) && x[u] != l) ++m;
+                    }
+                    E[l] = data_term(g->y[v], mu[l], sigma[l]) + beta * (double)m;
+                    if (E[l] < E[lab]) lab = l;
+                }
+                Emin_el[g->hood_off[c] + i] = E[lab];
+                lab_el[g->hood_off[c] + i] = lab;
+                S += E[lab];
+            }
+            if (S_hood) S_hood[c] = S;
+        }
+        free(E);
+    }
+    if (oom) { free(Emin_el); free(lab_el); return ORC_ERR_OOM; }
+#pragma omp parallel for num_threads(n_threads) schedule(static)
+    for (int32_t v = 0; v < g->V; ++v) {
+        double bE = INFINITY;
+        int32_t bl = -1;
+        for (int64_t k = rep_off[v]; k < rep_off[v + 1]; ++k) {
+            const double e = Emin_el[rep_el[k]];
+            const int32_t l = lab_el[rep_el[k]];
+            if (e < bE || (e == bE && l < bl)) { bE = e; bl = l; }
+        }
+        if (x_new) x_new[v] = (uint8_t)bl;
+        if (E_star) E_star[v] = bE;
+    }
+    free(Emin_el); free(lab_el);
+    return ORC_OK;
+}
+
+/* ------------------------------------------------------------------------ */
+/*
  * Parameter update (Section 3.2.2, EM step 4, "Update Parameters": mu and sigma
  * of each label from the intensities of the vertices carrying that label, plus
  * the per-label sums of the vertex energies).  Readings (G8): moments over
@@ -880,6 +972,63 @@ int orc_init_params(const orc_graph* g, int32_t L, double lo, double hi, double 
 
 /* ------------------------------------------------------------------------ */
 /*
+ * The two convergence tests of Section 3.2.2 after iteration t (reading G9),
+ * on rings of the last W+1 hood sums (Shist, C entries per slot) and totals
+ * (Thist), slot t % (W+1) holding iteration t:
+ *   MAP convergence check: every hood c has t > W and
+ *       max_{k=1..W} |S^t_c - S^{t-k}_c| < tol            -> *hood_ok = 1
+ *   EM convergence check:  t > W and
+ *       max_{k=1..W} |T^t - T^{t-k}| < tol                 -> *total_ok = 1
+ * ("the change over the previous W iterations" read as the largest absolute
+ * difference against each of them).
+ */
+static void stop_tests(int32_t t, int32_t W, double tol, int64_t C, const double* Shist, const double* Thist,
+                       int32_t* hood_ok, int32_t* total_ok) {
+    *hood_ok = 0;
+    *total_ok = 0;
+    if (t <= W) return;
+    const double* S = Shist + (size_t)(t % (W + 1)) * (size_t)C;
+    int32_t all = 1;
+    for (int64_t c = 0; c < C && all; ++c) {
+        double dmax = 0.0;
+        for (int32_t k = 1; k <= W; ++k) {
+            double d = fabs(S[c] - Shist[(size_t)((t - k) % (W + 1)) * (size_t)C + (size_t)c]);
+            if (d > dmax) dmax = d;
+        }
+        if (!(dmax < tol)) all = 0;
+    }
+    const double T = Thist[t % (W + 1)];
+    double dT = 0.0;
+    for (int32_t k = 1; k <= W; ++k) {
+        double d = fabs(T - Thist[(t - k) % (W + 1)]);
+        if (d > dT) dT = d;
+    }
+    *hood_ok = all;
+    *total_ok = dT < tol ? 1 : 0;
+}
+
+/*
+ * The convergence tests of stop_tests on given histories: S_seq [t][C] holds
+ * S^1 .. S^t (row k-1 = iteration k), T_seq [t] holds T^1 .. T^t; the tests
+ * are evaluated after iteration t, exactly as the EM loop evaluates them.
+ */
+int orc_stop_rule(int32_t t, int32_t W, double tol, int64_t C, const double* S_seq, const double* T_seq,
+                  int32_t* hood_ok, int32_t* total_ok) {
+    if (t < 1 || W < 1 || C < 0 || !S_seq || !T_seq || !hood_ok || !total_ok) return ORC_ERR_ARG;
+    double* Shist = (double*)calloc((size_t)(W + 1) * (size_t)(C > 0 ? C : 1), sizeof(double));
+    double* Thist = (double*)calloc((size_t)(W + 1), sizeof(double));
+    if (!Shist || !Thist) { free(Shist); free(Thist); return ORC_ERR_OOM; }
+    for (int32_t k = (t - W > 1 ? t - W : 1); k <= t; ++k) {
+        memcpy(Shist + (size_t)(k % (W + 1)) * (size_t)C, S_seq + (size_t)(k - 1) * (size_t)C,
+               sizeof(double) * (size_t)C);
+        Thist[k % (W + 1)] = T_seq[k - 1];
+    }
+    stop_tests(t, W, tol, C, Shist, Thist, hood_ok, total_ok);
+    free(Shist); free(Thist);
+    return ORC_OK;
+}
+
+/*
  * The EM loop (Algorithm 2, steps 6-11; Section 3.2.2, EM steps 2-5), with the
  * sweep variant cfg->potts_scope / cfg->replica_rule (G13, G14).  The start
  * (Algorithm 2 step 3): cfg->init_mode 0 thresholds the region means (G3);
@@ -890,17 +1039,18 @@ int orc_init_params(const orc_graph* g, int32_t L, double lo, double hi, double 
  *   for t = 1, 2, ...:
  *     (x^t, E*, S^t) = sweep(x^{t-1}, theta^{t-1});  theta^t = params(x^t, E*)
  *     T^t = sum_c S^t_c (ascending c)
- *     hood c converged at t  <=>  t > W and max_{k=1..W} |S^t_c - S^{t-k}_c| < tol
- *     stop when every hood converged (MAP convergence check), or when t > W and
- *     max_{k=1..W} |T^t - T^{t-k}| < tol (EM convergence check), or t = max_iters.
- * Readings (G9): "change over the previous W iterations" is the largest
- * absolute difference against each of them; either test ends the loop.
+ *     stop when the MAP convergence check (every hood converged) or the EM
+ *     convergence check (the total) holds (stop_tests), or t = max_iters.
+ * Either test ends the loop (G9).  With cfg->n_threads > 1 the default sweep
+ * runs on that many threads (orc_map_sweep_par: identical results).
  * Outputs: x = x^t, theta = theta^t, *iters = t, *converged = 1 when a
  * convergence test (not the cap) ended the loop; T_hist[t-1] = T^t (optional,
- * length max_iters).  V == 0 returns at once with iters 0, converged 1.
+ * length max_iters); *reason (optional): which tests held at the last
+ * iteration, bit 0 the MAP (hood) check, bit 1 the EM (total) check, 0 when the
+ * cap ended the loop.  V == 0 returns at once with iters 0, converged 1.
  */
-int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta, int32_t* iters, int32_t* converged,
-           double* T_hist) {
+int orc_em_ex(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta, int32_t* iters,
+              int32_t* converged, double* T_hist, int32_t* reason) {
     if (!g || !cfg || cfg->n_labels < 1 || cfg->max_iters < 1 || cfg->conv_window < 1) return ORC_ERR_ARG;
     if (cfg->potts_scope < 0 || cfg->potts_scope > 1 || cfg->replica_rule < 0 || cfg->replica_rule > 2)
         return ORC_ERR_ARG;
@@ -920,6 +1070,7 @@ int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta,
         }
     if (rc) return rc;
     *iters = 0; *converged = 1;
+    if (reason) *reason = 0;
     if (V == 0) return ORC_OK;
     double* Shist = (double*)malloc(sizeof(double) * (size_t)((W + 1) * C + 1)); /* ring of W+1 */
     double* Thist = (double*)malloc(sizeof(double) * (size_t)(W + 1));
@@ -928,12 +1079,18 @@ int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta,
     double* mu = (double*)malloc(sizeof(double) * (size_t)L);
     double* sg = (double*)malloc(sizeof(double) * (size_t)L);
     double* th2 = (double*)malloc(sizeof(double) * 4 * (size_t)L);
+    int64_t *rep_off = NULL, *rep_el = NULL;
+    const int par = cfg->n_threads > 1 && cfg->potts_scope == ORC_SCOPE_HOOD && cfg->replica_rule == ORC_RULE_MIN;
     if (!Shist || !Thist || !xn || !Es || !mu || !sg || !th2) { rc = ORC_ERR_OOM; goto done; }
+    if (par && (rc = orc_replica_lists(g, &rep_off, &rep_el)) != ORC_OK) goto done;
     *converged = 0;
     for (int32_t t = 1; t <= cfg->max_iters; ++t) {
         for (int32_t l = 0; l < L; ++l) { mu[l] = theta[4 * l + 1]; sg[l] = theta[4 * l + 2]; }
         double* S = Shist + (size_t)(t % (W + 1)) * (size_t)C;
-        rc = orc_map_sweep_v(g, L, cfg->beta, cfg->potts_scope, cfg->replica_rule, x, mu, sg, xn, Es, S, NULL);
+        if (par)
+            rc = orc_map_sweep_par(g, L, cfg->beta, x, mu, sg, rep_off, rep_el, cfg->n_threads, xn, Es, S);
+        else
+            rc = orc_map_sweep_v(g, L, cfg->beta, cfg->potts_scope, cfg->replica_rule, x, mu, sg, xn, Es, S, NULL);
         if (rc) goto done;
         memcpy(x, xn, (size_t)V);
         rc = orc_params(g, L, x, Es, theta, cfg->sigma_min, th2);
@@ -944,27 +1101,22 @@ int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta,
         Thist[t % (W + 1)] = T;
         if (T_hist) T_hist[t - 1] = T;
         *iters = t;
-        if (t > W) {
-            int all = 1;
-            for (int64_t c = 0; c < C && all; ++c) {
-                double dmax = 0.0;
-                for (int32_t k = 1; k <= W; ++k) {
-                    double d = fabs(S[c] - Shist[(size_t)((t - k) % (W + 1)) * (size_t)C + (size_t)c]);
-                    if (d > dmax) dmax = d;
-                }
-                if (!(dmax < cfg->conv_tol)) all = 0;
-            }
-            double dT = 0.0;
-            for (int32_t k = 1; k <= W; ++k) {
-                double d = fabs(T - Thist[(t - k) % (W + 1)]);
-                if (d > dT) dT = d;
-            }
-            if (all || dT < cfg->conv_tol) { *converged = 1; break; }
+        int32_t hood_ok = 0, total_ok = 0;
+        stop_tests(t, W, cfg->conv_tol, C, Shist, Thist, &hood_ok, &total_ok);
+        if (hood_ok || total_ok) {
+            *converged = 1;
+            if (reason) *reason = hood_ok | (total_ok << 1);
+            break;
         }
     }
 done:
-    free(Shist); free(Thist); free(xn); free(Es); free(mu); free(sg); free(th2);
+    free(Shist); free(Thist); free(xn); free(Es); free(mu); free(sg); free(th2); free(rep_off); free(rep_el);
     return rc;
+}
+
+int orc_em(const orc_graph* g, const orc_config* cfg, uint8_t* x, double* theta, int32_t* iters, int32_t* converged,
+           double* T_hist) {
+    return orc_em_ex(g, cfg, x, theta, iters, converged, T_hist, NULL);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -1019,6 +1171,42 @@ int orc_pll(const orc_graph* g, int32_t L, const uint8_t* x, const double* mu, c
     if (pll) *pll = acc;
     if (g_beta) *g_beta = gb;
     free(E); free(p); free(m);
+    return ORC_OK;
+}
+
+/*
+ * Fit of the Potts weight beta by gradient ascent on the summed vertex
+ * pseudo-log-likelihood of a batch of n slices (reading G11, beside the
+ * paper): labels and every slice's (mu, sigma) held fixed,
+ *   beta_{k+1} = max(0, beta_k + lr * (1 / sum_s V_s) * sum_s dPLL_s/dbeta (beta_k))
+ * for k = 0 .. steps-1, the slices' derivatives (orc_pll) summed in ascending
+ * s.  gs[s], xs[s]: graph and labels of slice s; mu, sigma [n][L].
+ * traj [steps+1] receives beta_0 .. beta_steps.
+ */
+int orc_fit_beta(const orc_graph* const* gs, int32_t n, int32_t L, const uint8_t* const* xs, const double* mu,
+                 const double* sigma, double beta0, int32_t steps, double lr, double* traj) {
+    if (!gs || !xs || !mu || !sigma || !traj || n < 1 || L < 1 || steps < 0) return ORC_ERR_ARG;
+    int64_t Vtot = 0;
+    for (int32_t s = 0; s < n; ++s) {
+        if (!gs[s] || !xs[s]) return ORC_ERR_ARG;
+        Vtot += gs[s]->V;
+    }
+    if (Vtot < 1) Vtot = 1;
+    double beta = beta0;
+    traj[0] = beta;
+    for (int32_t k = 0; k < steps; ++k) {
+        double gsum = 0.0;
+        for (int32_t s = 0; s < n; ++s) {
+            double gb = 0.0;
+            int rc = orc_pll(gs[s], L, xs[s], mu + (size_t)s * (size_t)L, sigma + (size_t)s * (size_t)L, beta, NULL,
+                             NULL, NULL, &gb);
+            if (rc) return rc;
+            gsum += gb;
+        }
+        beta = beta + lr * (gsum / (double)Vtot);
+        if (beta < 0.0) beta = 0.0;
+        traj[k + 1] = beta;
+    }
     return ORC_OK;
 }
 

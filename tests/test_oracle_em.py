@@ -295,3 +295,213 @@ def test_pll_is_concave_in_beta():
     bs = np.linspace(0.0, 3.0, 13)
     f = np.array([g.pll(2, x, th[:, 1], th[:, 2], b)[0] for b in bs])
     assert (np.diff(f, 2) <= 1e-9).all()
+
+
+# --------------------------------------------------------------------------
+# the two convergence tests of Section 3.2.2 (reading G9), on hand-written
+# histories and on two hand-derived EM runs
+
+TAU = 1e-4
+
+
+def test_stop_rule_total_test_alone():
+    # two hoods move by +-1 every iteration in opposite directions; the total
+    # does not move: only the EM (total) check holds
+    S = [[0.0, 0.0], [1.0, -1.0], [0.0, 0.0], [1.0, -1.0]]
+    T = [0.0, 0.0, 0.0, 0.0]
+    assert oracle.stop_rule(S, T) == (False, True)
+
+
+def test_stop_rule_hood_test_alone():
+    # three hoods each move by 0.6 tau (below tau) at the last iteration: their
+    # total moves by 1.8 tau: only the MAP (hood) check holds
+    d = 0.6 * TAU
+    S = [[0.0] * 3, [0.0] * 3, [0.0] * 3, [d] * 3]
+    T = [0.0, 0.0, 0.0, 3 * d]
+    assert oracle.stop_rule(S, T) == (True, False)
+
+
+def test_stop_rule_compares_every_iteration_of_the_window():
+    # constant for the last two iterations only: k = 1 and 2 agree, k = 3
+    # does not, so neither check holds at t = 4; one iteration later both do
+    assert oracle.stop_rule([[5.0], [7.0], [7.0], [7.0]], [10.0, 20.0, 20.0, 20.0]) == (False, False)
+    assert oracle.stop_rule([[5.0], [7.0], [7.0], [7.0], [7.0]], [10.0, 20.0, 20.0, 20.0, 20.0]) == (True, True)
+    # a change at k = 2 only
+    assert oracle.stop_rule([[7.0], [7.0], [5.0], [7.0]], [7.0, 7.0, 5.0, 7.0]) == (False, False)
+    # the window W sets how far back: with W = 1 only the last change counts
+    assert oracle.stop_rule([[5.0], [7.0], [7.0]], [5.0, 7.0, 7.0], W=1) == (True, True)
+    assert oracle.stop_rule([[5.0], [7.0], [7.0]], [5.0, 7.0, 7.0], W=2) == (False, False)
+
+
+def test_stop_rule_needs_more_than_window_iterations():
+    S = [[1.0, 2.0]] * 3
+    T = [3.0] * 3
+    assert oracle.stop_rule(S, T) == (False, False)  # t = W
+    assert oracle.stop_rule(S + [[1.0, 2.0]], T + [3.0]) == (True, True)  # t = W + 1
+
+
+def test_stop_rule_is_strict_and_absolute():
+    # a change of exactly tol is not below it
+    assert oracle.stop_rule([[0.0], [0.0], [0.0], [0.5]], [0.0, 0.0, 0.0, 0.5], tol=0.5) == (False, False)
+    assert oracle.stop_rule([[0.0], [0.0], [0.0], [0.25]], [0.0, 0.0, 0.0, 0.25], tol=0.5) == (True, True)
+    # absolute, not relative: a change of 1 on a value of 1e6 fails tau = 1e-4
+    big = 1e6
+    assert oracle.stop_rule([[big]] * 3 + [[big + 1.0]], [big] * 3 + [big + 1.0]) == (False, False)
+
+
+def _anchored_pairs(two_components):
+    """Hand-derived EM runs (adjacency given directly).  Vertices: f0 (y 0.00,
+    isolated), a1 (0.55) - a2 (0.45) an edge, [b1 (0.55) - b2 (0.45) an edge],
+    f1 (1.00, isolated).  Hoods: {f0}, {a1, a2}, [{b1, b2}], {f1}."""
+    if two_components:
+        y = [0.0, 0.55, 0.45, 0.55, 0.45, 1.0]
+        nb = [[], [2], [1], [4], [3], []]
+    else:
+        y = [0.0, 0.55, 0.45, 1.0]
+        nb = [[], [2], [1], []]
+    return oracle.Graph.from_adjacency(np.array(y), nb)
+
+
+def test_em_total_test_alone_ends_a_symmetric_two_cycle():
+    # Start x = (f0, a1, a2, b1, b2, f1) = (0, 0, 1, 1, 0, 1): label 0 holds
+    # {0, 0.55, 0.45} and label 1 {0.45, 0.55, 1}, so mu = (1/3, 2/3) and the
+    # two sigmas are equal (mirror sets).  At y = 0.55 the data terms differ by
+    # D_0 - D_1 = ((0.55 - 1/3)^2 - (0.55 - 2/3)^2) / (2 sigma^2) = 0.291 (and the
+    # opposite at 0.45), less than beta = 1: each pair member takes the label
+    # its partner holds, so both pairs swap every iteration, and the swapped
+    # state has the same label sets, so theta never changes.  Hood {a1, a2}
+    # alternates between D_1(0.55) + D_0(0.45) and D_0(0.55) + D_1(0.45) (apart
+    # by 0.58 > tau), hood {b1, b2} does the opposite, the total is constant:
+    # only the EM check can stop the loop, first at t = W + 1 = 4.
+    g = _anchored_pairs(True)
+    x0 = np.array([0, 0, 1, 1, 0, 1], np.uint8)
+    cfg = oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20, init_mode=1)
+    r = g.em(cfg, x0=x0)
+    assert r["iters"] == 4 and r["converged"] == 1 and r["stop"] == 2
+    assert r["labels"].tolist() == x0.tolist()  # four swaps
+    var = (1 / 9 + (0.55 - 1 / 3) ** 2 + (0.45 - 1 / 3) ** 2) / 3
+    assert np.allclose(r["theta"][:, 1], [1 / 3, 2 / 3], rtol=0, atol=1e-15)
+    assert np.allclose(r["theta"][:, 2], [math.sqrt(var)] * 2, rtol=1e-14, atol=0)
+    assert np.ptp(r["T_hist"]) < 1e-12
+    # without the total test the hoods never settle: the run ends at the cap
+    no_total = g.em(oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20, init_mode=1, conv_tol=0.0), x0=x0)
+    assert no_total["iters"] == 20 and no_total["converged"] == 0
+    # the hood sums really alternate by more than tau
+    s1 = g.map_sweep(2, 1.0, x0, r["theta"][:, 1], r["theta"][:, 2])["S"]
+    x1 = np.array([0, 1, 0, 0, 1, 1], np.uint8)
+    s2 = g.map_sweep(2, 1.0, x1, r["theta"][:, 1], r["theta"][:, 2])["S"]
+    assert abs(s1[1] - s2[1]) > 0.5 and abs(s1[2] - s2[2]) > 0.5 and abs(s1[1] - s2[2]) < 1e-12
+
+
+def test_em_window_reaches_back_w_iterations():
+    # One pair only: x0 = (f0, a1, a2, f1) = (0, 0, 1, 1): mu = (0.275, 0.725),
+    # sigma = (0.275, 0.275).  Sweep 1: a1 (0.55) -> 1 and a2 (0.45) -> 0 on the
+    # data term alone.  Then mu = (0.225, 0.775), sigma = 0.225, and at y =
+    # 0.55 the data terms differ by D_0 - D_1 = (0.325^2 - 0.225^2) / (2 0.225^2)
+    # = 0.543 > beta = 0.2, so the labels (0, 1, 0, 1) never change again: the
+    # sums of iterations 2, 3, ... are equal and those of iteration 1 differ.
+    # Both checks compare against W = 3 earlier iterations, so they first hold
+    # at t = 5 (at t = 4 the window still reaches iteration 1).
+    g = _anchored_pairs(False)
+    x0 = np.array([0, 0, 1, 1], np.uint8)
+    r = g.em(oracle.EMConfig(n_labels=2, beta=0.2, max_iters=20, init_mode=1), x0=x0)
+    assert r["labels"].tolist() == [0, 1, 0, 1]
+    assert r["iters"] == 5 and r["converged"] == 1 and r["stop"] == 3
+    assert np.allclose(r["theta"][:, 1], [0.225, 0.775], rtol=0, atol=1e-15)
+    assert np.allclose(r["theta"][:, 2], [0.225, 0.225], rtol=1e-14, atol=0)
+    T = r["T_hist"]
+    assert abs(T[0] - T[1]) > 0.1 and T[1] == T[2] == T[3] == T[4]
+    # with a window of 1 the same run stops at t = 3 (first t > W with an
+    # unchanged predecessor)
+    r1 = g.em(oracle.EMConfig(n_labels=2, beta=0.2, max_iters=20, init_mode=1, conv_window=1), x0=x0)
+    assert r1["iters"] == 3 and r1["stop"] == 3
+
+
+# --------------------------------------------------------------------------
+# beta fit (reading G11): gradient ascent on the summed pseudo-log-likelihood
+
+def _fit_batch(seeds=(31, 32), L=2):
+    gs, xs, mus, sgs = [], [], [], []
+    for sd in seeds:
+        g, x, th = _pll_setup(seed=sd, L=L)
+        gs.append(g)
+        xs.append(x)
+        mus.append(th[:, 1])
+        sgs.append(th[:, 2])
+    return gs, xs, np.array(mus), np.array(sgs)
+
+
+def _pll_total(gs, xs, mu, sg, b):
+    return sum(g.pll(mu.shape[1], x, m, s, b)[0] for g, x, m, s in zip(gs, xs, mu, sg))
+
+
+def test_fit_beta_first_step_is_the_scaled_derivative():
+    gs, xs, mu, sg = _fit_batch()
+    V = sum(g.V for g in gs)
+    traj = oracle.fit_beta(gs, xs, mu, sg, beta0=0.2, steps=1, lr=1.0)
+    h = 1e-6
+    fd = (_pll_total(gs, xs, mu, sg, 0.2 + h) - _pll_total(gs, xs, mu, sg, 0.2 - h)) / (2 * h)
+    assert traj[0] == 0.2
+    assert abs(traj[1] - (0.2 + fd / V)) <= 1e-7
+    traj2 = oracle.fit_beta(gs, xs, mu, sg, beta0=0.2, steps=1, lr=0.5)
+    assert abs((traj2[1] - 0.2) - 0.5 * (traj[1] - 0.2)) <= 1e-15
+
+
+def test_fit_beta_climbs_to_the_maximiser():
+    from scipy.optimize import minimize_scalar
+    gs, xs, mu, sg = _fit_batch()
+    # a larger step than the default so that 300 steps reach the maximiser
+    traj = oracle.fit_beta(gs, xs, mu, sg, beta0=0.2, steps=300, lr=20.0)
+    f = [_pll_total(gs, xs, mu, sg, b) for b in traj[:31]]
+    assert all(b2 >= b1 - 1e-9 for b1, b2 in zip(f, f[1:]))  # ascent
+    best = minimize_scalar(lambda b: -_pll_total(gs, xs, mu, sg, b), bounds=(0.0, 20.0), method="bounded",
+                           options=dict(xatol=1e-10))
+    assert abs(traj[-1] - best.x) <= 1e-6
+
+
+def test_fit_beta_normalises_by_the_batch_size():
+    # a batch of two copies of one slice has twice the derivative and twice
+    # the vertices: the same trajectory as the slice alone
+    gs, xs, mu, sg = _fit_batch(seeds=(31,))
+    one = oracle.fit_beta(gs, xs, mu, sg, steps=10)
+    two = oracle.fit_beta(gs * 2, xs * 2, np.vstack([mu, mu]), np.vstack([sg, sg]), steps=10)
+    assert np.allclose(one, two, rtol=1e-13, atol=0)
+
+
+def test_fit_beta_stops_at_zero():
+    # labels that disagree with every neighbour: the likelihood grows as beta
+    # falls, so the ascent reaches the bound beta = 0 and stays there
+    g = oracle.Graph.from_adjacency(np.array([0.4, 0.6, 0.4, 0.6]), [[1], [0, 2], [1, 3], [2]])
+    x = np.array([0, 1, 0, 1], np.uint8)
+    mu, sg = np.array([[0.45, 0.55]]), np.array([[0.2, 0.2]])
+    assert g.pll(2, x, mu[0], sg[0], 0.2)[3] < 0
+    traj = oracle.fit_beta([g], [x], mu, sg, beta0=0.2, steps=50, lr=1.0)
+    assert traj[-1] == 0.0 and (np.diff(traj) <= 0).all()
+
+
+# --------------------------------------------------------------------------
+# the multi-core sweep gives the serial sweep's results exactly
+
+@pytest.mark.parametrize("L", [2, 3])
+def test_parallel_sweep_equals_serial(L):
+    sp = synth.scaled(synth.workload("slice256").slices[0], 120, 100, seed=77)
+    s = synth.make_slice(sp)
+    g = oracle.Graph.from_image(s.image, s.region_ids)
+    rng = np.random.default_rng(L)
+    x = rng.integers(0, L, g.V).astype(np.uint8)
+    mu, sg = np.sort(rng.random(L)), rng.uniform(0.05, 0.3, L)
+    a = g.map_sweep(L, 0.9, x, mu, sg)
+    b = g.map_sweep_par(L, 0.9, x, mu, sg, n_threads=4)
+    assert np.array_equal(a["x_new"], b["x_new"])
+    assert np.array_equal(a["E_star"], b["E_star"]) and np.array_equal(a["S"], b["S"])
+
+
+def test_parallel_em_equals_serial():
+    sp = synth.scaled(synth.workload("slice256").slices[0], 96, 112, seed=78)
+    s = synth.make_slice(sp)
+    g = oracle.Graph.from_image(s.image, s.region_ids)
+    a = g.em(oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20))
+    b = g.em(oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20, n_threads=4))
+    assert a["iters"] == b["iters"] and a["stop"] == b["stop"]
+    assert np.array_equal(a["labels"], b["labels"]) and np.array_equal(a["theta"], b["theta"])
+    assert np.array_equal(a["T_hist"], b["T_hist"])
