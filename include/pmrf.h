@@ -376,18 +376,22 @@ PMRF_API int pmrf_pll_value_and_grad(pmrf_graph* g, int32_t n_labels, const uint
  * Same inputs, outputs and results as pmrf_pll_grad, but it allocates no
  * memory: no cudaMalloc, no stream-ordered allocation, no host allocation on
  * the device's behalf.  It is meant for callers that cannot allocate when they
- * need the gradient -- for example code issuing work while a stream is being
- * captured into a CUDA graph, or an application whose device memory is held by
- * its own allocator -- once the graph itself has been built.
+ * need the gradient, once the graph itself has been built: an application
+ * whose device memory is already claimed by its own caching allocator (a new
+ * allocation would fail, or force that allocator to give memory back), or a
+ * latency-critical loop that must not pay for, or be implicitly synchronised
+ * by, an allocation.
  *   Scratch: the per-block partial sums go to one fixed array inside the
  *   library, PMRF_PLL_NOALLOC_MAX_DOUBLES doubles (8 MiB), which every GPU that
  *   loads the library keeps until the process exits.  A call needs
  *   S * ceil(V_max / 256) * (2 * n_labels + 2) + S doubles (S slices, V_max the
  *   regions of the largest slice); a larger request fails with
- *   PMRF_ERR_UNSUPPORTED and a message giving the size.
- *   Set-up: the first call on a device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call
- *   before any stream capture.
+ *   PMRF_ERR_UNSUPPORTED and a message giving the size, before any work is
+ *   enqueued.
+ *   Set-up: every call looks up the array's device address
+ *   (cudaGetSymbolAddress) with the caller's device current; the first call on
+ *   a device also loads the library's device code there, so make that first
+ *   call before any stream capture.  A device reset between calls is handled.
  *   Sharing: all calls use the same array.  Each call writes every entry it
  *   reads, so earlier calls leave nothing behind that matters, but calls whose
  *   work overlaps on the GPU (different streams or threads) race on the array;

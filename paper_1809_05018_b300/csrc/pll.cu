@@ -9,7 +9,6 @@
 // One pass over the vertices writes per-block partial sums (deterministic
 // order); a per-slice pass adds them in block order.
 #include <algorithm>
-#include <mutex>
 #include <string>
 
 #include "graph.cuh"
@@ -235,19 +234,22 @@ int export_rep_hood(pmrf_graph* g, int32_t* dst, cudaStream_t s) {
 // Allocation-free adjoint (pmrf_pll_grad_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need the
-// gradient: code running while a stream is being captured into a CUDA graph
-// (allocation calls are not allowed there), code inside a host callback, or an
-// application whose memory is fully claimed by its own pool allocator.  For
-// them the adjoint's per-block partial sums live in the fixed array below,
-// which is part of the loaded module: every GPU that loads this library holds
-// PMRF_PLL_NOALLOC_MAX_DOUBLES doubles (8 MiB) of it until the process exits.
+// gradient: an application whose device memory is already claimed by its own
+// caching allocator (a cudaMalloc would fail, or force that allocator to give
+// memory back), or a latency-critical loop that must not pay for, or be
+// implicitly synchronised by, an allocation.  For them the adjoint's per-block
+// partial sums live in the fixed array below, which is part of the loaded
+// module: every GPU that loads this library holds PMRF_PLL_NOALLOC_MAX_DOUBLES
+// doubles (8 MiB) of it until the process exits.
 //
 // The array's name is only a stand-in in host code; its device address is
-// looked up with cudaGetSymbolAddress once per device (with that device
-// current), on the first call made on that device.  Every call shares the
-// array, so calls whose work overlaps on the GPU (other streams, other host
-// threads) race on it and must be ordered by the caller.  Each call writes
-// every entry it later reads, so nothing left by an earlier call is used.
+// obtained with cudaGetSymbolAddress, with the caller's device current, on
+// every call (after the first call on a device has loaded the module this is a
+// lookup, and it stays right if the caller resets the device between calls).
+// Every call shares the array, so calls whose work overlaps on the GPU (other
+// streams, other host threads) race on it and must be ordered by the caller.
+// Each call writes every entry it later reads, so nothing left by an earlier
+// call is used.
 
 static __device__ __align__(256) double pmrf_pll_noalloc_scratch[PMRF_PLL_NOALLOC_MAX_DOUBLES];
 
@@ -255,22 +257,11 @@ namespace pmrf {
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_noalloc_mu;
-double* g_noalloc_ptr[kMaxDevices] = {};
-
 int noalloc_scratch(double** out) {
-    int dev = -1;
-    PMRF_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return fail(PMRF_ERR_UNSUPPORTED, "device index beyond 63");
-    std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, pmrf_pll_noalloc_scratch);
-        if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(pmrf_pll_noalloc_scratch)");
-        g_noalloc_ptr[dev] = (double*)p;
-    }
-    *out = g_noalloc_ptr[dev];
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, pmrf_pll_noalloc_scratch);
+    if (e != cudaSuccess || !p) return cuda_fail(e, "cudaGetSymbolAddress(pmrf_pll_noalloc_scratch)");
+    *out = (double*)p;
     return PMRF_OK;
 }
 
