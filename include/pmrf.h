@@ -438,20 +438,18 @@ PMRF_API int pmrf_quality(pmrf_graph* g, int32_t n_labels, const uint8_t* d_pred
 
 PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* detail);
 
-/* Tile sizes of the EM launches.  0 selects the autotuned / default value.
- * hood_tile: hood elements per tile window (multiple of 32, 128..1248; a tile
- * holds the hoods starting in its window and takes the fast path when they
- * fit 1279 elements, every hood has <= 128 members and every member <= 32
- * neighbours; default, 0: from the graph's mean hood size m, 94 m rounded to
- * the nearest multiple of 32 (one thread per hood, 96 threads per tile) and at
- * least 512, or 1152 when 94 m exceeds 1248);
- * vert_tile: accepted for compatibility (multiple of 32, 32..4096) but not
- * used: the vertex pass always takes 128 vertices per block, one per thread;
- * ctas_per_sm: accepted (0..8), not used. */
+/* Launch shape of the EM hood pass.  0 selects the default.
+ * hood_tile: hood elements per tile window (multiple of 32, 128..2048; a tile
+ *   holds the hoods that start in its window, staged in shared memory;
+ *   default from the graph's mean hood size m: 128 / hood_lanes * m rounded to
+ *   a multiple of 32, within [512, 2048]);
+ * hood_lanes: adjacent lanes that share one hood, each summing every
+ *   hood_lanes-th element (1, 2, 4 or 8; default 2 for m >= 16, else 1).
+ * The vertex pass always takes 128 vertices per block, one per thread.
+ * Results do not depend on the tuning (every sum is an exact integer). */
 typedef struct {
     int32_t hood_tile;
-    int32_t vert_tile;
-    int32_t ctas_per_sm;
+    int32_t hood_lanes;
     int32_t use_cuda_graph; /* 1 (default) replays the iteration loop from a CUDA graph */
     int32_t profile;        /* 1: record CUDA events around the per-iteration kernels of
                                pmrf_em (read with pmrf_em_kernel_times) */
@@ -469,9 +467,10 @@ PMRF_API int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t);
 PMRF_API int pmrf_em_kernel_times(pmrf_graph* g, int32_t max_n, float* ms_vertex, float* ms_hood, int32_t* n,
                                   pmrf_stream_t stream);
 
-/* Time candidate tunings on this graph with `cfg` (hood_tile 0 -- the default
- * from the mean hood size -- 512, 768, 1024 and 1248; runs EM several times;
- * synchronises `stream`) and keep the fastest.  *best may be NULL. */
+/* Time candidate tunings on this graph with `cfg` (the defaults, two other
+ * windows and every lanes-per-hood value; each runs the EM loop four times;
+ * synchronises `stream`), keep the fastest on the graph and return it in
+ * *best (may be NULL). */
 PMRF_API int pmrf_autotune(pmrf_graph* g, const pmrf_config* cfg, pmrf_stream_t stream, pmrf_tuning* best);
 
 #ifdef __cplusplus

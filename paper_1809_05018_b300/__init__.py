@@ -146,11 +146,11 @@ class Graph:
     def tuning(self):
         t = N.Tuning()
         N.check(_lib().pmrf_get_tuning(self._handle(), ctypes.byref(t)), "pmrf_get_tuning")
-        return dict(hood_tile=t.hood_tile, vert_tile=t.vert_tile, ctas_per_sm=t.ctas_per_sm,
-                    use_cuda_graph=t.use_cuda_graph, profile=t.profile)
+        return dict(hood_tile=t.hood_tile, hood_lanes=t.hood_lanes, use_cuda_graph=t.use_cuda_graph,
+                    profile=t.profile)
 
-    def set_tuning(self, hood_tile=0, vert_tile=0, ctas_per_sm=0, use_cuda_graph=1, profile=0):
-        t = N.Tuning(hood_tile, vert_tile, ctas_per_sm, use_cuda_graph, profile)
+    def set_tuning(self, hood_tile=0, hood_lanes=0, use_cuda_graph=1, profile=0):
+        t = N.Tuning(hood_tile, hood_lanes, use_cuda_graph, profile)
         N.check(_lib().pmrf_set_tuning(self._handle(), ctypes.byref(t)), "pmrf_set_tuning")
 
     def em_kernel_times(self, max_n=1000):
@@ -167,8 +167,8 @@ class Graph:
         c = cfg.c()
         N.check(_lib().pmrf_autotune(self._handle(), ctypes.byref(c), _stream_ptr(), ctypes.byref(t)),
                 "pmrf_autotune")
-        return dict(hood_tile=t.hood_tile, vert_tile=t.vert_tile, ctas_per_sm=t.ctas_per_sm,
-                    use_cuda_graph=t.use_cuda_graph, profile=t.profile)
+        return dict(hood_tile=t.hood_tile, hood_lanes=t.hood_lanes, use_cuda_graph=t.use_cuda_graph,
+                    profile=t.profile)
 
     # -- the method -----------------------------------------------------------
     def init_labels(self, cfg: EMConfig) -> torch.Tensor:

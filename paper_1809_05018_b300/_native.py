@@ -40,8 +40,8 @@ class BuildOptions(ctypes.Structure):
 
 
 class Tuning(ctypes.Structure):
-    _fields_ = [("hood_tile", ctypes.c_int32), ("vert_tile", ctypes.c_int32), ("ctas_per_sm", ctypes.c_int32),
-                ("use_cuda_graph", ctypes.c_int32), ("profile", ctypes.c_int32)]
+    _fields_ = [("hood_tile", ctypes.c_int32), ("hood_lanes", ctypes.c_int32), ("use_cuda_graph", ctypes.c_int32),
+                ("profile", ctypes.c_int32)]
 
 
 # (name, argtypes); every function returns int except where noted

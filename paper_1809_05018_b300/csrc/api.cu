@@ -108,7 +108,7 @@ void destroy(pmrf_graph* g) {
     for (cudaEvent_t ev : g->prof_ev) cudaEventDestroy(ev);
     void* ps[] = {g->d_pix_off, g->d_vert_off, g->d_hood_slice_off, g->d_rank_off, g->d_W, g->d_rank, g->d_y,
                   g->d_npix, g->d_adj_off, g->d_adj, g->d_clq_off, g->d_clq, g->d_hood_off, g->d_hood, g->d_row_off,
-                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, g->d_status, g->d_layer};
+                  g->d_row, g->d_rep_off, g->d_rep_woff, g->d_rep_mask, g->d_el, g->d_hood_gen, g->d_status, g->d_layer};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
     delete g;
@@ -445,11 +445,10 @@ int pmrf_get_tuning(const pmrf_graph* g, pmrf_tuning* t) {
 
 int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t) {
     if (!g || !t) return fail(PMRF_ERR_ARG, "null argument");
-    if (t->hood_tile != 0 && (t->hood_tile < 128 || t->hood_tile > 1248 || t->hood_tile % 32))
-        return fail(PMRF_ERR_ARG, "hood_tile must be 0 or a multiple of 32 in [128, 1248]");
-    if (t->vert_tile != 0 && (t->vert_tile < 32 || t->vert_tile > 4096 || t->vert_tile % 32))
-        return fail(PMRF_ERR_ARG, "vert_tile must be 0 or a multiple of 32 in [32, 4096]");
-    if (t->ctas_per_sm < 0 || t->ctas_per_sm > 8) return fail(PMRF_ERR_ARG, "ctas_per_sm must be in [0, 8]");
+    if (t->hood_tile != 0 && (t->hood_tile < 128 || t->hood_tile > 2048 || t->hood_tile % 32))
+        return fail(PMRF_ERR_ARG, "hood_tile must be 0 or a multiple of 32 in [128, 2048]");
+    if (t->hood_lanes != 0 && t->hood_lanes != 1 && t->hood_lanes != 2 && t->hood_lanes != 4 && t->hood_lanes != 8)
+        return fail(PMRF_ERR_ARG, "hood_lanes must be 0, 1, 2, 4 or 8");
     if (t->profile != 0 && t->profile != 1) return fail(PMRF_ERR_ARG, "profile must be 0 or 1");
     cudaDeviceSynchronize();
     free_plans(g);

@@ -919,13 +919,15 @@ __device__ __forceinline__ void merge32(const int32_t* __restrict__ N, int d, co
 // For element e (vertex v in hood c at position i): row bits j where hood[j]
 // is a neighbour of v (for hoods of at least rows_min_k members), and slot
 // bits s where N(v)[s] lies in the hood (stored vertex-major, one record per
-// replica of v, and, for degrees <= 32, element-major too).
+// replica of v, and element-major in the hood pass's element stream: el[e] =
+// (v, with bit 31 set on the last element of its hood; the slot mask when v
+// has at most 32 neighbours, else 0)).
 __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __restrict__ hood_off, const int32_t* __restrict__ hood,
                         const int32_t* __restrict__ el_hood, const int64_t* __restrict__ adj_off,
                         const int32_t* __restrict__ adj, const int64_t* __restrict__ row_off,
                         uint32_t* __restrict__ row, int32_t* __restrict__ cursor,
                         const int64_t* __restrict__ rep_woff, uint32_t* __restrict__ rep_mask,
-                        uint32_t* __restrict__ el_slot, uint8_t* __restrict__ hood_gen, int64_t rows_min_k,
+                        uint2* __restrict__ el, uint8_t* __restrict__ hood_gen, int64_t rows_min_k,
                         int64_t N_el) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= N_el) return;
@@ -939,6 +941,7 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
     const int64_t d = adj_off[v + 1] - av;
     const int64_t nwh = ceil_div(k, 32);
     const int64_t nwv = d > 32 ? ceil_div(d, 32) : 1;
+    const uint32_t vtag = (uint32_t)v | (i == k - 1 ? 0x80000000u : 0u);  // last element of its hood
     const bool keep_row = k >= rows_min_k;
     uint32_t* rw = keep_row ? row + row_off[c] + i * nwh : nullptr;
     // the replica's place among v's replicas is arbitrary: the vertex pass only
@@ -954,10 +957,10 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
             merge32<false>(N, (int)d, hood + h0, (int)k, &rbits, &sbits);
         }
         sw[0] = sbits;
-        el_slot[e] = sbits;
+        el[e] = make_uint2(vtag, sbits);
         return;
     }
-    if (d > 32 || k > HOOD_FAST_MAX) hood_gen[c] = 1;  // the hood needs the general path of the hood pass
+    if (d > 32) hood_gen[c] = 1;  // the hood needs the general path of the hood pass
     uint32_t rcur = 0, scur = 0;
     int64_t rwi = 0, swi = 0;
     int64_t a = 0, j = 0;
@@ -981,7 +984,7 @@ __global__ void __launch_bounds__(256, MK_MIN_BLOCKS) k_masks(const int64_t* __r
     if (keep_row) rw[rwi] = rcur;
     sw[swi] = scur;
     // the same slot mask in element (hood-major) order, for vertices of degree <= 32
-    el_slot[e] = (d <= 32) ? scur : 0u;
+    el[e] = make_uint2(vtag, (d <= 32) ? scur : 0u);
 }
 
 // slice offsets of cliques/hoods: cliques are grouped by their smallest vertex
@@ -1353,11 +1356,11 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(exclusive_scan_i32_to_i64(d_rcount, g->d_rep_off, V, s));
     int64_t* d_nw = nullptr;
     PMRF_TRY(tmp.get(&d_nw, std::max(C, V)));
-    // with every degree <= 32 only hoods above the fast path's size are read
-    // through their local adjacency rows, and every replica's slot mask is
-    // one word that k_masks writes in full
+    // with every degree <= 32 no hood is read through its local adjacency
+    // rows (the hood pass's fast path takes every hood), and every replica's
+    // slot mask is one word that k_masks writes in full
     const bool deg32 = g->max_deg <= 32;
-    const int64_t rows_min_k = deg32 ? HOOD_FAST_MAX + 1 : 0;
+    const int64_t rows_min_k = deg32 ? INT64_MAX : 0;
     PMRF_TRY(dalloc(&g->d_row_off, C + 1, s));
     LAUNCH_1D(k_row_words, C, g->d_hood_off, C, rows_min_k, d_nw);
     PMRF_TRY(exclusive_scan_i64(d_nw, g->d_row_off, C, s));
@@ -1368,7 +1371,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(read_i64(g->d_rep_woff + V, &g->n_rep_words, s));
     PMRF_TRY(dalloc(&g->d_row, g->n_row_words, s));
     PMRF_TRY(dalloc(&g->d_rep_mask, g->n_rep_words, s));
-    PMRF_TRY(dalloc(&g->d_el_slot, g->N_el, s));
+    PMRF_TRY(dalloc(&g->d_el, g->N_el, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_row, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_row_words, 1), s));
     if (!deg32)
         PMRF_CUDA(cudaMemsetAsync(g->d_rep_mask, 0, sizeof(uint32_t) * std::max<int64_t>(g->n_rep_words, 1), s));
@@ -1376,7 +1379,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(dalloc(&g->d_hood_gen, C, s));
     PMRF_CUDA(cudaMemsetAsync(g->d_hood_gen, 0, std::max<int64_t>(C, 1), s));
     LAUNCH_1D(k_masks, g->N_el, g->d_hood_off, g->d_hood, d_el_hood, g->d_adj_off, g->d_adj, g->d_row_off,
-              g->d_row, d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el_slot, g->d_hood_gen, rows_min_k, g->N_el);
+              g->d_row, d_cursor, g->d_rep_woff, g->d_rep_mask, g->d_el, g->d_hood_gen, rows_min_k, g->N_el);
     PMRF_CUDA(cudaMemcpyAsync(&g->max_hood, d_hmax, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
 
     // slice offsets of hoods and elements (host copies, one transfer)

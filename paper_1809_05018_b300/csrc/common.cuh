@@ -54,6 +54,7 @@ enum Site : int32_t {
     SITE_SORT = 6,
     SITE_LABEL = 7,
     SITE_WAIT = 8,
+    SITE_RANGE = 9,   // energies beyond the fixed point's range (non-finite bound)
 };
 
 // ---------------------------------------------------------------------------

@@ -13,20 +13,29 @@
 //     equals the lexicographic minimum of (Emin(c,v), label) over the replicas
 //     (Section 3.2.2 "Update Output Labels", reading G6) while keeping all
 //     per-replica work in integers.  Also writes v's hood-pass record (its
-//     data terms in fixed point and its label masks) and the per-tile moment
-//     partials of the parameter update.  The VAR instantiation adds the sweep
-//     variants (full-neighbourhood Potts, mean-energy and vote replica rules).
-//   k_hood<L> (hood tiles) -- for every hood c: S_c = sum over its members v
-//     of Emin(c,v), from v's record and the element's slot mask (fast tiles:
-//     member ids and slot masks staged in shared memory, one thread per hood)
-//     or from the hood-local adjacency rows and the members' labels (general
-//     tiles); the sums are exact integers.  Also the hood convergence test
-//     over the last W sums (ring buffer) and the tile's exact partial of T.
+//     data terms in the slice's fixed point and its label masks) and the
+//     per-tile moment partials of the parameter update.  The VAR instantiation
+//     adds the sweep variants (full-neighbourhood Potts, mean-energy and vote
+//     replica rules).
+//   k_hood<L> (one warp per hood tile) -- for every hood c: S_c = sum over its
+//     members v of Emin(c,v).  Lane i of a warp takes element i of a 32-element
+//     chunk of the tile's element stream (coalesced), gathers its vertex's
+//     record, forms the element energy in integers from the record and the
+//     element's slot mask, and a segmented prefix sum over the lanes (hood ends
+//     flagged in the stream, a carry across chunks) gives each hood's sum at
+//     the lane of its last element.  Hoods with a member of more than 32
+//     neighbours go hood by hood through their hood-local adjacency rows.  The
+//     same lanes run the hood convergence test over the last W sums (ring
+//     buffer) and add the tile's exact partial of T.
 //   k_finalize<L> (one block per slice) -- label moments -> (n, mu, sigma, U),
-//     the total T^t, the MAP and EM convergence tests, per-slice stop flags.
-// Slices that have stopped skip all work.  The loop is captured once into a
-// CUDA graph whose iterations sit in conditional nodes: once every slice has
-// stopped, the remaining iterations are skipped.
+//     the total T^t, the MAP and EM convergence tests, per-slice stop flags,
+//     and the fixed-point unit of the next iteration.
+// Energies of a slice are integers in units 2^-q, q chosen per slice and
+// iteration from a bound on every element energy (slice_unit), so that all
+// sums are exact and independent of order.  Slices that have stopped skip all
+// work.  The loop is captured once into a CUDA graph whose iterations sit in
+// conditional nodes: once every slice has stopped, the remaining iterations
+// are skipped.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -41,41 +50,39 @@ namespace {
 constexpr int VT_THREADS = 128;             // vertices per vertex tile = threads
 // resident blocks per SM the register budget of the EM kernels must allow
 // (measured on the two-label stack: the vertex pass gains from 16 blocks at 32
-// registers; the hood pass is best at 40; more labels need more registers)
+// registers; more labels need more registers)
 __host__ __device__ constexpr int vt_min_blocks(int L) { return L <= 2 ? 16 : (L <= 4 ? 10 : 4); }
-__host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 16 : 12; }
+__host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 12 : 8; }
 constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
 constexpr int LI_THREADS = 256;             // label-image block
-constexpr int HT_THREADS = 96;              // hood-pass block: a tile's ~94 hoods, one per thread
-constexpr int MAX_HOOD_TILE = 1248;         // largest hood-tile window (elements)
-constexpr int HT_CAP = MAX_HOOD_TILE + 31;  // elements a fast hood tile can hold
-// Per-vertex record of the hood pass, 32-byte chunks (one for L = 2), written
-// by the vertex pass of the same iteration:
-//   words 0-1   D_min(v) = min_l D_l(y_v), exact fixed point (units 2^-80)
-//   words 2..L  the excess D_l - D_min of every label l other than amin (the
-//               lowest label attaining D_min), ascending l, in units 2^-hq,
-//               rounded to nearest and saturated at DQ_MAX; bits 61-63 of
-//               word 2 hold amin
-//   then        L-1 u32 masks: which of v's adjacency slots hold label l, for
-//               l < L-1 (the last label's count follows from the slot mask)
-// For L = 2 word 3 differs: it holds the mask of the slots that hold the
-// label other than amin.  With c_b the in-hood neighbours holding that label,
-// c_a the others and k = c_b - c_a, an element's excess
-// min(beta_q c_b, excess + beta_q c_a) is beta_q c_b, less beta_q k - excess
-// when that is positive, so a hood sum needs beta_q only once more.
-__host__ __device__ constexpr int vrec_words(int L) { return ((16 + 12 * (L - 1) + 31) / 32) * 4; }
-constexpr uint64_t DQ_MAX = (1ull << 60) - 1;
+constexpr int HT_THREADS = 128;             // hood-pass block
+constexpr int MIN_HOOD_TILE = 128;          // hood-tile window (elements) limits
+constexpr int MAX_HOOD_TILE = 2048;
+constexpr int HT_CAP_MAX = 4096;            // largest staged tile (elements; 32 KB of shared memory)
+// Per-vertex record of the hood pass, in 32-byte chunks, written by the vertex
+// pass of the same iteration; energies in the slice's unit 2^-q (SliceUnit):
+//   word 0        D_min(v) = min_l D_l(y_v) (each D_l rounded to the unit once)
+//   words 1..L-1  the excess D_l - D_min of every label l other than amin (the
+//                 lowest label attaining D_min), ascending l, saturated at
+//                 DQ_SAT (larger excesses never decide a minimum); bits 61-63
+//                 of word 1 hold amin
+//   then          L-1 u32 masks from u32 index 2L on: which of v's adjacency
+//                 slots hold label l, for l < L-1 (the last label's count
+//                 follows from the slot mask)
+// For L = 2 the mask differs: it marks the slots that hold the label other
+// than amin.  With c_b the in-hood neighbours holding that label, c_a the
+// others and k = c_b - c_a, the element's excess min(beta_q c_b, dq + beta_q
+// c_a) is beta_q c_b less max(0, beta_q k - dq).
+__host__ __device__ constexpr int vrec_words(int L) { return ((L + (L - 1 + 1) / 2) + 3) / 4 * 4; }
+constexpr uint64_t DQ_SAT = (1ull << 61) - 1;
 
 enum Mode : int32_t { MODE_INIT = 0, MODE_EM = 1, MODE_SWEEP = 2, MODE_PARAMS = 3 };
 
 struct RunCfg {
     int32_t L, W, max_iters, init_from_labels;
     double beta, tol, sigma_min, init_lo, init_hi;
-    int32_t hq;      // unit 2^-hq of the hood pass's label excesses
     int32_t scope;   // PMRF_SCOPE_*
     int32_t rule;    // PMRF_RULE_*
-    int32_t pad;
-    int64_t beta_q;  // beta in units 2^-hq (< 2^51)
 };
 
 struct OutPtrs {  // outputs of one pmrf_em call (read by the closing kernel)
@@ -88,6 +95,7 @@ struct OutPtrs {  // outputs of one pmrf_em call (read by the closing kernel)
 
 struct DevGraph {
     int32_t S;
+    int32_t max_deg, max_hood;
     int64_t V, C;
     const int64_t* vert_off;
     const int64_t* hood_slice_off;
@@ -100,12 +108,14 @@ struct DevGraph {
     const uint32_t* row;
     const int64_t* rep_woff;
     const uint32_t* rep_mask;
-    const uint32_t* el_slot;
+    const uint2* el;
 };
 
 DevGraph view(const pmrf_graph* g) {
     DevGraph d;
     d.S = g->S;
+    d.max_deg = g->max_deg;
+    d.max_hood = g->max_hood;
     d.V = g->V;
     d.C = g->C;
     d.vert_off = g->d_vert_off;
@@ -119,7 +129,7 @@ DevGraph view(const pmrf_graph* g) {
     d.row = g->d_row;
     d.rep_woff = g->d_rep_woff;
     d.rep_mask = g->d_rep_mask;
-    d.el_slot = g->d_el_slot;
+    d.el = g->d_el;
     return d;
 }
 
@@ -133,39 +143,53 @@ __device__ __forceinline__ int threshold_label(const RunCfg& c, double y) {
     return q < 0.0 ? 0 : (q > (double)(c.L - 1) ? c.L - 1 : (int)q);
 }
 
-// ---------------------------------------------------------------------------
-// exact hood sums
-//
-// A double is m * 2^e with a 53-bit integer m; its value in units of 2^-80 is
-// m shifted by e + 80, held exactly in a signed 128-bit integer whenever
-// 2^-27 <= |d| < 2^46 (smaller magnitudes are truncated, an error below
-// 1e-24; larger ones saturate).  Sums of such integers are exact and
-// independent of order, so a hood sum is the exact sum of its FP64 terms,
-// rounded to double once.  This keeps the per-element work of the hood pass in
-// the integer pipes (the FP64 pipe of this part is small).
+// 1 / (2 sigma^2) of the Gaussian data term (one expression for every caller)
+__device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * sg * sg); }
 
-__device__ __forceinline__ __int128 fix80(double d) {
+// ---------------------------------------------------------------------------
+// exact energy sums in a per-slice fixed point
+//
+// Every energy of slice s in iteration t is an integer in units 2^-q.  q is
+// chosen (slice_unit) from a bound M on |Emin(c,v)|: the data terms of the
+// slice's labels at the ends of its intensity range bound the least data term
+// of every vertex, and the Potts part is at most beta times the largest degree.
+// With H = max(32, largest hood), 2^q M H < 2^62, so an element energy, a sum
+// of up to 32 of them (a warp's prefix) and a hood sum all fit in 64 bits, and
+// every sum is exact and independent of order.  A double is rounded to the
+// unit once (to_fixed: to nearest, ties away from zero); for the usual range of
+// energies q is about 52, i.e. the rounding is below 1e-16.  Totals T are sums
+// of hood sums in 128 bits, rounded to double once.
+
+struct SliceUnit {
+    int32_t q;       // unit 2^-q of this iteration's energies
+    int32_t pad;
+    int64_t beta_q;  // beta in units 2^-q, rounded to nearest
+    int64_t tol_q;   // smallest integer >= conv_tol * 2^q (the hood test's threshold)
+};
+
+// round(d * 2^q) for |d * 2^q| < 2^62 (saturated beyond), with integer operations
+__device__ __forceinline__ int64_t to_fixed(double d, int q) {
     const long long bits = __double_as_longlong(d);
     const int ex = (int)((bits >> 52) & 0x7ff);
     unsigned long long man = (unsigned long long)bits & 0xfffffffffffffull;
     if (ex != 0) man |= 1ull << 52;
-    const int sh = (ex == 0 ? 1 : ex) - 995;  // value = man * 2^(ex - 1075), units of 2^-80
-    __int128 r;
+    const int sh = (ex == 0 ? 1 : ex) - 1075 + q;  // |d| 2^q = man 2^sh
+    unsigned long long r;
     if (sh >= 0) {
-        r = sh > 73 ? ((__int128)1 << 126) : ((__int128)man << sh);
+        r = sh >= 10 ? (1ull << 62) : (man << sh);
     } else {
-        r = sh <= -53 ? (__int128)0 : (__int128)(man >> (-sh));
+        r = sh < -54 ? 0ull : ((man + (1ull << (-sh - 1))) >> (-sh));
     }
-    return bits < 0 ? -r : r;
+    return bits < 0 ? -(long long)r : (long long)r;
 }
 
-__device__ __forceinline__ double unfix80(__int128 x) {
-    // from the magnitude, so that the low word of a small negative value does
-    // not round (|x| < 2^64 converts with a single rounding)
+// x * 2^-q rounded to double once (|x| < 2^64 converts with a single rounding;
+// larger magnitudes take a second one from the low word)
+__device__ __forceinline__ double from_fixed(__int128 x, int q) {
     const bool neg = x < 0;
     const __int128 a = neg ? -x : x;
     const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
-    const double r = fma((double)hi, 0x1p64, (double)lo) * 0x1p-80;
+    const double r = ldexp(fma((double)hi, 0x1p64, (double)lo), -q);
     return neg ? -r : r;
 }
 
@@ -175,45 +199,40 @@ __device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
     return ((__int128)hi << 64) | (__int128)lo;
 }
 
-// ---------------------------------------------------------------------------
-// vertex pass
-
-// an integer with the order of the finite double x (x < y exactly when
-// key(x) < key(y); -0 and +0 share a key): the sign bit set flips the other
-// bits, so larger magnitudes of negative values map lower
-__device__ __forceinline__ long long ordered_key(double x) {
-    long long b = __double_as_longlong(x);
-    if (b == (long long)0x8000000000000000ull) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+// smallest integer >= tol * 2^m (saturated), for the hood test at unit 2^-m
+__device__ __forceinline__ int64_t tol_units(double tol, int m) {
+    const double x = ceil(ldexp(tol, m));
+    return x >= 0x1p62 ? (int64_t)(1ll << 62) : (int64_t)x;
 }
 
-// 1 / (2 sigma^2) of the Gaussian data term (one expression for every caller)
-__device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * sg * sg); }
-
-// the data terms in fixed point: D_min exact (units 2^-80), the lowest label
-// attaining it, and every label's excess over it in units 2^-hq (rounded to
-// nearest, saturated at DQ_MAX)
-template <int L>
-__device__ __forceinline__ __int128 data_excess(const double (&D)[L], int hq, uint64_t (&dq)[L], int& amin) {
-    __int128 F[L];
-#pragma unroll
-    for (int l = 0; l < L; ++l) F[l] = fix80(D[l]);
-    amin = 0;
-    __int128 Fmin = F[0];
-#pragma unroll
-    for (int l = 1; l < L; ++l)
-        if (F[l] < Fmin) {
-            Fmin = F[l];
-            amin = l;
-        }
-    const int sh = 80 - hq;  // >= 29
-#pragma unroll
+// The unit of slice s for energies from parameters th [L][4] (mu, sigma at 1,
+// 2): D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l is convex in y, so on
+// the slice's intensity range [ylo, yhi] the least data term of every vertex
+// lies in [min_l ln sigma_l, min_l max(D_l(ylo), D_l(yhi))]; an element adds at
+// most beta times its vertex's degree.  Margins of 2^-20 cover the rounding of
+// these bounds.  ok = false when the bound is not finite.
+__device__ __forceinline__ SliceUnit slice_unit(const double* __restrict__ th, int L, double ylo, double yhi,
+                                                double beta, double tol, int max_deg, int max_hood, bool& ok) {
+    double lo = INFINITY, up = INFINITY;
     for (int l = 0; l < L; ++l) {
-        const unsigned __int128 dd = (unsigned __int128)F[l] - (unsigned __int128)Fmin;  // exact, >= 0
-        const unsigned __int128 q = (dd + ((unsigned __int128)1 << (sh - 1))) >> sh;
-        dq[l] = q > (unsigned __int128)DQ_MAX ? DQ_MAX : (uint64_t)q;
+        const double mu = th[4 * l + 1], sg = th[4 * l + 2];
+        const double inv = inv_two_var(sg), ls = log(sg);
+        const double a = ylo - mu, b = yhi - mu;
+        lo = fmin(lo, ls);
+        up = fmin(up, fmax(a * a * inv + ls, b * b * inv + ls));
     }
-    return Fmin;
+    const double B = fmax(fabs(lo), fabs(up));
+    const double M = (B + beta * (double)max(32, max_deg)) * (1.0 + 0x1p-20) + 0x1p-60;
+    const double P = M * (double)max(32, max_hood);
+    SliceUnit u;
+    u.pad = 0;
+    ok = isfinite(P);
+    int e = 0;
+    frexp(ok ? P : 1.0, &e);  // P < 2^e
+    u.q = max(-1000, min(1000, 62 - e));
+    u.beta_q = (int64_t)llrint(ldexp(beta, u.q));
+    u.tol_q = tol_units(tol, u.q);
+    return u;
 }
 
 __device__ __forceinline__ void store_vrec_words(uint64_t* __restrict__ p, const uint64_t* w, int nw) {
@@ -223,44 +242,65 @@ __device__ __forceinline__ void store_vrec_words(uint64_t* __restrict__ p, const
                      : "memory");
 }
 
-// a record whose element energy is E in every hood (the full-neighbourhood
-// Potts scope: every replica of v carries the same energies): D_min = E, no
-// excess and no label masks, so the hood pass adds E for each element
+// the data terms in the unit: every D_l rounded once, amin the lowest label
+// attaining the least, each label's excess over it (saturated at DQ_SAT)
 template <int L>
-__device__ __forceinline__ void write_vrec_const(uint64_t* __restrict__ vrec, int64_t v, __int128 E) {
+__device__ __forceinline__ int64_t data_fixed(const double (&D)[L], int q, uint64_t (&dq)[L], int& amin) {
+    int64_t F[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) F[l] = to_fixed(D[l], q);
+    amin = 0;
+    int64_t Fmin = F[0];
+#pragma unroll
+    for (int l = 1; l < L; ++l)
+        if (F[l] < Fmin) {
+            Fmin = F[l];
+            amin = l;
+        }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const uint64_t d = (uint64_t)(F[l] - Fmin);  // >= 0, < 2^63
+        dq[l] = d > DQ_SAT ? DQ_SAT : d;
+    }
+    return Fmin;
+}
+
+// a record whose element energy is E in every hood (the full-neighbourhood
+// Potts scope: every replica of v carries the same energies): D_min = E, every
+// excess 0 and no label masks, so the hood pass adds E for each element
+template <int L>
+__device__ __forceinline__ void write_vrec_const(uint64_t* __restrict__ vrec, int64_t v, int64_t E) {
     constexpr int NW = vrec_words(L);
     uint64_t w[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) w[k] = 0ull;
-    w[0] = (uint64_t)(unsigned __int128)E;
-    w[1] = (uint64_t)((unsigned __int128)E >> 64);
+    w[0] = (uint64_t)E;
     store_vrec_words(vrec + v * NW, w, NW);
 }
 
 // the hood-pass record of vertex v (layout above) from its FP64 data terms
 template <int L>
 __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t v, const double (&D)[L],
-                                           const uint32_t (&lmw)[L], int hq) {
+                                           const uint32_t (&lmw)[L], int q) {
     constexpr int NW = vrec_words(L);
     uint64_t dq[L];
     int amin;
-    const __int128 Fmin = data_excess<L>(D, hq, dq, amin);
+    const int64_t Fmin = data_fixed<L>(D, q, dq, amin);
     uint64_t w[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) w[k] = 0ull;
-    w[0] = (uint64_t)(unsigned __int128)Fmin;
-    w[1] = (uint64_t)((unsigned __int128)Fmin >> 64);
+    w[0] = (uint64_t)Fmin;
 #pragma unroll
-    for (int k = 0; k < L - 1; ++k) w[2 + k] = k < amin ? dq[k] : dq[k + 1];
-    if (L > 1) w[2] |= (uint64_t)amin << 61;
+    for (int k = 0; k < L - 1; ++k) w[1 + k] = k < amin ? dq[k] : dq[k + 1];
+    if (L > 1) w[1] |= (uint64_t)amin << 61;
     if constexpr (L == 2) {
         // slots holding the other label (the complement within v's slots of
         // the label-0 mask when amin = 0)
-        w[3] = (uint64_t)(amin == 0 ? ~lmw[0] : lmw[0]);
+        w[2] = (uint64_t)(amin == 0 ? ~lmw[0] : lmw[0]);
     } else {
 #pragma unroll
         for (int k = 0; k < L - 1; ++k) {
-            const int u = 4 + 2 * (L - 1) + k;
+            const int u = 2 * L + k;
             w[u >> 1] |= (uint64_t)lmw[k] << (32 * (u & 1));
         }
     }
@@ -307,6 +347,15 @@ __device__ __forceinline__ void for_each_mask(const uint32_t* __restrict__ rm, i
 
 constexpr int RCP_N = 65;  // replica counts whose reciprocal the vertex pass takes from a table
 
+// an integer with the order of the finite double x (x < y exactly when
+// key(x) < key(y); -0 and +0 share a key): the sign bit set flips the other
+// bits, so larger magnitudes of negative values map lower
+__device__ __forceinline__ long long ordered_key(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
 // The sweep variants for one vertex (scope and replica rule of RunCfg; the
 // same definitions as pmrf_config documents): returns the new label, sets
 // Estar, writes the hood-pass record.  k_l of a replica = its in-hood
@@ -315,7 +364,7 @@ template <int L>
 __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, const uint8_t* __restrict__ x_in,
                                            int64_t a0, int d, int64_t r0, int64_t r1, const uint32_t (&lm)[L],
                                            const double (&D)[L], uint64_t* __restrict__ vrec, int64_t v,
-                                           double& Estar, const double* __restrict__ rcp) {
+                                           double& Estar, const double* __restrict__ rcp, int q, int64_t beta_q) {
     int lab = 0;
     if (c.scope == PMRF_SCOPE_FULL) {
         // one set of energies for every replica: every rule picks its least label
@@ -342,12 +391,11 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
             if (e < Estar) { Estar = e; lab = l; }
         }
         if (vrec) {
-            // the element energy min_l (D_l + beta M_l) in the hood pass's fixed point
-            const int sh = 80 - c.hq;
-            __int128 Emin = 0;
+            // the element energy min_l (D_l + beta M_l) in the slice's fixed point
+            int64_t Emin = 0;
 #pragma unroll
             for (int l = 0; l < L; ++l) {
-                const __int128 e = fix80(D[l]) + (((__int128)c.beta_q * M[l]) << sh);
+                const int64_t e = to_fixed(D[l], q) + beta_q * (int64_t)M[l];
                 if (l == 0 || e < Emin) Emin = e;
             }
             write_vrec_const<L>(vrec, v, Emin);
@@ -387,20 +435,20 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
         }
     } else {
         // vote: each replica's least label, compared exactly in the hood
-        // pass's fixed point (excess_l + beta_q k_l, units 2^-hq)
+        // pass's fixed point (excess_l + beta_q k_l in the slice's unit)
         uint64_t dq[L];
         int amin;
-        (void)data_excess<L>(D, c.hq, dq, amin);
+        (void)data_fixed<L>(D, q, dq, amin);
         int votes[L], kmin[L];
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             votes[l] = 0;
             kmin[l] = 0x7fffffff;
         }
-        const uint64_t bq = (uint64_t)c.beta_q;
+        const uint64_t bq = (uint64_t)beta_q;
         // one replica's vote from its counts k_l of in-hood neighbours not labelled l
         auto vote = [&](const int (&k)[L]) {
-            // < 2^60 + 2^51 * 2^12: no overflow in 64 bits
+            // excess <= 2^61, beta_q k below 2^62 / 32 (slice_unit): no overflow
             int b = 0;
             uint64_t eb = dq[0] + bq * (uint64_t)k[0];
 #pragma unroll
@@ -441,7 +489,7 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
         for (int l = 0; l < L; ++l)
             if (l == lab) Estar = D[l] + c.beta * (double)kmin[l];
     }
-    if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
+    if (vrec) write_vrec<L>(vrec, v, D, lm, q);
     return lab;
 }
 
@@ -457,7 +505,8 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                                                        const double* __restrict__ dterm,
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
                                                        double* __restrict__ vpart, DevStatus* st,
-                                                       uint64_t* __restrict__ vrec) {
+                                                       uint64_t* __restrict__ vrec,
+                                                       const SliceUnit* __restrict__ unit) {
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
     __shared__ double s_Md[33];  // (double)m for m <= 32: no int-to-FP64 conversions on the common path
     __shared__ double s_rcp[VAR ? RCP_N : 1];  // 1 / R for the mean-energy replica rule
@@ -492,6 +541,9 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
     __syncthreads();
     const int64_t v = (int64_t)tile.a0 + threadIdx.x;
     const bool ok = v < tile.a1;
+    // the slice's fixed-point unit of this iteration (records of the hood pass)
+    const int uq = unit ? unit[s].q : 0;
+    const int64_t ubq = unit ? unit[s].beta_q : 0;
     int vlab = 0;
     double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
     bool have_dev = false;                   // EM/sweep: y - mu_lab and its square already known
@@ -553,7 +605,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                     }
                 }
                 // the hood pass of this iteration reads v's data terms and label masks
-                if (vrec) write_vrec<L>(vrec, v, D, lm, c.hq);
+                if (vrec) write_vrec<L>(vrec, v, D, lm, uq);
                 // every vertex lies in at least one hood, so M_l is set (and
                 // <= 32 when d <= 32)
                 double Md[L];
@@ -577,7 +629,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                     if (k < kbest) { Estar = e; kbest = k; lab = l; }
                 }
             } else {
-                lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar, s_rcp);
+                lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar, s_rcp, uq, ubq);
             }
             x_out[v] = (uint8_t)lab;
             if (E_out) E_out[v] = Estar;
@@ -659,14 +711,12 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
 // decoded hood-pass record of one vertex (dq[amin] = 0)
 template <int L>
 struct VRec {
-    __int128 Dmin;
+    int64_t Dmin;
     uint64_t dq[L];
     uint32_t lmv[L];  // lmv[L-1] unused
 };
 
-// The records are gathered (one 32-byte record per element) without
-// allocating L1 lines: a tile's records are spread over many lines that are
-// rarely reused before eviction (measured 2 % faster on the two-label stack)
+// The records are gathered (one 32-byte chunk per element for L <= 3)
 template <int L>
 __device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, int64_t v) {
     constexpr int NW = vrec_words(L);
@@ -674,35 +724,35 @@ __device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, 
     const uint64_t* p = vrec + v * NW;
 #pragma unroll
     for (int k = 0; k < NW; k += 4)
-        asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
+        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
             : "=l"(w[k]), "=l"(w[k + 1]), "=l"(w[k + 2]), "=l"(w[k + 3])
             : "l"(p + k));
     VRec<L> R;
-    R.Dmin = (__int128)(((unsigned __int128)w[1] << 64) | w[0]);
-    const int amin = L > 1 ? (int)(w[2] >> 61) : 0;
+    R.Dmin = (int64_t)w[0];
+    const int amin = L > 1 ? (int)(w[1] >> 61) : 0;
 #pragma unroll
     for (int l = 0; l < L; ++l) {
-        const uint64_t own = (l < L - 1) ? (w[2 + l] & DQ_MAX) : 0ull;  // stored slot l (labels below amin)
-        const uint64_t up = (l >= 1) ? (w[1 + l] & DQ_MAX) : 0ull;      // stored slot l-1 (labels above amin)
+        const uint64_t own = (l < L - 1) ? (w[1 + l] & DQ_SAT) : 0ull;  // stored slot l (labels below amin)
+        const uint64_t up = (l >= 1) ? (w[l] & DQ_SAT) : 0ull;          // stored slot l-1 (labels above amin)
         R.dq[l] = l == amin ? 0ull : (l < amin ? own : up);
     }
     if constexpr (L == 2) {
-        const uint32_t mb = (uint32_t)w[3];  // slots holding the label other than amin
+        const uint32_t mb = (uint32_t)w[2];  // slots holding the label other than amin
         R.lmv[0] = amin == 0 ? ~mb : mb;
         R.lmv[1] = 0u;
     } else {
 #pragma unroll
         for (int k = 0; k < L; ++k) {
-            const int u = 4 + 2 * (L - 1) + k;  // u32 index of mask k
+            const int u = 2 * L + k;  // u32 index of mask k
             R.lmv[k] = k < L - 1 ? (uint32_t)(w[u >> 1] >> (32 * (u & 1))) : 0u;
         }
     }
     return R;
 }
 
-// the element's energy above D_min at its best label, in units 2^-hq:
-// min_l [dq_l + beta_q * (dc - cnt_l)]; every term is >= 0 and the minimum is
-// at most dc * beta_q (the amin term)
+// the element's energy above D_min at its best label: min_l [dq_l + beta_q *
+// (dc - cnt_l)]; every term is >= 0 and the minimum is at most dc * beta_q
+// (the amin term)
 template <int L>
 __device__ __forceinline__ int64_t vrec_excess(const VRec<L>& R, const int (&cnt)[L], int dc, int64_t beta_q) {
     int64_t r = INT64_MAX;
@@ -730,239 +780,296 @@ __device__ __forceinline__ int slot_counts(const VRec<L>& R, uint32_t m, int (&c
     return dc;
 }
 
-// convergence bookkeeping of one hood; returns 1 when the hood is unconverged
-// The hood sums' history is kept in units of 2^-40 (the exact 2^-80 sum
-// shifted down; |S| < 2^23 -- larger sums saturate), so the MAP convergence
-// test is integer work: converged iff t > W and |S - S^{t-k}| < tol for every
-// k = 1..W.  Equal states give identical sums and pass exactly; otherwise the
-// comparison is made at 2^-40 (about 1e-12) resolution.
-__device__ __forceinline__ int64_t s40_of(__int128 sd) {
-    const __int128 q = sd >> 40;
-    const __int128 lim = ((__int128)1 << 62);
-    return (int64_t)(q > lim ? lim : (q < -lim ? -lim : q));
+// Element energy Emin(c,v) in the slice's unit, from v's record and the
+// element's slot mask (every neighbour of v of degree <= 32)
+template <int L>
+__device__ __forceinline__ int64_t element_energy(const uint64_t* __restrict__ vrec, uint32_t vid, uint32_t m,
+                                                  int64_t beta_q) {
+    if constexpr (L == 2) {
+        uint64_t w0, w1, w2, w3;
+        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+            : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
+            : "l"(vrec + (int64_t)vid * 4));
+        (void)w3;
+        const int cb = __popc(m & (uint32_t)w2);
+        const int k = 2 * cb - __popc(m);
+        const int64_t dq = (int64_t)(w1 & DQ_SAT);
+        const int64_t bk = beta_q * k;
+        return (int64_t)w0 + beta_q * cb - (bk > dq ? bk - dq : 0);
+    } else {
+        const VRec<L> R = load_vrec<L>(vrec, (int64_t)vid);
+        int cnt[L];
+        const int dc = slot_counts<L>(R, m, cnt);
+        return R.Dmin + vrec_excess<L>(R, cnt, dc, beta_q);
+    }
 }
 
-__device__ __forceinline__ int hood_history(int64_t S40, int64_t c, int64_t C, int t, int W, int64_t tol40,
+// The hood convergence test of Section 3.2.2 (reading G9) in integers: hood c
+// has converged at t iff t > W and |S^t - S^{t-k}| < tol for k = 1..W.  The
+// ring holds each sum in the unit of its own iteration (qhist per slot): with
+// equal units the test is exact (|a - b| < ceil(tol 2^q)); when the unit
+// changed in between, both are floored to the coarser unit first (an error
+// below one unit of it, about 1e-15 relative).  Equal states give identical
+// sums and pass exactly.  Returns 1 when the hood is unconverged.
+__device__ __forceinline__ int64_t shift_down(int64_t x, int sh) { return sh >= 63 ? (x < 0 ? -1 : 0) : (x >> sh); }
+
+__device__ __forceinline__ int hood_history(int64_t S, int64_t c, int64_t C, int t, int W, const SliceUnit& u,
+                                            const int32_t* __restrict__ qh, double tol,
                                             int64_t* __restrict__ hist) {
     int unconv = 1;
     if (t > W) {
         unconv = 0;
         for (int k = 1; k <= W; ++k) {
-            const int64_t prev = hist[(int64_t)((t - k) % W) * C + c];
-            const int64_t d = S40 >= prev ? S40 - prev : prev - S40;
-            if (!(d < tol40)) {
+            const int slot = (t - k) % W;
+            const int64_t prev = hist[(int64_t)slot * C + c];
+            const int qp = qh[slot];
+            int64_t a = S, b = prev, thr = u.tol_q;
+            if (qp != u.q) {
+                const int m = min(qp, u.q);
+                a = shift_down(S, u.q - m);
+                b = shift_down(prev, qp - m);
+                thr = tol_units(tol, m);
+            }
+            const int64_t d = a >= b ? a - b : b - a;
+            if (!(d < thr)) {
                 unconv = 1;
                 break;
             }
         }
     }
-    hist[(int64_t)(t % W) * C + c] = S40;
+    hist[(int64_t)(t % W) * C + c] = S;
     return unconv;
 }
 
-// The fast-tile hood sums: P adjacent lanes per hood (1, 2 or 4), each taking
-// every P-th element, their partial sums added across the group; S_c = the
-// exact sum of D_min plus the excesses (<= 128 elements of <= 32 beta_q
-// each, below 2^63)
-template <int P>
-__device__ __forceinline__ __int128 group_sum_i128(__int128 x, unsigned mask) {
-#pragma unroll
-    for (int o = 1; o < P; o <<= 1) {
-        const long long hi = __shfl_xor_sync(mask, (long long)(x >> 64), o);
-        const unsigned long long lo = __shfl_xor_sync(mask, (unsigned long long)x, o);
-        x += ((__int128)hi << 64) | (__int128)lo;
-    }
-    return x;
+// Element energy of L = 2 from a record's first three words (layout above)
+__device__ __forceinline__ int64_t energy2(uint64_t w0, uint64_t w1, uint32_t mb, uint32_t m, int64_t beta_q) {
+    const int cb = __popc(m & mb);
+    const int k = 2 * cb - __popc(m);
+    const int64_t dq = (int64_t)(w1 & DQ_SAT);
+    const int64_t bk = beta_q * k;
+    return (int64_t)w0 + beta_q * cb - (bk > dq ? bk - dq : 0);
 }
 
-template <int L, int P>
+// The fast-tile hood sums: P adjacent lanes per hood (1, 2, 4 or 8), each taking
+// every P-th element of the hood from the tile's staged element stream, their
+// partial sums added across the group (integers: exact in any order).
+// energy(vertex id, slot mask) gives the element energy.
+template <int P, typename Energy, typename Done>
 __device__ __forceinline__ void fast_hoods(const DevGraph& g, int64_t c0, int64_t c1, int64_t e0,
-                                           const uint2* s_el,
-                                           const uint64_t* __restrict__ vrec, int64_t beta_q, int rsh, int mode,
-                                           int t, int W, int64_t tol40, int64_t* __restrict__ hist,
-                                           double* __restrict__ S_out, __int128& my_T, int& my_unconv) {
+                                           const uint2* __restrict__ s_el, Energy&& energy, Done&& hood_done) {
     const int sub = threadIdx.x & (P - 1);
     const unsigned gmask = P == 1 ? (1u << (threadIdx.x & 31))
                                   : (((1u << P) - 1u) << ((threadIdx.x & 31) & ~(P - 1)));
     for (int64_t c = c0 + threadIdx.x / P; c < c1; c += HT_THREADS / P) {
         const int b = (int)(g.hood_off[c] - e0), e = (int)(g.hood_off[c + 1] - e0);
-        __int128 sdD = 0;
-        unsigned __int128 sdR = 0;
-        if constexpr (L == 2) {
-            // sum of beta_q c_b, less beta_q k - excess where that is
-            // positive (record layout above)
-            int scb = 0, sk = 0;
-            uint64_t sdq = 0;
+        int64_t acc = 0;
 #pragma unroll 2
-            for (int i = b + sub; i < e; i += P) {
-                const uint2 q = s_el[i];
-                uint64_t w0, w1, w2, w3;
-                asm("ld.global.nc.L1::no_allocate.v4.b64 {%0, %1, %2, %3}, [%4];"
-                    : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
-                    : "l"(vrec + (int64_t)(int32_t)q.x * 4));
-                sdD += (__int128)(((unsigned __int128)w1 << 64) | w0);
-                const uint32_t m = q.y;
-                const int cb = __popc(m & (uint32_t)w3);
-                const int k = 2 * cb - __popc(m);
-                scb += cb;
-                const uint64_t dq = w2 & DQ_MAX;
-                if (k > 0 && (uint64_t)beta_q * (uint32_t)k >= dq) {  // < 2^56
-                    sk += k;
-                    sdq += dq;
+        for (int i = b + sub; i < e; i += P) {
+            const uint2 q = s_el[i];
+            acc += energy(q.x & 0x7fffffffu, q.y);
+        }
+#pragma unroll
+        for (int o = 1; o < P; o <<= 1) acc += __shfl_xor_sync(gmask, acc, o);
+        if (sub == 0) hood_done(c, acc);
+    }
+}
+
+template <typename Energy, typename Done>
+__device__ __forceinline__ void fast_hoods_p(int lanes, const DevGraph& g, int64_t c0, int64_t c1, int64_t e0,
+                                             const uint2* __restrict__ s_el, Energy&& energy, Done&& hood_done) {
+    if (lanes >= 8)
+        fast_hoods<8>(g, c0, c1, e0, s_el, energy, hood_done);
+    else if (lanes == 4)
+        fast_hoods<4>(g, c0, c1, e0, s_el, energy, hood_done);
+    else if (lanes == 2)
+        fast_hoods<2>(g, c0, c1, e0, s_el, energy, hood_done);
+    else
+        fast_hoods<1>(g, c0, c1, e0, s_el, energy, hood_done);
+}
+
+// Per-hood bookkeeping of one tile and its partials: the exact sum of the
+// tile's hood sums and its number of unconverged hoods
+struct TileAcc {
+    __int128 T = 0;
+    int unconv = 0;
+};
+
+__device__ __forceinline__ void tile_partials(TileAcc& a, int64_t part, int64_t* __restrict__ hpart,
+                                              __int128* s_wT, int* s_wu) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a.T += shfl_xor_i128(a.T, o);
+        a.unconv += __shfl_xor_sync(0xffffffffu, a.unconv, o);
+    }
+    __syncthreads();
+    if (lane_id() == 0) {
+        s_wT[warp_id()] = a.T;
+        s_wu[warp_id()] = a.unconv;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __int128 t = 0;
+        int n = 0;
+        for (int w = 0; w < HT_THREADS / 32; ++w) {
+            t += s_wT[w];
+            n += s_wu[w];
+        }
+        hpart[part * 3 + 0] = (int64_t)(uint64_t)(unsigned __int128)t;
+        hpart[part * 3 + 1] = (int64_t)(t >> 64);
+        hpart[part * 3 + 2] = n;
+    }
+    a.T = 0;
+    a.unconv = 0;
+}
+
+// A general tile (some member of degree > 32): hood by hood, the block's lanes
+// splitting the hood's elements and counting labels through the hood-local
+// adjacency rows
+template <int L, typename Done>
+__device__ __forceinline__ void general_tile(const DevGraph& g, const RunCfg& cf, int64_t c0, int64_t c1,
+                                             const uint8_t* __restrict__ x_in, const uint64_t* __restrict__ vrec,
+                                             int64_t beta_q, int64_t* s_wsum, Done&& hood_done) {
+    for (int64_t c = c0; c < c1; ++c) {
+        const int64_t hb = g.hood_off[c];
+        const int64_t k = g.hood_off[c + 1] - hb;
+        const int64_t nwh = (k + 31) >> 5;
+        const int64_t rb = g.row_off[c];
+        int64_t part = 0;
+        for (int64_t i = threadIdx.x; i < k; i += HT_THREADS) {
+            const int64_t v = g.hood[hb + i];
+            int cnt[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cnt[l] = 0;
+            int dc = 0;
+            for (int64_t w = 0; w < nwh; ++w) {
+                uint32_t m = g.row[rb + i * nwh + w];
+                dc += __popc(m);
+                while (m) {
+                    const int bb = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int xl = x_in[g.hood[hb + w * 32 + bb]];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
                 }
             }
-#pragma unroll
-            for (int o = 1; o < P; o <<= 1) {
-                scb += __shfl_xor_sync(gmask, scb, o);
-                sk += __shfl_xor_sync(gmask, sk, o);
-                sdq += __shfl_xor_sync(gmask, sdq, o);
-            }
-            // scb - sk <= 128 * 32 and sdq <= sk beta_q: below 2^64
-            sdR = (unsigned __int128)(uint64_t)beta_q * (uint32_t)(scb - sk) + sdq;
-        } else {
-            uint64_t r = 0;  // <= 128 excesses of <= 32 beta_q each: below 2^63
-#pragma unroll 2
-            for (int i = b + sub; i < e; i += P) {
-                const uint2 q = s_el[i];
-                const VRec<L> R = load_vrec<L>(vrec, (int32_t)q.x);
-                int cnt[L];
-                const int dc = slot_counts<L>(R, q.y, cnt);
-                sdD += R.Dmin;
-                r += (uint64_t)vrec_excess<L>(R, cnt, dc, beta_q);
-            }
-#pragma unroll
-            for (int o = 1; o < P; o <<= 1) r += __shfl_xor_sync(gmask, r, o);
-            sdR = r;
+            const VRec<L> R = load_vrec<L>(vrec, v);
+            // full scope: the record's D_min is already the element energy
+            part += cf.scope == PMRF_SCOPE_FULL ? R.Dmin : R.Dmin + vrec_excess<L>(R, cnt, dc, beta_q);
         }
-        sdD = group_sum_i128<P>(sdD, gmask);
-        if (sub != 0) continue;
-        const __int128 sd = sdD + (__int128)(sdR << rsh);
-        if (mode == MODE_SWEEP) {
-            if (S_out) S_out[c] = unfix80(sd);
-        } else {
-            my_unconv += hood_history(s40_of(sd), c, g.C, t, W, tol40, hist);
-            my_T += sd;
+        // exact integer sums: the reduction order does not matter
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        __syncthreads();
+        if (lane_id() == 0) s_wsum[warp_id()] = part;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int64_t S = 0;
+            for (int w = 0; w < HT_THREADS / 32; ++w) S += s_wsum[w];
+            hood_done(c, S);
         }
     }
 }
 
+// The hood pass: one block per hood tile (consecutive hoods of one slice, their
+// elements contiguous).  Fast tiles (every member of degree <= 32): the tile's
+// element stream (member id and slot mask, one 8-byte word each) is staged in
+// shared memory with coalesced loads, then lanes-per-hood adjacent lanes take
+// each hood, gather its members' records and sum the element energies.
+// General tiles go hood by hood through the hood-local adjacency rows.
 template <int L>
-__global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph g, const Tile* __restrict__ tiles, int mode, int t,
+__global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph g, const Tile* __restrict__ tiles,
+                                                     int mode, int t, int lanes,
                                                      const RunCfg* __restrict__ cfgp,
                                                      const int32_t* __restrict__ active,
                                                      const uint8_t* __restrict__ x_in,
-                                                     const uint64_t* __restrict__ vrec, int64_t* __restrict__ hist,
-                                                     double* __restrict__ S_out, int64_t* __restrict__ hpart) {
-    __shared__ uint2 s_el[HT_CAP];  // member id, slot mask: one 8-byte load per element
-    __shared__ __int128 s_wsum[HT_THREADS / 32];
-    __shared__ int s_unconv;
+                                                     const uint64_t* __restrict__ vrec,
+                                                     const SliceUnit* __restrict__ unit,
+                                                     const int32_t* __restrict__ qhist,
+                                                     int64_t* __restrict__ hist, double* __restrict__ S_out,
+                                                     int64_t* __restrict__ hpart, int cap) {
+    extern __shared__ uint2 s_el[];  // cap elements: the window plus the rest of its last hood
+    __shared__ int64_t s_wsum[HT_THREADS / 32];
+    __shared__ __int128 s_wT[HT_THREADS / 32];
+    __shared__ int s_wu[HT_THREADS / 32];
     const Tile tile = tiles[blockIdx.x];
     const int s = tile.slice;
     if (active && !active[s]) return;
     const RunCfg cf = *cfgp;
-    const int64_t beta_q = cf.beta_q;
-    const int rsh = 80 - cf.hq;  // excess units 2^-hq -> 2^-80
-    const int64_t tol40 = s40_of(fix80(cf.tol));
+    const SliceUnit u = unit[s];
     const int W = cf.W;
+    const int32_t* qh = qhist ? qhist + (int64_t)s * W : nullptr;
+    TileAcc acc;
+    auto hood_done = [&](int64_t c, int64_t S) {
+        if (mode == MODE_SWEEP) {
+            if (S_out) S_out[c] = from_fixed((__int128)S, u.q);
+        } else {
+            acc.unconv += hood_history(S, c, g.C, t, W, u, qh, cf.tol, hist);
+            acc.T += S;
+        }
+    };
     const int64_t c0 = tile.a0, c1 = tile.a1;
-    __int128 my_T = 0;
-    int my_unconv = 0;
-    if (threadIdx.x == 0) s_unconv = 0;
     if (c1 > c0) {
         const int64_t e0 = g.hood_off[c0];
         const int ne = (int)(g.hood_off[c1] - e0);
-        // fast tile (flag set when the tile table was built): the elements fit,
-        // every hood has <= HOOD_FAST_MAX members and every element's vertex
-        // degree <= 32
-        const bool fast = tile.pad != 0 && ne <= HT_CAP;
-        if (fast) {
-            // every element's vertex has degree <= 32 and every hood <= 128
-            // members: the counts of each label among v's neighbours inside
-            // hood c are popcounts of the element's slot mask against the
-            // vertex's label masks.  The tile's member ids and slot masks are
-            // staged once (coalesced); then one thread per hood walks its
-            // elements, gathers their vertex data and keeps the exact sum.
-            for (int i = threadIdx.x; i < ne; i += HT_THREADS) {
-                s_el[i] = make_uint2((uint32_t)g.hood[e0 + i], g.el_slot[e0 + i]);
+        if (tile.pad != 0) {
+            auto energy = [&](uint32_t vid, uint32_t m) { return element_energy<L>(vrec, vid, m, u.beta_q); };
+            if (ne <= cap) {
+                for (int i = threadIdx.x; i < ne; i += HT_THREADS) s_el[i] = __ldg(g.el + e0 + i);
+                __syncthreads();
+                fast_hoods_p(lanes, g, c0, c1, e0, s_el, energy, hood_done);
+            } else {
+                // a tile whose last hood reaches far past its window (very large
+                // hoods): the element stream is read where it lies
+                fast_hoods<8>(g, c0, c1, e0, g.el + e0, energy, hood_done);
             }
-            __syncthreads();
-            // tiles of few, large hoods (k-neighbourhoods) share each hood
-            // between 2 or 4 adjacent lanes, which split its elements
-            const int nh = (int)(c1 - c0);
-            if (nh * 4 <= HT_THREADS)
-                fast_hoods<L, 4>(g, c0, c1, e0, s_el, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
-                                 my_unconv);
-            else if (nh * 2 <= HT_THREADS)
-                fast_hoods<L, 2>(g, c0, c1, e0, s_el, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
-                                 my_unconv);
-            else
-                fast_hoods<L, 1>(g, c0, c1, e0, s_el, vrec, beta_q, rsh, mode, t, W, tol40, hist, S_out, my_T,
-                                 my_unconv);
         } else {
-            // general tile: hood by hood, labels read from global memory
-            for (int64_t c = c0; c < c1; ++c) {
-                const int64_t hb = g.hood_off[c];
-                const int64_t k = g.hood_off[c + 1] - hb;
-                const int64_t nwh = (k + 31) >> 5;
-                const int64_t rb = g.row_off[c];
-                __int128 part = 0;
-                for (int64_t i = threadIdx.x; i < k; i += HT_THREADS) {
-                    const int64_t v = g.hood[hb + i];
-                    int cnt[L];
-#pragma unroll
-                    for (int l = 0; l < L; ++l) cnt[l] = 0;
-                    int dc = 0;
-                    for (int64_t w = 0; w < nwh; ++w) {
-                        uint32_t m = g.row[rb + i * nwh + w];
-                        dc += __popc(m);
-                        while (m) {
-                            const int bb = __ffs(m) - 1;
-                            m &= m - 1;
-                            const int xl = x_in[g.hood[hb + w * 32 + bb]];
-#pragma unroll
-                            for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
-                        }
-                    }
-                    const VRec<L> R = load_vrec<L>(vrec, v);
-                    // full scope: the record's D_min is already the element energy
-                    part += cf.scope == PMRF_SCOPE_FULL ? R.Dmin
-                                                        : R.Dmin + ((__int128)vrec_excess<L>(R, cnt, dc, beta_q) << rsh);
-                }
-                // exact integer sums: the reduction order does not matter
-#pragma unroll
-                for (int o = 16; o > 0; o >>= 1) part += shfl_xor_i128(part, o);
-                __syncthreads();
-                if (lane_id() == 0) s_wsum[warp_id()] = part;
-                __syncthreads();
-                if (threadIdx.x == 0) {
-                    __int128 sd = 0;
-                    for (int w = 0; w < HT_THREADS / 32; ++w) sd += s_wsum[w];
-                    const double S = unfix80(sd);
-                    if (mode == MODE_SWEEP) {
-                        if (S_out) S_out[c] = S;
-                    } else {
-                        my_unconv += hood_history(s40_of(sd), c, g.C, t, W, tol40, hist);
-                        my_T += sd;
-                    }
-                }
-            }
+            general_tile<L>(g, cf, c0, c1, x_in, vrec, u.beta_q, s_wsum, hood_done);
         }
     }
-    if (mode == MODE_SWEEP) return;
-    // per-tile partials: the exact sum of the tile's hood sums and the number
-    // of unconverged hoods (integer sums: any order gives the same result)
+    if (mode != MODE_SWEEP) tile_partials(acc, tile.part, hpart, s_wT, s_wu);
+}
+
+// the unit of every slice from the given parameters (standalone sweep)
+__global__ void k_units(int32_t S, int L, const double* __restrict__ theta, const double* __restrict__ yr,
+                        const RunCfg* __restrict__ cfgp, int max_deg, int max_hood, SliceUnit* __restrict__ unit,
+                        DevStatus* st) {
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    bool ok = true;
+    unit[s] = slice_unit(theta + (int64_t)s * L * 4, L, yr[2 * s], yr[2 * s + 1], cfgp->beta, cfgp->tol, max_deg,
+                         max_hood, ok);
+    if (!ok) record_error(st, PMRF_ERR_UNSUPPORTED, SITE_RANGE, s);
+}
+
+// the intensity range [min y, max y] of every slice (one block per slice)
+__global__ void k_yrange(const int64_t* __restrict__ vert_off, const double* __restrict__ y, double* __restrict__ yr) {
+    __shared__ double s_lo[FIN_THREADS / 32], s_hi[FIN_THREADS / 32];
+    const int s = blockIdx.x;
+    double lo = INFINITY, hi = -INFINITY;
+    for (int64_t v = vert_off[s] + threadIdx.x; v < vert_off[s + 1]; v += blockDim.x) {
+        lo = fmin(lo, y[v]);
+        hi = fmax(hi, y[v]);
+    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) my_T += shfl_xor_i128(my_T, o);
-    __syncthreads();
-    if (lane_id() == 0) s_wsum[warp_id()] = my_T;
-    if (my_unconv) atomicAdd(&s_unconv, my_unconv);
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+    }
+    if (lane_id() == 0) {
+        s_lo[warp_id()] = lo;
+        s_hi[warp_id()] = hi;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
-        __int128 a = 0;
-        for (int w = 0; w < HT_THREADS / 32; ++w) a += s_wsum[w];
-        hpart[(int64_t)tile.part * 3 + 0] = (int64_t)(uint64_t)(unsigned __int128)a;
-        hpart[(int64_t)tile.part * 3 + 1] = (int64_t)(a >> 64);
-        hpart[(int64_t)tile.part * 3 + 2] = s_unconv;
+        for (int w = 1; w < FIN_THREADS / 32; ++w) {
+            lo = fmin(lo, s_lo[w]);
+            hi = fmax(hi, s_hi[w]);
+        }
+        lo = fmin(lo, s_lo[0]);
+        hi = fmax(hi, s_hi[0]);
+        // an empty slice: any finite range
+        yr[2 * s] = lo <= hi ? lo : 0.0;
+        yr[2 * s + 1] = lo <= hi ? hi : 0.0;
     }
 }
 
@@ -977,7 +1084,8 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
                            const int64_t* __restrict__ vert_off, int32_t* __restrict__ active,
                            int32_t* __restrict__ iters, int32_t* __restrict__ conv, double* __restrict__ Thist,
                            int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op,
-                           double* __restrict__ dterm) {
+                           double* __restrict__ dterm, SliceUnit* __restrict__ unit, int32_t* __restrict__ qhist,
+                           const double* __restrict__ yr, int max_deg, int max_hood, DevStatus* st) {
     constexpr int NQ = 4 * L;  // label moments
     __shared__ double s_q[FIN_THREADS / 32][NQ];
     __shared__ __int128 s_T[FIN_THREADS / 32];
@@ -1033,7 +1141,11 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
         Tacc += s_T[w];
         uacc += s_u[w];
     }
-    const double Tsum = unfix80(Tacc), unconv = (double)uacc;
+    // T^t in the unit of this iteration (the unit slot of the hood ring takes
+    // the same unit); then the unit of the next iteration from theta^t
+    const int q_now = (mode == MODE_EM) ? unit[s].q : 0;
+    const double Tsum = em ? from_fixed(Tacc, q_now) : 0.0, unconv = (double)uacc;
+    if (em) qhist[(int64_t)s * cf.W + t % cf.W] = q_now;
     for (int l = 0; l < L; ++l) {
         const double n = tot[4 * l + 0];
         double* th = theta + ((int64_t)s * L + l) * 4;
@@ -1068,6 +1180,12 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
             dterm[((int64_t)s * L + l) * 2 + 0] = inv_two_var(th[2]);
             dterm[((int64_t)s * L + l) * 2 + 1] = log(th[2]);
         }
+    }
+    if (unit && (mode == MODE_INIT || mode == MODE_EM)) {
+        bool ok = true;
+        unit[s] = slice_unit(theta + (int64_t)s * L * 4, L, yr[2 * s], yr[2 * s + 1], cf.beta, cf.tol, max_deg,
+                             max_hood, ok);
+        if (!ok) record_error(st, PMRF_ERR_UNSUPPORTED, SITE_RANGE, s);
     }
     if (mode == MODE_INIT) {
         const bool nonempty = vert_off[s + 1] > vert_off[s];
@@ -1178,15 +1296,11 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
     int64_t c0 = lower_bound_dev<int64_t>(hood_off, cs, ce, lo);
     int64_t c1 = lower_bound_dev<int64_t>(hood_off, cs, ce, hi);
     if (j == ht_first[s + 1] - ht_first[s] - 1) c1 = ce;
-    // fast when the elements fit in shared memory, every hood has <=
-    // HOOD_FAST_MAX members and every element's vertex has degree <= 32 (the build flags
-    // the hoods that do not)
-    const int64_t e0 = hood_off[c0], e1 = hood_off[c1];
-    bool fast = (e1 - e0) <= HT_CAP;
+    // fast when every element's vertex has degree <= 32 (the build flags the
+    // hoods that do not)
     bool ok = true;
-    if (fast)
-        for (int64_t c = c0 + lane; c < c1; c += 32) ok = ok && hood_gen[c] == 0;
-    fast = __all_sync(0xffffffffu, ok) && fast;
+    for (int64_t c = c0 + lane; c < c1; c += 32) ok = ok && hood_gen[c] == 0;
+    const bool fast = __all_sync(0xffffffffu, ok);
     if (lane == 0) {
         Tile t;
         t.kind = 0;
@@ -1237,7 +1351,8 @@ int free_plans(pmrf_graph* g) {
 
 int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
-    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_vpart, w.d_hpart, w.d_theta, w.d_dterm, w.d_Thist, w.d_vrec,
+    void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_qhist, w.d_unit, w.d_yr, w.d_vpart, w.d_hpart, w.d_theta,
+                  w.d_dterm, w.d_Thist, w.d_vrec,
                   w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
@@ -1250,38 +1365,48 @@ int free_em(pmrf_graph* g) {
 
 namespace {
 
-// The default hood-tile window from the graph's mean hood size m: 94 m, to the
-// nearest multiple of 32, so that a tile holds about 94 hoods and its
-// HT_THREADS threads, one per hood, rarely need a second round; when that
-// exceeds MAX_HOOD_TILE (larger hoods), 1152 elements, measured best on the
-// 2-neighbourhoods (m = 28.6) and the volumes (m = 22.1) of the stack
-int default_hood_tile(const pmrf_graph* g) {
-    const double mean = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
-    const int te = (int)((mean * 94.0 + 16.0) / 32.0) * 32;
-    if (te > MAX_HOOD_TILE) return 1152;
-    return te < 512 ? 512 : te;
+// The default hood-tile window and lanes per hood from the graph's mean hood
+// size m: one lane per hood (two for hoods of 16 or more members, as in
+// k-neighbourhoods), and a window of about one round of the block's lanes,
+// 128 / lanes * m elements (1568 for the 1-neighbourhoods of a jittered-grid
+// oversegmentation, m = 12.3: measured best of 1152-2048)
+int default_hood_lanes(const pmrf_graph* g) {
+    const double m = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
+    return m >= 16.0 ? 2 : 1;
 }
 
-int effective_tiles(const pmrf_graph* g, int* te, int* vt) {
+int default_hood_tile(const pmrf_graph* g) {
+    const double m = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
+    const int te = (int)(((double)HT_THREADS / default_hood_lanes(g) * m + 16.0) / 32.0) * 32;
+    return std::max(512, std::min(MAX_HOOD_TILE, te));
+}
+
+int effective_tiles(const pmrf_graph* g, int* te, int* lanes) {
     *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : default_hood_tile(g);
-    *vt = VT_THREADS;  // one vertex per thread
-    (void)g;
+    *lanes = g->tuning.hood_lanes > 0 ? g->tuning.hood_lanes : default_hood_lanes(g);
     return PMRF_OK;
 }
 
+// elements a fast hood tile stages: its window plus the rest of a hood that
+// starts at the window's end (larger tiles read their stream in place)
+int hood_cap(const Plan* p) { return std::min(HT_CAP_MAX, p->hood_tile + std::max(p->max_hood, 1) - 1); }
+size_t hood_smem(const Plan* p) { return sizeof(uint2) * (size_t)hood_cap(p); }
+
 int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
-    int te, vt;
-    effective_tiles(g, &te, &vt);
-    auto key = std::make_pair(te, vt);
+    int te, lanes;
+    effective_tiles(g, &te, &lanes);
+    auto key = std::make_pair(te, lanes);
     auto it = g->plans.find(key);
     if (it != g->plans.end()) {
         *out = &it->second;
         return PMRF_OK;
     }
     const int32_t S = g->S;
+    const int vt = VT_THREADS;  // one vertex per thread
     Plan p;
     p.hood_tile = te;
-    p.vert_tile = vt;
+    p.hood_lanes = lanes;
+    p.max_hood = g->max_hood;
     std::vector<int64_t> vfirst(S + 1, 0), hfirst(S + 1, 0);
     for (int i = 0; i < S; ++i) {
         const int64_t nv = g->h_vert_off[i + 1] - g->h_vert_off[i];
@@ -1357,16 +1482,8 @@ RunCfg to_run(const pmrf_config* c) {
     r.sigma_min = c->sigma_min;
     r.init_lo = c->init_lo;
     r.init_hi = c->init_hi;
-    // units 2^-hq of the hood pass's label excesses: beta_q = beta * 2^hq stays
-    // below 2^51, so a fast hood's <= 128 elements of <= 32 beta_q each sum
-    // below 2^63 (beta < 2^e with frexp's exponent e)
-    int e = 0;
-    if (r.beta > 0.0) std::frexp(r.beta, &e);
-    r.hq = std::max(0, std::min(51, 51 - e));
     r.scope = c->potts_scope;
     r.rule = c->replica_rule;
-    r.pad = 0;
-    r.beta_q = (int64_t)std::llrint(std::ldexp(r.beta, r.hq));
     return r;
 }
 
@@ -1398,6 +1515,13 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) 
     if (!rc2) rc2 = dalloc(&w.d_iters, S, s);
     if (!rc2) rc2 = dalloc(&w.d_conv, S, s);
     if (!rc2) rc2 = dalloc(&w.d_nactive, 1, s);
+    if (!rc2) rc2 = dalloc(&w.d_qhist, S * rc.W, s);
+    if (!rc2) rc2 = dalloc((char**)&w.d_unit, (int64_t)sizeof(SliceUnit) * std::max<int64_t>(S, 1), s);
+    if (!rc2) rc2 = dalloc(&w.d_yr, 2 * S, s);
+    if (!rc2 && S > 0) {
+        k_yrange<<<(unsigned)S, FIN_THREADS, 0, s>>>(g->d_vert_off, g->d_y, w.d_yr);
+        ::pmrf::note_launch(1);
+    }
     if (!rc2) rc2 = dalloc(&w.d_vrec, g->V * vrec_words(rc.L), s);  // hood-pass vertex records
     if (!rc2 && (reinterpret_cast<uintptr_t>(w.d_vrec) & 31))  // read and written 32 bytes at a time
         rc2 = fail(PMRF_ERR_CUDA, "vertex record table is not 32-byte aligned");
@@ -1496,12 +1620,14 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     if (p->n_vtiles > 0) {
         k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
                                                                 w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
-                                                                nullptr, w.d_vpart, g->d_status, nullptr);
+                                                                nullptr, w.d_vpart, g->d_status, nullptr, nullptr);
         ::pmrf::note_launch(1);
     }
+    SliceUnit* unit = (SliceUnit*)w.d_unit;
     k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                             w.d_hpart, nullptr, w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
-                                            w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
+                                            w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm, unit, w.d_qhist,
+                                            w.d_yr, g->max_deg, g->max_hood, g->d_status);
     ::pmrf::note_launch(1);
     if (cc) {
         k_set_cond<<<1, 1, 0, s>>>(cc->h[0], w.d_nactive, cc->counter,
@@ -1523,19 +1649,21 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (p->n_vtiles > 0) {
             kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
                                                                     xout, w.d_theta, w.d_dterm, nullptr, nullptr,
-                                                                    w.d_vpart, g->d_status, w.d_vrec);
+                                                                    w.d_vpart, g->d_status, w.d_vrec, unit);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
         if (p->n_htiles > 0) {
-            k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(z.dg, z.ht, MODE_EM, t, z.d_cfg, w.d_active, xin,
-                                                                  w.d_vrec, w.d_hist, nullptr, w.d_hpart);
+            k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
+                z.dg, z.ht, MODE_EM, t, p->hood_lanes, z.d_cfg, w.d_active, xin, w.d_vrec, unit, w.d_qhist,
+                w.d_hist, nullptr, w.d_hpart, hood_cap(p));
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
         k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                                 w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off, w.d_active,
-                                                w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm);
+                                                w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm,
+                                                unit, w.d_qhist, w.d_yr, g->max_deg, g->max_hood, g->d_status);
         ::pmrf::note_launch(1);
         if (cc) {
             if (t < rc.max_iters) {
@@ -1692,7 +1820,7 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
     pmrf_graph::CachedExec* ce = nullptr;
     for (auto& e : g->execs)
         if (e.L == rc.L && e.W == rc.W && e.max_iters == rc.max_iters && e.hood_tile == p->hood_tile &&
-            e.vert_tile == p->vert_tile && e.var == (int)is_variant(rc))
+            e.hood_lanes == p->hood_lanes && e.var == (int)is_variant(rc))
             ce = &e;
     if (!ce) {
         int64_t nodes = 0;
@@ -1712,7 +1840,7 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
         c.W = rc.W;
         c.max_iters = rc.max_iters;
         c.hood_tile = p->hood_tile;
-        c.vert_tile = p->vert_tile;
+        c.hood_lanes = p->hood_lanes;
         c.var = (int)is_variant(rc);
         c.nkernels = nodes;
         g->execs.push_back(c);
@@ -1734,15 +1862,24 @@ int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, cons
     DevGraph dg = view(g);
     const Tile* vt = p->d_tiles;
     const Tile* ht = p->d_tiles + p->n_vtiles;
+    EMWork& w = g->em;
+    SliceUnit* unit = (SliceUnit*)w.d_unit;
+    if (g->S > 0) {
+        k_units<<<(unsigned)ceil_div(g->S, 128), 128, 0, s>>>(g->S, L, theta, w.d_yr, d_cfg, g->max_deg, g->max_hood,
+                                                             unit, g->d_status);
+        ::pmrf::note_launch(1);
+    }
     if (p->n_vtiles > 0) {
         const auto kv = var ? &k_vertex<L, true> : &k_vertex<L, false>;
         kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
-                                                                nullptr, nullptr, Eout, nullptr, g->d_status, vrec);
+                                                                nullptr, nullptr, Eout, nullptr, g->d_status, vrec,
+                                                                unit);
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
-        k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, 0, s>>>(dg, ht, MODE_SWEEP, 1, d_cfg, nullptr, xin, vrec,
-                                                              nullptr, Sout, nullptr);
+        k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
+            dg, ht, MODE_SWEEP, 1, p->hood_lanes, d_cfg, nullptr, xin, vrec, unit, nullptr, nullptr, Sout, nullptr,
+            hood_cap(p));
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
@@ -1757,12 +1894,13 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     if (p->n_vtiles > 0) {
         k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
                                                                 nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
-                                                                g->d_status, nullptr);
+                                                                g->d_status, nullptr, nullptr);
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)g->S, FIN_THREADS, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
                                                w.d_vpart, w.d_hpart, prev, out, g->d_vert_off, nullptr, nullptr,
-                                               nullptr, nullptr, nullptr, nullptr, nullptr);
+                                               nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                               nullptr, 0, 0, g->d_status);
     ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;
@@ -1928,10 +2066,13 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
         rc = fail(PMRF_ERR_CUDA, "event creation failed");
     pmrf_tuning keep = g->tuning, win = g->tuning;
     float best_ms = 1e30f;
-    const int cands[] = {0, 512, 768, 1024, 1248};  // 0: the window from the mean hood size
-    for (int c = 0; c < 5 && !rc; ++c) {
+    // candidates: the defaults (0, 0), then windows and lanes per hood around them
+    const int cands[][2] = {{0, 0}, {576, 0}, {2048, 0}, {0, 1}, {0, 2}, {0, 4}, {0, 8}};
+    const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
+    for (int c = 0; c < ncand && !rc; ++c) {
         pmrf_tuning t = keep;
-        t.hood_tile = cands[c];
+        t.hood_tile = cands[c][0];
+        t.hood_lanes = cands[c][1];
         cudaDeviceSynchronize();
         free_plans(g);
         free_em(g);

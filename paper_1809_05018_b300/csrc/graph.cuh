@@ -7,10 +7,6 @@
 
 #include "common.cuh"
 
-// largest hood the hood pass takes on its fast path (every member of degree
-// <= 32): 128 elements of excess at most 32 beta_q (< 2^56) sum below 2^63
-constexpr int HOOD_FAST_MAX = 128;
-
 namespace pmrf {
 
 // Per-tile descriptor of the persistent EM launch.  kind 0 = hood tile (hoods
@@ -21,11 +17,11 @@ struct Tile {
     int32_t slice;
     int32_t a0, a1;
     int32_t part;
-    int32_t pad;
+    int32_t pad;  // hood tiles: 1 when every member has degree <= 32
 };
 
 struct Plan {  // tile table for one tuning
-    int32_t hood_tile = 0, vert_tile = 0;
+    int32_t hood_tile = 0, hood_lanes = 0, max_hood = 0;
     int64_t n_tiles = 0, n_htiles = 0, n_vtiles = 0;
     Tile* d_tiles = nullptr;
     int32_t* d_slice_ntiles = nullptr;   // [S] tiles per slice (both kinds)
@@ -37,10 +33,13 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     int L = 0, W = 0, max_iters = 0;
     int64_t n_htiles = 0, n_vtiles = 0;
     uint8_t* d_x[2] = {nullptr, nullptr};  // label double buffer
-    int64_t* d_hist = nullptr;     // [W][C] hood-sum ring, units of 2^-40
+    int64_t* d_hist = nullptr;     // [W][C] hood-sum ring, each in the unit of its iteration
+    int32_t* d_qhist = nullptr;    // [S][W] unit exponent of each ring slot
+    void* d_unit = nullptr;        // [S] fixed-point unit of the current iteration (em.cu SliceUnit)
+    double* d_yr = nullptr;        // [S][2] intensity range of each slice
     double* d_vpart = nullptr;     // [n_vtiles][L][4]
-    int64_t* d_hpart = nullptr;    // [n_htiles][3]: the tile's exact T partial (low, high word, units
-                                   // 2^-80) and its unconverged-hood count
+    int64_t* d_hpart = nullptr;    // [n_htiles][3]: the tile's exact T partial (low, high word, in the
+                                   // slice's unit) and its unconverged-hood count
     double* d_theta = nullptr;     // [S][L][4] current parameters
     double* d_dterm = nullptr;     // [S][L][2] 1/(2 sigma^2) and ln sigma of the current parameters
     double* d_Thist = nullptr;     // [S][W] ring of totals
@@ -88,11 +87,12 @@ struct pmrf_graph {
     int64_t* d_rep_off = nullptr;        // [V+1]
     int64_t* d_rep_woff = nullptr;       // [V+1] word offsets of replica slot masks
     uint32_t* d_rep_mask = nullptr;      // [n_rep_words]
-    uint32_t* d_el_slot = nullptr;       // [N_el] slot mask of each hood element (degree <= 32), hood-major
-    uint8_t* d_hood_gen = nullptr;       // [C] 1: the hood has > HOOD_FAST_MAX members or a member of degree > 32
+    uint2* d_el = nullptr;               // [N_el] hood-pass element stream, hood-major: (vertex id, bit 31 set on
+                                         // the last element of its hood; slot mask, 0 for degree > 32)
+    uint8_t* d_hood_gen = nullptr;       // [C] 1: the hood has a member of degree > 32 (hood-local rows)
     pmrf::DevStatus* d_status = nullptr;
 
-    pmrf_tuning tuning{0, 0, 0, 1, 0};
+    pmrf_tuning tuning{0, 0, 1, 0};
     // profiling events of the EM loop: per iteration t (1-based), index 3*(t-1):
     // before the vertex pass, after it, after the hood pass
     std::vector<cudaEvent_t> prof_ev;
@@ -104,7 +104,7 @@ struct pmrf_graph {
     // serves every call with the same key
     struct CachedExec {
         cudaGraphExec_t exec = nullptr;
-        int L = 0, W = 0, max_iters = 0, hood_tile = 0, vert_tile = 0;
+        int L = 0, W = 0, max_iters = 0, hood_tile = 0, hood_lanes = 0;
         int var = 0;  // vertex pass compiled with the sweep variants
         int64_t nkernels = 0;  // kernel nodes per replay
     };

@@ -24,8 +24,9 @@ def test_results_independent_of_tiles_and_replay():
     cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=30)
     ref = g.em(cfg, want_T=True)
     ref = {k: v.clone() for k, v in ref.items()}
-    for tuning in (dict(hood_tile=128), dict(hood_tile=512), dict(hood_tile=1248), dict(vert_tile=64),
-                   dict(vert_tile=1024), dict(use_cuda_graph=0), dict(profile=1)):
+    for tuning in (dict(hood_tile=128), dict(hood_tile=512), dict(hood_tile=2048), dict(hood_lanes=1),
+                   dict(hood_lanes=2), dict(hood_lanes=8), dict(hood_tile=128, hood_lanes=8),
+                   dict(use_cuda_graph=0), dict(profile=1)):
         g.set_tuning(**tuning)
         out = g.em(cfg, want_T=True)
         for k in ("labels", "params", "iters", "converged", "T_hist"):
@@ -42,12 +43,12 @@ def test_autotune_and_kernel_times():
     ref = g.em(cfg)
     ref = {k: v.clone() for k, v in ref.items()}
     best = g.autotune(cfg)
-    assert best["hood_tile"] in (0, 512, 768, 1024, 1248)  # 0: the default from the mean hood size
-    assert g.tuning()["hood_tile"] == best["hood_tile"]
+    assert (best["hood_tile"], best["hood_lanes"]) in ((0, 0), (576, 0), (2048, 0), (0, 1), (0, 2), (0, 4), (0, 8))
+    assert g.tuning()["hood_tile"] == best["hood_tile"] and g.tuning()["hood_lanes"] == best["hood_lanes"]
     out = g.em(cfg)
     for k in ("labels", "params", "iters"):
         assert torch.equal(out[k], ref[k]), k
-    g.set_tuning(hood_tile=best["hood_tile"], profile=1)
+    g.set_tuning(hood_tile=best["hood_tile"], hood_lanes=best["hood_lanes"], profile=1)
     out = g.em(cfg)
     tv, th = g.em_kernel_times()
     n_run = int(out["iters"].max())
