@@ -242,6 +242,24 @@ __device__ __forceinline__ void store_vrec_words(uint64_t* __restrict__ p, const
                      : "memory");
 }
 
+// For L = 2 the record is split: words 0-1 in a 16-byte array [V][2], the mask
+// in a 4-byte array [V] after it, so that a hood-pass gather moves 16 + 4
+// bytes (more records per cache line) instead of 32
+__device__ __forceinline__ const uint32_t* vrec2_masks(const uint64_t* vrec, int64_t V) {
+    return reinterpret_cast<const uint32_t*>(vrec + 2 * V);
+}
+
+template <int L>
+__device__ __forceinline__ void store_vrec(uint64_t* __restrict__ vrec, int64_t V, int64_t v, const uint64_t* w) {
+    if constexpr (L == 2) {
+        asm volatile("st.global.v2.b64 [%0], {%1, %2};" ::"l"(vrec + 2 * v), "l"(w[0]), "l"(w[1]) : "memory");
+        reinterpret_cast<uint32_t*>(vrec + 2 * V)[v] = (uint32_t)w[2];
+    } else {
+        constexpr int NW = vrec_words(L);
+        store_vrec_words(vrec + v * NW, w, NW);
+    }
+}
+
 // the data terms in the unit: every D_l rounded once, amin the lowest label
 // attaining the least, each label's excess over it (saturated at DQ_SAT)
 template <int L>
@@ -269,18 +287,18 @@ __device__ __forceinline__ int64_t data_fixed(const double (&D)[L], int q, uint6
 // Potts scope: every replica of v carries the same energies): D_min = E, every
 // excess 0 and no label masks, so the hood pass adds E for each element
 template <int L>
-__device__ __forceinline__ void write_vrec_const(uint64_t* __restrict__ vrec, int64_t v, int64_t E) {
+__device__ __forceinline__ void write_vrec_const(uint64_t* __restrict__ vrec, int64_t V, int64_t v, int64_t E) {
     constexpr int NW = vrec_words(L);
     uint64_t w[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) w[k] = 0ull;
     w[0] = (uint64_t)E;
-    store_vrec_words(vrec + v * NW, w, NW);
+    store_vrec<L>(vrec, V, v, w);
 }
 
 // the hood-pass record of vertex v (layout above) from its FP64 data terms
 template <int L>
-__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t v, const double (&D)[L],
+__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t V, int64_t v, const double (&D)[L],
                                            const uint32_t (&lmw)[L], int q) {
     constexpr int NW = vrec_words(L);
     uint64_t dq[L];
@@ -304,7 +322,7 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
             w[u >> 1] |= (uint64_t)lmw[k] << (32 * (u & 1));
         }
     }
-    store_vrec_words(vrec + v * NW, w, NW);
+    store_vrec<L>(vrec, V, v, w);
 }
 
 // label counts among the neighbours of v in one replica with a multi-word
@@ -398,7 +416,7 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
                 const int64_t e = to_fixed(D[l], q) + beta_q * (int64_t)M[l];
                 if (l == 0 || e < Emin) Emin = e;
             }
-            write_vrec_const<L>(vrec, v, Emin);
+            write_vrec_const<L>(vrec, g.V, v, Emin);
         }
         return lab;
     }
@@ -489,7 +507,7 @@ __device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, c
         for (int l = 0; l < L; ++l)
             if (l == lab) Estar = D[l] + c.beta * (double)kmin[l];
     }
-    if (vrec) write_vrec<L>(vrec, v, D, lm, q);
+    if (vrec) write_vrec<L>(vrec, g.V, v, D, lm, q);
     return lab;
 }
 
@@ -605,7 +623,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                     }
                 }
                 // the hood pass of this iteration reads v's data terms and label masks
-                if (vrec) write_vrec<L>(vrec, v, D, lm, uq);
+                if (vrec) write_vrec<L>(vrec, g.V, v, D, lm, uq);
                 // every vertex lies in at least one hood, so M_l is set (and
                 // <= 32 when d <= 32)
                 double Md[L];
@@ -718,15 +736,21 @@ struct VRec {
 
 // The records are gathered (one 32-byte chunk per element for L <= 3)
 template <int L>
-__device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, int64_t v) {
+__device__ __forceinline__ VRec<L> load_vrec(const uint64_t* __restrict__ vrec, int64_t V, int64_t v) {
     constexpr int NW = vrec_words(L);
     uint64_t w[NW];
-    const uint64_t* p = vrec + v * NW;
+    if constexpr (L == 2) {
+        asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(w[0]), "=l"(w[1]) : "l"(vrec + 2 * v));
+        w[2] = __ldg(vrec2_masks(vrec, V) + v);
+        w[3] = 0;
+    } else {
+        const uint64_t* p = vrec + v * NW;
 #pragma unroll
-    for (int k = 0; k < NW; k += 4)
-        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-            : "=l"(w[k]), "=l"(w[k + 1]), "=l"(w[k + 2]), "=l"(w[k + 3])
-            : "l"(p + k));
+        for (int k = 0; k < NW; k += 4)
+            asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
+                : "=l"(w[k]), "=l"(w[k + 1]), "=l"(w[k + 2]), "=l"(w[k + 3])
+                : "l"(p + k));
+    }
     VRec<L> R;
     R.Dmin = (int64_t)w[0];
     const int amin = L > 1 ? (int)(w[1] >> 61) : 0;
@@ -783,21 +807,19 @@ __device__ __forceinline__ int slot_counts(const VRec<L>& R, uint32_t m, int (&c
 // Element energy Emin(c,v) in the slice's unit, from v's record and the
 // element's slot mask (every neighbour of v of degree <= 32)
 template <int L>
-__device__ __forceinline__ int64_t element_energy(const uint64_t* __restrict__ vrec, uint32_t vid, uint32_t m,
-                                                  int64_t beta_q) {
+__device__ __forceinline__ int64_t element_energy(const uint64_t* __restrict__ vrec, int64_t V, uint32_t vid,
+                                                  uint32_t m, int64_t beta_q) {
     if constexpr (L == 2) {
-        uint64_t w0, w1, w2, w3;
-        asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];"
-            : "=l"(w0), "=l"(w1), "=l"(w2), "=l"(w3)
-            : "l"(vrec + (int64_t)vid * 4));
-        (void)w3;
-        const int cb = __popc(m & (uint32_t)w2);
+        uint64_t w0, w1;
+        asm("ld.global.nc.v2.b64 {%0, %1}, [%2];" : "=l"(w0), "=l"(w1) : "l"(vrec + 2 * (int64_t)vid));
+        const uint32_t mb = __ldg(vrec2_masks(vrec, V) + vid);
+        const int cb = __popc(m & mb);
         const int k = 2 * cb - __popc(m);
         const int64_t dq = (int64_t)(w1 & DQ_SAT);
         const int64_t bk = beta_q * k;
         return (int64_t)w0 + beta_q * cb - (bk > dq ? bk - dq : 0);
     } else {
-        const VRec<L> R = load_vrec<L>(vrec, (int64_t)vid);
+        const VRec<L> R = load_vrec<L>(vrec, V, (int64_t)vid);
         int cnt[L];
         const int dc = slot_counts<L>(R, m, cnt);
         return R.Dmin + vrec_excess<L>(R, cnt, dc, beta_q);
@@ -839,15 +861,6 @@ __device__ __forceinline__ int hood_history(int64_t S, int64_t c, int64_t C, int
     }
     hist[(int64_t)(t % W) * C + c] = S;
     return unconv;
-}
-
-// Element energy of L = 2 from a record's first three words (layout above)
-__device__ __forceinline__ int64_t energy2(uint64_t w0, uint64_t w1, uint32_t mb, uint32_t m, int64_t beta_q) {
-    const int cb = __popc(m & mb);
-    const int k = 2 * cb - __popc(m);
-    const int64_t dq = (int64_t)(w1 & DQ_SAT);
-    const int64_t bk = beta_q * k;
-    return (int64_t)w0 + beta_q * cb - (bk > dq ? bk - dq : 0);
 }
 
 // The fast-tile hood sums: P adjacent lanes per hood (1, 2, 4 or 8), each taking
@@ -952,7 +965,7 @@ __device__ __forceinline__ void general_tile(const DevGraph& g, const RunCfg& cf
                     for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
                 }
             }
-            const VRec<L> R = load_vrec<L>(vrec, v);
+            const VRec<L> R = load_vrec<L>(vrec, g.V, v);
             // full scope: the record's D_min is already the element energy
             part += cf.scope == PMRF_SCOPE_FULL ? R.Dmin : R.Dmin + vrec_excess<L>(R, cnt, dc, beta_q);
         }
@@ -1012,7 +1025,7 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
         const int64_t e0 = g.hood_off[c0];
         const int ne = (int)(g.hood_off[c1] - e0);
         if (tile.pad != 0) {
-            auto energy = [&](uint32_t vid, uint32_t m) { return element_energy<L>(vrec, vid, m, u.beta_q); };
+            auto energy = [&](uint32_t vid, uint32_t m) { return element_energy<L>(vrec, g.V, vid, m, u.beta_q); };
             if (ne <= cap) {
                 for (int i = threadIdx.x; i < ne; i += HT_THREADS) s_el[i] = __ldg(g.el + e0 + i);
                 __syncthreads();
