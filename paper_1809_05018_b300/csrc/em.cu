@@ -983,11 +983,51 @@ __device__ __forceinline__ void general_tile(const DevGraph& g, const RunCfg& cf
     }
 }
 
+// ---------------------------------------------------------------------------
+// bulk copies into shared memory (the TMA engine) tracked by an mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// copy `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared
+// memory; completion is counted on bar
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// wait for the phase `parity` of bar to complete, at most ~2^20 polls; false
+// (and the status word set) when the wait gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    record_error(st, PMRF_ERR_TIMEOUT, SITE_WAIT, 0);
+    return false;
+}
+
 // The hood pass: one block per hood tile (consecutive hoods of one slice, their
 // elements contiguous).  Fast tiles (every member of degree <= 32): the tile's
 // element stream (member id and slot mask, one 8-byte word each) is staged in
-// shared memory with coalesced loads, then lanes-per-hood adjacent lanes take
-// each hood, gather its members' records and sum the element energies.
+// shared memory by one bulk copy (the TMA engine, completion counted on an
+// mbarrier), then lanes-per-hood adjacent lanes take each hood, gather its
+// members' records and sum the element energies.
 // General tiles go hood by hood through the hood-local adjacency rows.
 template <int L>
 __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph g, const Tile* __restrict__ tiles,
@@ -999,8 +1039,11 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                                                      const SliceUnit* __restrict__ unit,
                                                      const int32_t* __restrict__ qhist,
                                                      int64_t* __restrict__ hist, double* __restrict__ S_out,
-                                                     int64_t* __restrict__ hpart, int cap) {
-    extern __shared__ uint2 s_el[];  // cap elements: the window plus the rest of its last hood
+                                                     int64_t* __restrict__ hpart, int cap, DevStatus* st) {
+    // cap + 2 elements: the window plus the rest of its last hood, and one word
+    // either side for the 16-byte alignment of the bulk copy
+    extern __shared__ __align__(16) uint2 s_el[];
+    __shared__ __align__(8) uint64_t s_bar;
     __shared__ int64_t s_wsum[HT_THREADS / 32];
     __shared__ __int128 s_wT[HT_THREADS / 32];
     __shared__ int s_wu[HT_THREADS / 32];
@@ -1027,9 +1070,20 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
         if (tile.pad != 0) {
             auto energy = [&](uint32_t vid, uint32_t m) { return element_energy<L>(vrec, g.V, vid, m, u.beta_q); };
             if (ne <= cap) {
-                for (int i = threadIdx.x; i < ne; i += HT_THREADS) s_el[i] = __ldg(g.el + e0 + i);
-                __syncthreads();
-                fast_hoods_p(lanes, g, c0, c1, e0, s_el, energy, hood_done);
+                const int64_t ea = e0 & ~1ll, eb = (e0 + ne + 1) & ~1ll;  // 16-byte aligned bounds
+                if (threadIdx.x == 0) {
+                    mbar_init(&s_bar);
+                    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                    const uint32_t bytes = (uint32_t)((eb - ea) * 8);
+                    mbar_expect(&s_bar, bytes);
+                    bulk_copy(s_el, g.el + ea, bytes, &s_bar);
+                }
+                __syncthreads();  // the barrier is initialised before anyone polls it
+                // a wait that gives up has set the status word; it waits once
+                // more (bounded) so that no copy is left in flight, and the
+                // tile's sums are left out
+                if (mbar_wait(&s_bar, 0, st) || mbar_wait(&s_bar, 0, st))
+                    fast_hoods_p(lanes, g, c0, c1, e0, s_el + (e0 - ea), energy, hood_done);
             } else {
                 // a tile whose last hood reaches far past its window (very large
                 // hoods): the element stream is read where it lies
@@ -1403,7 +1457,7 @@ int effective_tiles(const pmrf_graph* g, int* te, int* lanes) {
 // elements a fast hood tile stages: its window plus the rest of a hood that
 // starts at the window's end (larger tiles read their stream in place)
 int hood_cap(const Plan* p) { return std::min(HT_CAP_MAX, p->hood_tile + std::max(p->max_hood, 1) - 1); }
-size_t hood_smem(const Plan* p) { return sizeof(uint2) * (size_t)hood_cap(p); }
+size_t hood_smem(const Plan* p) { return sizeof(uint2) * (size_t)(hood_cap(p) + 2); }
 
 int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
     int te, lanes;
@@ -1420,6 +1474,8 @@ int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
     p.hood_tile = te;
     p.hood_lanes = lanes;
     p.max_hood = g->max_hood;
+    // the hood pass bulk-copies the element stream from 16-byte boundaries
+    if (reinterpret_cast<uintptr_t>(g->d_el) & 15) return fail(PMRF_ERR_CUDA, "element stream is not 16-byte aligned");
     std::vector<int64_t> vfirst(S + 1, 0), hfirst(S + 1, 0);
     for (int i = 0; i < S; ++i) {
         const int64_t nv = g->h_vert_off[i + 1] - g->h_vert_off[i];
@@ -1669,7 +1725,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         if (p->n_htiles > 0) {
             k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
                 z.dg, z.ht, MODE_EM, t, p->hood_lanes, z.d_cfg, w.d_active, xin, w.d_vrec, unit, w.d_qhist,
-                w.d_hist, nullptr, w.d_hpart, hood_cap(p));
+                w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status);
             ::pmrf::note_launch(1);
         }
         if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
@@ -1892,7 +1948,7 @@ int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, cons
     if (p->n_htiles > 0) {
         k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
             dg, ht, MODE_SWEEP, 1, p->hood_lanes, d_cfg, nullptr, xin, vrec, unit, nullptr, nullptr, Sout, nullptr,
-            hood_cap(p));
+            hood_cap(p), g->d_status);
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
