@@ -39,17 +39,18 @@ import synth  # noqa: E402
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 FALLBACK_HBM_GBS = 6400.0
 
-# DRAM traffic of the dominant kernel from one ncu capture (the command and the
-# counters are in profiles/k_hood_stack512.md): dram__bytes_read.sum +
-# dram__bytes_write.sum of the hood-pass launch of iteration 4 of this bench's
-# first step (every slice active), with the SHA-1 of the sources it was taken
-# on: the opening section of em.cu (constants and shared structures) and its
-# hood-pass section (from the "// hood pass" header to the next section), and
-# the headers em.cu includes.  It is reported, scaled to the average
-# launch by its algorithmic bytes, only while those sources are unchanged;
-# otherwise the field is null.
-TRAFFIC_CAPTURE = {"kernel": "k_hood", "workload": "stack512", "bytes_all_active": 3488671488.0,
-                   "sources_sha1": "10a4cc49b4f58dfbba6fe3df78c57ae176ae4edf"}
+# DRAM traffic of the dominant kernel, from one ncu capture of
+# dram__bytes_read.sum + dram__bytes_write.sum on a launch with every slice
+# active, taken on the first 64 slices of stack512 (a capture of the full
+# batch would hold far more device memory than a counter capture should),
+# stored as bytes per algorithmic byte of the same launch, with the SHA-1 of
+# the sources it was taken on: the opening section of em.cu (constants and
+# shared structures), its hood-pass section (from the "// hood pass" header to
+# the next section) and the headers em.cu includes.  bench.py reports it,
+# scaled to its own average launch by the algorithmic bytes, only while those
+# sources are unchanged; otherwise the field is null.
+TRAFFIC_CAPTURE = {"kernel": "k_hood", "workload": "stack512", "per_alg_byte": 0.8875,
+                   "sources_sha1": "c71dce1f0247b83ece937d15a6e1615132b211ab"}
 TRAFFIC_SECTION = ("paper_1809_05018_b300/csrc/em.cu", "// hood pass\n")
 TRAFFIC_SOURCES = ("paper_1809_05018_b300/csrc/graph.cuh", "paper_1809_05018_b300/csrc/common.cuh")
 
@@ -70,12 +71,12 @@ def sources_sha1() -> str:
     return h.hexdigest()
 
 
-def captured_traffic(kernel: str, workload: str, per_launch: float, all_active: float):
+def captured_traffic(kernel: str, workload: str, per_launch: float):
     c = TRAFFIC_CAPTURE
-    if (c["bytes_all_active"] is None or kernel != c["kernel"] or workload != c["workload"]
-            or c["sources_sha1"] != sources_sha1() or all_active <= 0):
+    if (c["per_alg_byte"] is None or kernel != c["kernel"] or workload != c["workload"]
+            or c["sources_sha1"] != sources_sha1()):
         return None
-    return round(c["bytes_all_active"] * per_launch / all_active, 1)
+    return round(c["per_alg_byte"] * per_launch, 1)
 
 
 def parse():
@@ -91,7 +92,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--e2e-chunks", type=int, default=4, help="chunks per step in the end-to-end leg")
-    # the scope table's NEXT rows, measured on the same workload (default: the paper's form)
+    # variants of the method beside the paper's form, measured on the same workload
     ap.add_argument("--hood-depth", type=int, default=1, help="k of the k-neighbourhoods")
     ap.add_argument("--potts-scope", type=int, default=0, choices=[0, 1], help="0 hood, 1 full neighbourhood")
     ap.add_argument("--replica-rule", type=int, default=0, choices=[0, 1, 2], help="0 min, 1 mean energy, 2 vote")
@@ -234,7 +235,8 @@ def host_inputs(wl, threads=None):
 def sweep_bytes(g, L, W):
     """Algorithmic bytes of one MAP sweep of every slice, split by kernel, plus
     the per-slice vectors needed to weight iterations by the slices still
-    active (see the design notes for the model)."""
+    active.  A vertex record carries D_min (8 B) and, per other label, its
+    excess (8 B) and a label mask (4 B): 8 + 12 (L - 1) bytes."""
     vo = g.array("VERT_OFF").numpy()
     hso = g.array("HOOD_SLICE_OFF").numpy()
     ho = g.array("HOOD_OFF").numpy()
@@ -245,12 +247,13 @@ def sweep_bytes(g, L, W):
     Es = ho[hso[1:]] - ho[hso[:-1]]
     Adj = ao[vo[1:]] - ao[vo[:-1]]
     Rep = ro[vo[1:]] - ro[vo[:-1]]  # replica words (== replicas when every degree <= 32)
-    # vertex pass: per vertex adj_off, rep_woff, y (8 each), label in+out (2), D table write (8L);
-    # per adjacency entry 4 B, per replica mask word 4 B
-    vb = Vs * (24 + 2 + 8 * L) + 4 * Adj + 4 * Rep
-    # hood pass: per hood hood_off + row_off (16) and the W-deep history ring (8W read + 8 write);
-    # per element hood member id + row word (8); per vertex its label and D row, read once (1 + 8L)
-    hb = Cs * (16 + 8 * W + 8) + 8 * Es + Vs * (1 + 8 * L)
+    rec = 8 + 12 * (L - 1)
+    # vertex pass: per vertex adj_off, rep_woff, y (8 each), label in + out (2), its record written;
+    # per adjacency entry 4 B (neighbour id; its label byte comes with it), per replica mask word 4 B
+    vb = Vs * (24 + 2 + rec) + 4 * Adj + 4 * Rep
+    # hood pass: per hood its element offset (8) and the W-deep history ring (8W read + 8 write);
+    # per element member id + slot mask (8); per vertex its record, read once
+    hb = Cs * (8 + 8 * W + 8) + 8 * Es + Vs * rec
     return vb.astype(np.float64), hb.astype(np.float64), dict(V=int(Vs.sum()), C=int(Cs.sum()), N_el=int(Es.sum()),
                                                                E=int(Adj.sum() // 2), Es=Es)
 
@@ -332,11 +335,43 @@ def run_ours(a):
     ee1.record()
     torch.cuda.synchronize()
     em_ms = ee0.elapsed_time(ee1) / reps
+    # the same loop launched kernel by kernel (no CUDA graph replay)
+    g.set_tuning(use_cuda_graph=0)
+    g.em(cfg)
+    torch.cuda.synchronize()
+    ee0.record()
+    for _ in range(reps):
+        g.em(cfg)
+    ee1.record()
+    torch.cuda.synchronize()
+    em_ms_direct = ee0.elapsed_time(ee1) / reps
     g.set_tuning(profile=1)
     g.em(cfg)  # capture
     g.em(cfg)
     torch.cuda.synchronize()
     msv, msh = g.em_kernel_times()
+    g.set_tuning()
+    extra = {}
+    if wl.name == "grad64":
+        # the adjoint of the summed pseudo-log-likelihood (value and gradient in
+        # one pass) and the 30-step beta fit through torch.autograd, at the
+        # final labels
+        from paper_1809_05018_b300.autograd import fit_beta
+        mu = o2["params"][:, :, 1].contiguous()
+        sg = o2["params"][:, :, 2].contiguous()
+        g.pll_value_and_grad(L, o2["labels"], mu, sg, 0.2, ones)
+        torch.cuda.synchronize()
+        ee0.record()
+        for _ in range(reps):
+            g.pll_value_and_grad(L, o2["labels"], mu, sg, 0.2, ones)
+        ee1.record()
+        torch.cuda.synchronize()
+        adj_ms = ee0.elapsed_time(ee1) / reps
+        t0 = time.perf_counter()
+        traj = fit_beta(g, o2["labels"], mu, sg, beta0=0.2, steps=30)
+        torch.cuda.synchronize()
+        extra.update(adjoint_ms=round(adj_ms, 3), beta_fit_ms=round((time.perf_counter() - t0) * 1e3, 3),
+                     beta_fit_final=traj[-1])
     vb, hb, st = sweep_bytes(g, L, cfg.conv_window)
     # bytes per iteration t: slices still iterating at t
     tb_v, tb_h = [], []
@@ -352,7 +387,8 @@ def run_ours(a):
     ach = bw_h if dom == "k_hood" else bw_v
     per_launch = (sum(tb_h) / len(tb_h)) if dom == "k_hood" else (sum(tb_v) / len(tb_v))
     all_active = float(hb.sum()) if dom == "k_hood" else float(vb.sum())
-    traffic = captured_traffic(dom, wl.name, per_launch, all_active)
+    traffic = captured_traffic(dom, wl.name, per_launch)
+    n_sw = len(msv)  # iterations of the longest slice (the loop's sweeps)
 
     # ---- plain: one call per slice on a sample of slices
     ps = min(a.plain_sample, S)
@@ -451,12 +487,13 @@ def run_ours(a):
                             f"previous chunk computes, its label image is read back beside the next"}
 
     # ---- CPU baseline: the oracle on a bounded sample, rank 0 only
-    cpu = None
+    cpu = cpu_omp = None
     if rank == 0 and world == 1 and not a.no_cpu:
         if D > 1:
             cpu = cpu_baseline_volume(img_np[:D], ids_np[:D], wl, a)
         else:
             cpu = cpu_baseline(sl[:a.cpu_slices], wl, a)
+            cpu_omp = cpu_baseline(sl[:a.cpu_slices], wl, a, threads=os.cpu_count() or 1)
 
     if rank == 0:
         line = {
@@ -471,6 +508,9 @@ def run_ours(a):
                        **({"variant": variant(a)} if variant(a) else {})},
             "energy_evals_per_s": round(evals / (em_ms / 1e3), 1),
             "em_ms": round(em_ms, 3), "em_slices_per_s": round(S / (em_ms / 1e3), 3),
+            "em_ms_direct_launches": round(em_ms_direct, 3),
+            "us_per_iteration": round(em_ms / max(1, int(iters.max())) * 1e3, 2),
+            "us_per_sweep": round((sum(msv) + sum(msh)) / max(1, n_sw) * 1e3, 2), **extra,
             "plain_slices_per_s": round(plain, 3), "plain_sample": ps,
             "iters_mean": float(iters.mean()), "iters_max": int(iters.max()),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(ach, 1), "peak": hbm,
@@ -479,7 +519,7 @@ def run_ours(a):
                          "bytes_per_launch_all_active": all_active, "sources_sha1": sources_sha1(),
                          "k_vertex_GBs": round(bw_v, 1), "k_hood_GBs": round(bw_h, 1),
                          "k_vertex_ms": round(sum(msv), 3), "k_hood_ms": round(sum(msh), 3)},
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+            "cpu_baseline": cpu, "cpu_baseline_multicore": cpu_omp, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "gen_s": round(gen_s, 1),
         }
         print(json.dumps(line), flush=True)
@@ -487,12 +527,15 @@ def run_ours(a):
         dist.destroy_process_group()
 
 
-def cpu_baseline(slices, wl, a=None):
-    """The oracle as it stands (serial C), full per-slice pipeline."""
+def cpu_baseline(slices, wl, a=None, threads=1):
+    """The oracle as it stands (serial C), full per-slice pipeline; with
+    threads > 1 its MAP sweep runs on that many threads (the oracle's
+    multi-core form, identical results; the rest stays serial)."""
     import oracle
     k = a.hood_depth if a else 1
     cfg = oracle.EMConfig(n_labels=wl.n_labels, beta=wl.beta, max_iters=wl.max_iters,
-                          potts_scope=a.potts_scope if a else 0, replica_rule=a.replica_rule if a else 0)
+                          potts_scope=a.potts_scope if a else 0, replica_rule=a.replica_rule if a else 0,
+                          n_threads=threads)
     t0 = time.perf_counter()
     for s in slices:
         g = oracle.Graph.from_image(s.image, s.region_ids, hood_depth=k)
@@ -500,9 +543,10 @@ def cpu_baseline(slices, wl, a=None):
         g.label_image(s.region_ids, r["labels"])
         g.pll(wl.n_labels, r["labels"], r["theta"][:, 1], r["theta"][:, 2], wl.beta)
     dt = time.perf_counter() - t0
-    return {"value": round(len(slices) / dt, 4), "unit": "slices/s", "cores": 1, "kind": "oracle",
+    form = "serial C oracle" if threads == 1 else f"C oracle, MAP sweep on {threads} threads (OpenMP over hoods)"
+    return {"value": round(len(slices) / dt, 4), "unit": "slices/s", "cores": threads, "kind": "oracle",
             "sample": f"{len(slices)} slices of {wl.name} ({slices[0].image.shape[0]}x{slices[0].image.shape[1]}), "
-                      f"serial C oracle: graph, cliques, hoods, EM, label image, PLL"}
+                      f"{form}: graph, cliques, hoods, EM, label image, PLL"}
 
 
 def cpu_baseline_volume(img, ids, wl, a):
