@@ -91,6 +91,7 @@ def parse():
     ap.add_argument("--cpu-slices", type=int, default=2, help="slices the oracle baseline runs")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="run with the default hood-pass launch shape")
     ap.add_argument("--e2e-chunks", type=int, default=4, help="chunks per step in the end-to-end leg")
     # variants of the method beside the paper's form, measured on the same workload
     ap.add_argument("--hood-depth", type=int, default=1, help="k of the k-neighbourhoods")
@@ -302,8 +303,13 @@ def run_ours(a):
         pll, gm, gs, gb = g.pll_value_and_grad(L, out["labels"], mu, sg, beta, ones[:g.S])
         return g, out, seg, pll
 
-    for _ in range(a.warmup):
-        step(img_d, ids_d)
+    tuned = None
+    for k in range(a.warmup):
+        gw, _, _, _ = step(img_d, ids_d)
+        if k == 0 and not a.no_autotune:
+            # the hood pass's launch shape for this batch's shape, kept by the
+            # library for the graphs the timed steps build
+            tuned = gw.autotune(cfg)
     torch.cuda.synchronize()
 
     # ---- timed region: inputs resident in HBM
@@ -367,6 +373,10 @@ def run_ours(a):
         ee1.record()
         torch.cuda.synchronize()
         adj_ms = ee0.elapsed_time(ee1) / reps
+        # one step first: torch's autograd engine starts its device threads on
+        # the first backward pass (seconds), which is not part of the fit
+        fit_beta(g, o2["labels"], mu, sg, beta0=0.2, steps=1)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         traj = fit_beta(g, o2["labels"], mu, sg, beta0=0.2, steps=30)
         torch.cuda.synchronize()
@@ -519,6 +529,7 @@ def run_ours(a):
                          "bytes_per_launch_all_active": all_active, "sources_sha1": sources_sha1(),
                          "k_vertex_GBs": round(bw_v, 1), "k_hood_GBs": round(bw_h, 1),
                          "k_vertex_ms": round(sum(msv), 3), "k_hood_ms": round(sum(msh), 3)},
+            "hood_pass_tuning": None if tuned is None else {k: tuned[k] for k in ("hood_tile", "hood_lanes")},
             "cpu_baseline": cpu, "cpu_baseline_multicore": cpu_omp, "e2e": e2e, "gpu_launches": int(launches),
             "clocks": clk.summary(), "gen_s": round(gen_s, 1),
         }

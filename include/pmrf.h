@@ -446,7 +446,9 @@ PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* deta
  * hood_lanes: adjacent lanes that share one hood, each summing every
  *   hood_lanes-th element (1, 2, 4 or 8; default 2 for m >= 16, else 1).
  * The vertex pass always takes 128 vertices per block, one per thread.
- * Results do not depend on the tuning (every sum is an exact integer). */
+ * With both fields 0 a result of pmrf_autotune for a graph of the same shape
+ * is used when one exists.  Results do not depend on the tuning (every sum is
+ * an exact integer). */
 typedef struct {
     int32_t hood_tile;
     int32_t hood_lanes;
@@ -467,10 +469,15 @@ PMRF_API int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t);
 PMRF_API int pmrf_em_kernel_times(pmrf_graph* g, int32_t max_n, float* ms_vertex, float* ms_hood, int32_t* n,
                                   pmrf_stream_t stream);
 
-/* Time candidate tunings on this graph with `cfg` (the defaults, two other
- * windows and every lanes-per-hood value; each runs the EM loop four times;
- * synchronises `stream`), keep the fastest on the graph and return it in
- * *best (may be NULL). */
+/* Time candidate tunings on this graph with `cfg` (the defaults, windows of
+ * half and 4/3 the default, and every lanes-per-hood value at the default
+ * window; each candidate runs the EM loop four times; synchronises `stream`),
+ * keep the fastest on the graph (with its window and lanes filled in) and
+ * return it in *best (may be NULL).  The result is also kept for the rest of
+ * the process under the graph's shape (slices, regions, hood elements) and
+ * cfg->n_labels: a graph whose hood_tile and hood_lanes are both 0 runs with
+ * the kept result of its shape when there is one (so a batch rebuilt with the
+ * same oversegmentation reuses one tuning run). */
 PMRF_API int pmrf_autotune(pmrf_graph* g, const pmrf_config* cfg, pmrf_stream_t stream, pmrf_tuning* best);
 
 #ifdef __cplusplus

@@ -37,8 +37,11 @@
 // conditional nodes: once every slice has stopped, the remaining iterations
 // are skipped.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "graph.cuh"
@@ -1448,9 +1451,27 @@ int default_hood_tile(const pmrf_graph* g) {
     return std::max(512, std::min(MAX_HOOD_TILE, te));
 }
 
-int effective_tiles(const pmrf_graph* g, int* te, int* lanes) {
-    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : default_hood_tile(g);
-    *lanes = g->tuning.hood_lanes > 0 ? g->tuning.hood_lanes : default_hood_lanes(g);
+// The autotuner's results for this process, keyed by the graph's shape
+// (slices, regions, hood elements) and the number of labels: a graph whose
+// tuning is left at 0 takes the entry of its shape when there is one
+using TuneKey = std::array<int64_t, 4>;
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<int, int>> g_tune_cache;
+
+TuneKey tune_key(const pmrf_graph* g, int L) { return TuneKey{(int64_t)g->S, g->V, g->N_el, (int64_t)L}; }
+
+int effective_tiles(const pmrf_graph* g, int L, int* te, int* lanes) {
+    int ct = 0, cl = 0;
+    if (g->tuning.hood_tile == 0 && g->tuning.hood_lanes == 0) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        auto it = g_tune_cache.find(tune_key(g, L));
+        if (it != g_tune_cache.end()) {
+            ct = it->second.first;
+            cl = it->second.second;
+        }
+    }
+    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : (ct > 0 ? ct : default_hood_tile(g));
+    *lanes = g->tuning.hood_lanes > 0 ? g->tuning.hood_lanes : (cl > 0 ? cl : default_hood_lanes(g));
     return PMRF_OK;
 }
 
@@ -1459,9 +1480,9 @@ int effective_tiles(const pmrf_graph* g, int* te, int* lanes) {
 int hood_cap(const Plan* p) { return std::min(HT_CAP_MAX, p->hood_tile + std::max(p->max_hood, 1) - 1); }
 size_t hood_smem(const Plan* p) { return sizeof(uint2) * (size_t)(hood_cap(p) + 2); }
 
-int get_plan(pmrf_graph* g, cudaStream_t s, Plan** out) {
+int get_plan(pmrf_graph* g, int L, cudaStream_t s, Plan** out) {
     int te, lanes;
-    effective_tiles(g, &te, &lanes);
+    effective_tiles(g, L, &te, &lanes);
     auto key = std::make_pair(te, lanes);
     auto it = g->plans.find(key);
     if (it != g->plans.end()) {
@@ -1835,7 +1856,7 @@ int em_run(pmrf_graph* g, const pmrf_config* cfg, uint8_t* d_labels, double* d_p
     if (!d_labels || !d_params || !d_iters || !d_conv) return fail(PMRF_ERR_ARG, "null output pointer");
     const RunCfg rc = to_run(cfg);
     Plan* p = nullptr;
-    PMRF_TRY(get_plan(g, s, &p));
+    PMRF_TRY(get_plan(g, rc.L, s, &p));
     PMRF_TRY(ensure_work(g, rc, *p, s));
     EMWork& w = g->em;
     // constants and output pointers for this call
@@ -1978,7 +1999,7 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
 int prepare(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, Plan** p, RunCfg* rc) {
     PMRF_TRY(check_cfg(g, cfg));
     *rc = to_run(cfg);
-    PMRF_TRY(get_plan(g, s, p));
+    PMRF_TRY(get_plan(g, rc->L, s, p));
     PMRF_TRY(ensure_work(g, *rc, **p, s));
     return PMRF_OK;
 }
@@ -2123,6 +2144,11 @@ namespace pmrf {
 int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tuning* best) {
     PMRF_TRY(check_cfg(g, cfg));
     const int64_t S = g->S, L = cfg->n_labels;
+    {
+        // the candidates' defaults are the plain defaults, not an earlier result
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache.erase(tune_key(g, (int)L));
+    }
     uint8_t* lab = nullptr;
     double* par = nullptr;
     int32_t *it = nullptr, *cv = nullptr;
@@ -2135,8 +2161,17 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
         rc = fail(PMRF_ERR_CUDA, "event creation failed");
     pmrf_tuning keep = g->tuning, win = g->tuning;
     float best_ms = 1e30f;
-    // candidates: the defaults (0, 0), then windows and lanes per hood around them
-    const int cands[][2] = {{0, 0}, {576, 0}, {2048, 0}, {0, 1}, {0, 2}, {0, 4}, {0, 8}};
+    // candidates: the defaults, windows of half and 1.3 times the default, and
+    // every lanes-per-hood value at the default window
+    pmrf_tuning base = keep;
+    base.hood_tile = 0;
+    base.hood_lanes = 0;
+    g->tuning = base;
+    int te0 = 0, ln0 = 0;
+    effective_tiles(g, (int)L, &te0, &ln0);
+    auto w32 = [](int x) { return std::max(MIN_HOOD_TILE, std::min(MAX_HOOD_TILE, (x + 16) / 32 * 32)); };
+    const int cands[][2] = {{te0, ln0}, {w32(te0 / 2), ln0}, {w32(te0 * 4 / 3), ln0}, {te0, 1}, {te0, 2},
+                            {te0, 4},   {te0, 8}};
     const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
     for (int c = 0; c < ncand && !rc; ++c) {
         pmrf_tuning t = keep;
@@ -2163,6 +2198,10 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
     free_plans(g);
     free_em(g);
     g->tuning = rc ? keep : win;
+    if (!rc) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        g_tune_cache[tune_key(g, (int)L)] = std::make_pair(win.hood_tile, win.hood_lanes);
+    }
     if (best && !rc) *best = win;
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
