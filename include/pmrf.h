@@ -439,12 +439,12 @@ PMRF_API int pmrf_quality(pmrf_graph* g, int32_t n_labels, const uint8_t* d_pred
 PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* detail);
 
 /* Launch shape of the EM hood pass.  0 selects the default.
- * hood_tile: hood elements per tile window (multiple of 32, 128..2048; a tile
- *   holds the hoods that start in its window, staged in shared memory;
- *   default from the graph's mean hood size m: 128 / hood_lanes * m rounded to
- *   a multiple of 32, within [512, 2048]);
+ * hood_tile: hoods per tile (one 128-thread block per tile; multiple of 32,
+ *   32..1024; default 128 / hood_lanes: one hood per lane group, one round);
+ *   a tile's element stream is staged in shared memory;
  * hood_lanes: adjacent lanes that share one hood, each summing every
- *   hood_lanes-th element (1, 2, 4 or 8; default 2 for m >= 16, else 1).
+ *   hood_lanes-th element (1, 2, 4 or 8; default 2 for a mean hood size of 16
+ *   or more, else 1).
  * The vertex pass always takes 128 vertices per block, one per thread.
  * With both fields 0 a result of pmrf_autotune for a graph of the same shape
  * is used when one exists.  Results do not depend on the tuning (every sum is
@@ -469,10 +469,11 @@ PMRF_API int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t);
 PMRF_API int pmrf_em_kernel_times(pmrf_graph* g, int32_t max_n, float* ms_vertex, float* ms_hood, int32_t* n,
                                   pmrf_stream_t stream);
 
-/* Time candidate tunings on this graph with `cfg` (the defaults, windows of
- * half and 4/3 the default, and every lanes-per-hood value at the default
- * window; each candidate runs the EM loop four times; synchronises `stream`),
- * keep the fastest on the graph (with its window and lanes filled in) and
+/* Time candidate tunings on this graph with `cfg` (the defaults, half and
+ * twice the default hoods per tile, and every lanes-per-hood value with one
+ * hood per lane group; each candidate runs the EM loop four times;
+ * synchronises `stream`), keep the fastest on the graph (with its hoods per
+ * tile and lanes filled in) and
  * return it in *best (may be NULL).  The result is also kept for the rest of
  * the process under the graph's shape (slices, regions, hood elements) and
  * cfg->n_labels: a graph whose hood_tile and hood_lanes are both 0 runs with

@@ -445,8 +445,8 @@ int pmrf_get_tuning(const pmrf_graph* g, pmrf_tuning* t) {
 
 int pmrf_set_tuning(pmrf_graph* g, const pmrf_tuning* t) {
     if (!g || !t) return fail(PMRF_ERR_ARG, "null argument");
-    if (t->hood_tile != 0 && (t->hood_tile < 128 || t->hood_tile > 2048 || t->hood_tile % 32))
-        return fail(PMRF_ERR_ARG, "hood_tile must be 0 or a multiple of 32 in [128, 2048]");
+    if (t->hood_tile != 0 && (t->hood_tile < 32 || t->hood_tile > 1024 || t->hood_tile % 32))
+        return fail(PMRF_ERR_ARG, "hood_tile must be 0 or a multiple of 32 in [32, 1024]");
     if (t->hood_lanes != 0 && t->hood_lanes != 1 && t->hood_lanes != 2 && t->hood_lanes != 4 && t->hood_lanes != 8)
         return fail(PMRF_ERR_ARG, "hood_lanes must be 0, 1, 2, 4 or 8");
     if (t->profile != 0 && t->profile != 1) return fail(PMRF_ERR_ARG, "profile must be 0 or 1");

@@ -59,8 +59,8 @@ __host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 12 : 8;
 constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
 constexpr int LI_THREADS = 256;             // label-image block
 constexpr int HT_THREADS = 128;             // hood-pass block
-constexpr int MIN_HOOD_TILE = 128;          // hood-tile window (elements) limits
-constexpr int MAX_HOOD_TILE = 2048;
+constexpr int MIN_HOOD_TILE = 32;           // hoods per hood tile, limits
+constexpr int MAX_HOOD_TILE = 1024;
 constexpr int HT_CAP_MAX = 4096;            // largest staged tile (elements; 32 KB of shared memory)
 // Per-vertex record of the hood pass, in 32-byte chunks, written by the vertex
 // pass of the same iteration; energies in the slice's unit 2^-q (SliceUnit):
@@ -1350,22 +1350,19 @@ __global__ void k_label_image(const int32_t* __restrict__ ids, const int64_t* __
 }
 
 // tile table: vertex tiles then hood tiles, each grouped by slice; one warp
-// per hood tile
+// per hood tile.  Hood tile j of a slice holds its hoods [j te, (j+1) te); the
+// largest tile's element count goes to *maxne (the staging buffer's size)
 __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const int64_t* __restrict__ hood_slice_off,
                                   const uint8_t* __restrict__ hood_gen, const int64_t* __restrict__ ht_first,
                                   int32_t S, int64_t n_htiles, int32_t te, Tile* __restrict__ tiles,
-                                  int64_t tile_base) {
+                                  int64_t tile_base, unsigned long long* __restrict__ maxne) {
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (k >= n_htiles) return;  // whole warps leave together
     const int s = (int)(upper_bound_dev<int64_t>(ht_first, 0, S + 1, k) - 1);
     const int64_t j = k - ht_first[s];
     const int64_t cs = hood_slice_off[s], ce = hood_slice_off[s + 1];
-    const int64_t es = hood_off[cs];
-    const int64_t lo = es + j * te, hi = lo + te;
-    int64_t c0 = lower_bound_dev<int64_t>(hood_off, cs, ce, lo);
-    int64_t c1 = lower_bound_dev<int64_t>(hood_off, cs, ce, hi);
-    if (j == ht_first[s + 1] - ht_first[s] - 1) c1 = ce;
+    const int64_t c0 = cs + j * te, c1 = min(ce, c0 + te);
     // fast when every element's vertex has degree <= 32 (the build flags the
     // hoods that do not)
     bool ok = true;
@@ -1380,6 +1377,7 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
         t.part = (int32_t)k;
         t.pad = fast ? 1 : 0;
         tiles[tile_base + k] = t;
+        atomicMax(maxne, (unsigned long long)(hood_off[c1] - hood_off[c0]));
     }
 }
 
@@ -1435,21 +1433,17 @@ int free_em(pmrf_graph* g) {
 
 namespace {
 
-// The default hood-tile window and lanes per hood from the graph's mean hood
-// size m: one lane per hood (two for hoods of 16 or more members, as in
-// k-neighbourhoods), and a window of about one round of the block's lanes,
-// 128 / lanes * m elements (1568 for the 1-neighbourhoods of a jittered-grid
-// oversegmentation, m = 12.3: measured best of 1152-2048)
+// The default hood tile and lanes per hood: one lane per hood (two for a mean
+// hood size m of 16 or more, as in k-neighbourhoods) and as many hoods as the
+// block has lane groups, so that every lane takes one hood in one round (128
+// hoods, about 1570 elements, for the 1-neighbourhoods of a jittered-grid
+// oversegmentation, m = 12.3)
 int default_hood_lanes(const pmrf_graph* g) {
     const double m = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
     return m >= 16.0 ? 2 : 1;
 }
 
-int default_hood_tile(const pmrf_graph* g) {
-    const double m = g->C > 0 ? (double)g->N_el / (double)g->C : 1.0;
-    const int te = (int)(((double)HT_THREADS / default_hood_lanes(g) * m + 16.0) / 32.0) * 32;
-    return std::max(512, std::min(MAX_HOOD_TILE, te));
-}
+int default_hood_tile(int lanes) { return HT_THREADS / lanes; }
 
 // The autotuner's results for this process, keyed by the graph's shape
 // (slices, regions, hood elements) and the number of labels: a graph whose
@@ -1470,14 +1464,14 @@ int effective_tiles(const pmrf_graph* g, int L, int* te, int* lanes) {
             cl = it->second.second;
         }
     }
-    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : (ct > 0 ? ct : default_hood_tile(g));
     *lanes = g->tuning.hood_lanes > 0 ? g->tuning.hood_lanes : (cl > 0 ? cl : default_hood_lanes(g));
+    *te = g->tuning.hood_tile > 0 ? g->tuning.hood_tile : (ct > 0 ? ct : default_hood_tile(*lanes));
     return PMRF_OK;
 }
 
-// elements a fast hood tile stages: its window plus the rest of a hood that
-// starts at the window's end (larger tiles read their stream in place)
-int hood_cap(const Plan* p) { return std::min(HT_CAP_MAX, p->hood_tile + std::max(p->max_hood, 1) - 1); }
+// elements a fast hood tile stages: the largest tile's (up to HT_CAP_MAX;
+// larger tiles read their stream in place)
+int hood_cap(const Plan* p) { return p->cap; }
 size_t hood_smem(const Plan* p) { return sizeof(uint2) * (size_t)(hood_cap(p) + 2); }
 
 int get_plan(pmrf_graph* g, int L, cudaStream_t s, Plan** out) {
@@ -1503,7 +1497,8 @@ int get_plan(pmrf_graph* g, int L, cudaStream_t s, Plan** out) {
         const int64_t ne = g->h_el_slice_off[i + 1] - g->h_el_slice_off[i];
         const int64_t nh = g->h_hood_slice_off[i + 1] - g->h_hood_slice_off[i];
         vfirst[i + 1] = vfirst[i] + ceil_div(nv, vt);
-        hfirst[i + 1] = hfirst[i] + (nh > 0 ? std::max<int64_t>(1, ceil_div(ne, te)) : 0);
+        hfirst[i + 1] = hfirst[i] + ceil_div(nh, te);
+        (void)ne;
     }
     p.n_vtiles = vfirst[S];
     p.n_htiles = hfirst[S];
@@ -1525,15 +1520,22 @@ int get_plan(pmrf_graph* g, int L, cudaStream_t s, Plan** out) {
                                                                               p.n_vtiles, vt, p.d_tiles);
         ::pmrf::note_launch(1);
     }
+    unsigned long long maxne = 0;
     if (p.n_htiles > 0) {
+        unsigned long long* d_maxne = nullptr;
+        PMRF_TRY(dalloc(&d_maxne, 1, s));
+        PMRF_CUDA(cudaMemsetAsync(d_maxne, 0, sizeof(unsigned long long), s));
         k_make_hood_tiles<<<(unsigned)ceil_div(p.n_htiles, 8), 256, 0, s>>>(
             g->d_hood_off, g->d_hood_slice_off, g->d_hood_gen, p.d_slice_ht0, S, p.n_htiles,
             te, p.d_tiles,
-            p.n_vtiles);
+            p.n_vtiles, d_maxne);
         ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaMemcpyAsync(&maxne, d_maxne, sizeof(maxne), cudaMemcpyDeviceToHost, s));
+        dfree(d_maxne, s);
     }
     PMRF_CUDA(cudaGetLastError());
     PMRF_CUDA(cudaStreamSynchronize(s));  // host vectors go out of scope
+    p.cap = (int)std::min<unsigned long long>(HT_CAP_MAX, std::max<unsigned long long>(maxne, 1));
     auto res = g->plans.emplace(key, p);
     *out = &res.first->second;
     return PMRF_OK;
@@ -2169,9 +2171,11 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
     g->tuning = base;
     int te0 = 0, ln0 = 0;
     effective_tiles(g, (int)L, &te0, &ln0);
-    auto w32 = [](int x) { return std::max(MIN_HOOD_TILE, std::min(MAX_HOOD_TILE, (x + 16) / 32 * 32)); };
-    const int cands[][2] = {{te0, ln0}, {w32(te0 / 2), ln0}, {w32(te0 * 4 / 3), ln0}, {te0, 1}, {te0, 2},
-                            {te0, 4},   {te0, 8}};
+    // the defaults; half and twice as many hoods per tile; each lanes-per-hood
+    // value with one hood per lane group
+    auto h32 = [](int x) { return std::max(MIN_HOOD_TILE, std::min(MAX_HOOD_TILE, x / 32 * 32)); };
+    const int cands[][2] = {{te0, ln0}, {h32(te0 / 2), ln0}, {h32(te0 * 2), ln0}, {HT_THREADS, 1},
+                            {HT_THREADS / 2, 2}, {HT_THREADS / 4, 4}, {HT_THREADS / 8, 8}};
     const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
     for (int c = 0; c < ncand && !rc; ++c) {
         pmrf_tuning t = keep;

@@ -22,6 +22,7 @@ struct Tile {
 
 struct Plan {  // tile table for one tuning
     int32_t hood_tile = 0, hood_lanes = 0, max_hood = 0;
+    int32_t cap = 1;  // elements of the largest hood tile, up to the staging limit
     int64_t n_tiles = 0, n_htiles = 0, n_vtiles = 0;
     Tile* d_tiles = nullptr;
     int32_t* d_slice_ntiles = nullptr;   // [S] tiles per slice (both kinds)

@@ -24,8 +24,8 @@ def test_results_independent_of_tiles_and_replay():
     cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=30)
     ref = g.em(cfg, want_T=True)
     ref = {k: v.clone() for k, v in ref.items()}
-    for tuning in (dict(hood_tile=128), dict(hood_tile=512), dict(hood_tile=2048), dict(hood_lanes=1),
-                   dict(hood_lanes=2), dict(hood_lanes=8), dict(hood_tile=128, hood_lanes=8),
+    for tuning in (dict(hood_tile=32), dict(hood_tile=256), dict(hood_tile=1024), dict(hood_lanes=1),
+                   dict(hood_lanes=2), dict(hood_lanes=8), dict(hood_tile=32, hood_lanes=8),
                    dict(use_cuda_graph=0), dict(profile=1)):
         g.set_tuning(**tuning)
         out = g.em(cfg, want_T=True)
@@ -43,7 +43,7 @@ def test_autotune_and_kernel_times():
     ref = g.em(cfg)
     ref = {k: v.clone() for k, v in ref.items()}
     best = g.autotune(cfg)
-    assert 128 <= best["hood_tile"] <= 2048 and best["hood_tile"] % 32 == 0
+    assert 32 <= best["hood_tile"] <= 1024 and best["hood_tile"] % 32 == 0
     assert best["hood_lanes"] in (1, 2, 4, 8)
     assert g.tuning()["hood_tile"] == best["hood_tile"] and g.tuning()["hood_lanes"] == best["hood_lanes"]
     # a second graph of the same shape left at the defaults runs with the kept result
