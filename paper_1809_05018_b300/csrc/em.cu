@@ -156,9 +156,9 @@ __device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * s
 // chosen (slice_unit) from a bound M on |Emin(c,v)|: the data terms of the
 // slice's labels at the ends of its intensity range bound the least data term
 // of every vertex, and the Potts part is at most beta times the largest degree.
-// With H = max(32, largest hood), 2^q M H < 2^62, so an element energy, a sum
-// of up to 32 of them (a warp's prefix) and a hood sum all fit in 64 bits, and
-// every sum is exact and independent of order.  A double is rounded to the
+// With H = max(128, largest hood), 2^q M H < 2^62, so an element energy, a hood
+// sum and a vertex tile's sum of vertex energies (128 vertices) all fit in 64
+// bits, and every sum is exact and independent of order.  A double is rounded to the
 // unit once (to_fixed: to nearest, ties away from zero); for the usual range of
 // energies q is about 52, i.e. the rounding is below 1e-16.  Totals T are sums
 // of hood sums in 128 bits, rounded to double once.
@@ -226,7 +226,7 @@ __device__ __forceinline__ SliceUnit slice_unit(const double* __restrict__ th, i
     }
     const double B = fmax(fabs(lo), fabs(up));
     const double M = (B + beta * (double)max(32, max_deg)) * (1.0 + 0x1p-20) + 0x1p-60;
-    const double P = M * (double)max(32, max_hood);
+    const double P = M * (double)max(VT_THREADS, max_hood);
     SliceUnit u;
     u.pad = 0;
     ok = isfinite(P);
@@ -299,14 +299,26 @@ __device__ __forceinline__ void write_vrec_const(uint64_t* __restrict__ vrec, in
     store_vrec<L>(vrec, V, v, w);
 }
 
-// the hood-pass record of vertex v (layout above) from its FP64 data terms
+// the hood-pass record of vertex v (layout above) from its data terms in the
+// slice's unit
 template <int L>
-__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t V, int64_t v, const double (&D)[L],
-                                           const uint32_t (&lmw)[L], int q) {
+__device__ __forceinline__ void write_vrec_fixed(uint64_t* __restrict__ vrec, int64_t V, int64_t v,
+                                                 const int64_t (&F)[L], const uint32_t (&lmw)[L]) {
     constexpr int NW = vrec_words(L);
     uint64_t dq[L];
-    int amin;
-    const int64_t Fmin = data_fixed<L>(D, q, dq, amin);
+    int amin = 0;
+    int64_t Fmin = F[0];
+#pragma unroll
+    for (int l = 1; l < L; ++l)
+        if (F[l] < Fmin) {
+            Fmin = F[l];
+            amin = l;
+        }
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        const uint64_t d = (uint64_t)(F[l] - Fmin);
+        dq[l] = d > DQ_SAT ? DQ_SAT : d;
+    }
     uint64_t w[NW];
 #pragma unroll
     for (int k = 0; k < NW; ++k) w[k] = 0ull;
@@ -326,6 +338,16 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
         }
     }
     store_vrec<L>(vrec, V, v, w);
+}
+
+// the same from FP64 data terms (each rounded to the unit once)
+template <int L>
+__device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t V, int64_t v, const double (&D)[L],
+                                           const uint32_t (&lmw)[L], int q) {
+    int64_t F[L];
+#pragma unroll
+    for (int l = 0; l < L; ++l) F[l] = to_fixed(D[l], q);
+    write_vrec_fixed<L>(vrec, V, v, F, lmw);
 }
 
 // label counts among the neighbours of v in one replica with a multi-word
@@ -567,6 +589,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
     const int64_t ubq = unit ? unit[s].beta_q : 0;
     int vlab = 0;
     double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
+    int64_t Eq = 0;                          // EM: E* in the slice's unit (its moments are exact integer sums)
     bool have_dev = false;                   // EM/sweep: y - mu_lab and its square already known
     if (ok) {
         const double y = g.y[v];
@@ -626,31 +649,32 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                     }
                 }
                 // the hood pass of this iteration reads v's data terms and label masks
-                if (vrec) write_vrec<L>(vrec, g.V, v, D, lm, uq);
                 // every vertex lies in at least one hood, so M_l is set (and
-                // <= 32 when d <= 32)
-                double Md[L];
-                if (d <= 32) {
+                // <= 32 when d <= 32).  The data terms in the slice's unit serve
+                // the hood pass's record and the label choice: the least of
+                // D_l + beta M_l compared on the integer pipes (ties to the lower
+                // label; the FP64 pipe of this part is the scarce unit), its
+                // value E*_v in the unit for the moments
+                int64_t F[L];
 #pragma unroll
-                    for (int l = 0; l < L; ++l) Md[l] = s_Md[M[l]];
-                } else {
-#pragma unroll
-                    for (int l = 0; l < L; ++l) Md[l] = (double)M[l];
-                }
-                // the least energy compared on the integer pipes: finite
-                // doubles order like their bit patterns mapped to ordered
-                // integers (negative values' magnitude bits flipped, -0 as +0)
-                Estar = D[0] + c.beta * Md[0];
-                long long kbest = ordered_key(Estar);
+                for (int l = 0; l < L; ++l) F[l] = to_fixed(D[l], uq);
+                if (vrec) write_vrec_fixed<L>(vrec, g.V, v, F, lm);
+                int64_t eb = F[0] + ubq * (int64_t)M[0];
                 lab = 0;
 #pragma unroll
                 for (int l = 1; l < L; ++l) {
-                    const double e = D[l] + c.beta * Md[l];
-                    const long long k = ordered_key(e);
-                    if (k < kbest) { Estar = e; kbest = k; lab = l; }
+                    const int64_t e = F[l] + ubq * (int64_t)M[l];
+                    if (e < eb) { eb = e; lab = l; }
+                }
+                Eq = eb;
+                if (E_out) {  // the chosen label's energy in FP64 (standalone sweep)
+#pragma unroll
+                    for (int l = 0; l < L; ++l)
+                        if (l == lab) Estar = D[l] + c.beta * (d <= 32 ? s_Md[M[l]] : (double)M[l]);
                 }
             } else {
                 lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar, s_rcp, uq, ubq);
+                Eq = to_fixed(Estar, uq);
             }
             x_out[v] = (uint8_t)lab;
             if (E_out) E_out[v] = Estar;
@@ -671,7 +695,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                 vq1 = dv * dv;
             }
             vlab = lab;
-            vq2 = Estar;
+            vq2 = mode == MODE_EM ? __longlong_as_double(Eq) : Estar;
         }
     }
     if (mode == MODE_SWEEP) return;
@@ -712,16 +736,29 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                 if (m == l) n += cw;
             }
         const int lo = base + (k * n) / 8, hi = base + ((k + 1) * n) / 8;
-        double a = 0.0;
-        for (int i = lo; i < hi; ++i) a += s_vq[q][i];
-        s_vc[lq][k] = a;
+        if (q == 2 && mode == MODE_EM) {
+            // E* in the slice's unit: an exact integer sum (|E*| < 2^62 / 128)
+            int64_t a = 0;
+            for (int i = lo; i < hi; ++i) a += __double_as_longlong(s_vq[q][i]);
+            s_vc[lq][k] = __longlong_as_double(a);
+        } else {
+            double a = 0.0;
+            for (int i = lo; i < hi; ++i) a += s_vq[q][i];
+            s_vc[lq][k] = a;
+        }
         if (q == 0 && k == 0) vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
     }
     __syncthreads();
     if (threadIdx.x < 3 * L) {
-        double a = 0.0;
-        for (int w = 0; w < 8; ++w) a += s_vc[threadIdx.x][w];
         const int l = threadIdx.x / 3, q = threadIdx.x % 3;
+        double a = 0.0;
+        if (q == 2 && mode == MODE_EM) {
+            int64_t ai = 0;
+            for (int w = 0; w < 8; ++w) ai += __double_as_longlong(s_vc[threadIdx.x][w]);
+            a = __longlong_as_double(ai);
+        } else {
+            for (int w = 0; w < 8; ++w) a += s_vc[threadIdx.x][w];
+        }
         vpart[(int64_t)tile.part * 4 * L + 4 * l + 1 + q] = a;
     }
 }
@@ -1085,7 +1122,8 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                 // a wait that gives up has set the status word; it waits once
                 // more (bounded) so that no copy is left in flight, and the
                 // tile's sums are left out
-                if (mbar_wait(&s_bar, 0, st) || mbar_wait(&s_bar, 0, st))
+                // (the same decision in every thread: lanes of a hood shuffle together)
+                if (__syncthreads_and(mbar_wait(&s_bar, 0, st) || mbar_wait(&s_bar, 0, st)))
                     fast_hoods_p(lanes, g, c0, c1, e0, s_el + (e0 - ea), energy, hood_done);
             } else {
                 // a tile whose last hood reaches far past its window (very large
@@ -1160,6 +1198,7 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
     __shared__ double s_q[FIN_THREADS / 32][NQ];
     __shared__ __int128 s_T[FIN_THREADS / 32];
     __shared__ int64_t s_u[FIN_THREADS / 32];
+    __shared__ __int128 s_U[FIN_THREADS / 32][L];
     const int s = blockIdx.x;
     if (s >= S) return;
     const RunCfg cf = *cfgp;
@@ -1167,12 +1206,22 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
     if (em && !active[s]) return;
     // the slice's tile partials: a fixed thread per partial, then fixed-order
     // warp and block sums (deterministic)
+    // in EM mode the vertex energies' sums (entry 3 of each label) are integers
+    // in the slice's unit: exact 128-bit sums, rounded once
     double tot[NQ];
+    __int128 Ufix[L];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) tot[k] = 0.0;
+#pragma unroll
+    for (int l = 0; l < L; ++l) Ufix[l] = 0;
     for (int64_t p = vt0[s] + threadIdx.x; p < vt0[s + 1]; p += FIN_THREADS) {
 #pragma unroll
-        for (int k = 0; k < 4 * L; ++k) tot[k] += vpart[p * 4 * L + k];
+        for (int k = 0; k < 4 * L; ++k) {
+            if (em && (k & 3) == 3)
+                Ufix[k >> 2] += (__int128)__double_as_longlong(vpart[p * 4 * L + k]);
+            else
+                tot[k] += vpart[p * 4 * L + k];
+        }
     }
     // T: the exact sum of the tiles' exact partials (integers: independent
     // of the tiling and of the order), rounded once
@@ -1191,14 +1240,29 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
         Tacc += shfl_xor_i128(Tacc, o);
         uacc += __shfl_xor_sync(0xffffffffu, uacc, o);
     }
+    if (em) {
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) Ufix[l] += shfl_xor_i128(Ufix[l], o);
+    }
     if (lane_id() == 0) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) s_q[warp_id()][k] = tot[k];
         s_T[warp_id()] = Tacc;
         s_u[warp_id()] = uacc;
+#pragma unroll
+        for (int l = 0; l < L; ++l) s_U[warp_id()][l] = Ufix[l];
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
+    if (em) {
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+            Ufix[l] = 0;
+            for (int w = 0; w < FIN_THREADS / 32; ++w) Ufix[l] += s_U[w][l];
+        }
+    }
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
         double a = 0.0;
@@ -1239,7 +1303,7 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
             th[0] = n;
             th[1] = mu_prev + m1;
             th[2] = sd > cf.sigma_min ? sd : cf.sigma_min;
-            th[3] = (mode == MODE_INIT) ? 0.0 : tot[4 * l + 3];
+            th[3] = (mode == MODE_INIT) ? 0.0 : (em ? from_fixed(Ufix[l], q_now) : tot[4 * l + 3]);
         } else {
             th[0] = 0.0;
             th[1] = mu_prev;
@@ -1443,7 +1507,7 @@ int default_hood_lanes(const pmrf_graph* g) {
     return m >= 16.0 ? 2 : 1;
 }
 
-int default_hood_tile(int lanes) { return HT_THREADS / lanes; }
+int default_hood_tile(int lanes) { return std::max(MIN_HOOD_TILE, HT_THREADS / lanes); }
 
 // The autotuner's results for this process, keyed by the graph's shape
 // (slices, regions, hood elements) and the number of labels: a graph whose
@@ -2174,8 +2238,9 @@ int autotune_run(pmrf_graph* g, const pmrf_config* cfg, cudaStream_t s, pmrf_tun
     // the defaults; half and twice as many hoods per tile; each lanes-per-hood
     // value with one hood per lane group
     auto h32 = [](int x) { return std::max(MIN_HOOD_TILE, std::min(MAX_HOOD_TILE, x / 32 * 32)); };
-    const int cands[][2] = {{te0, ln0}, {h32(te0 / 2), ln0}, {h32(te0 * 2), ln0}, {HT_THREADS, 1},
-                            {HT_THREADS / 2, 2}, {HT_THREADS / 4, 4}, {HT_THREADS / 8, 8}};
+    const int cands[][2] = {{te0, ln0},          {h32(te0 / 2), ln0},     {h32(te0 * 2), ln0},
+                            {h32(HT_THREADS), 1}, {h32(HT_THREADS / 2), 2}, {h32(HT_THREADS / 4), 4},
+                            {h32(HT_THREADS / 8), 8}};
     const int ncand = (int)(sizeof(cands) / sizeof(cands[0]));
     for (int c = 0; c < ncand && !rc; ++c) {
         pmrf_tuning t = keep;
