@@ -350,6 +350,48 @@ __device__ __forceinline__ void write_vrec(uint64_t* __restrict__ vrec, int64_t 
     write_vrec_fixed<L>(vrec, V, v, F, lmw);
 }
 
+// ---------------------------------------------------------------------------
+// bulk copies into shared memory (the TMA engine) tracked by an mbarrier
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// copy `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared
+// memory; completion is counted on bar
+__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// wait for the phase `parity` of bar to complete, at most ~2^20 polls; false
+// (and the status word set) when the wait gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st) {
+    for (int it = 0; it < (1 << 20); ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(done)
+            : "r"(smem_u32(bar)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    record_error(st, PMRF_ERR_TIMEOUT, SITE_WAIT, 0);
+    return false;
+}
+
+// ---------------------------------------------------------------------------
+// vertex pass
+
 // label counts among the neighbours of v in one replica with a multi-word
 // slot mask (degree > 32): returns the replica's in-hood degree
 template <int L>
@@ -1021,45 +1063,6 @@ __device__ __forceinline__ void general_tile(const DevGraph& g, const RunCfg& cf
             hood_done(c, S);
         }
     }
-}
-
-// ---------------------------------------------------------------------------
-// bulk copies into shared memory (the TMA engine) tracked by an mbarrier
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-// copy `bytes` (a multiple of 16, both addresses 16-byte aligned) into shared
-// memory; completion is counted on bar
-__device__ __forceinline__ void bulk_copy(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-
-// wait for the phase `parity` of bar to complete, at most ~2^20 polls; false
-// (and the status word set) when the wait gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st) {
-    for (int it = 0; it < (1 << 20); ++it) {
-        uint32_t done;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(done)
-            : "r"(smem_u32(bar)), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    record_error(st, PMRF_ERR_TIMEOUT, SITE_WAIT, 0);
-    return false;
 }
 
 // The hood pass: one block per hood tile (consecutive hoods of one slice, their
