@@ -38,30 +38,32 @@ __device__ __forceinline__ int32_t vertex_of(const int32_t* ids, const int32_t* 
 // ---------------------------------------------------------------------------
 // regions
 
-// ids must be non-negative (they index the per-slice rank table) and the
-// intensities finite (checked on their exponent bits)
-__global__ void k_validate(const double* __restrict__ img, const int32_t* __restrict__ ids,
-                           const int64_t* __restrict__ pix_off, int32_t* __restrict__ maxid, DevStatus* st) {
+constexpr int VAL_ITEMS = 16;  // pixels per thread in k_validate
+
+// ids must be non-negative (they index the per-slice rank table).  The
+// intensities' finiteness is checked where they are summed (every pixel is
+// added into exactly one region mean): a non-finite sum sends its region's
+// thread back over its pixels to name the first non-finite one.
+__global__ void k_validate(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
+                           int32_t* __restrict__ maxid, DevStatus* st) {
     __shared__ int32_t s_m[PIX_THREADS / 32];
     const int s = blockIdx.y;
     const int64_t b = pix_off[s], e = pix_off[s + 1];
     const int64_t step = (int64_t)gridDim.x * blockDim.x;
     int32_t m = -1;
-    for (int64_t p0 = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < e; p0 += 4 * step) {
-        // four pixels' loads issued together
-        int32_t id[4];
-        long long bits[4];
+    for (int64_t p0 = b + (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p0 < e; p0 += VAL_ITEMS * step) {
+        // a thread's pixels' loads issued together (enough bytes in flight per
+        // thread to keep HBM busy with 4-byte loads)
+        int32_t id[VAL_ITEMS];
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < VAL_ITEMS; ++k) {
             const int64_t p = p0 + k * step;
             id[k] = p < e ? ids[p] : 0;
-            bits[k] = p < e ? __double_as_longlong(img[p]) : 0ll;
         }
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < VAL_ITEMS; ++k) {
             const int64_t p = p0 + k * step;
             if (id[k] < 0) record_error(st, PMRF_ERR_ARG, SITE_BAD_ID, p);
-            if (((bits[k] >> 52) & 0x7ff) == 0x7ff) record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
             m = max(m, id[k]);
         }
     }
@@ -155,9 +157,11 @@ __global__ void k_inv_rank(const int32_t* __restrict__ rank, const int64_t* __re
 // accumulation.  The same scan, widened by one pixel above and to the left,
 // visits every horizontal and vertical 4-connected pixel pair that touches the
 // region: a pair with exactly one pixel in the region names a neighbouring
-// region.  Those ids go to a small unsorted buffer (a run of the same
-// neighbour along a boundary is appended once), sorted and de-duplicated after
-// the scan; raw ids and vertex ids sort alike within a slice.  Each pixel's
+// region.  Those ids go to a small unsorted buffer, sorted and de-duplicated
+// after the scan; raw ids and vertex ids sort alike within a slice.  A
+// neighbour is appended only when it differs from the last one appended for
+// the same side of the region (left, right, above, below), so a boundary that
+// runs down the rows or along a row adds its neighbour once.  Each pixel's
 // right neighbour is the next step's pixel, so a step loads one new id (and
 // the one below).
 // Outputs: y_v, n_v; the region's neighbour vertex ids, ascending, at
@@ -173,7 +177,8 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
     const int64_t* __restrict__ Wd, const int64_t* __restrict__ vert_off, const int64_t* __restrict__ rank_off,
     const int32_t* __restrict__ rank, int32_t S, const int32_t* __restrict__ inv, const int4* __restrict__ bbox_raw,
     const int32_t* __restrict__ npix_raw, int64_t V, double* __restrict__ y, int32_t* __restrict__ npix,
-    int32_t* __restrict__ fb_pix, int32_t* __restrict__ fb_adj, int32_t* __restrict__ deg, int32_t* __restrict__ nbr) {
+    int32_t* __restrict__ fb_pix, int32_t* __restrict__ fb_adj, int32_t* __restrict__ deg, int32_t* __restrict__ nbr,
+    DevStatus* st) {
     const int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     // every lane reaches the ballot below (the warp's row range is shared)
     bool scan = false;
@@ -204,7 +209,8 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
     const int H = (int)((pix_off[s + 1] - b) / W);
     int32_t buf[NB_BUF];
     int m = 0;
-    int32_t last_h = id, last_v = id;  // last neighbour appended per pair direction
+    // last neighbour appended on each side: left, right (horizontal pairs), above, below
+    int32_t last_l = id, last_r = id, last_a = id, last_b = id;
     double acc = 0.0;
     const int r0 = bb.x > 0 ? bb.x - 1 : 0, c0 = bb.z > 0 ? bb.z - 1 : 0;
     const int w = (int)W;
@@ -228,24 +234,43 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
             const int32_t below = down ? irow[w + c] : cur;
             const bool in = cur == id;
             if (in) acc += vrow[c];  // region pixels lie inside the box: row-major order
-            // the other pixel of a pair with exactly one pixel in the region
+            // the other pixel of a pair with exactly one pixel in the region:
+            // right of the region (in, right not) or left of it (cur not, right in);
+            // below it (in, below not) or above it (cur not, below in)
+            const bool pr = in && right != id, pl = !in && right == id;
+            const bool pb = in && below != id, pa = !in && below == id;
             const int32_t uh = in ? right : cur, uv = in ? below : cur;
-            const bool th = (in != (right == id)) && uh != last_h;
-            const bool tv = (in != (below == id)) && uv != last_v;
+            const bool th = (pr && uh != last_r) || (pl && uh != last_l);
+            const bool tv = (pb && uv != last_b) || (pa && uv != last_a);
             if (th) {
                 if (m < NB_BUF) buf[m] = uh;
                 ++m;
-                last_h = uh;
+                if (pr) last_r = uh;
+                else last_l = uh;
             }
             if (tv) {
                 if (m < NB_BUF) buf[m] = uv;
                 ++m;
-                last_v = uv;
+                if (pb) last_b = uv;
+                else last_a = uv;
             }
             cur = right;
         }
     }
     y[v] = acc / (double)n;
+    if (!finite_bits(acc)) {
+        // a non-finite pixel (or a sum of finite ones beyond the double range,
+        // which is not an input error): the first such pixel, row-major
+        for (int r = bb.x; r <= bb.y; ++r)
+            for (int c = bb.z; c <= bb.w; ++c) {
+                const int64_t p = b + (int64_t)r * W + c;
+                if (ids[p] == id && !finite_bits(img[p])) {
+                    record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, p);
+                    r = bb.y;
+                    break;
+                }
+            }
+    }
     bool over = m > NB_BUF;
     int nn = 0;
     if (!over) {
@@ -301,7 +326,7 @@ __global__ void k_fill_pix(const int32_t* __restrict__ ids, const int64_t* __res
 // row-major order, then divided by the count (the same sequence of IEEE
 // operations as a serial row-major accumulation).
 __global__ void k_means(const double* __restrict__ img, const uint32_t* __restrict__ pixlist,
-                        const int64_t* __restrict__ vpix_off, int64_t V, double* __restrict__ y) {
+                        const int64_t* __restrict__ vpix_off, int64_t V, double* __restrict__ y, DevStatus* st) {
     int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (v >= V) return;
     if (vpix_off[v + 1] == vpix_off[v]) return;  // region summed by k_region_scan
@@ -309,6 +334,13 @@ __global__ void k_means(const double* __restrict__ img, const uint32_t* __restri
     const int64_t b = vpix_off[v], e = vpix_off[v + 1];
     for (int64_t i = b; i < e; ++i) acc += img[pixlist[i]];
     y[v] = acc / (double)(e - b);
+    if (!finite_bits(acc)) {  // the first non-finite pixel, if any (as in k_region_scan)
+        for (int64_t i = b; i < e; ++i)
+            if (!finite_bits(img[pixlist[i]])) {
+                record_error(st, PMRF_ERR_NONFINITE, SITE_NONFINITE, (int64_t)pixlist[i]);
+                break;
+            }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -375,12 +407,26 @@ __global__ void k_edge_pairs(const int32_t* __restrict__ ids, const int64_t* __r
     }
 }
 
-__global__ void k_check_degree(const int32_t* __restrict__ deg, int64_t V, int32_t maxdeg, DevStatus* st,
-                               int32_t* __restrict__ dmax) {
-    int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (v >= V) return;
-    if (deg[v] > maxdeg) record_error(st, PMRF_ERR_UNSUPPORTED, SITE_DEGREE, v);
-    atomicMax(dmax, deg[v]);
+// the largest degree: a grid of a few blocks per SM strides over the vertices,
+// each block's maximum goes out in one atomic (atomics on one word serialise)
+constexpr int CD_THREADS = 256;
+__global__ void __launch_bounds__(CD_THREADS) k_check_degree(const int32_t* __restrict__ deg, int64_t V,
+                                                             int32_t maxdeg, DevStatus* st,
+                                                             int32_t* __restrict__ dmax) {
+    __shared__ unsigned s_m[CD_THREADS / 32];
+    unsigned m = 0;
+    for (int64_t v = (int64_t)blockIdx.x * CD_THREADS + threadIdx.x; v < V; v += (int64_t)gridDim.x * CD_THREADS) {
+        const int32_t d = deg[v];
+        if (d > maxdeg) record_error(st, PMRF_ERR_UNSUPPORTED, SITE_DEGREE, v);
+        m = max(m, (unsigned)d);
+    }
+    m = __reduce_max_sync(0xffffffffu, m);
+    if (lane_id() == 0) s_m[warp_id()] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < CD_THREADS / 32; ++w) m = max(m, s_m[w]);
+        if (m > 0) atomicMax(dmax, (int32_t)m);
+    }
 }
 
 // flagged vertices take their de-duplicated candidate count as degree
@@ -1120,11 +1166,15 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     const unsigned gx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(maxpix, PIX_THREADS * 4), 65535));
     const dim3 pgrid(gx, (unsigned)S);
 
-    // 1. validate + per-slice largest id
+    // 1. ids checked, per-slice largest id
     int32_t* d_maxid = nullptr;
     PMRF_TRY(tmp.get(&d_maxid, S));
     PMRF_CUDA(cudaMemsetAsync(d_maxid, 0xff, sizeof(int32_t) * S, s));
-    if (g->n_pix > 0) { k_validate<<<pgrid, PIX_THREADS, 0, s>>>(d_img, d_ids, g->d_pix_off, d_maxid, g->d_status); ::pmrf::note_launch(1); }
+    if (g->n_pix > 0) {
+        const unsigned vx = (unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(maxpix, PIX_THREADS * VAL_ITEMS), 65535));
+        k_validate<<<dim3(vx, (unsigned)S), PIX_THREADS, 0, s>>>(d_ids, g->d_pix_off, d_maxid, g->d_status);
+        ::pmrf::note_launch(1);
+    }
     PMRF_CUDA(cudaGetLastError());
     PMRF_TRY(check_status(g, s));
     std::vector<int32_t> hmax(S);
@@ -1181,7 +1231,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     PMRF_TRY(tmp.get(&d_nbr, V * NB_CAP));
     LAUNCH_1D(k_inv_rank, g->n_rank, g->d_rank, g->d_rank_off, S, g->n_rank, d_inv);
     LAUNCH_1D(k_region_scan, V, d_img, d_ids, g->d_pix_off, g->d_W, g->d_vert_off, g->d_rank_off, g->d_rank, S, d_inv,
-              d_bbox_raw, d_npix_raw, V, g->d_y, g->d_npix, d_fbpix, d_fbadj, d_deg, d_nbr);
+              d_bbox_raw, d_npix_raw, V, g->d_y, g->d_npix, d_fbpix, d_fbadj, d_deg, d_nbr, g->d_status);
     PMRF_TRY(exclusive_scan_i32_to_i64(d_fbpix, d_vpix_off, V, s));
     int64_t nfb = 0;
     PMRF_TRY(read_i64(d_vpix_off + V, &nfb, s));
@@ -1194,7 +1244,7 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         ::pmrf::note_launch(1);
         PMRF_CUDA(cudaGetLastError());
         PMRF_TRY(segmented_sort_u32(d_pixlist, d_vpix_off, V, nfb, false, nullptr, g->d_status, s));
-        LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y);
+        LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y, g->d_status);
     }
 
     // a volume's z-neighbours lie outside the bounding-box scan: every region
@@ -1234,7 +1284,12 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     int32_t* d_dmax = nullptr;
     PMRF_TRY(tmp.get(&d_dmax, 1));
     PMRF_CUDA(cudaMemsetAsync(d_dmax, 0, sizeof(int32_t), s));
-    LAUNCH_1D(k_check_degree, V, d_deg, V, (int32_t)PMRF_MAX_DEGREE, g->d_status, d_dmax);
+    if (V > 0) {
+        k_check_degree<<<(unsigned)std::min<int64_t>(ceil_div(V, CD_THREADS), 1184), CD_THREADS, 0, s>>>(
+            d_deg, V, (int32_t)PMRF_MAX_DEGREE, g->d_status, d_dmax);
+        ::pmrf::note_launch(1);
+    }
+    PMRF_CUDA(cudaGetLastError());
     PMRF_TRY(check_status(g, s));
     PMRF_TRY(dalloc(&g->d_adj_off, V + 1, s));
     PMRF_TRY(exclusive_scan_i32_to_i64(d_deg, g->d_adj_off, V, s));

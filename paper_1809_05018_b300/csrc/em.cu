@@ -161,7 +161,9 @@ __device__ __forceinline__ double inv_two_var(double sg) { return 1.0 / (2.0 * s
 // bits, and every sum is exact and independent of order.  A double is rounded to the
 // unit once (to_fixed: to nearest, ties away from zero); for the usual range of
 // energies q is about 52, i.e. the rounding is below 1e-16.  Totals T are sums
-// of hood sums in 128 bits, rounded to double once.
+// of hood sums in 128 bits, rounded to double once; a vertex tile's sum of its
+// label's vertex energies is rounded to double once and the label's total U is
+// the fixed-order FP64 sum of those.
 
 struct SliceUnit {
     int32_t q;       // unit 2^-q of this iteration's energies
@@ -190,11 +192,19 @@ __device__ __forceinline__ int64_t to_fixed(double d, int q) {
 // larger magnitudes take a second one from the low word)
 __device__ __forceinline__ double from_fixed(__int128 x, int q) {
     const bool neg = x < 0;
-    const __int128 a = neg ? -x : x;
-    const unsigned long long hi = (unsigned long long)(a >> 64), lo = (unsigned long long)a;
-    const double r = ldexp(fma((double)hi, 0x1p64, (double)lo), -q);
+    const unsigned __int128 a = neg ? -(unsigned __int128)x : (unsigned __int128)x;
+    // the top bits in 63 bits, the bits shifted out kept as a sticky bit below
+    // the rounding position: one conversion rounds the 128-bit value once
+    int sh = 0;
+    const unsigned long long hi = (unsigned long long)(a >> 64);
+    if (hi) sh = 65 - __clzll((long long)hi);
+    unsigned long long m = (unsigned long long)(a >> sh);
+    if (sh && (a & (((unsigned __int128)1 << sh) - 1))) m |= 1ull;
+    const double r = ldexp((double)m, sh - q);
     return neg ? -r : r;
 }
+
+__device__ __forceinline__ double from_fixed64(int64_t x, int q) { return ldexp((double)x, -q); }
 
 __device__ __forceinline__ __int128 shfl_xor_i128(__int128 x, int o) {
     const long long hi = __shfl_xor_sync(0xffffffffu, (long long)(x >> 64), o);
@@ -631,7 +641,7 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
     const int64_t ubq = unit ? unit[s].beta_q : 0;
     int vlab = 0;
     double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
-    int64_t Eq = 0;                          // EM: E* in the slice's unit (its moments are exact integer sums)
+    int64_t Eq = 0;                          // EM: E* in the slice's unit (exact sums within the tile)
     bool have_dev = false;                   // EM/sweep: y - mu_lab and its square already known
     if (ok) {
         const double y = g.y[v];
@@ -795,9 +805,10 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
         const int l = threadIdx.x / 3, q = threadIdx.x % 3;
         double a = 0.0;
         if (q == 2 && mode == MODE_EM) {
+            // the tile's exact sum of E*, rounded to double once
             int64_t ai = 0;
             for (int w = 0; w < 8; ++w) ai += __double_as_longlong(s_vc[threadIdx.x][w]);
-            a = __longlong_as_double(ai);
+            a = from_fixed64(ai, uq);
         } else {
             for (int w = 0; w < 8; ++w) a += s_vc[threadIdx.x][w];
         }
@@ -1201,7 +1212,6 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
     __shared__ double s_q[FIN_THREADS / 32][NQ];
     __shared__ __int128 s_T[FIN_THREADS / 32];
     __shared__ int64_t s_u[FIN_THREADS / 32];
-    __shared__ __int128 s_U[FIN_THREADS / 32][L];
     const int s = blockIdx.x;
     if (s >= S) return;
     const RunCfg cf = *cfgp;
@@ -1209,22 +1219,12 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
     if (em && !active[s]) return;
     // the slice's tile partials: a fixed thread per partial, then fixed-order
     // warp and block sums (deterministic)
-    // in EM mode the vertex energies' sums (entry 3 of each label) are integers
-    // in the slice's unit: exact 128-bit sums, rounded once
     double tot[NQ];
-    __int128 Ufix[L];
 #pragma unroll
     for (int k = 0; k < NQ; ++k) tot[k] = 0.0;
-#pragma unroll
-    for (int l = 0; l < L; ++l) Ufix[l] = 0;
     for (int64_t p = vt0[s] + threadIdx.x; p < vt0[s + 1]; p += FIN_THREADS) {
 #pragma unroll
-        for (int k = 0; k < 4 * L; ++k) {
-            if (em && (k & 3) == 3)
-                Ufix[k >> 2] += (__int128)__double_as_longlong(vpart[p * 4 * L + k]);
-            else
-                tot[k] += vpart[p * 4 * L + k];
-        }
+        for (int k = 0; k < 4 * L; ++k) tot[k] += vpart[p * 4 * L + k];
     }
     // T: the exact sum of the tiles' exact partials (integers: independent
     // of the tiling and of the order), rounded once
@@ -1243,29 +1243,14 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
         Tacc += shfl_xor_i128(Tacc, o);
         uacc += __shfl_xor_sync(0xffffffffu, uacc, o);
     }
-    if (em) {
-#pragma unroll
-        for (int l = 0; l < L; ++l)
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) Ufix[l] += shfl_xor_i128(Ufix[l], o);
-    }
     if (lane_id() == 0) {
 #pragma unroll
         for (int k = 0; k < NQ; ++k) s_q[warp_id()][k] = tot[k];
         s_T[warp_id()] = Tacc;
         s_u[warp_id()] = uacc;
-#pragma unroll
-        for (int l = 0; l < L; ++l) s_U[warp_id()][l] = Ufix[l];
     }
     __syncthreads();
     if (threadIdx.x != 0) return;
-    if (em) {
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-            Ufix[l] = 0;
-            for (int w = 0; w < FIN_THREADS / 32; ++w) Ufix[l] += s_U[w][l];
-        }
-    }
 #pragma unroll
     for (int k = 0; k < NQ; ++k) {
         double a = 0.0;
@@ -1306,7 +1291,7 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
             th[0] = n;
             th[1] = mu_prev + m1;
             th[2] = sd > cf.sigma_min ? sd : cf.sigma_min;
-            th[3] = (mode == MODE_INIT) ? 0.0 : (em ? from_fixed(Ufix[l], q_now) : tot[4 * l + 3]);
+            th[3] = (mode == MODE_INIT) ? 0.0 : tot[4 * l + 3];
         } else {
             th[0] = 0.0;
             th[1] = mu_prev;

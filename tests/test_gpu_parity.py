@@ -361,6 +361,49 @@ def test_large_regions_match_oracle():
     _em_compare(sl, oracle.EMConfig(n_labels=2, beta=1.0, max_iters=20), cfg, g, g.em(cfg))
 
 
+def _carved_ids(h, w, bs, rng):
+    """Square blocks of side bs, each with a notch given to the block on its
+    right (that region gets a detached island, the block a C shape: rows with
+    pixels of another region between their first and last pixel), plus a few
+    tall thin strips (boxes taller than the scan keeps spans for) and scattered
+    single pixels of the block above."""
+    r, c = np.mgrid[0:h, 0:w]
+    nbw = (w + bs - 1) // bs
+    ids = (r // bs) * nbw + (c // bs)
+    br, bc = r % bs, c % bs
+    notch = (br >= 2) & (br < bs - 2) & (bc >= bs // 2 - 1) & (bc < bs // 2 + 1) & (c // bs < nbw - 1)
+    ids = np.where(notch, ids + 1, ids)
+    # thin vertical strips, each a region of its own
+    nb = int(ids.max()) + 1
+    for k, col in enumerate(range(bs // 2, w - 1, 3 * bs)):
+        ids[1:h - 1, col] = nb + k
+    # single pixels carrying the id of the block above
+    pts = rng.integers(0, h * w, size=h * w // 97)
+    rr, cc = pts // w, pts % w
+    ok = rr >= bs
+    ids[rr[ok], cc[ok]] = ids[rr[ok] - bs, cc[ok]]
+    return ids.astype(np.int32)
+
+
+def test_nonconvex_regions_match_oracle():
+    """Regions whose rows hold other regions' pixels between their first and
+    last pixel (C shapes, detached islands, scattered pixels) and boxes taller
+    than the scan's span table: means bit-identical, graph exact."""
+    pmrf = _pmrf()
+    rng = np.random.default_rng(2024)
+    shapes = [(64, 64, 8), (96, 80, 12), (70, 45, 9), (48, 128, 20)]
+    sl = []
+    for h, w, bs in shapes:
+        ids = _carved_ids(h, w, bs, rng)
+        img = rng.normal(0.5, 0.2, size=(h, w))
+        sl.append(type("S", (), dict(image=img, region_ids=ids)))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    arrs = gpu_arrays(g)
+    for s, one in enumerate(sl):
+        assert_graph_equal(oracle.Graph.from_image(one.image, one.region_ids), slice_view(arrs, s))
+
+
 def test_em_conditional_graph_equals_unrolled():
     """The captured EM loop whose iterations sit in conditional graph nodes
     gives exactly what the unrolled capture (profiling mode) and the direct
