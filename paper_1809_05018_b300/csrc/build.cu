@@ -297,6 +297,34 @@ __global__ void __launch_bounds__(256, RS_MIN_BLOCKS) k_region_scan(
     }
 }
 
+// sums of two int32 arrays of length n (a grid of a few blocks per SM; one
+// atomic per block and array)
+constexpr int SUM_THREADS = 256;
+__global__ void __launch_bounds__(SUM_THREADS) k_sum2(const int32_t* __restrict__ a, const int32_t* __restrict__ b,
+                                                      int64_t n, unsigned long long* __restrict__ out) {
+    __shared__ unsigned long long s_a[SUM_THREADS / 32], s_b[SUM_THREADS / 32];
+    unsigned long long sa = 0, sb = 0;
+    for (int64_t i = (int64_t)blockIdx.x * SUM_THREADS + threadIdx.x; i < n; i += (int64_t)gridDim.x * SUM_THREADS) {
+        sa += (unsigned long long)(uint32_t)a[i];
+        sb += (unsigned long long)(uint32_t)b[i];
+    }
+    sa = warp_sum(sa);
+    sb = warp_sum(sb);
+    if (lane_id() == 0) {
+        s_a[warp_id()] = sa;
+        s_b[warp_id()] = sb;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < SUM_THREADS / 32; ++w) {
+            sa += s_a[w];
+            sb += s_b[w];
+        }
+        if (sa) atomicAdd(&out[0], sa);
+        if (sb) atomicAdd(&out[1], sb);
+    }
+}
+
 __global__ void k_fill_pix(const int32_t* __restrict__ ids, const int64_t* __restrict__ pix_off,
                            const int64_t* __restrict__ rank_off, const int32_t* __restrict__ rank,
                            const int64_t* __restrict__ vpix_off, int32_t* __restrict__ cursor,
@@ -1232,10 +1260,30 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     LAUNCH_1D(k_inv_rank, g->n_rank, g->d_rank, g->d_rank_off, S, g->n_rank, d_inv);
     LAUNCH_1D(k_region_scan, V, d_img, d_ids, g->d_pix_off, g->d_W, g->d_vert_off, g->d_rank_off, g->d_rank, S, d_inv,
               d_bbox_raw, d_npix_raw, V, g->d_y, g->d_npix, d_fbpix, d_fbadj, d_deg, d_nbr, g->d_status);
-    PMRF_TRY(exclusive_scan_i32_to_i64(d_fbpix, d_vpix_off, V, s));
-    int64_t nfb = 0;
-    PMRF_TRY(read_i64(d_vpix_off + V, &nfb, s));
+    // a volume's z-neighbours lie outside the bounding-box scan: every region
+    // of a 3-D volume takes the pixel-pair path below
+    if (g->volume_depth > 1) LAUNCH_1D(k_flag_all, V, d_fbadj, V);
+    // pixels of the regions whose mean needs a sorted pixel list, regions whose
+    // adjacency needs the pixel pairs (both usually none: no scan then)
+    int64_t nfb = 0, nfa = 0;
+    {
+        unsigned long long* d_sums = nullptr;
+        PMRF_TRY(tmp.get(&d_sums, 2));
+        PMRF_CUDA(cudaMemsetAsync(d_sums, 0, 2 * sizeof(unsigned long long), s));
+        if (V > 0) {
+            k_sum2<<<(unsigned)std::min<int64_t>(ceil_div(V, SUM_THREADS), 1184), SUM_THREADS, 0, s>>>(d_fbpix, d_fbadj,
+                                                                                                     V, d_sums);
+            ::pmrf::note_launch(1);
+        }
+        PMRF_CUDA(cudaGetLastError());
+        unsigned long long h2[2] = {0, 0};
+        PMRF_CUDA(cudaMemcpyAsync(h2, d_sums, sizeof(h2), cudaMemcpyDeviceToHost, s));
+        PMRF_CUDA(cudaStreamSynchronize(s));
+        nfb = (int64_t)h2[0];
+        nfa = (int64_t)h2[1];
+    }
     if (nfb > 0) {
+        PMRF_TRY(exclusive_scan_i32_to_i64(d_fbpix, d_vpix_off, V, s));
         uint32_t* d_pixlist = nullptr;
         PMRF_TRY(tmp.get(&d_pixlist, nfb));
         PMRF_CUDA(cudaMemsetAsync(d_cursor, 0, sizeof(int32_t) * std::max<int64_t>(V, 1), s));
@@ -1247,18 +1295,11 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
         LAUNCH_1D(k_means, V, d_img, d_pixlist, d_vpix_off, V, g->d_y, g->d_status);
     }
 
-    // a volume's z-neighbours lie outside the bounding-box scan: every region
-    // of a 3-D volume takes the pixel-pair path below
-    if (g->volume_depth > 1) LAUNCH_1D(k_flag_all, V, d_fbadj, V);
-
     // 4. adjacency: the scans' neighbour lists, and for the flagged regions the
     //    4-connected pixel pairs they take part in, sorted and de-duplicated
     int64_t* d_cand_off = nullptr;
     uint32_t* d_cand = nullptr;
     PMRF_TRY(tmp.get(&d_cand_off, V + 1));
-    PMRF_TRY(exclusive_scan_i32_to_i64(d_fbadj, d_cand_off, V, s));
-    int64_t nfa = 0;
-    PMRF_TRY(read_i64(d_cand_off + V, &nfa, s));
     if (nfa > 0 && g->n_pix > 0) {
         int32_t* d_cnt = nullptr;
         PMRF_TRY(tmp.get(&d_cnt, V));
@@ -1417,9 +1458,14 @@ int build_graph_impl(pmrf_graph* g, const double* d_img, const int32_t* d_ids, c
     const bool deg32 = g->max_deg <= 32;
     const int64_t rows_min_k = deg32 ? INT64_MAX : 0;
     PMRF_TRY(dalloc(&g->d_row_off, C + 1, s));
-    LAUNCH_1D(k_row_words, C, g->d_hood_off, C, rows_min_k, d_nw);
-    PMRF_TRY(exclusive_scan_i64(d_nw, g->d_row_off, C, s));
-    PMRF_TRY(read_i64(g->d_row_off + C, &g->n_row_words, s));
+    if (deg32) {
+        PMRF_CUDA(cudaMemsetAsync(g->d_row_off, 0, sizeof(int64_t) * (C + 1), s));
+        g->n_row_words = 0;
+    } else {
+        LAUNCH_1D(k_row_words, C, g->d_hood_off, C, rows_min_k, d_nw);
+        PMRF_TRY(exclusive_scan_i64(d_nw, g->d_row_off, C, s));
+        PMRF_TRY(read_i64(g->d_row_off + C, &g->n_row_words, s));
+    }
     PMRF_TRY(dalloc(&g->d_rep_woff, V + 1, s));
     LAUNCH_1D(k_rep_words, V, g->d_adj_off, d_rcount, V, d_nw);
     PMRF_TRY(exclusive_scan_i64(d_nw, g->d_rep_woff, V, s));

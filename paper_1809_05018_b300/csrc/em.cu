@@ -1151,6 +1151,9 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
     if (mode != MODE_SWEEP) tile_partials(acc, tile.part, hpart, s_wT, s_wu);
 }
 
+// ---------------------------------------------------------------------------
+// per slice: intensity range, fixed-point unit, parameters and convergence
+
 // the unit of every slice from the given parameters (standalone sweep)
 __global__ void k_units(int32_t S, int L, const double* __restrict__ theta, const double* __restrict__ yr,
                         const RunCfg* __restrict__ cfgp, int max_deg, int max_hood, SliceUnit* __restrict__ unit,
@@ -1168,9 +1171,20 @@ __global__ void k_yrange(const int64_t* __restrict__ vert_off, const double* __r
     __shared__ double s_lo[FIN_THREADS / 32], s_hi[FIN_THREADS / 32];
     const int s = blockIdx.x;
     double lo = INFINITY, hi = -INFINITY;
-    for (int64_t v = vert_off[s] + threadIdx.x; v < vert_off[s + 1]; v += blockDim.x) {
-        lo = fmin(lo, y[v]);
-        hi = fmax(hi, y[v]);
+    const int64_t v0 = vert_off[s], v1 = vert_off[s + 1];
+    // eight loads in flight per thread
+    for (int64_t v = v0 + threadIdx.x; v < v1; v += 8 * (int64_t)blockDim.x) {
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int64_t i = v + (int64_t)u * blockDim.x;
+            x[u] = i < v1 ? y[i] : y[v];
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            lo = fmin(lo, x[u]);
+            hi = fmax(hi, x[u]);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -1194,9 +1208,6 @@ __global__ void k_yrange(const int64_t* __restrict__ vert_off, const double* __r
         yr[2 * s + 1] = lo <= hi ? hi : 0.0;
     }
 }
-
-// ---------------------------------------------------------------------------
-// per-slice finalisation: parameters and convergence (one block per slice)
 
 template <int L>
 __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict__ cfgp,
@@ -1408,9 +1419,23 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
                                   const uint8_t* __restrict__ hood_gen, const int64_t* __restrict__ ht_first,
                                   int32_t S, int64_t n_htiles, int32_t te, Tile* __restrict__ tiles,
                                   int64_t tile_base, unsigned long long* __restrict__ maxne) {
+    __shared__ unsigned long long s_ne[8];
     const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
-    if (k >= n_htiles) return;  // whole warps leave together
+    if (lane == 0) s_ne[warp_id()] = 0;
+    // the block's largest tile goes out in one atomic (atomics on one word serialise)
+    auto block_max = [&]() {
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned long long m = 0;
+            for (int w = 0; w < 8; ++w) m = max(m, s_ne[w]);
+            if (m) atomicMax(maxne, m);
+        }
+    };
+    if (k >= n_htiles) {  // whole warps
+        block_max();
+        return;
+    }
     const int s = (int)(upper_bound_dev<int64_t>(ht_first, 0, S + 1, k) - 1);
     const int64_t j = k - ht_first[s];
     const int64_t cs = hood_slice_off[s], ce = hood_slice_off[s + 1];
@@ -1429,8 +1454,9 @@ __global__ void k_make_hood_tiles(const int64_t* __restrict__ hood_off, const in
         t.part = (int32_t)k;
         t.pad = fast ? 1 : 0;
         tiles[tile_base + k] = t;
-        atomicMax(maxne, (unsigned long long)(hood_off[c1] - hood_off[c0]));
+        s_ne[warp_id()] = (unsigned long long)(hood_off[c1] - hood_off[c0]);
     }
+    block_max();
 }
 
 __global__ void k_make_vert_tiles(const int64_t* __restrict__ vert_off, const int64_t* __restrict__ vt_first,
