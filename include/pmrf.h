@@ -138,7 +138,7 @@ PMRF_API const char* pmrf_last_error(void);
 
 /* Number of kernels this library has launched in this process so far (a
  * replay of a captured EM loop counts every kernel node it runs; the kernels
- * inside its conditional iteration nodes are counted on the device, so this
+ * of its conditional loop body are counted on the device, so this
  * call synchronises every device on which an EM loop was captured). */
 PMRF_API int64_t pmrf_launch_count(void);
 

@@ -33,9 +33,9 @@
 // Energies of a slice are integers in units 2^-q, q chosen per slice and
 // iteration from a bound on every element energy (slice_unit), so that all
 // sums are exact and independent of order.  Slices that have stopped skip all
-// work.  The loop is captured once into a CUDA graph whose iterations sit in
-// conditional nodes: once every slice has stopped, the remaining iterations
-// are skipped.
+// work.  The loop is captured once into a CUDA graph as one conditional WHILE
+// node whose body is one iteration (the kernels read the iteration number from
+// device memory); it ends once every slice has stopped.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -601,8 +601,16 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
                                                        double* __restrict__ vpart, DevStatus* st,
                                                        uint64_t* __restrict__ vrec,
-                                                       const SliceUnit* __restrict__ unit) {
+                                                       const SliceUnit* __restrict__ unit,
+                                                       const int32_t* __restrict__ tp) {
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
+    // in a loop graph the iteration t comes from device memory: x_in, x_out
+    // are the label buffers of odd t, exchanged for even t
+    if (tp && !(*tp & 1)) {
+        uint8_t* const xi = const_cast<uint8_t*>(x_in);
+        x_in = x_out;
+        x_out = xi;
+    }
     __shared__ double s_Md[33];  // (double)m for m <= 32: no int-to-FP64 conversions on the common path
     __shared__ double s_rcp[VAR ? RCP_N : 1];  // 1 / R for the mean-energy replica rule
     __shared__ double s_vq[3][VT_THREADS];
@@ -1093,7 +1101,15 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                                                      const SliceUnit* __restrict__ unit,
                                                      const int32_t* __restrict__ qhist,
                                                      int64_t* __restrict__ hist, double* __restrict__ S_out,
-                                                     int64_t* __restrict__ hpart, int cap, DevStatus* st) {
+                                                     int64_t* __restrict__ hpart, int cap, DevStatus* st,
+                                                     const uint8_t* __restrict__ x_alt,
+                                                     const int32_t* __restrict__ tp) {
+    // in a loop graph t comes from device memory and x_alt holds the labels
+    // that even iterations read
+    if (tp) {
+        t = *tp;
+        if (!(t & 1)) x_in = x_alt;
+    }
     // cap + 2 elements: the window plus the rest of its last hood, and one word
     // either side for the 16-byte alignment of the bulk copy
     extern __shared__ __align__(16) uint2 s_el[];
@@ -1218,7 +1234,9 @@ __global__ void k_finalize(int32_t S, int mode, int t, const RunCfg* __restrict_
                            int32_t* __restrict__ iters, int32_t* __restrict__ conv, double* __restrict__ Thist,
                            int32_t* __restrict__ nactive, const OutPtrs* __restrict__ op,
                            double* __restrict__ dterm, SliceUnit* __restrict__ unit, int32_t* __restrict__ qhist,
-                           const double* __restrict__ yr, int max_deg, int max_hood, DevStatus* st) {
+                           const double* __restrict__ yr, int max_deg, int max_hood, DevStatus* st,
+                           const int32_t* __restrict__ tp) {
+    if (tp) t = *tp;  // a loop graph's iteration
     constexpr int NQ = 4 * L;  // label moments
     __shared__ double s_q[FIN_THREADS / 32][NQ];
     __shared__ __int128 s_T[FIN_THREADS / 32];
@@ -1499,7 +1517,7 @@ int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
     void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_qhist, w.d_unit, w.d_yr, w.d_vpart, w.d_hpart, w.d_theta,
                   w.d_dterm, w.d_Thist, w.d_vrec,
-                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_cfg};
+                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_t, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
     g->em = EMWork();
@@ -1685,6 +1703,7 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) 
     if (!rc2) rc2 = dalloc(&w.d_iters, S, s);
     if (!rc2) rc2 = dalloc(&w.d_conv, S, s);
     if (!rc2) rc2 = dalloc(&w.d_nactive, 1, s);
+    if (!rc2) rc2 = dalloc(&w.d_t, 1, s);
     if (!rc2) rc2 = dalloc(&w.d_qhist, S * rc.W, s);
     if (!rc2) rc2 = dalloc((char**)&w.d_unit, (int64_t)sizeof(SliceUnit) * std::max<int64_t>(S, 1), s);
     if (!rc2) rc2 = dalloc(&w.d_yr, 2 * S, s);
@@ -1718,38 +1737,42 @@ namespace {
 
 __global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
 
-// condition of the next EM iteration's graph body: run it while any slice is
-// still active; the kernels that body will run are added to the device-side
-// launch counter
-__global__ void k_set_cond(cudaGraphConditionalHandle h, const int32_t* __restrict__ nactive,
-                           unsigned long long* __restrict__ counter, unsigned int body_kernels) {
-    const unsigned int run = *nactive > 0 ? 1u : 0u;
+// condition of the loop graph's next iteration: run iteration t + 1 while a
+// slice is still active and t < max_iters, t being t0 (>= 0: after the initial
+// pass) or the iteration just run (*tp); advances *tp and adds the kernels the
+// body will run to the device-side launch counter
+__global__ void k_next_iter(cudaGraphConditionalHandle h, const int32_t* __restrict__ nactive,
+                            int32_t* __restrict__ tp, int t0, int max_iters,
+                            unsigned long long* __restrict__ counter, unsigned int body_kernels) {
+    const int t = t0 >= 0 ? t0 : *tp;
+    const unsigned int run = (*nactive > 0 && t < max_iters) ? 1u : 0u;
+    if (run) {
+        *tp = t + 1;
+        atomicAdd(counter, (unsigned long long)body_kernels);
+    }
     cudaGraphSetConditional(h, run);
-    if (run) atomicAdd(counter, (unsigned long long)body_kernels);
 }
 
-// state of a capture that wraps each EM iteration in a conditional (IF) node
+// state of a capture that runs the EM iterations as the body of one
+// conditional WHILE node
 struct CondCapture {
-    cudaStream_t body_stream = nullptr;        // captures the bodies
-    unsigned long long* counter = nullptr;     // device-side launch counter
-    std::vector<cudaGraphConditionalHandle> h;  // h[t-1] guards iteration t
-    int64_t* parent_nodes = nullptr;           // kernels outside the bodies
-    int64_t body_nodes = 0;                    // counted on the device instead
+    cudaStream_t body_stream = nullptr;      // captures the body
+    unsigned long long* counter = nullptr;   // device-side launch counter
+    cudaGraphConditionalHandle h = 0;        // the loop's condition
+    int64_t* parent_nodes = nullptr;         // kernels outside the body
+    int64_t body_nodes = 0;                  // counted on the device instead
 };
 __global__ void k_set_active_all(int32_t* a, int32_t S) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < S) a[i] = 1;
 }
 
-// kernels one EM iteration body launches (the condition setter of the next
-// iteration included when there is one)
-int iter_kernels(const Plan* p, int t, int max_iters) {
-    return (p->n_vtiles > 0) + (p->n_htiles > 0) + 1 + (t < max_iters ? 1 : 0);
-}
+// kernels one EM iteration body launches (its condition setter included)
+int iter_kernels(const Plan* p) { return (p->n_vtiles > 0) + (p->n_htiles > 0) + 2; }
 
-// open the IF node of iteration t on the capturing stream s and start
-// capturing its body on cc->body_stream
-int open_cond_body(CondCapture* cc, cudaStream_t s, int t) {
+// open the loop's WHILE node on the capturing stream s and start capturing
+// its body on cc->body_stream
+int open_while_body(CondCapture* cc, cudaStream_t s) {
     cudaStreamCaptureStatus st;
     cudaGraph_t pg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -1760,8 +1783,8 @@ int open_cond_body(CondCapture* cc, cudaStream_t s, int t) {
     cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
     std::memset(&np, 0, sizeof(np));  // reserved fields must be zero
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = cc->h[t - 1];
-    np.conditional.type = cudaGraphCondTypeIf;
+    np.conditional.handle = cc->h;
+    np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     cudaGraphNode_t node;
     PMRF_CUDA(cudaGraphAddNode(&node, pg, deps, ed, nd, &np));
@@ -1772,9 +1795,9 @@ int open_cond_body(CondCapture* cc, cudaStream_t s, int t) {
     return PMRF_OK;
 }
 
-// with cc set (graph capture on s) every iteration is the body of an IF node
-// whose condition the previous iteration sets, so the iterations after all
-// slices converged cost one skipped node each; without it the loop is unrolled
+// with cc set (graph capture on s) the iterations are the body of one WHILE
+// node that runs while a slice is active (a graph of a few nodes, quick to
+// instantiate and to release); without it the loop is unrolled
 template <int L>
 int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_from_labels,
             CondCapture* cc = nullptr) {
@@ -1790,62 +1813,79 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
     if (p->n_vtiles > 0) {
         k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
                                                                 w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
-                                                                nullptr, w.d_vpart, g->d_status, nullptr, nullptr);
+                                                                nullptr, w.d_vpart, g->d_status, nullptr, nullptr,
+                                                                nullptr);
         ::pmrf::note_launch(1);
     }
     SliceUnit* unit = (SliceUnit*)w.d_unit;
     k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_INIT, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
                                             w.d_hpart, nullptr, w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
                                             w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm, unit, w.d_qhist,
-                                            w.d_yr, g->max_deg, g->max_hood, g->d_status);
+                                            w.d_yr, g->max_deg, g->max_hood, g->d_status, nullptr);
     ::pmrf::note_launch(1);
-    if (cc) {
-        k_set_cond<<<1, 1, 0, s>>>(cc->h[0], w.d_nactive, cc->counter,
-                                   (unsigned)iter_kernels(p, 1, rc.max_iters));
-        ::pmrf::note_launch(1);
-    }
-    const bool prof = !cc && g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
     const auto kv = is_variant(rc) ? &k_vertex<L, true> : &k_vertex<L, false>;
-    const cudaStream_t s0 = s;
-    for (int t = 1; t <= rc.max_iters; ++t) {
-        const uint8_t* xin = w.d_x[(t - 1) & 1];
-        uint8_t* xout = w.d_x[t & 1];
-        if (cc) {
-            PMRF_TRY(open_cond_body(cc, s0, t));
-            s = cc->body_stream;
-            set_capture_counter(&cc->body_nodes);
-        }
-        if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
+    if (cc) {
+        // one WHILE node whose body is one iteration; the kernels read t from
+        // w.d_t, which the condition setter at the end of each body advances
+        const unsigned body = (unsigned)iter_kernels(p);
+        k_next_iter<<<1, 1, 0, s>>>(cc->h, w.d_nactive, w.d_t, 0, rc.max_iters, cc->counter, body);
+        ::pmrf::note_launch(1);
+        const cudaStream_t s0 = s;
+        PMRF_TRY(open_while_body(cc, s0));
+        s = cc->body_stream;
+        set_capture_counter(&cc->body_nodes);
         if (p->n_vtiles > 0) {
-            kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
-                                                                    xout, w.d_theta, w.d_dterm, nullptr, nullptr,
-                                                                    w.d_vpart, g->d_status, w.d_vrec, unit);
+            kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, w.d_x[0],
+                                                            w.d_x[1], w.d_theta, w.d_dterm, nullptr, nullptr,
+                                                            w.d_vpart, g->d_status, w.d_vrec, unit, w.d_t);
             ::pmrf::note_launch(1);
         }
-        if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
         if (p->n_htiles > 0) {
             k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
-                z.dg, z.ht, MODE_EM, t, p->hood_lanes, z.d_cfg, w.d_active, xin, w.d_vrec, unit, w.d_qhist,
-                w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status);
+                z.dg, z.ht, MODE_EM, 0, p->hood_lanes, z.d_cfg, w.d_active, w.d_x[0], w.d_vrec, unit, w.d_qhist,
+                w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status, w.d_x[1], w.d_t);
             ::pmrf::note_launch(1);
         }
-        if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
-        k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0, w.d_vpart,
-                                                w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off, w.d_active,
-                                                w.d_iters, w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm,
-                                                unit, w.d_qhist, w.d_yr, g->max_deg, g->max_hood, g->d_status);
+        k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0,
+                                                          w.d_vpart, w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off,
+                                                          w.d_active, w.d_iters, w.d_conv, w.d_Thist, w.d_nactive,
+                                                          z.d_out, w.d_dterm, unit, w.d_qhist, w.d_yr, g->max_deg,
+                                                          g->max_hood, g->d_status, w.d_t);
         ::pmrf::note_launch(1);
-        if (cc) {
-            if (t < rc.max_iters) {
-                k_set_cond<<<1, 1, 0, s>>>(cc->h[t], w.d_nactive, cc->counter,
-                                           (unsigned)iter_kernels(p, t + 1, rc.max_iters));
+        k_next_iter<<<1, 1, 0, s>>>(cc->h, w.d_nactive, w.d_t, -1, rc.max_iters, cc->counter, body);
+        ::pmrf::note_launch(1);
+        PMRF_CUDA(cudaGetLastError());
+        cudaGraph_t bg = nullptr;
+        PMRF_CUDA(cudaStreamEndCapture(s, &bg));
+        s = s0;
+        set_capture_counter(cc->parent_nodes);
+    } else {
+        const bool prof = g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
+        for (int t = 1; t <= rc.max_iters; ++t) {
+            const uint8_t* xin = w.d_x[(t - 1) & 1];
+            uint8_t* xout = w.d_x[t & 1];
+            if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 0], s, cudaEventRecordExternal);
+            if (p->n_vtiles > 0) {
+                kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
+                                                                xout, w.d_theta, w.d_dterm, nullptr, nullptr,
+                                                                w.d_vpart, g->d_status, w.d_vrec, unit, nullptr);
                 ::pmrf::note_launch(1);
             }
-            PMRF_CUDA(cudaGetLastError());
-            cudaGraph_t body = nullptr;
-            PMRF_CUDA(cudaStreamEndCapture(s, &body));
-            s = s0;
-            set_capture_counter(cc->parent_nodes);
+            if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
+            if (p->n_htiles > 0) {
+                k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
+                    z.dg, z.ht, MODE_EM, t, p->hood_lanes, z.d_cfg, w.d_active, xin, w.d_vrec, unit, w.d_qhist,
+                    w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status, nullptr, nullptr);
+                ::pmrf::note_launch(1);
+            }
+            if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
+            k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, t, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0,
+                                                              w.d_vpart, w.d_hpart, w.d_theta, w.d_theta,
+                                                              g->d_vert_off, w.d_active, w.d_iters, w.d_conv,
+                                                              w.d_Thist, w.d_nactive, z.d_out, w.d_dterm, unit,
+                                                              w.d_qhist, w.d_yr, g->max_deg, g->max_hood,
+                                                              g->d_status, nullptr);
+            ::pmrf::note_launch(1);
         }
     }
     k_close<<<(unsigned)std::max<int64_t>(1, std::min<int64_t>(ceil_div(g->V, 256), 4096)), 256, 0, s>>>(
@@ -1883,9 +1923,7 @@ int capture_em(pmrf_graph* g, Plan* p, const RunCfg& rc, bool init_from_labels, 
         cudaStreamCaptureStatus st;
         cudaGraph_t pg = nullptr;
         e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &pg);
-        cc.h.resize(rc.max_iters);
-        for (int t = 0; t < rc.max_iters && e == cudaSuccess; ++t)
-            e = cudaGraphConditionalHandleCreate(&cc.h[t], pg, 0, cudaGraphCondAssignDefault);
+        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cc.h, pg, 0, cudaGraphCondAssignDefault);
     }
     if (e == cudaSuccess) {
         set_capture_counter(nodes);
@@ -2043,13 +2081,13 @@ int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, cons
         const auto kv = var ? &k_vertex<L, true> : &k_vertex<L, false>;
         kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
                                                                 nullptr, nullptr, Eout, nullptr, g->d_status, vrec,
-                                                                unit);
+                                                                unit, nullptr);
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
         k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
             dg, ht, MODE_SWEEP, 1, p->hood_lanes, d_cfg, nullptr, xin, vrec, unit, nullptr, nullptr, Sout, nullptr,
-            hood_cap(p), g->d_status);
+            hood_cap(p), g->d_status, nullptr, nullptr);
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
@@ -2064,13 +2102,13 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     if (p->n_vtiles > 0) {
         k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
                                                                 nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
-                                                                g->d_status, nullptr, nullptr);
+                                                                g->d_status, nullptr, nullptr, nullptr);
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)g->S, FIN_THREADS, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,
                                                w.d_vpart, w.d_hpart, prev, out, g->d_vert_off, nullptr, nullptr,
                                                nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr,
-                                               nullptr, 0, 0, g->d_status);
+                                               nullptr, 0, 0, g->d_status, nullptr);
     ::pmrf::note_launch(1);
     PMRF_CUDA(cudaGetLastError());
     return PMRF_OK;

@@ -49,6 +49,7 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     int32_t* d_iters = nullptr;    // [S]
     int32_t* d_conv = nullptr;     // [S]
     int32_t* d_nactive = nullptr;  // [1]
+    int32_t* d_t = nullptr;        // [1] the loop graph's current iteration
     void* d_cfg = nullptr;         // device copy of the run's constants
 };
 
