@@ -456,7 +456,7 @@ __device__ __forceinline__ long long ordered_key(double x) {
 // Estar, writes the hood-pass record.  k_l of a replica = its in-hood
 // neighbours whose label is not l (every neighbour for the full scope).
 template <int L>
-__device__ __noinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, const uint8_t* __restrict__ x_in,
+__device__ __forceinline__ int vertex_variant(const DevGraph& g, const RunCfg& c, const uint8_t* __restrict__ x_in,
                                            int64_t a0, int d, int64_t r0, int64_t r1, const uint32_t (&lm)[L],
                                            const double (&D)[L], uint64_t* __restrict__ vrec, int64_t v,
                                            double& Estar, const double* __restrict__ rcp, int q, int64_t beta_q) {
