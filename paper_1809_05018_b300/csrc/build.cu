@@ -500,6 +500,33 @@ __device__ __forceinline__ bool bs_empty(const uint64_t* a, int nw) {
 __device__ void build_local_adj(const int64_t* __restrict__ adj_off, const int32_t* __restrict__ adj, int64_t v,
                                 int d, int nw, uint64_t* nbm) {
     const int32_t* N = adj + adj_off[v];
+    if (nw == 1) {
+        // d <= 64: the relation is symmetric, so row i intersects N(u_i) only
+        // with the slots above i (a branch-free two-pointer step) and each
+        // adjacent pair is mirrored into the lower row
+        for (int i = 0; i < d; ++i) nbm[i] = 0;
+        for (int i = 0; i + 1 < d; ++i) {
+            const int32_t u = N[i];
+            const int32_t* Nu = adj + adj_off[u];
+            const int du = (int)(adj_off[u + 1] - adj_off[u]);
+            uint64_t row = 0;
+            int a = 0, j = i + 1;
+            while (a < du && j < d) {
+                const int32_t x = __ldg(Nu + a), y = __ldg(N + j);
+                const bool le = x <= y, ge = x >= y;
+                row |= (uint64_t)(le && ge) << j;
+                a += le;
+                j += ge;
+            }
+            nbm[i] |= row;
+            while (row) {
+                const int j2 = __ffsll((long long)row) - 1;
+                row &= row - 1;
+                nbm[j2] |= 1ull << i;
+            }
+        }
+        return;
+    }
     for (int i = 0; i < d; ++i) {
         for (int w = 0; w < nw; ++w) nbm[(int64_t)i * nw + w] = 0;
         const int32_t u = N[i];

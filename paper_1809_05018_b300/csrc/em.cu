@@ -711,22 +711,54 @@ __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGrap
                 // the hood pass of this iteration reads v's data terms and label masks
                 // every vertex lies in at least one hood, so M_l is set (and
                 // <= 32 when d <= 32).  The data terms in the slice's unit serve
-                // the hood pass's record and the label choice: the least of
-                // D_l + beta M_l compared on the integer pipes (ties to the lower
-                // label; the FP64 pipe of this part is the scarce unit), its
-                // value E*_v in the unit for the moments
-                int64_t F[L];
+                // the hood pass's record.  The label is the least D_l + beta M_l
+                // in FP64 (ties to the lower label), the precision the oracle
+                // decides in.  The exact energies in the unit give the same
+                // label whenever the least one leads every other by more than
+                // both evaluations' rounding can move them (fixed point: half a
+                // unit per rounded term, so 1/2 + M/2; FP64: 2^-52 of the
+                // magnitude plus one unit; taken generously below); only closer
+                // labels are compared in FP64.  The label's energy in the unit
+                // enters the tile's exact sum of E*
+                int64_t F[L], e[L];
 #pragma unroll
-                for (int l = 0; l < L; ++l) F[l] = to_fixed(D[l], uq);
+                for (int l = 0; l < L; ++l) {
+                    F[l] = to_fixed(D[l], uq);
+                    e[l] = F[l] + ubq * (int64_t)M[l];
+                }
                 if (vrec) write_vrec_fixed<L>(vrec, g.V, v, F, lm);
-                int64_t eb = F[0] + ubq * (int64_t)M[0];
+                int64_t eb = e[0];
                 lab = 0;
 #pragma unroll
-                for (int l = 1; l < L; ++l) {
-                    const int64_t e = F[l] + ubq * (int64_t)M[l];
-                    if (e < eb) { eb = e; lab = l; }
+                for (int l = 1; l < L; ++l)
+                    if (e[l] < eb) { eb = e[l]; lab = l; }
+                uint64_t mag_b = 0;
+                int m_b = 0;
+#pragma unroll
+                for (int l = 0; l < L; ++l)
+                    if (l == lab) {
+                        mag_b = (uint64_t)(F[l] < 0 ? -F[l] : F[l]) + (uint64_t)ubq * (uint64_t)M[l];
+                        m_b = M[l];
+                    }
+                bool sure = true;
+#pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    const uint64_t mag = (uint64_t)(F[l] < 0 ? -F[l] : F[l]) + (uint64_t)ubq * (uint64_t)M[l];
+                    const int64_t eps = 4 + M[l] + m_b + (int64_t)((mag + mag_b) >> 50);
+                    if (l != lab && e[l] - eb <= eps) sure = false;
                 }
-                Eq = eb;
+                if (!sure) {
+                    double best = D[0] + c.beta * (d <= 32 ? s_Md[M[0]] : (double)M[0]);
+                    lab = 0;
+#pragma unroll
+                    for (int l = 1; l < L; ++l) {
+                        const double x = D[l] + c.beta * (d <= 32 ? s_Md[M[l]] : (double)M[l]);
+                        if (x < best) { best = x; lab = l; }
+                    }
+                }
+#pragma unroll
+                for (int l = 0; l < L; ++l)
+                    if (l == lab) Eq = e[l];
                 if (E_out) {  // the chosen label's energy in FP64 (standalone sweep)
 #pragma unroll
                     for (int l = 0; l < L; ++l)
