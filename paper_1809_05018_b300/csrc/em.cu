@@ -451,6 +451,122 @@ __device__ __forceinline__ long long ordered_key(double x) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
+// The votes of all replicas of v (vote rule): each replica's least label from
+// its counts k_l of in-hood neighbours not labelled l, by the exact energies in
+// the slice's unit (the caller has ruled out near-ties, see vertex_variant)
+template <int L>
+__device__ __forceinline__ void vote_tally(const DevGraph& g, const uint8_t* __restrict__ x_in, int64_t a0, int d,
+                                           int nw, int64_t r0, int64_t r1, const uint32_t (&lm)[L],
+                                           const uint64_t (&dq)[L], uint64_t bq, int (&votes)[L], int (&kmin)[L]) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        votes[l] = 0;
+        kmin[l] = 0x7fffffff;
+    }
+    auto vote = [&](const int (&k)[L]) {
+        // excess <= 2^61, beta_q k below 2^62 / 32 (slice_unit): no overflow
+        int b = 0;
+        uint64_t eb = dq[0] + bq * (uint64_t)k[0];
+#pragma unroll
+        for (int l = 1; l < L; ++l) {
+            const uint64_t e = dq[l] + bq * (uint64_t)k[l];
+            if (e < eb) {
+                eb = e;
+                b = l;
+            }
+        }
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            if (l == b) {
+                votes[l] += 1;
+                kmin[l] = min(kmin[l], k[l]);
+            }
+    };
+    if (d <= 32) {
+        for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
+            const int dc = __popc(m);
+            int k[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) k[l] = dc - __popc(m & lm[l]);
+            vote(k);
+        });
+    } else {
+        for (int64_t r = r0; r < r1; r += nw) {
+            int cnt[L], k[L];
+            const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+#pragma unroll
+            for (int l = 0; l < L; ++l) k[l] = dc - cnt[l];
+            vote(k);
+        }
+    }
+}
+
+// the vote tally of one vertex with every replica's least label taken in FP64
+// (D_l + beta k_l, lower label on ties); out of line and given values only, so
+// that the rare near-tie path adds nothing to the integer tally's code
+template <int L>
+struct VoteFP64 {
+    const uint32_t* rep_mask;
+    const int32_t* adj;
+    const uint8_t* x_in;
+    int64_t a0, r0, r1;
+    int d, nw;
+    double beta;
+    double D[L];
+    uint32_t lm[L];
+    int votes[L], kmin[L];
+};
+
+template <int L>
+__device__ __noinline__ VoteFP64<L> vote_tally_fp64(VoteFP64<L> a) {
+#pragma unroll
+    for (int l = 0; l < L; ++l) {
+        a.votes[l] = 0;
+        a.kmin[l] = 0x7fffffff;
+    }
+    for (int64_t r = a.r0; r < a.r1; r += a.nw) {
+        int k[L];
+        if (a.d <= 32) {
+            const uint32_t m = a.rep_mask[r];
+            const int dc = __popc(m);
+#pragma unroll
+            for (int l = 0; l < L; ++l) k[l] = dc - __popc(m & a.lm[l]);
+        } else {
+            int cnt[L];
+#pragma unroll
+            for (int l = 0; l < L; ++l) cnt[l] = 0;
+            int dc = 0;
+            for (int w = 0; w < a.nw; ++w) {
+                uint32_t m = a.rep_mask[r + w];
+                dc += __popc(m);
+                while (m) {
+                    const int b = __ffs(m) - 1;
+                    m &= m - 1;
+                    const int xl = a.x_in[a.adj[a.a0 + w * 32 + b]];
+#pragma unroll
+                    for (int l = 0; l < L; ++l) cnt[l] += (xl == l);
+                }
+            }
+#pragma unroll
+            for (int l = 0; l < L; ++l) k[l] = dc - cnt[l];
+        }
+        int b = 0;
+        double best = a.D[0] + a.beta * (double)k[0];
+#pragma unroll
+        for (int l = 1; l < L; ++l) {
+            const double x = a.D[l] + a.beta * (double)k[l];
+            if (x < best) { best = x; b = l; }
+        }
+#pragma unroll
+        for (int l = 0; l < L; ++l)
+            if (l == b) {
+                a.votes[l] += 1;
+                a.kmin[l] = min(a.kmin[l], k[l]);
+            }
+    }
+    return a;
+}
+
 // The sweep variants for one vertex (scope and replica rule of RunCfg; the
 // same definitions as pmrf_config documents): returns the new label, sets
 // Estar, writes the hood-pass record.  k_l of a replica = its in-hood
@@ -529,50 +645,75 @@ __device__ __forceinline__ int vertex_variant(const DevGraph& g, const RunCfg& c
             if (e < Estar) { Estar = e; lab = l; }
         }
     } else {
-        // vote: each replica's least label, compared exactly in the hood
-        // pass's fixed point (excess_l + beta_q k_l in the slice's unit)
+        // vote: each replica's least label D_l + beta k_l with FP64 semantics:
+        // the exact energies of the hood pass's fixed point (excess_l +
+        // beta_q k_l in the slice's unit) decide when the least leads every
+        // other label by more than both evaluations' rounding bound (as for the
+        // default rule), FP64 compares the rest
         uint64_t dq[L];
         int amin;
-        (void)data_fixed<L>(D, q, dq, amin);
-        int votes[L], kmin[L];
+        const int64_t Fmin = data_fixed<L>(D, q, dq, amin);
+        int votes[L], kmin[L];  // set by vote_tally
+        const uint64_t bq = (uint64_t)beta_q;
+        // one bound for every replica of v: counts k_l <= d, so both
+        // evaluations' rounding stays below 8 + 2d units plus 2^-50 of twice
+        // the largest magnitude |F_l| + beta_q d
+        uint64_t maxF = 0;
 #pragma unroll
         for (int l = 0; l < L; ++l) {
-            votes[l] = 0;
-            kmin[l] = 0x7fffffff;
+            const int64_t F = Fmin + (int64_t)dq[l];
+            maxF = max(maxF, (uint64_t)(F < 0 ? -F : F));
         }
-        const uint64_t bq = (uint64_t)beta_q;
-        // one replica's vote from its counts k_l of in-hood neighbours not labelled l
-        auto vote = [&](const int (&k)[L]) {
-            // excess <= 2^61, beta_q k below 2^62 / 32 (slice_unit): no overflow
-            int b = 0;
-            uint64_t eb = dq[0] + bq * (uint64_t)k[0];
+        const uint64_t eps = 8 + 2 * (uint64_t)d + ((2 * (maxF + bq * (uint64_t)d)) >> 50);
+        // a near-tie needs two labels l, m whose energies differ by at most
+        // eps in some replica: (dq_l - dq_m) + beta_q (k_l - k_m) with
+        // |k_l - k_m| <= d, i.e. dq_m - dq_l within eps of a multiple beta_q
+        // delta, |delta| <= d.  With beta_q > 2 eps at most the nearest
+        // multiple qualifies, and a float quotient is within one of it, so
+        // three exact integer checks settle it; a smaller beta_q counts as a
+        // possible near-tie.  Once per vertex
+        bool near = false;
 #pragma unroll
-            for (int l = 1; l < L; ++l) {
-                const uint64_t e = dq[l] + bq * (uint64_t)k[l];
-                if (e < eb) { eb = e; b = l; }
-            }
+        for (int l = 0; l < L; ++l)
 #pragma unroll
-            for (int l = 0; l < L; ++l)
-                if (l == b) {
-                    votes[l] += 1;
-                    kmin[l] = min(kmin[l], k[l]);
+            for (int m = l + 1; m < L; ++m) {
+                const int64_t y = (int64_t)dq[m] - (int64_t)dq[l];
+                const uint64_t ay = (uint64_t)(y < 0 ? -y : y);
+                if (bq <= 2 * eps) {
+                    near = near || ay <= bq * (uint64_t)d + eps;
+                } else if (ay <= bq * (uint64_t)d + eps) {
+                    const int est = (int)rintf((float)y / (float)bq);
+                    for (int dd = -1; dd <= 1; ++dd) {
+                        const int64_t delta = (int64_t)est + dd;
+                        if (delta < -(int64_t)d || delta > (int64_t)d) continue;
+                        const int64_t diff = y - (int64_t)bq * delta;
+                        near = near || (uint64_t)(diff < 0 ? -diff : diff) <= eps;
+                    }
                 }
-        };
-        if (d <= 32) {
-            for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
-                const int dc = __popc(m);
-                int k[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) k[l] = dc - __popc(m & lm[l]);
-                vote(k);
-            });
+            }
+        if (!near) {
+            vote_tally<L>(g, x_in, a0, d, nw, r0, r1, lm, dq, bq, votes, kmin);
         } else {
-            for (int64_t r = r0; r < r1; r += nw) {
-                int cnt[L], k[L];
-                const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+            VoteFP64<L> a;
+            a.rep_mask = g.rep_mask;
+            a.adj = g.adj;
+            a.x_in = x_in;
+            a.a0 = a0;
+            a.r0 = r0;
+            a.r1 = r1;
+            a.d = d;
+            a.nw = nw;
+            a.beta = c.beta;
 #pragma unroll
-                for (int l = 0; l < L; ++l) k[l] = dc - cnt[l];
-                vote(k);
+            for (int l = 0; l < L; ++l) {
+                a.D[l] = D[l];
+                a.lm[l] = lm[l];
+            }
+            a = vote_tally_fp64<L>(a);
+#pragma unroll
+            for (int l = 0; l < L; ++l) {
+                votes[l] = a.votes[l];
+                kmin[l] = a.kmin[l];
             }
         }
         int best = votes[0];
