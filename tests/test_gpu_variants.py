@@ -110,3 +110,43 @@ def test_default_variant_unchanged_and_graph_cache_keyed():
     for k in ("labels", "params", "iters", "converged"):
         assert torch.equal(a1[k], a2[k]), k
         assert torch.equal(b1[k], b2[k]), k
+
+
+@pytest.mark.parametrize("L", [2, 3])
+@pytest.mark.parametrize("scope,rule", [(0, 0)] + VARIANTS)
+def test_sweep_exact_ties_take_the_lower_label(scope, rule, L):
+    """Every region mean exactly 0.5, labels 0 and 1 at means 0.25 and 0.75
+    with equal deviations (any further label far away): labels 0 and 1 get
+    bit-identical data terms, so their energies tie wherever their Potts
+    counts tie.  Both sides must then
+    take the lower label (readings G5, G6, G14), so every label is compared
+    exactly, the ties included; the kernel's fixed-point decisions hand such
+    near-ties to FP64.  The mean-energy rule is the one exception: the oracle
+    sums each label's per-replica energies in FP64 before dividing, so an
+    exact tie of the means can come out an ulp apart there while the kernel's
+    integer count sums tie exactly; for it labels are compared where the
+    oracle's gap is exactly 0 or at least 1e-9."""
+    pmrf = _pmrf()
+    pairs = [(np.full_like(a, 0.5), b) for a, b in _slices(840 + L)]
+    g = pmrf.build_graph([torch.from_numpy(a).cuda() for a, _ in pairs],
+                         [torch.from_numpy(b).cuda() for _, b in pairs])
+    rng = np.random.default_rng(100 + 10 * scope + rule + L)
+    x = rng.integers(0, L, g.V).astype(np.uint8)
+    theta = np.zeros((g.S, L, 4))
+    theta[:, :, 1] = [0.25, 0.75] + [2.0 + l for l in range(2, L)]
+    theta[:, :, 2] = 0.1
+    cfg = pmrf.EMConfig(n_labels=L, beta=1.0, potts_scope=scope, replica_rule=rule)
+    xo, ev, _ = g.map_sweep(cfg, torch.from_numpy(x).cuda(), torch.from_numpy(theta).cuda())
+    xo, ev = xo.cpu().numpy(), ev.cpu().numpy()
+    g.sync_status()
+    arrs = gpu_arrays(g)
+    ties = 0
+    for s, (a, b) in enumerate(pairs):
+        og = oracle.Graph.from_image(a, b)
+        v0, v1 = arrs["VERT_OFF"][s], arrs["VERT_OFF"][s + 1]
+        r = og.map_sweep_variant(L, cfg.beta, x[v0:v1], theta[s, :, 1], theta[s, :, 2], scope, rule)
+        ok = np.ones(v1 - v0, bool) if rule != 1 else (r["gap"] == 0) | (r["gap"] >= 1e-9)
+        assert np.array_equal(xo[v0:v1][ok], r["x_new"][ok]), f"slice {s}"
+        assert rel_close(ev[v0:v1][ok], r["E_star"][ok], 1e-12, 1e-13), s
+        ties += int((r["gap"] == 0).sum())
+    assert ties > 0  # the case under test occurred
