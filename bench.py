@@ -303,13 +303,20 @@ def run_ours(a):
         pll, gm, gs, gb = g.pll_value_and_grad(L, out["labels"], mu, sg, beta, ones[:g.S])
         return g, out, seg, pll
 
+    # A batch's graph is released before the next batch is built (the release
+    # runs inside the step): the next build then reuses the memory, at the
+    # same addresses, that the previous step just worked on; built while the
+    # previous graph is still alive it took about 3.7 ms longer on stack512
     tuned = None
+    gw = None
     for k in range(a.warmup):
+        gw = None
         gw, _, _, _ = step(img_d, ids_d)
         if k == 0 and not a.no_autotune:
             # the hood pass's launch shape for this batch's shape, kept by the
             # library for the graphs the timed steps build
             tuned = gw.autotune(cfg)
+    gw = None
     torch.cuda.synchronize()
 
     # ---- timed region: inputs resident in HBM
@@ -319,7 +326,9 @@ def run_ours(a):
     torch.cuda.synchronize()
     with Clocks(local) as clk:
         e0.record()
+        g = None
         for _ in range(a.steps):
+            g = out = seg = pll = None
             g, out, seg, pll = step(img_d, ids_d)
         e1.record()
         torch.cuda.synchronize()
