@@ -226,7 +226,11 @@ PMRF_API int pmrf_build_graph(const double* d_image, const int32_t* d_region_ids
                      pmrf_graph** out);
 
 /* Free a graph and its device memory (NULL is accepted).  Synchronises the
- * device work that used the graph. */
+ * device work that used the graph.  The memory returns to the library's pool,
+ * so a batch built after its predecessor's graph is freed reuses the same
+ * memory (for a stream of same-sized batches, freeing the previous graph
+ * before the next build made that build faster: 19.5 against 23.3 ms on
+ * 512 slices of 1024x1024). */
 PMRF_API int pmrf_graph_destroy(pmrf_graph* g);
 
 /* Totals of a graph: vertices, undirected edges, maximal cliques (= hoods),
