@@ -55,7 +55,7 @@ constexpr int VT_THREADS = 128;             // vertices per vertex tile = thread
 // (measured on the two-label stack: the vertex pass gains from 16 blocks at 32
 // registers; more labels need more registers)
 __host__ __device__ constexpr int vt_min_blocks(int L) { return L <= 2 ? 16 : (L <= 4 ? 10 : 4); }
-__host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 2 ? 12 : 8; }
+__host__ __device__ constexpr int ht_min_blocks(int L) { return L <= 4 ? 12 : 8; }
 constexpr int FIN_THREADS = 256;            // finaliser block (one per slice)
 constexpr int LI_THREADS = 256;             // label-image block
 constexpr int HT_THREADS = 128;             // hood-pass block
