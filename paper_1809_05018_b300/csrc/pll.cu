@@ -18,21 +18,27 @@ namespace pmrf {
 namespace {
 
 constexpr int PLL_THREADS = 256;
+// vertices a thread in the allocating calls (the allocation-free call keeps
+// one, so its scratch bound stays S ceil(V_max / 256) (2L + 2) + S doubles)
+constexpr int PLL_VPT = 4;
 
 template <int L>
 __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* __restrict__ vert_off,
                                                      const double* __restrict__ y, const int64_t* __restrict__ adj_off,
                                                      const int32_t* __restrict__ adj, const uint8_t* __restrict__ x,
                                                      const double* __restrict__ mu, const double* __restrict__ sigma,
-                                                     double beta, int64_t nchunk, double* __restrict__ part) {
+                                                     double beta, int64_t nchunk, int vpt,
+                                                     double* __restrict__ part) {
     constexpr int NP = 2 * L + 2;  // pll, gmu[L], gsigma[L], gbeta
     __shared__ double s_mu[L], s_inv[L], s_ln[L], s_isg[L], s_isg2[L], s_isg3[L];
     __shared__ double s_acc[NP][PLL_THREADS];
     __shared__ double s_red[NP][8];
     const int s = blockIdx.y;
     const int64_t vb = vert_off[s], ve = vert_off[s + 1];
-    const int64_t v = vb + (int64_t)blockIdx.x * PLL_THREADS + threadIdx.x;
-    if (vb + (int64_t)blockIdx.x * PLL_THREADS >= ve) return;  // whole block beyond this slice
+    // vpt vertices a thread, PLL_THREADS apart: block b takes the slice's
+    // vertices [b vpt PLL_THREADS, (b + 1) vpt PLL_THREADS)
+    const int64_t vblk = vb + (int64_t)blockIdx.x * vpt * PLL_THREADS;
+    if (vblk >= ve) return;  // whole block beyond this slice
     if (threadIdx.x < L) {
         const double m = mu[(int64_t)s * L + threadIdx.x], sg = sigma[(int64_t)s * L + threadIdx.x];
         s_mu[threadIdx.x] = m;
@@ -48,7 +54,9 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
     double acc[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) acc[k] = 0.0;
-    if (v < ve) {
+    for (int r = 0; r < vpt; ++r) {
+        const int64_t v = vblk + (int64_t)r * PLL_THREADS + threadIdx.x;
+        if (v >= ve) break;
         const double yv = y[v];
         const int xv = x[v];
         int cnt[L];
@@ -97,14 +105,14 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
             if (l == xv) { Ex = E[l]; mx = (double)(d - cnt[l]); }
             eb += p[l] * (double)(d - cnt[l]);
         }
-        acc[0] = -Ex - (-emin + logz);
+        acc[0] += -Ex - (-emin + logz);
 #pragma unroll
         for (int l = 0; l < L; ++l) {
             const double w = p[l] - (l == xv ? 1.0 : 0.0);
-            acc[1 + l] = -w * dev[l] * s_isg2[l];
-            acc[1 + L + l] = w * (s_isg[l] - dev2[l] * s_isg3[l]);
+            acc[1 + l] += -w * dev[l] * s_isg2[l];
+            acc[1 + L + l] += w * (s_isg[l] - dev2[l] * s_isg3[l]);
         }
-        acc[1 + 2 * L] = eb - mx;
+        acc[1 + 2 * L] += eb - mx;
     }
     // block sums in a fixed order without shuffle trees (the FP64 pipe is the
     // scarce unit): 8 threads per quantity add 32 consecutive entries each,
@@ -127,12 +135,12 @@ __global__ void __launch_bounds__(PLL_THREADS) k_pll(int32_t S, const int64_t* _
 }
 
 template <int L>
-__global__ void k_pll_final(int32_t S, const int64_t* __restrict__ vert_off, int64_t nchunk,
+__global__ void k_pll_final(int32_t S, const int64_t* __restrict__ vert_off, int64_t nchunk, int vpt,
                             const double* __restrict__ part, double* __restrict__ pll, const double* __restrict__ gout,
                             double* __restrict__ gmu, double* __restrict__ gsigma, double* __restrict__ gbeta_s) {
     constexpr int NP = 2 * L + 2;
     const int s = blockIdx.x;
-    const int64_t nb = ceil_div(vert_off[s + 1] - vert_off[s], PLL_THREADS);
+    const int64_t nb = ceil_div(vert_off[s + 1] - vert_off[s], (int64_t)PLL_THREADS * vpt);  // k_pll's blocks
     double tot[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) tot[k] = 0.0;
@@ -175,7 +183,7 @@ int pll_body(pmrf_graph* g, const uint8_t* x, const double* mu, const double* si
     constexpr int NP = 2 * L + 2;
     int64_t maxv = 0;
     for (int i = 0; i < g->S; ++i) maxv = std::max(maxv, g->h_vert_off[i + 1] - g->h_vert_off[i]);
-    const int64_t nchunk = std::max<int64_t>(1, ceil_div(maxv, PLL_THREADS));
+    const int64_t nchunk = std::max<int64_t>(1, ceil_div(maxv, (int64_t)PLL_THREADS * PLL_VPT));
     if (nchunk > 2147483647ll) return fail(PMRF_ERR_UNSUPPORTED, "slice too large");
     double* part = nullptr;
     double* gb = nullptr;
@@ -185,9 +193,10 @@ int pll_body(pmrf_graph* g, const uint8_t* x, const double* mu, const double* si
     if (maxv > 0) {
         const dim3 grid((unsigned)nchunk, (unsigned)g->S);
         k_pll<L><<<grid, PLL_THREADS, 0, s>>>(g->S, g->d_vert_off, g->d_y, g->d_adj_off, g->d_adj, x, mu, sigma, beta,
-                                             nchunk, part); ::pmrf::note_launch(1);
+                                             nchunk, PLL_VPT, part); ::pmrf::note_launch(1);
     }
-    k_pll_final<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, g->d_vert_off, nchunk, part, pll, gout, gmu, gsigma, gb); ::pmrf::note_launch(1);
+    k_pll_final<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, g->d_vert_off, nchunk, PLL_VPT, part, pll, gout, gmu, gsigma,
+                                                 gb); ::pmrf::note_launch(1);
     if (gout && gbeta) { k_sum_slices<<<1, 32, 0, s>>>(g->S, gb, gbeta); ::pmrf::note_launch(1); }
     cudaError_t e = cudaGetLastError();
     dfree(part, s);
@@ -286,10 +295,10 @@ int pll_grad_noalloc_body(pmrf_graph* g, const uint8_t* x, const double* mu, con
     if (maxv > 0) {
         const dim3 grid((unsigned)nchunk, (unsigned)g->S);
         k_pll<L><<<grid, PLL_THREADS, 0, s>>>(g->S, g->d_vert_off, g->d_y, g->d_adj_off, g->d_adj, x, mu, sigma, beta,
-                                             nchunk, part);
+                                             nchunk, 1, part);
         ::pmrf::note_launch(1);
     }
-    k_pll_final<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, g->d_vert_off, nchunk, part, nullptr, gout, gmu, gsigma, gb);
+    k_pll_final<L><<<(unsigned)g->S, 32, 0, s>>>(g->S, g->d_vert_off, nchunk, 1, part, nullptr, gout, gmu, gsigma, gb);
     ::pmrf::note_launch(1);
     if (gbeta) {
         k_sum_slices<<<1, 32, 0, s>>>(g->S, gb, gbeta);
