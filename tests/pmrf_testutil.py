@@ -7,7 +7,7 @@ import numpy as np
 import oracle
 import synth
 
-# tolerances (spec: labels equal wherever the oracle's label-energy gap
+# tolerances (labels equal wherever the oracle's label-energy gap
 # exceeds 1e-9 relative; parameters within 1e-10 relative; hood and total
 # energies within 1e-12 relative, i.e. summation order only)
 GAP_TOL = 1e-9
