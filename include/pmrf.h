@@ -330,8 +330,10 @@ PMRF_API int pmrf_map_sweep(pmrf_graph* g, const pmrf_config* cfg, const uint8_t
  *   hood c has converged when t > W and max_{k=1..W} |S_c^t - S_c^{t-k}| <
  *   conv_tol; a slice stops when all its hoods have converged, or t > W and
  *   max_{k=1..W} |T^t - T^{t-k}| < conv_tol, or t = max_iters.
- * All slices run in one persistent launch per iteration; the whole loop is
- * replayed from a CUDA graph.
+ * All slices run in the same launches, one vertex pass and one hood pass per
+ * iteration; a stopped slice's tiles are skipped, and once they are most of
+ * the table the passes take only the active slices' tiles.  The whole loop is
+ * replayed from a CUDA graph (two conditional loops in sequence).
  *   d_labels    u8  [V]        out (in as well when init_from_labels = 1)
  *   d_params    f64 [S][L][4]  out: (n, mu, sigma, U) of the final iteration
  *   d_iters     i32 [S]        out: iterations run per slice

@@ -2,7 +2,8 @@
 // Section 3.2.2 EM steps 2-5), plus the standalone MAP sweep, parameter
 // update, starts (threshold, random) and label image.
 //
-// One EM iteration t is three kernels over a tile table:
+// One EM iteration t is three kernels over a tile table (and the loop's
+// condition setter):
 //   k_vertex<L, VAR> (vertex tiles) -- for every vertex v: the neighbour-label
 //     masks from x^{t-1}; for every replica (hood c containing v) the
 //     disagreement counts m(c,v,l) = #{u in N(v) n H_c : x_u != l} by popcount
@@ -17,25 +18,28 @@
 //     per-tile moment partials of the parameter update.  The VAR instantiation
 //     adds the sweep variants (full-neighbourhood Potts, mean-energy and vote
 //     replica rules).
-//   k_hood<L> (one warp per hood tile) -- for every hood c: S_c = sum over its
-//     members v of Emin(c,v).  Lane i of a warp takes element i of a 32-element
-//     chunk of the tile's element stream (coalesced), gathers its vertex's
-//     record, forms the element energy in integers from the record and the
-//     element's slot mask, and a segmented prefix sum over the lanes (hood ends
-//     flagged in the stream, a carry across chunks) gives each hood's sum at
-//     the lane of its last element.  Hoods with a member of more than 32
-//     neighbours go hood by hood through their hood-local adjacency rows.  The
-//     same lanes run the hood convergence test over the last W sums (ring
-//     buffer) and add the tile's exact partial of T.
+//   k_hood<L> (one block per hood tile) -- for every hood c: S_c = sum over
+//     its members v of Emin(c,v).  The tile's element stream (member id and
+//     slot mask per element) is staged in shared memory by one bulk copy;
+//     adjacent lanes take each hood, gather its members' records and form the
+//     element energies in integers from a record and the element's slot mask.
+//     Hoods with a member of more than 32 neighbours go hood by hood through
+//     their hood-local adjacency rows.  The same lanes run the hood
+//     convergence test over the last W sums (ring buffer) and add the tile's
+//     exact partial of T.
 //   k_finalize<L> (one block per slice) -- label moments -> (n, mu, sigma, U),
 //     the total T^t, the MAP and EM convergence tests, per-slice stop flags,
 //     and the fixed-point unit of the next iteration.
 // Energies of a slice are integers in units 2^-q, q chosen per slice and
 // iteration from a bound on every element energy (slice_unit), so that all
 // sums are exact and independent of order.  Slices that have stopped skip all
-// work.  The loop is captured once into a CUDA graph as one conditional WHILE
-// node whose body is one iteration (the kernels read the iteration number from
-// device memory); it ends once every slice has stopped.
+// work.  The loop is captured once into a CUDA graph as two conditional WHILE
+// nodes in sequence, each body one iteration (the kernels read the iteration
+// number from device memory): the dense loop runs one block per tile while at
+// least a quarter of the tiles belong to slices still iterating, the sparse
+// loop the remaining iterations with blocks that take only those tiles
+// (k_vertex<L, VAR, true>, k_hood<L, true>); it ends once every slice has
+// stopped.
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -400,6 +404,67 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevSta
 }
 
 // ---------------------------------------------------------------------------
+// which tiles a block takes
+//
+// Blocks launched for the tiles of stopped slices return at once, but on 512
+// slices of 1024x1024 they still cost 0.06 ms (vertex pass) and 0.10 ms (hood
+// pass) a pass once most slices have stopped: the rate at which blocks start.
+// The sparse EM loop therefore lists the tiles of the slices still iterating
+// (k_next_iter, after each iteration: cum[s] = the tiles of the active slices
+// before s, cum[S] all of them) and launches one block per resident slot, each
+// block taking the k-th listed tile from a counter until none is left (0.02 ms
+// a pass at the end of the run).  With most tiles active the one-tile blocks
+// are faster (a fully active pass took 0.74 against 0.64 ms, vertex, and 1.09
+// against 0.91 ms, hood, in the listed form: its per-tile claim, binary search
+// and barriers), so the dense loop keeps them.
+struct TileSched {
+    const int32_t* cum;  // [S+1] prefix sums over the active slices' tile counts
+    const int64_t* t0;   // [S+1] first tile of each slice in the table
+    int32_t* next;       // the pass's tile counter (zeroed by k_next_iter)
+    int32_t S;
+};
+
+// the table index of the k-th listed tile: slice s with cum[s] <= k < cum[s+1]
+// (binary search; cum is non-decreasing, cum[0] = 0 <= k < cum[S])
+__device__ __forceinline__ int64_t sched_tile(const TileSched& sc, int k) {
+    int lo = 0, hi = sc.S;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sc.cum[mid] <= k) lo = mid;
+        else hi = mid;
+    }
+    return sc.t0[lo] + (k - sc.cum[lo]);
+}
+
+// run body(tile index) for each tile this block takes; body returns false to
+// stop the block (a staging wait that gave up).  LISTED: the listed tiles of
+// sc, the next one claimed while the current one runs, the barriers between
+// tiles ending every thread's use of the shared buffers before the next tile
+// writes them; otherwise tile blockIdx.x of the table (a separate kernel
+// instance, so that one-tile blocks carry no loop)
+template <bool LISTED, typename Body>
+__device__ __forceinline__ void for_each_tile(const TileSched& sc, int* s_k, Body&& body) {
+    if constexpr (!LISTED) {
+        (void)sc;
+        (void)s_k;
+        body((int64_t)blockIdx.x);
+    } else {
+        if (threadIdx.x == 0) *s_k = atomicAdd(sc.next, 1);
+        __syncthreads();
+        int k = *s_k;
+        while (k < sc.cum[sc.S]) {
+            int kn = 0;
+            if (threadIdx.x == 0) kn = atomicAdd(sc.next, 1);
+            if (!body(sched_tile(sc, k))) return;
+            __syncthreads();
+            if (threadIdx.x == 0) *s_k = kn;
+            __syncthreads();
+            k = *s_k;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
 // vertex pass
 
 // label counts among the neighbours of v in one replica with a multi-word
@@ -731,270 +796,274 @@ __device__ __forceinline__ int vertex_variant(const DevGraph& g, const RunCfg& c
 
 // VAR: the sweep variants of RunCfg (Potts scope, replica rule) read at run
 // time; without it the default (hood scope, least-energy replica) is compiled
-// alone, so the variants cost the default nothing
-template <int L, bool VAR>
+// alone, so the variants cost the default nothing.  LISTED: each block takes
+// listed tiles of sc (the sparse EM loop); otherwise tile blockIdx.x
+template <int L, bool VAR, bool LISTED = false>
 __global__ void __launch_bounds__(VT_THREADS, vt_min_blocks(L)) k_vertex(DevGraph g, const Tile* __restrict__ tiles, int mode,
                                                        const RunCfg* __restrict__ cfgp,
                                                        const int32_t* __restrict__ active,
-                                                       const uint8_t* __restrict__ x_in, uint8_t* __restrict__ x_out,
+                                                       const uint8_t* __restrict__ x_in0, uint8_t* __restrict__ x_out0,
                                                        const double* __restrict__ theta,
                                                        const double* __restrict__ dterm,
                                                        const double* __restrict__ E_in, double* __restrict__ E_out,
                                                        double* __restrict__ vpart, DevStatus* st,
                                                        uint64_t* __restrict__ vrec,
                                                        const SliceUnit* __restrict__ unit,
-                                                       const int32_t* __restrict__ tp) {
+                                                       const int32_t* __restrict__ tp,
+                                                       const TileSched sc) {
     __shared__ double s_mu[L], s_inv[L], s_lnsig[L], s_K[L];
-    // in a loop graph the iteration t comes from device memory: x_in, x_out
-    // are the label buffers of odd t, exchanged for even t
-    if (tp && !(*tp & 1)) {
-        uint8_t* const xi = const_cast<uint8_t*>(x_in);
-        x_in = x_out;
-        x_out = xi;
-    }
     __shared__ double s_Md[33];  // (double)m for m <= 32: no int-to-FP64 conversions on the common path
     __shared__ double s_rcp[VAR ? RCP_N : 1];  // 1 / R for the mean-energy replica rule
     __shared__ double s_vq[3][VT_THREADS];
     __shared__ double s_vc[3 * L][8];
     __shared__ int s_cnt[VT_THREADS / 32][L];
-    const Tile tile = tiles[blockIdx.x];
-    const int s = tile.slice;
-    if (active && !active[s]) return;
-    const RunCfg c = *cfgp;
-    if (threadIdx.x < 33) s_Md[threadIdx.x] = (double)threadIdx.x;
-    if (VAR && threadIdx.x < RCP_N && c.rule == PMRF_RULE_SUM)
-        s_rcp[threadIdx.x] = threadIdx.x > 0 ? 1.0 / (double)threadIdx.x : 0.0;
-    if (threadIdx.x < L) {
-        const int l = threadIdx.x;
-        if (mode == MODE_INIT) {
-            s_K[l] = bin_centre(c, l);
-        } else {
-            const double mu = theta[((int64_t)s * L + l) * 4 + 1];
-            s_mu[l] = mu;
-            s_K[l] = mu;
-            if (dterm) {  // the finaliser's per-slice values (EM loop)
-                s_inv[l] = dterm[((int64_t)s * L + l) * 2 + 0];
-                s_lnsig[l] = dterm[((int64_t)s * L + l) * 2 + 1];
+    __shared__ int s_k;
+    for_each_tile<LISTED>(sc, &s_k, [&](int64_t ti) -> bool {
+        const Tile tile = tiles[ti];
+        const int s = tile.slice;
+        if (active && !active[s]) return true;
+        // in a loop graph the iteration t comes from device memory: x_in,
+        // x_out are the label buffers of odd t, exchanged for even t
+        const bool swap = tp && !(*tp & 1);
+        const uint8_t* __restrict__ x_in = swap ? x_out0 : x_in0;
+        uint8_t* __restrict__ x_out = swap ? const_cast<uint8_t*>(x_in0) : x_out0;
+        const RunCfg c = *cfgp;
+        if (threadIdx.x < 33) s_Md[threadIdx.x] = (double)threadIdx.x;
+        if (VAR && threadIdx.x < RCP_N && c.rule == PMRF_RULE_SUM)
+            s_rcp[threadIdx.x] = threadIdx.x > 0 ? 1.0 / (double)threadIdx.x : 0.0;
+        if (threadIdx.x < L) {
+            const int l = threadIdx.x;
+            if (mode == MODE_INIT) {
+                s_K[l] = bin_centre(c, l);
             } else {
-                const double sg = theta[((int64_t)s * L + l) * 4 + 2];
-                s_inv[l] = inv_two_var(sg);
-                s_lnsig[l] = log(sg);
+                const double mu = theta[((int64_t)s * L + l) * 4 + 1];
+                s_mu[l] = mu;
+                s_K[l] = mu;
+                if (dterm) {  // the finaliser's per-slice values (EM loop)
+                    s_inv[l] = dterm[((int64_t)s * L + l) * 2 + 0];
+                    s_lnsig[l] = dterm[((int64_t)s * L + l) * 2 + 1];
+                } else {
+                    const double sg = theta[((int64_t)s * L + l) * 4 + 2];
+                    s_inv[l] = inv_two_var(sg);
+                    s_lnsig[l] = log(sg);
+                }
             }
         }
-    }
-    __syncthreads();
-    const int64_t v = (int64_t)tile.a0 + threadIdx.x;
-    const bool ok = v < tile.a1;
-    // the slice's fixed-point unit of this iteration (records of the hood pass)
-    const int uq = unit ? unit[s].q : 0;
-    const int64_t ubq = unit ? unit[s].beta_q : 0;
-    int vlab = 0;
-    double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
-    int64_t Eq = 0;                          // EM: E* in the slice's unit (exact sums within the tile)
-    bool have_dev = false;                   // EM/sweep: y - mu_lab and its square already known
-    if (ok) {
-        const double y = g.y[v];
-        int lab = 0;
-        double Estar = 0.0;
-        if (mode == MODE_INIT) {
-            lab = c.init_from_labels ? (int)x_in[v] : threshold_label(c, y);
-            if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
-        } else if (mode == MODE_PARAMS) {
-            lab = (int)x_in[v];
-            if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
-            Estar = E_in ? E_in[v] : 0.0;
-        } else {
-            // a caller's labels (standalone sweep) must lie in [0, L)
-            if (mode == MODE_SWEEP && x_in[v] >= L) record_error(st, PMRF_ERR_ARG, SITE_LABEL, v);
-            // data term D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l
-            double D[L], dev[L], dev2[L];
-#pragma unroll
-            for (int l = 0; l < L; ++l) {
-                dev[l] = y - s_mu[l];
-                dev2[l] = dev[l] * dev[l];
-                D[l] = dev2[l] * s_inv[l] + s_lnsig[l];
-            }
-            const int64_t a0 = g.adj_off[v];
-            const int d = (int)(g.adj_off[v + 1] - a0);
-            const int64_t r0 = g.rep_woff[v], r1 = g.rep_woff[v + 1];
-            int M[L];
-#pragma unroll
-            for (int l = 0; l < L; ++l) M[l] = 0x7fffffff;
-            uint32_t lm[L];  // label masks over v's adjacency slots (degree <= 32; else unused)
-#pragma unroll
-            for (int l = 0; l < L; ++l) lm[l] = 0;
-            if (d <= 32) {
-                for (int j = 0; j < d; ++j) {
-                    const int xl = x_in[g.adj[a0 + j]];
-#pragma unroll
-                    for (int l = 0; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
+        __syncthreads();
+        const int64_t v = (int64_t)tile.a0 + threadIdx.x;
+        const bool ok = v < tile.a1;
+        // the slice's fixed-point unit of this iteration (records of the hood pass)
+        const int uq = unit ? unit[s].q : 0;
+        const int64_t ubq = unit ? unit[s].beta_q : 0;
+        int vlab = 0;
+        double vq0 = 0.0, vq1 = 0.0, vq2 = 0.0;  // y - K_lab, (y - K_lab)^2, E* of this vertex
+        int64_t Eq = 0;                          // EM: E* in the slice's unit (exact sums within the tile)
+        bool have_dev = false;                   // EM/sweep: y - mu_lab and its square already known
+        if (ok) {
+            const double y = g.y[v];
+            int lab = 0;
+            double Estar = 0.0;
+            if (mode == MODE_INIT) {
+                lab = c.init_from_labels ? (int)x_in[v] : threshold_label(c, y);
+                if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
+            } else if (mode == MODE_PARAMS) {
+                lab = (int)x_in[v];
+                if (lab >= L) { record_error(st, PMRF_ERR_ARG, SITE_LABEL, v); lab = L - 1; }
+                Estar = E_in ? E_in[v] : 0.0;
+            } else {
+                // a caller's labels (standalone sweep) must lie in [0, L)
+                if (mode == MODE_SWEEP && x_in[v] >= L) record_error(st, PMRF_ERR_ARG, SITE_LABEL, v);
+                // data term D_l(y) = (y - mu_l)^2 / (2 sigma_l^2) + ln sigma_l
+                double D[L], dev[L], dev2[L];
+    #pragma unroll
+                for (int l = 0; l < L; ++l) {
+                    dev[l] = y - s_mu[l];
+                    dev2[l] = dev[l] * dev[l];
+                    D[l] = dev2[l] * s_inv[l] + s_lnsig[l];
                 }
-            }
-            if (!VAR || (c.scope == PMRF_SCOPE_HOOD && c.rule == PMRF_RULE_MIN)) {
+                const int64_t a0 = g.adj_off[v];
+                const int d = (int)(g.adj_off[v + 1] - a0);
+                const int64_t r0 = g.rep_woff[v], r1 = g.rep_woff[v + 1];
+                int M[L];
+    #pragma unroll
+                for (int l = 0; l < L; ++l) M[l] = 0x7fffffff;
+                uint32_t lm[L];  // label masks over v's adjacency slots (degree <= 32; else unused)
+    #pragma unroll
+                for (int l = 0; l < L; ++l) lm[l] = 0;
                 if (d <= 32) {
-                    // neighbours in the hood whose label is not l, minimised over
-                    // the replicas; the masks are read four at a time once the
-                    // address is 16-byte aligned (fewer load requests per warp)
-                    for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
-                        const int dc = __popc(m);
-#pragma unroll
-                        for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - __popc(m & lm[l]));
-                    });
-                } else {
-                    const int nw = (d + 31) >> 5;
-                    for (int64_t r = r0; r < r1; r += nw) {
-                        int cnt[L];
-                        const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
-#pragma unroll
-                        for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - cnt[l]);
+                    for (int j = 0; j < d; ++j) {
+                        const int xl = x_in[g.adj[a0 + j]];
+    #pragma unroll
+                        for (int l = 0; l < L; ++l) lm[l] |= (xl == l ? 1u : 0u) << j;
                     }
                 }
-                // the hood pass of this iteration reads v's data terms and label masks
-                // every vertex lies in at least one hood, so M_l is set (and
-                // <= 32 when d <= 32).  The data terms in the slice's unit serve
-                // the hood pass's record.  The label is the least D_l + beta M_l
-                // in FP64 (ties to the lower label), the precision the oracle
-                // decides in.  The exact energies in the unit give the same
-                // label whenever the least one leads every other by more than
-                // both evaluations' rounding can move them (fixed point: half a
-                // unit per rounded term, so 1/2 + M/2; FP64: 2^-52 of the
-                // magnitude plus one unit; taken generously below); only closer
-                // labels are compared in FP64.  The label's energy in the unit
-                // enters the tile's exact sum of E*
-                int64_t F[L], e[L];
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    F[l] = to_fixed(D[l], uq);
-                    e[l] = F[l] + ubq * (int64_t)M[l];
+                if (!VAR || (c.scope == PMRF_SCOPE_HOOD && c.rule == PMRF_RULE_MIN)) {
+                    if (d <= 32) {
+                        // neighbours in the hood whose label is not l, minimised over
+                        // the replicas; the masks are read four at a time once the
+                        // address is 16-byte aligned (fewer load requests per warp)
+                        for_each_mask(g.rep_mask, r0, r1, [&](uint32_t m) {
+                            const int dc = __popc(m);
+    #pragma unroll
+                            for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - __popc(m & lm[l]));
+                        });
+                    } else {
+                        const int nw = (d + 31) >> 5;
+                        for (int64_t r = r0; r < r1; r += nw) {
+                            int cnt[L];
+                            const int dc = slot_label_counts<L>(g, x_in, a0, r, nw, cnt);
+    #pragma unroll
+                            for (int l = 0; l < L; ++l) M[l] = min(M[l], dc - cnt[l]);
+                        }
+                    }
+                    // the hood pass of this iteration reads v's data terms and label masks
+                    // every vertex lies in at least one hood, so M_l is set (and
+                    // <= 32 when d <= 32).  The data terms in the slice's unit serve
+                    // the hood pass's record.  The label is the least D_l + beta M_l
+                    // in FP64 (ties to the lower label), the precision the oracle
+                    // decides in.  The exact energies in the unit give the same
+                    // label whenever the least one leads every other by more than
+                    // both evaluations' rounding can move them (fixed point: half a
+                    // unit per rounded term, so 1/2 + M/2; FP64: 2^-52 of the
+                    // magnitude plus one unit; taken generously below); only closer
+                    // labels are compared in FP64.  The label's energy in the unit
+                    // enters the tile's exact sum of E*
+                    int64_t F[L], e[L];
+    #pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        F[l] = to_fixed(D[l], uq);
+                        e[l] = F[l] + ubq * (int64_t)M[l];
+                    }
+                    if (vrec) write_vrec_fixed<L>(vrec, g.V, v, F, lm);
+                    int64_t eb = e[0];
+                    lab = 0;
+    #pragma unroll
+                    for (int l = 1; l < L; ++l)
+                        if (e[l] < eb) { eb = e[l]; lab = l; }
+                    uint64_t mag_b = 0;
+                    int m_b = 0;
+    #pragma unroll
+                    for (int l = 0; l < L; ++l)
+                        if (l == lab) {
+                            mag_b = (uint64_t)(F[l] < 0 ? -F[l] : F[l]) + (uint64_t)ubq * (uint64_t)M[l];
+                            m_b = M[l];
+                        }
+                    bool sure = true;
+    #pragma unroll
+                    for (int l = 0; l < L; ++l) {
+                        const uint64_t mag = (uint64_t)(F[l] < 0 ? -F[l] : F[l]) + (uint64_t)ubq * (uint64_t)M[l];
+                        const int64_t eps = 4 + M[l] + m_b + (int64_t)((mag + mag_b) >> 50);
+                        if (l != lab && e[l] - eb <= eps) sure = false;
+                    }
+                    if (!sure) {
+                        double best = D[0] + c.beta * (d <= 32 ? s_Md[M[0]] : (double)M[0]);
+                        lab = 0;
+    #pragma unroll
+                        for (int l = 1; l < L; ++l) {
+                            const double x = D[l] + c.beta * (d <= 32 ? s_Md[M[l]] : (double)M[l]);
+                            if (x < best) { best = x; lab = l; }
+                        }
+                    }
+    #pragma unroll
+                    for (int l = 0; l < L; ++l)
+                        if (l == lab) Eq = e[l];
+                    if (E_out) {  // the chosen label's energy in FP64 (standalone sweep)
+    #pragma unroll
+                        for (int l = 0; l < L; ++l)
+                            if (l == lab) Estar = D[l] + c.beta * (d <= 32 ? s_Md[M[l]] : (double)M[l]);
+                    }
+                } else {
+                    lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar, s_rcp, uq, ubq);
+                    Eq = to_fixed(Estar, uq);
                 }
-                if (vrec) write_vrec_fixed<L>(vrec, g.V, v, F, lm);
-                int64_t eb = e[0];
-                lab = 0;
-#pragma unroll
-                for (int l = 1; l < L; ++l)
-                    if (e[l] < eb) { eb = e[l]; lab = l; }
-                uint64_t mag_b = 0;
-                int m_b = 0;
-#pragma unroll
+                x_out[v] = (uint8_t)lab;
+                if (E_out) E_out[v] = Estar;
+                // K = mu here: the moments reuse y - mu_lab and its square
+    #pragma unroll
                 for (int l = 0; l < L; ++l)
                     if (l == lab) {
-                        mag_b = (uint64_t)(F[l] < 0 ? -F[l] : F[l]) + (uint64_t)ubq * (uint64_t)M[l];
-                        m_b = M[l];
+                        vq0 = dev[l];
+                        vq1 = dev2[l];
                     }
-                bool sure = true;
-#pragma unroll
-                for (int l = 0; l < L; ++l) {
-                    const uint64_t mag = (uint64_t)(F[l] < 0 ? -F[l] : F[l]) + (uint64_t)ubq * (uint64_t)M[l];
-                    const int64_t eps = 4 + M[l] + m_b + (int64_t)((mag + mag_b) >> 50);
-                    if (l != lab && e[l] - eb <= eps) sure = false;
+                have_dev = true;
+            }
+            if (mode == MODE_INIT) x_out[v] = (uint8_t)lab;
+            if (mode != MODE_SWEEP) {
+                if (!have_dev) {
+                    const double dv = y - s_K[lab];
+                    vq0 = dv;
+                    vq1 = dv * dv;
                 }
-                if (!sure) {
-                    double best = D[0] + c.beta * (d <= 32 ? s_Md[M[0]] : (double)M[0]);
-                    lab = 0;
-#pragma unroll
-                    for (int l = 1; l < L; ++l) {
-                        const double x = D[l] + c.beta * (d <= 32 ? s_Md[M[l]] : (double)M[l]);
-                        if (x < best) { best = x; lab = l; }
-                    }
+                vlab = lab;
+                vq2 = mode == MODE_EM ? __longlong_as_double(Eq) : Estar;
+            }
+        }
+        if (mode == MODE_SWEEP) return true;
+        // deterministic per-label sums of the tile: each vertex contributes to the
+        // label it carries (no shuffle trees: the FP64 pipe is the scarce unit).
+        // Label counts of the tile by warp ballots; each vertex's place in its
+        // label's run (tile order kept) so the sums below add only that label's
+        // values
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        unsigned mine = 0u;
+    #pragma unroll
+        for (int l = 0; l < L; ++l) {
+            const unsigned b = __ballot_sync(0xffffffffu, ok && vlab == l);
+            if (lane == 0) s_cnt[warp][l] = __popc(b);
+            if (ok && vlab == l) mine = b;
+        }
+        __syncthreads();
+        if (ok) {
+            int pos = __popc(mine & ((1u << lane) - 1u));
+            for (int l = 0; l < vlab; ++l)
+                for (int w = 0; w < VT_THREADS / 32; ++w) pos += s_cnt[w][l];
+            for (int w = 0; w < warp; ++w) pos += s_cnt[w][vlab];
+            s_vq[0][pos] = vq0;
+            s_vq[1][pos] = vq1;
+            s_vq[2][pos] = vq2;
+        }
+        __syncthreads();
+        // 8 threads per (label, quantity) add fixed consecutive chunks of the
+        // label's run in order, then one thread adds the 8 results in order
+        for (int job = threadIdx.x; job < 3 * L * 8; job += VT_THREADS) {  // two jobs a thread when L > 5
+            const int lq = job >> 3, k = job & 7;
+            const int l = lq / 3, q = lq % 3;
+            int base = 0, n = 0;
+            for (int m = 0; m < L; ++m)
+                for (int w = 0; w < VT_THREADS / 32; ++w) {
+                    const int cw = s_cnt[w][m];
+                    if (m < l) base += cw;
+                    if (m == l) n += cw;
                 }
-#pragma unroll
-                for (int l = 0; l < L; ++l)
-                    if (l == lab) Eq = e[l];
-                if (E_out) {  // the chosen label's energy in FP64 (standalone sweep)
-#pragma unroll
-                    for (int l = 0; l < L; ++l)
-                        if (l == lab) Estar = D[l] + c.beta * (d <= 32 ? s_Md[M[l]] : (double)M[l]);
-                }
+            const int lo = base + (k * n) / 8, hi = base + ((k + 1) * n) / 8;
+            if (q == 2 && mode == MODE_EM) {
+                // E* in the slice's unit: an exact integer sum (|E*| < 2^62 / 128)
+                int64_t a = 0;
+                for (int i = lo; i < hi; ++i) a += __double_as_longlong(s_vq[q][i]);
+                s_vc[lq][k] = __longlong_as_double(a);
             } else {
-                lab = vertex_variant<L>(g, c, x_in, a0, d, r0, r1, lm, D, vrec, v, Estar, s_rcp, uq, ubq);
-                Eq = to_fixed(Estar, uq);
+                double a = 0.0;
+                for (int i = lo; i < hi; ++i) a += s_vq[q][i];
+                s_vc[lq][k] = a;
             }
-            x_out[v] = (uint8_t)lab;
-            if (E_out) E_out[v] = Estar;
-            // K = mu here: the moments reuse y - mu_lab and its square
-#pragma unroll
-            for (int l = 0; l < L; ++l)
-                if (l == lab) {
-                    vq0 = dev[l];
-                    vq1 = dev2[l];
-                }
-            have_dev = true;
+            if (q == 0 && k == 0) vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
         }
-        if (mode == MODE_INIT) x_out[v] = (uint8_t)lab;
-        if (mode != MODE_SWEEP) {
-            if (!have_dev) {
-                const double dv = y - s_K[lab];
-                vq0 = dv;
-                vq1 = dv * dv;
-            }
-            vlab = lab;
-            vq2 = mode == MODE_EM ? __longlong_as_double(Eq) : Estar;
-        }
-    }
-    if (mode == MODE_SWEEP) return;
-    // deterministic per-label sums of the tile: each vertex contributes to the
-    // label it carries (no shuffle trees: the FP64 pipe is the scarce unit).
-    // Label counts of the tile by warp ballots; each vertex's place in its
-    // label's run (tile order kept) so the sums below add only that label's
-    // values
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned mine = 0u;
-#pragma unroll
-    for (int l = 0; l < L; ++l) {
-        const unsigned b = __ballot_sync(0xffffffffu, ok && vlab == l);
-        if (lane == 0) s_cnt[warp][l] = __popc(b);
-        if (ok && vlab == l) mine = b;
-    }
-    __syncthreads();
-    if (ok) {
-        int pos = __popc(mine & ((1u << lane) - 1u));
-        for (int l = 0; l < vlab; ++l)
-            for (int w = 0; w < VT_THREADS / 32; ++w) pos += s_cnt[w][l];
-        for (int w = 0; w < warp; ++w) pos += s_cnt[w][vlab];
-        s_vq[0][pos] = vq0;
-        s_vq[1][pos] = vq1;
-        s_vq[2][pos] = vq2;
-    }
-    __syncthreads();
-    // 8 threads per (label, quantity) add fixed consecutive chunks of the
-    // label's run in order, then one thread adds the 8 results in order
-    for (int job = threadIdx.x; job < 3 * L * 8; job += VT_THREADS) {  // two jobs a thread when L > 5
-        const int lq = job >> 3, k = job & 7;
-        const int l = lq / 3, q = lq % 3;
-        int base = 0, n = 0;
-        for (int m = 0; m < L; ++m)
-            for (int w = 0; w < VT_THREADS / 32; ++w) {
-                const int cw = s_cnt[w][m];
-                if (m < l) base += cw;
-                if (m == l) n += cw;
-            }
-        const int lo = base + (k * n) / 8, hi = base + ((k + 1) * n) / 8;
-        if (q == 2 && mode == MODE_EM) {
-            // E* in the slice's unit: an exact integer sum (|E*| < 2^62 / 128)
-            int64_t a = 0;
-            for (int i = lo; i < hi; ++i) a += __double_as_longlong(s_vq[q][i]);
-            s_vc[lq][k] = __longlong_as_double(a);
-        } else {
+        __syncthreads();
+        if (threadIdx.x < 3 * L) {
+            const int l = threadIdx.x / 3, q = threadIdx.x % 3;
             double a = 0.0;
-            for (int i = lo; i < hi; ++i) a += s_vq[q][i];
-            s_vc[lq][k] = a;
+            if (q == 2 && mode == MODE_EM) {
+                // the tile's exact sum of E*, rounded to double once
+                int64_t ai = 0;
+                for (int w = 0; w < 8; ++w) ai += __double_as_longlong(s_vc[threadIdx.x][w]);
+                a = from_fixed64(ai, uq);
+            } else {
+                for (int w = 0; w < 8; ++w) a += s_vc[threadIdx.x][w];
+            }
+            vpart[(int64_t)tile.part * 4 * L + 4 * l + 1 + q] = a;
         }
-        if (q == 0 && k == 0) vpart[(int64_t)tile.part * 4 * L + 4 * l + 0] = (double)n;
-    }
-    __syncthreads();
-    if (threadIdx.x < 3 * L) {
-        const int l = threadIdx.x / 3, q = threadIdx.x % 3;
-        double a = 0.0;
-        if (q == 2 && mode == MODE_EM) {
-            // the tile's exact sum of E*, rounded to double once
-            int64_t ai = 0;
-            for (int w = 0; w < 8; ++w) ai += __double_as_longlong(s_vc[threadIdx.x][w]);
-            a = from_fixed64(ai, uq);
-        } else {
-            for (int w = 0; w < 8; ++w) a += s_vc[threadIdx.x][w];
-        }
-        vpart[(int64_t)tile.part * 4 * L + 4 * l + 1 + q] = a;
-    }
+        return true;
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -1264,7 +1333,7 @@ __device__ __forceinline__ void general_tile(const DevGraph& g, const RunCfg& cf
 // mbarrier), then lanes-per-hood adjacent lanes take each hood, gather its
 // members' records and sum the element energies.
 // General tiles go hood by hood through the hood-local adjacency rows.
-template <int L>
+template <int L, bool LISTED = false>
 __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph g, const Tile* __restrict__ tiles,
                                                      int mode, int t, int lanes,
                                                      const RunCfg* __restrict__ cfgp,
@@ -1276,7 +1345,8 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
                                                      int64_t* __restrict__ hist, double* __restrict__ S_out,
                                                      int64_t* __restrict__ hpart, int cap, DevStatus* st,
                                                      const uint8_t* __restrict__ x_alt,
-                                                     const int32_t* __restrict__ tp) {
+                                                     const int32_t* __restrict__ tp,
+                                                     const TileSched sc) {
     // in a loop graph t comes from device memory and x_alt holds the labels
     // that even iterations read
     if (tp) {
@@ -1290,54 +1360,70 @@ __global__ void __launch_bounds__(HT_THREADS, ht_min_blocks(L)) k_hood(DevGraph 
     __shared__ int64_t s_wsum[HT_THREADS / 32];
     __shared__ __int128 s_wT[HT_THREADS / 32];
     __shared__ int s_wu[HT_THREADS / 32];
-    const Tile tile = tiles[blockIdx.x];
-    const int s = tile.slice;
-    if (active && !active[s]) return;
-    const RunCfg cf = *cfgp;
-    const SliceUnit u = unit[s];
-    const int W = cf.W;
-    const int32_t* qh = qhist ? qhist + (int64_t)s * W : nullptr;
-    TileAcc acc;
-    auto hood_done = [&](int64_t c, int64_t S) {
-        if (mode == MODE_SWEEP) {
-            if (S_out) S_out[c] = from_fixed((__int128)S, u.q);
-        } else {
-            acc.unconv += hood_history(S, c, g.C, t, W, u, qh, cf.tol, hist);
-            acc.T += S;
-        }
-    };
-    const int64_t c0 = tile.a0, c1 = tile.a1;
-    if (c1 > c0) {
-        const int64_t e0 = g.hood_off[c0];
-        const int ne = (int)(g.hood_off[c1] - e0);
-        if (tile.pad != 0) {
-            auto energy = [&](uint32_t vid, uint32_t m) { return element_energy<L>(vrec, g.V, vid, m, u.beta_q); };
-            if (ne <= cap) {
-                const int64_t ea = e0 & ~1ll, eb = (e0 + ne + 1) & ~1ll;  // 16-byte aligned bounds
-                if (threadIdx.x == 0) {
-                    mbar_init(&s_bar);
-                    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-                    const uint32_t bytes = (uint32_t)((eb - ea) * 8);
-                    mbar_expect(&s_bar, bytes);
-                    bulk_copy(s_el, g.el + ea, bytes, &s_bar);
-                }
-                __syncthreads();  // the barrier is initialised before anyone polls it
-                // a wait that gives up has set the status word; it waits once
-                // more (bounded) so that no copy is left in flight, and the
-                // tile's sums are left out
-                // (the same decision in every thread: lanes of a hood shuffle together)
-                if (__syncthreads_and(mbar_wait(&s_bar, 0, st) || mbar_wait(&s_bar, 0, st)))
-                    fast_hoods_p(lanes, g, c0, c1, e0, s_el + (e0 - ea), energy, hood_done);
+    __shared__ int s_k;
+    // the staging barrier, initialised by the block's first staged tile: each
+    // staged tile completes one phase of it (parity ph)
+    bool bar_ready = false;
+    uint32_t ph = 0;
+    for_each_tile<LISTED>(sc, &s_k, [&](int64_t ti) -> bool {
+        const Tile tile = tiles[ti];
+        const int s = tile.slice;
+        if (active && !active[s]) return true;
+        const RunCfg cf = *cfgp;
+        const SliceUnit u = unit[s];
+        const int W = cf.W;
+        const int32_t* qh = qhist ? qhist + (int64_t)s * W : nullptr;
+        TileAcc acc;
+        auto hood_done = [&](int64_t c, int64_t S) {
+            if (mode == MODE_SWEEP) {
+                if (S_out) S_out[c] = from_fixed((__int128)S, u.q);
             } else {
-                // a tile whose last hood reaches far past its window (very large
-                // hoods): the element stream is read where it lies
-                fast_hoods<8>(g, c0, c1, e0, g.el + e0, energy, hood_done);
+                acc.unconv += hood_history(S, c, g.C, t, W, u, qh, cf.tol, hist);
+                acc.T += S;
             }
-        } else {
-            general_tile<L>(g, cf, c0, c1, x_in, vrec, u.beta_q, s_wsum, hood_done);
+        };
+        const int64_t c0 = tile.a0, c1 = tile.a1;
+        if (c1 > c0) {
+            const int64_t e0 = g.hood_off[c0];
+            const int ne = (int)(g.hood_off[c1] - e0);
+            if (tile.pad != 0) {
+                auto energy = [&](uint32_t vid, uint32_t m) { return element_energy<L>(vrec, g.V, vid, m, u.beta_q); };
+                if (ne <= cap) {
+                    const int64_t ea = e0 & ~1ll, eb = (e0 + ne + 1) & ~1ll;  // 16-byte aligned bounds
+                    if (!bar_ready) {  // (the same in every thread)
+                        if (threadIdx.x == 0) {
+                            mbar_init(&s_bar);
+                            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+                        }
+                        __syncthreads();  // initialised before anyone polls it
+                        bar_ready = true;
+                    }
+                    if (threadIdx.x == 0) {
+                        const uint32_t bytes = (uint32_t)((eb - ea) * 8);
+                        mbar_expect(&s_bar, bytes);
+                        bulk_copy(s_el, g.el + ea, bytes, &s_bar);
+                    }
+                    // a wait that gives up has set the status word; it waits
+                    // once more (bounded) so that no copy is left in flight,
+                    // and the block stops: the barrier's phase is unknown
+                    // (the same decision in every thread: lanes of a hood
+                    // shuffle together)
+                    const bool staged = __syncthreads_and(mbar_wait(&s_bar, ph, st) || mbar_wait(&s_bar, ph, st));
+                    ph ^= 1u;
+                    if (!staged) return false;
+                    fast_hoods_p(lanes, g, c0, c1, e0, s_el + (e0 - ea), energy, hood_done);
+                } else {
+                    // a tile whose last hood reaches far past its window (very
+                    // large hoods): the element stream is read where it lies
+                    fast_hoods<8>(g, c0, c1, e0, g.el + e0, energy, hood_done);
+                }
+            } else {
+                general_tile<L>(g, cf, c0, c1, x_in, vrec, u.beta_q, s_wsum, hood_done);
+            }
         }
-    }
-    if (mode != MODE_SWEEP) tile_partials(acc, tile.part, hpart, s_wT, s_wu);
+        if (mode != MODE_SWEEP) tile_partials(acc, tile.part, hpart, s_wT, s_wu);
+        return true;
+    });
 }
 
 // ---------------------------------------------------------------------------
@@ -1690,7 +1776,7 @@ int free_em(pmrf_graph* g) {
     EMWork& w = g->em;
     void* ps[] = {w.d_x[0], w.d_x[1], w.d_hist, w.d_qhist, w.d_unit, w.d_yr, w.d_vpart, w.d_hpart, w.d_theta,
                   w.d_dterm, w.d_Thist, w.d_vrec,
-                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_t, w.d_cfg};
+                  w.d_active, w.d_iters, w.d_conv, w.d_nactive, w.d_t, w.d_sched, w.d_cfg};
     for (void* p : ps)
         if (p) cudaFreeAsync(p, 0);
     g->em = EMWork();
@@ -1877,6 +1963,7 @@ int ensure_work(pmrf_graph* g, const RunCfg& rc, const Plan& p, cudaStream_t s) 
     if (!rc2) rc2 = dalloc(&w.d_conv, S, s);
     if (!rc2) rc2 = dalloc(&w.d_nactive, 1, s);
     if (!rc2) rc2 = dalloc(&w.d_t, 1, s);
+    if (!rc2) rc2 = dalloc(&w.d_sched, 2 * (S + 1) + 2, s);
     if (!rc2) rc2 = dalloc(&w.d_qhist, S * rc.W, s);
     if (!rc2) rc2 = dalloc((char**)&w.d_unit, (int64_t)sizeof(SliceUnit) * std::max<int64_t>(S, 1), s);
     if (!rc2) rc2 = dalloc(&w.d_yr, 2 * S, s);
@@ -1910,28 +1997,102 @@ namespace {
 
 __global__ void k_set_i32(int32_t* p, int32_t v) { *p = v; }
 
-// condition of the loop graph's next iteration: run iteration t + 1 while a
-// slice is still active and t < max_iters, t being t0 (>= 0: after the initial
-// pass) or the iteration just run (*tp); advances *tp and adds the kernels the
-// body will run to the device-side launch counter
-__global__ void k_next_iter(cudaGraphConditionalHandle h, const int32_t* __restrict__ nactive,
-                            int32_t* __restrict__ tp, int t0, int max_iters,
-                            unsigned long long* __restrict__ counter, unsigned int body_kernels) {
-    const int t = t0 >= 0 ? t0 : *tp;
-    const unsigned int run = (*nactive > 0 && t < max_iters) ? 1u : 0u;
-    if (run) {
-        *tp = t + 1;
-        atomicAdd(counter, (unsigned long long)body_kernels);
+// The condition setter of the loop graph's two WHILE loops, run after the INIT
+// pass (t0 = 0), at the end of each iteration and between the loops (t0 < 0:
+// t = *tp, the iteration just run).  It lists the tiles of the slices still
+// iterating (the cum arrays of TileSched: vertex and hood tiles) and zeroes the
+// passes' tile counters for the next iteration, then lets iteration t + 1 run
+// while a slice is still active and t < max_iters; in the dense loop
+// (dense_only) only while the listed tiles are at least a quarter of the table.
+// It stores the next iteration in *tp (t when none runs) and adds the kernels
+// the body will run to the device-side launch counter.  One block of
+// NX_THREADS.
+constexpr int NX_THREADS = 1024;
+
+__global__ void __launch_bounds__(NX_THREADS) k_next_iter(cudaGraphConditionalHandle h, int dense_only,
+                                                          const int32_t* __restrict__ nactive,
+                                                          int32_t* __restrict__ tp, int t0, int max_iters,
+                                                          unsigned long long* __restrict__ counter,
+                                                          unsigned int body_kernels, int32_t S,
+                                                          const int32_t* __restrict__ active,
+                                                          const int64_t* __restrict__ vt0,
+                                                          const int64_t* __restrict__ ht0,
+                                                          int32_t* __restrict__ sched, int64_t n_tiles) {
+    __shared__ int2 s_w[NX_THREADS / 32];
+    __shared__ int2 s_carry;
+    int32_t* const vcum = sched;
+    int32_t* const hcum = sched + (S + 1);
+    if (threadIdx.x == 0) s_carry = make_int2(0, 0);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int base = 0; base < S; base += NX_THREADS) {
+        const int i = base + threadIdx.x;
+        int2 n = make_int2(0, 0);
+        if (i < S && active[i]) n = make_int2((int)(vt0[i + 1] - vt0[i]), (int)(ht0[i + 1] - ht0[i]));
+        // inclusive scan within the warp, then over the warps
+        int2 x = n;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int yv = __shfl_up_sync(0xffffffffu, x.x, o), yh = __shfl_up_sync(0xffffffffu, x.y, o);
+            if (lane >= o) {
+                x.x += yv;
+                x.y += yh;
+            }
+        }
+        if (lane == 31) s_w[warp] = x;
+        __syncthreads();
+        int2 off = s_carry;
+        for (int w = 0; w < warp; ++w) {
+            off.x += s_w[w].x;
+            off.y += s_w[w].y;
+        }
+        if (i < S) {
+            vcum[i] = off.x + x.x - n.x;
+            hcum[i] = off.y + x.y - n.y;
+        }
+        __syncthreads();  // every thread has read s_carry and s_w
+        if (threadIdx.x == NX_THREADS - 1) s_carry = make_int2(off.x + x.x, off.y + x.y);
+        __syncthreads();
     }
-    cudaGraphSetConditional(h, run);
+    if (threadIdx.x == 0) {
+        vcum[S] = s_carry.x;
+        hcum[S] = s_carry.y;
+        sched[2 * (S + 1)] = 0;      // vertex-pass tile counter
+        sched[2 * (S + 1) + 1] = 0;  // hood-pass tile counter
+        const int t = t0 >= 0 ? t0 : *tp;
+        const bool dense = 4 * ((int64_t)s_carry.x + s_carry.y) >= n_tiles;
+        const unsigned int run = (*nactive > 0 && t < max_iters && (dense || !dense_only)) ? 1u : 0u;
+        *tp = run ? t + 1 : t;
+        if (run) atomicAdd(counter, (unsigned long long)body_kernels);
+        cudaGraphSetConditional(h, run);
+    }
 }
 
-// state of a capture that runs the EM iterations as the body of one
-// conditional WHILE node
+// the schedules of an EM iteration's passes (TileSched)
+TileSched vertex_sched(const EMWork& w, const Plan* p, int32_t S) {
+    return TileSched{w.d_sched, p->d_slice_vt0, w.d_sched + 2 * (S + 1), S};
+}
+TileSched hood_sched(const EMWork& w, const Plan* p, int32_t S) {
+    return TileSched{w.d_sched + (S + 1), p->d_slice_ht0, w.d_sched + 2 * (S + 1) + 1, S};
+}
+
+// blocks of a pass that takes listed tiles: one per resident slot of the
+// device (fewer when the table has fewer tiles)
+unsigned sched_grid(const void* fn, int threads, size_t smem, int64_t n_tiles) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem);
+    const int64_t slots = (int64_t)std::max(sms, 1) * std::max(per_sm, 1);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(n_tiles, slots));
+}
+
+// state of a capture that runs the EM iterations as the bodies of two
+// conditional WHILE nodes in sequence (dense loop, sparse loop)
 struct CondCapture {
-    cudaStream_t body_stream = nullptr;      // captures the body
+    cudaStream_t body_stream = nullptr;      // captures a body
     unsigned long long* counter = nullptr;   // device-side launch counter
-    cudaGraphConditionalHandle h = 0;        // the loop's condition
+    cudaGraphConditionalHandle h[2] = {0, 0};  // the loops' conditions
     int64_t* parent_nodes = nullptr;         // kernels outside the body
     int64_t body_nodes = 0;                  // counted on the device instead
 };
@@ -1943,9 +2104,9 @@ __global__ void k_set_active_all(int32_t* a, int32_t S) {
 // kernels one EM iteration body launches (its condition setter included)
 int iter_kernels(const Plan* p) { return (p->n_vtiles > 0) + (p->n_htiles > 0) + 2; }
 
-// open the loop's WHILE node on the capturing stream s and start capturing
-// its body on cc->body_stream
-int open_while_body(CondCapture* cc, cudaStream_t s) {
+// open a WHILE node with condition h on the capturing stream s and start
+// capturing its body on cc->body_stream
+int open_while_body(CondCapture* cc, cudaStream_t s, cudaGraphConditionalHandle h) {
     cudaStreamCaptureStatus st;
     cudaGraph_t pg = nullptr;
     const cudaGraphNode_t* deps = nullptr;
@@ -1956,7 +2117,7 @@ int open_while_body(CondCapture* cc, cudaStream_t s) {
     cudaGraphNodeParams np = {cudaGraphNodeTypeConditional};
     std::memset(&np, 0, sizeof(np));  // reserved fields must be zero
     np.type = cudaGraphNodeTypeConditional;
-    np.conditional.handle = cc->h;
+    np.conditional.handle = h;
     np.conditional.type = cudaGraphCondTypeWhile;
     np.conditional.size = 1;
     cudaGraphNode_t node;
@@ -1987,7 +2148,7 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
         k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_INIT, z.d_cfg, nullptr,
                                                                 w.d_x[1], w.d_x[0], nullptr, nullptr, nullptr,
                                                                 nullptr, w.d_vpart, g->d_status, nullptr, nullptr,
-                                                                nullptr);
+                                                                nullptr, TileSched{});
         ::pmrf::note_launch(1);
     }
     SliceUnit* unit = (SliceUnit*)w.d_unit;
@@ -1997,43 +2158,65 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
                                             w.d_yr, g->max_deg, g->max_hood, g->d_status, nullptr);
     ::pmrf::note_launch(1);
     const auto kv = is_variant(rc) ? &k_vertex<L, true> : &k_vertex<L, false>;
+    const auto kvl = is_variant(rc) ? &k_vertex<L, true, true> : &k_vertex<L, false, true>;
     if (cc) {
-        // one WHILE node whose body is one iteration; the kernels read t from
-        // w.d_t, which the condition setter at the end of each body advances
+        // two WHILE nodes in sequence, each body one iteration; the kernels
+        // read t from w.d_t, which the condition setter at the end of each
+        // body advances.  The dense loop launches one block per tile of the
+        // table (blocks of stopped slices return at once) while at least a
+        // quarter of the tiles belong to slices still iterating; the sparse
+        // loop runs the remaining iterations with one block per resident slot,
+        // the blocks taking only those tiles.  Slices only ever stop, so the
+        // sparse loop never has to hand back.
         const unsigned body = (unsigned)iter_kernels(p);
-        k_next_iter<<<1, 1, 0, s>>>(cc->h, w.d_nactive, w.d_t, 0, rc.max_iters, cc->counter, body);
-        ::pmrf::note_launch(1);
+        const unsigned gv = sched_grid((const void*)kvl, VT_THREADS, 0, p->n_vtiles);
+        const unsigned gh = sched_grid((const void*)&k_hood<L, true>, HT_THREADS, hood_smem(p), p->n_htiles);
         const cudaStream_t s0 = s;
-        PMRF_TRY(open_while_body(cc, s0));
-        s = cc->body_stream;
-        set_capture_counter(&cc->body_nodes);
-        if (p->n_vtiles > 0) {
-            kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, w.d_x[0],
-                                                            w.d_x[1], w.d_theta, w.d_dterm, nullptr, nullptr,
-                                                            w.d_vpart, g->d_status, w.d_vrec, unit, w.d_t);
+        for (int sparse = 0; sparse < 2; ++sparse) {
+            const cudaGraphConditionalHandle h = cc->h[sparse];
+            auto next_iter = [&](cudaStream_t st, int t0) {
+                k_next_iter<<<1, NX_THREADS, 0, st>>>(h, sparse ? 0 : 1, w.d_nactive, w.d_t, t0, rc.max_iters,
+                                                      cc->counter, body, S, w.d_active, p->d_slice_vt0,
+                                                      p->d_slice_ht0, w.d_sched, p->n_tiles);
+                ::pmrf::note_launch(1);
+            };
+            next_iter(s0, sparse ? -1 : 0);
+            PMRF_TRY(open_while_body(cc, s0, h));
+            s = cc->body_stream;
+            set_capture_counter(&cc->body_nodes);
+            if (p->n_vtiles > 0) {
+                (sparse ? kvl : kv)<<<sparse ? gv : (unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(
+                    z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, w.d_x[0], w.d_x[1], w.d_theta, w.d_dterm, nullptr,
+                    nullptr, w.d_vpart, g->d_status, w.d_vrec, unit, w.d_t,
+                    sparse ? vertex_sched(w, p, S) : TileSched{});
+                ::pmrf::note_launch(1);
+            }
+            if (p->n_htiles > 0) {
+                (sparse ? &k_hood<L, true> : &k_hood<L>)<<<sparse ? gh : (unsigned)p->n_htiles, HT_THREADS,
+                                                           hood_smem(p), s>>>(
+                    z.dg, z.ht, MODE_EM, 0, p->hood_lanes, z.d_cfg, w.d_active, w.d_x[0], w.d_vrec, unit,
+                    w.d_qhist, w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status, w.d_x[1], w.d_t,
+                    sparse ? hood_sched(w, p, S) : TileSched{});
+                ::pmrf::note_launch(1);
+            }
+            k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, 0, z.d_cfg, p->d_slice_vt0,
+                                                              p->d_slice_ht0, w.d_vpart, w.d_hpart, w.d_theta,
+                                                              w.d_theta, g->d_vert_off, w.d_active, w.d_iters,
+                                                              w.d_conv, w.d_Thist, w.d_nactive, z.d_out, w.d_dterm,
+                                                              unit, w.d_qhist, w.d_yr, g->max_deg, g->max_hood,
+                                                              g->d_status, w.d_t);
             ::pmrf::note_launch(1);
+            next_iter(s, -1);
+            PMRF_CUDA(cudaGetLastError());
+            cudaGraph_t bg = nullptr;
+            PMRF_CUDA(cudaStreamEndCapture(s, &bg));
+            s = s0;
+            set_capture_counter(cc->parent_nodes);
         }
-        if (p->n_htiles > 0) {
-            k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
-                z.dg, z.ht, MODE_EM, 0, p->hood_lanes, z.d_cfg, w.d_active, w.d_x[0], w.d_vrec, unit, w.d_qhist,
-                w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status, w.d_x[1], w.d_t);
-            ::pmrf::note_launch(1);
-        }
-        k_finalize<L><<<(unsigned)S, FIN_THREADS, 0, s>>>(S, MODE_EM, 0, z.d_cfg, p->d_slice_vt0, p->d_slice_ht0,
-                                                          w.d_vpart, w.d_hpart, w.d_theta, w.d_theta, g->d_vert_off,
-                                                          w.d_active, w.d_iters, w.d_conv, w.d_Thist, w.d_nactive,
-                                                          z.d_out, w.d_dterm, unit, w.d_qhist, w.d_yr, g->max_deg,
-                                                          g->max_hood, g->d_status, w.d_t);
-        ::pmrf::note_launch(1);
-        k_next_iter<<<1, 1, 0, s>>>(cc->h, w.d_nactive, w.d_t, -1, rc.max_iters, cc->counter, body);
-        ::pmrf::note_launch(1);
-        PMRF_CUDA(cudaGetLastError());
-        cudaGraph_t bg = nullptr;
-        PMRF_CUDA(cudaStreamEndCapture(s, &bg));
-        s = s0;
-        set_capture_counter(cc->parent_nodes);
     } else {
         const bool prof = g->tuning.profile != 0 && (int)g->prof_ev.size() >= 3 * rc.max_iters;
+        // the host does not see which slices are still iterating: every
+        // iteration launches one block per tile of the table
         for (int t = 1; t <= rc.max_iters; ++t) {
             const uint8_t* xin = w.d_x[(t - 1) & 1];
             uint8_t* xout = w.d_x[t & 1];
@@ -2041,14 +2224,15 @@ int em_body(pmrf_graph* g, Plan* p, const RunCfg& rc, cudaStream_t s, bool init_
             if (p->n_vtiles > 0) {
                 kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(z.dg, z.vt, MODE_EM, z.d_cfg, w.d_active, xin,
                                                                 xout, w.d_theta, w.d_dterm, nullptr, nullptr,
-                                                                w.d_vpart, g->d_status, w.d_vrec, unit, nullptr);
+                                                                w.d_vpart, g->d_status, w.d_vrec, unit, nullptr,
+                                                                TileSched{});
                 ::pmrf::note_launch(1);
             }
             if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 1], s, cudaEventRecordExternal);
             if (p->n_htiles > 0) {
                 k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
                     z.dg, z.ht, MODE_EM, t, p->hood_lanes, z.d_cfg, w.d_active, xin, w.d_vrec, unit, w.d_qhist,
-                    w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status, nullptr, nullptr);
+                    w.d_hist, nullptr, w.d_hpart, hood_cap(p), g->d_status, nullptr, nullptr, TileSched{});
                 ::pmrf::note_launch(1);
             }
             if (prof) cudaEventRecordWithFlags(g->prof_ev[3 * (t - 1) + 2], s, cudaEventRecordExternal);
@@ -2096,7 +2280,8 @@ int capture_em(pmrf_graph* g, Plan* p, const RunCfg& rc, bool init_from_labels, 
         cudaStreamCaptureStatus st;
         cudaGraph_t pg = nullptr;
         e = cudaStreamGetCaptureInfo(cs, &st, nullptr, &pg);
-        if (e == cudaSuccess) e = cudaGraphConditionalHandleCreate(&cc.h, pg, 0, cudaGraphCondAssignDefault);
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k)
+            e = cudaGraphConditionalHandleCreate(&cc.h[k], pg, 0, cudaGraphCondAssignDefault);
     }
     if (e == cudaSuccess) {
         set_capture_counter(nodes);
@@ -2254,13 +2439,13 @@ int sweep_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, cons
         const auto kv = var ? &k_vertex<L, true> : &k_vertex<L, false>;
         kv<<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, vt, MODE_SWEEP, d_cfg, nullptr, xin, xout, theta,
                                                                 nullptr, nullptr, Eout, nullptr, g->d_status, vrec,
-                                                                unit, nullptr);
+                                                                unit, nullptr, TileSched{});
         ::pmrf::note_launch(1);
     }
     if (p->n_htiles > 0) {
         k_hood<L><<<(unsigned)p->n_htiles, HT_THREADS, hood_smem(p), s>>>(
             dg, ht, MODE_SWEEP, 1, p->hood_lanes, d_cfg, nullptr, xin, vrec, unit, nullptr, nullptr, Sout, nullptr,
-            hood_cap(p), g->d_status, nullptr, nullptr);
+            hood_cap(p), g->d_status, nullptr, nullptr, TileSched{});
         ::pmrf::note_launch(1);
     }
     PMRF_CUDA(cudaGetLastError());
@@ -2275,7 +2460,7 @@ int params_body(pmrf_graph* g, Plan* p, cudaStream_t s, const RunCfg* d_cfg, con
     if (p->n_vtiles > 0) {
         k_vertex<L, false><<<(unsigned)p->n_vtiles, VT_THREADS, 0, s>>>(dg, p->d_tiles, MODE_PARAMS, d_cfg, nullptr, x,
                                                                 nullptr, prev, nullptr, Ein, nullptr, w.d_vpart,
-                                                                g->d_status, nullptr, nullptr, nullptr);
+                                                                g->d_status, nullptr, nullptr, nullptr, TileSched{});
         ::pmrf::note_launch(1);
     }
     k_finalize<L><<<(unsigned)g->S, FIN_THREADS, 0, s>>>(g->S, MODE_PARAMS, 0, d_cfg, p->d_slice_vt0, p->d_slice_ht0,

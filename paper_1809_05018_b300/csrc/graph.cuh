@@ -50,6 +50,9 @@ struct EMWork {  // EM scratch, sized for (L, W, plan)
     int32_t* d_conv = nullptr;     // [S]
     int32_t* d_nactive = nullptr;  // [1]
     int32_t* d_t = nullptr;        // [1] the loop graph's current iteration
+    int32_t* d_sched = nullptr;    // [2 (S + 1) + 2] tiles of the slices still iterating: vertex- and
+                                   // hood-tile prefix sums over the active slices, then the two
+                                   // passes' tile counters
     void* d_cfg = nullptr;         // device copy of the run's constants
 };
 

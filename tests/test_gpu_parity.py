@@ -215,6 +215,65 @@ def test_em_slice256_matches_oracle(use_graph):
     assert rel_close(T, r["T_hist"], ENERGY_RTOL)
 
 
+@pytest.mark.parametrize("use_graph", [1, 0])
+def test_em_iteration_cap_mixed_with_converged_slices(use_graph):
+    """Six slices run for at most 6 iterations: with these seeds the oracle's
+    runs of two of them converge (after 5 and 4 iterations) and four stop at
+    the cap unconverged.  The loop ends for the whole batch on the cap, whether
+    it runs as the conditional graph node or kernel by kernel, and every slice
+    keeps its own count, flag, labels and parameters."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(6, seed0=4200))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    g.set_tuning(use_cuda_graph=use_graph)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=6)
+    out = g.em(cfg)
+    g.sync_status()
+    ocfg = oracle.EMConfig(n_labels=2, beta=1.0, max_iters=6)
+    ref = [oracle.Graph.from_image(s.image, s.region_ids).em(ocfg) for s in sl]
+    # the case needs both kinds of slice
+    assert any(r["converged"] == 1 and r["iters"] < 6 for r in ref)
+    assert any(r["converged"] == 0 and r["iters"] == 6 for r in ref)
+    assert list(out["iters"].cpu().numpy()) == [r["iters"] for r in ref]
+    assert list(out["converged"].cpu().numpy()) == [r["converged"] for r in ref]
+    _em_compare(sl, ocfg, cfg, g, out)
+
+
+@pytest.mark.parametrize("seed0", [800, 700])
+def test_em_sparse_loop_matches_oracle_and_direct(seed0):
+    """24 small slices whose oracle runs stop between 4 and 60 iterations.  The
+    loop graph runs its later iterations in the sparse loop (blocks that take
+    only the tiles of slices still iterating) once those tiles are fewer than a
+    quarter of the table: with seed 800 from t = 8 with five slices left, with
+    seed 700 from t = 14 with two left, one of them to the 60-iteration cap.
+    Every slice matches the oracle's run, and the whole output equals that of
+    the kernel-by-kernel loop (one block per tile throughout)."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(24, seed0=seed0))
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+    ocfg = oracle.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+    # the case reaches the sparse loop with more than one slice left (tiles of
+    # 128 vertices and of 128 hoods)
+    its, tiles = [], []
+    for one in sl:
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        its.append(og.em(ocfg)["iters"])
+        tiles.append(-(-og.V // 128) + -(-og.C // 128))
+    its, tiles = np.array(its), np.array(tiles)
+    sparse = [t for t in range(1, its.max() + 1) if 4 * tiles[its >= t].sum() < tiles.sum()]
+    assert sum((its >= t).sum() >= 2 for t in sparse) >= 3
+    out = g.em(cfg, want_T=True)
+    g.sync_status()
+    _em_compare(sl, ocfg, cfg, g, out)
+    g.set_tuning(use_cuda_graph=0)
+    od = g.em(cfg, want_T=True)
+    for k in ("labels", "params", "iters", "converged", "T_hist"):
+        assert torch.equal(out[k], od[k]), k
+
+
 @pytest.mark.parametrize("L,beta", [(2, 1.0), (3, 1.5), (2, 0.0)])
 def test_em_batch_uneven_matches_oracle(L, beta):
     pmrf = _pmrf()
@@ -408,8 +467,9 @@ def test_em_conditional_graph_equals_unrolled():
     """The captured EM loop whose iterations sit in conditional graph nodes
     gives exactly what the unrolled capture (profiling mode) and the direct
     launches give, runs the same kernels as the unrolled loop cut at the last
-    active iteration plus one condition setter per run iteration and one after
-    the initial pass, and a repeated replay gives the same outputs."""
+    active iteration plus one condition setter per run iteration, one after the
+    initial pass and one between the dense and the sparse loop, and a repeated
+    replay gives the same outputs."""
     pmrf = _pmrf()
     sl = synth.make_stack(small_specs(7, seed0=500))
     imgs, ids = dev_tensors(sl)
@@ -437,7 +497,7 @@ def test_em_conditional_graph_equals_unrolled():
     assert nc == nc2
     cut = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=T)
     _, nu = run(cut, profile=1)
-    assert nc == nu + T + 1
+    assert nc == nu + T + 2
 
 
 def test_pll_value_and_grad_equals_separate_calls():
