@@ -417,11 +417,6 @@ PMRF_API int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const 
                      pmrf_stream_t stream);
 
 /*
- * Synchronise `stream` and return the graph's device status word: PMRF_OK, or
- * the first error a kernel recorded since the last call (the word is then
- * cleared).  *detail (may be NULL) receives a kernel-specific code.
- */
-/*
  * Segmentation quality against a ground truth (Section 4.2.1, evaluation
  * metrics: precision TP/(TP+FP), recall TP/(TP+FN), accuracy
  * (TP+TN)/(TP+TN+FP+FN), porosity = void volume / total volume).
@@ -442,6 +437,11 @@ PMRF_API int pmrf_label_image(pmrf_graph* g, const int32_t* d_region_ids, const 
 PMRF_API int pmrf_quality(pmrf_graph* g, int32_t n_labels, const uint8_t* d_pred, const uint8_t* d_truth,
                           int64_t* d_confusion, double* d_metrics, pmrf_stream_t stream);
 
+/*
+ * Synchronise `stream` and return the graph's device status word: PMRF_OK, or
+ * the first error a kernel recorded since the last call (the word is then
+ * cleared).  *detail (may be NULL) receives a kernel-specific code.
+ */
 PMRF_API int pmrf_sync_status(pmrf_graph* g, pmrf_stream_t stream, int64_t* detail);
 
 /* Launch shape of the EM hood pass.  0 selects the default.
