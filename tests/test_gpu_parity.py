@@ -274,6 +274,43 @@ def test_em_sparse_loop_matches_oracle_and_direct(seed0):
         assert torch.equal(out[k], od[k]), k
 
 
+@pytest.mark.parametrize("L,beta,scope,rule,seed0", [(2, 1.0, 0, 1, 700), (2, 1.0, 0, 2, 700), (2, 1.0, 1, 0, 700),
+                                                     (2, 1.0, 1, 1, 700), (2, 1.0, 1, 2, 700), (3, 1.5, 0, 0, 900)])
+def test_em_sparse_loop_variants_and_three_labels(L, beta, scope, rule, seed0):
+    """The sparse loop's other kernel instances: the sweep variants' vertex
+    pass (Potts scope, replica rule) and the three-label hood pass, taking only
+    the listed tiles.  24 small slices (three-phase ones for three labels)
+    whose oracle runs leave at least two slices iterating in at least two of
+    the sparse loop's iterations; every slice matches the oracle's run and the
+    whole output equals the kernel-by-kernel loop's."""
+    pmrf = _pmrf()
+    specs = small_specs(24, seed0=seed0)
+    if L == 3:
+        specs = [synth.scaled(synth.workload("large8192").slices[0], sp.height, sp.width, seed=sp.seed)
+                 for sp in specs]
+    sl = synth.make_stack(specs)
+    cfg = pmrf.EMConfig(n_labels=L, beta=beta, max_iters=60, potts_scope=scope, replica_rule=rule)
+    ocfg = oracle.EMConfig(n_labels=L, beta=beta, max_iters=60, potts_scope=scope, replica_rule=rule)
+    its, tiles = [], []
+    for one in sl:
+        og = oracle.Graph.from_image(one.image, one.region_ids)
+        its.append(og.em(ocfg)["iters"])
+        tiles.append(-(-og.V // 128) + -(-og.C // 128))
+    its, tiles = np.array(its), np.array(tiles)
+    sparse = [t for t in range(1, its.max() + 1) if 4 * tiles[its >= t].sum() < tiles.sum()]
+    assert sum((its >= t).sum() >= 2 for t in sparse) >= 2
+    imgs, ids = dev_tensors(sl)
+    g = pmrf.build_graph(imgs, ids)
+    out = g.em(cfg, want_T=True)
+    g.sync_status()
+    _em_compare(sl, ocfg, cfg, g, out)
+    g.set_tuning(use_cuda_graph=0)
+    od = g.em(cfg, want_T=True)
+    g.sync_status()
+    for k in ("labels", "params", "iters", "converged", "T_hist"):
+        assert torch.equal(out[k], od[k]), k
+
+
 @pytest.mark.parametrize("L,beta", [(2, 1.0), (3, 1.5), (2, 0.0)])
 def test_em_batch_uneven_matches_oracle(L, beta):
     pmrf = _pmrf()
