@@ -507,15 +507,6 @@ __device__ __forceinline__ void for_each_mask(const uint32_t* __restrict__ rm, i
 
 constexpr int RCP_N = 65;  // replica counts whose reciprocal the vertex pass takes from a table
 
-// an integer with the order of the finite double x (x < y exactly when
-// key(x) < key(y); -0 and +0 share a key): the sign bit set flips the other
-// bits, so larger magnitudes of negative values map lower
-__device__ __forceinline__ long long ordered_key(double x) {
-    long long b = __double_as_longlong(x);
-    if (b == (long long)0x8000000000000000ull) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
-}
-
 // The votes of all replicas of v (vote rule): each replica's least label from
 // its counts k_l of in-hood neighbours not labelled l, by the exact energies in
 // the slice's unit (the caller has ruled out near-ties, see vertex_variant)
