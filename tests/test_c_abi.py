@@ -45,16 +45,27 @@ int main(void) {
     printf("size pmrf_config %zu\nsize pmrf_build_options %zu\nsize pmrf_tuning %zu\n", sizeof(pmrf_config),
            sizeof(pmrf_build_options), sizeof(pmrf_tuning));
     %LAYOUT%
+    %CONSTS%
+    printf("count PMRF_ARR_COUNT %d\n", (int)PMRF_ARR_COUNT);
     return 0;
 }
 """
+
+
+def _constants():
+    """The header's named constants against the binding's copies of them."""
+    c = {f"PMRF_ARR_{k}": v for k, v in _native.ARR.items()}
+    c.update({name: code for code, name in _native.STATUS_NAMES.items()})
+    c.update(PMRF_MAX_LABELS=_native.MAX_LABELS, PMRF_MAX_DEGREE=_native.MAX_DEGREE)
+    return c
 
 
 def _program():
     lines = []
     for name, (_, fields) in STRUCTS.items():
         lines += [f"LAYOUT({name}, {f});" for f in fields]
-    return PROGRAM.replace("%LAYOUT%", "\n    ".join(lines))
+    consts = [f'printf("const {k} %lld\\n", (long long)({k}));' for k in _constants()]
+    return PROGRAM.replace("%LAYOUT%", "\n    ".join(lines)).replace("%CONSTS%", "\n    ".join(consts))
 
 
 @pytest.fixture(scope="module")
@@ -95,3 +106,11 @@ def test_ctypes_structures_match_the_c_layout(c_output):
         for f, _ in cls._fields_:
             desc = getattr(cls, f)
             assert (desc.offset, desc.size) == layout[(name, f)], (name, f)
+
+
+def test_binding_constants_match_the_header(c_output):
+    got = {ln.split()[1]: int(ln.split()[2]) for ln in c_output if ln.startswith("const ")}
+    want = _constants()
+    assert got == want
+    count = [int(ln.split()[2]) for ln in c_output if ln.startswith("count PMRF_ARR_COUNT")]
+    assert count == [len(_native.ARR)]  # the binding names every array the header lists
