@@ -71,6 +71,43 @@ def test_em_on_two_hoods_matches_oracle():
         assert rel_close(T[s, :r["iters"]], r["T_hist"], ENERGY_RTOL)
 
 
+def test_em_sparse_loop_on_two_hoods():
+    """The sparse EM loop with two lanes per hood (64-hood tiles, the launch
+    shape of 2-neighbourhoods, whose hoods hold 23 members on average here): 24
+    small slices whose oracle runs keep several slices iterating in the sparse
+    loop.  Every slice matches the oracle's run; the whole output equals the
+    kernel-by-kernel loop's."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(24, seed0=700))
+    pairs = [(s.image, s.region_ids) for s in sl]
+    ocfg = oracle.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+    ogs = [oracle.Graph.from_image(a, b, hood_depth=2) for a, b in pairs]
+    runs = [og.em(ocfg) for og in ogs]
+    its = np.array([r["iters"] for r in runs])
+    assert sum(og.N_el for og in ogs) >= 16 * sum(og.C for og in ogs)  # two lanes per hood
+    tiles = np.array([-(-og.V // 128) + -(-og.C // 64) for og in ogs])
+    sparse = [t for t in range(1, its.max() + 1) if 4 * tiles[its >= t].sum() < tiles.sum()]
+    assert sum((its >= t).sum() >= 2 for t in sparse) >= 2
+    g = _build(pairs, 2)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+    out = g.em(cfg, want_T=True)
+    g.sync_status()
+    x = out["labels"].cpu().numpy()
+    th = out["params"].cpu().numpy()
+    T = out["T_hist"].cpu().numpy()
+    vo = g.array("VERT_OFF").numpy()
+    assert list(out["iters"].cpu().numpy()) == list(its)
+    for s, r in enumerate(runs):
+        assert np.array_equal(x[vo[s]:vo[s + 1]], r["labels"]), s
+        assert rel_close(th[s, :, 1:3], r["theta"][:, 1:3], PARAM_RTOL)
+        assert rel_close(T[s, :r["iters"]], r["T_hist"], ENERGY_RTOL)
+    g.set_tuning(use_cuda_graph=0)
+    od = g.em(cfg, want_T=True)
+    g.sync_status()
+    for k in ("labels", "params", "iters", "converged", "T_hist"):
+        assert torch.equal(out[k], od[k]), k
+
+
 def test_sweep_on_three_hoods_three_labels():
     pmrf = _pmrf()
     pairs = _pairs(970)

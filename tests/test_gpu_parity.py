@@ -311,6 +311,40 @@ def test_em_sparse_loop_variants_and_three_labels(L, beta, scope, rule, seed0):
         assert torch.equal(out[k], od[k]), k
 
 
+def test_em_sparse_loop_with_a_wide_region():
+    """The sparse loop's general hood tiles (a member with more than 32
+    neighbours, taken hood by hood through the hood-local rows): 24 small
+    slices plus one whose two middle rows are a single region touching 77
+    cells, which keeps iterating for several of the sparse loop's iterations.
+    Every slice matches the oracle's run; the whole output equals the
+    kernel-by-kernel loop's."""
+    pmrf = _pmrf()
+    sl = synth.make_stack(small_specs(24, seed0=700))
+    band = synth.make_slice(synth.scaled(small_specs(1, seed0=5018)[0], 48, 320, seed=5018))
+    bids = band.region_ids.copy()
+    bids[24:26, :] = bids.max() + 1
+    sl.append(type("S", (), dict(image=band.image, region_ids=bids)))
+    ocfg = oracle.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+    ogs = [oracle.Graph.from_image(one.image, one.region_ids) for one in sl]
+    assert np.diff(ogs[-1].adj_off).max() > 32
+    its = np.array([og.em(ocfg)["iters"] for og in ogs])
+    tiles = np.array([-(-og.V // 128) + -(-og.C // 128) for og in ogs])
+    sparse = [t for t in range(1, its.max() + 1) if 4 * tiles[its >= t].sum() < tiles.sum()]
+    assert sum(its[-1] >= t for t in sparse) >= 2
+    imgs = [torch.from_numpy(one.image).cuda() for one in sl]
+    ids = [torch.from_numpy(one.region_ids).cuda() for one in sl]
+    g = pmrf.build_graph(imgs, ids)
+    cfg = pmrf.EMConfig(n_labels=2, beta=1.0, max_iters=60)
+    out = g.em(cfg, want_T=True)
+    g.sync_status()
+    _em_compare(sl, ocfg, cfg, g, out)
+    g.set_tuning(use_cuda_graph=0)
+    od = g.em(cfg, want_T=True)
+    g.sync_status()
+    for k in ("labels", "params", "iters", "converged", "T_hist"):
+        assert torch.equal(out[k], od[k]), k
+
+
 @pytest.mark.parametrize("L,beta", [(2, 1.0), (3, 1.5), (2, 0.0)])
 def test_em_batch_uneven_matches_oracle(L, beta):
     pmrf = _pmrf()
