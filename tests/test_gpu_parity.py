@@ -86,6 +86,23 @@ def test_graph_edge_cases():
                     oracle.EMConfig(n_labels=L, beta=0.3, max_iters=15), cfg, g, out)
 
 
+def test_graph_of_one_pixel_regions():
+    """Every pixel its own region, ids a random permutation scattered over
+    three times their number: one-pixel runs everywhere in the region-size
+    pass, one-pixel boxes in the region scan, a grid graph with no triangle
+    (every maximal clique an edge); sizes, means and the graph equal the
+    oracle's."""
+    pmrf = _pmrf()
+    rng = np.random.default_rng(31)
+    H, W = 40, 300
+    ids = rng.permutation(H * W).astype(np.int32).reshape(H, W) * 3 + 1
+    img = rng.random((H, W))
+    g = pmrf.build_graph(torch.from_numpy(img).cuda(), torch.from_numpy(ids).cuda())
+    og = oracle.Graph.from_image(img, ids)
+    assert og.V == H * W
+    assert_graph_equal(og, slice_view(gpu_arrays(g), 0))
+
+
 def test_build_rejects_bad_input():
     pmrf = _pmrf()
     img = torch.rand(8, 8, dtype=torch.float64, device="cuda")
